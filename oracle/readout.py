@@ -1,0 +1,265 @@
+"""Readouts from a converged CTM environment (oracle; test infrastructure only).
+
+* nearest-neighbour reduced density matrices and the energy of the ruby model
+  (Eq. H-KR of Sec. IV in block-site form, App. A),
+* the fidelity per site (Sec. III, Eq. "fidelity" and Fig. 4),
+* the boundary density operator spectrum and entanglement entropy on an
+  infinite cylinder (Sec. IV, Eq. "rho" and Fig. "cylinder").
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .ctm import CTMState, rotate_k
+
+__all__ = [
+    "rdm_horizontal",
+    "bond_rdms",
+    "pauli_block_ops",
+    "ruby_bond_hamiltonians",
+    "energy_per_spin",
+    "site_type",
+    "partition_ratios",
+    "kappa",
+    "fidelity",
+    "ring_sigma",
+    "boundary_spectrum",
+    "entropy",
+]
+
+
+def _split(t: np.ndarray, axis: int, D: int) -> np.ndarray:
+    """Split a fused (ket, bra) leg of length D*D into two legs."""
+    shape = list(t.shape)
+    shape[axis:axis + 1] = [D, D]
+    return t.reshape(shape)
+
+
+def rdm_horizontal(st: CTMState, A_cell, x: int, y: int) -> np.ndarray:
+    """Two-site RDM of the horizontal bond (x,y)-(x+1,y), normalised to trace 1.
+
+    Returned as a (d^2, d^2) matrix with rows (p_left, q_right) (ket) and
+    columns (p', q') (bra): rho[(p q),(p' q')].
+    """
+    Lx, Ly, D = st.Lx, st.Ly, st.D
+    x0, x1, y0 = x % Lx, (x + 1) % Lx, y % Ly
+    C, T = st.C, st.T
+    A = A_cell[y0][x0].astype(np.complex128)
+    B = A_cell[y0][x1].astype(np.complex128)
+    t1 = _split(T[0][y0][x0], 1, D)   # [l, u, u', r]
+    t4 = _split(T[3][y0][x0], 1, D)   # [d, l, l', u]
+    t3 = _split(T[2][y0][x0], 1, D)   # [r, d, d', l]
+    # left half: (C1 T1) T4, open A and conj(A), then (C4 T3)
+    L = np.einsum("ab,bUVh->aUVh", C[0][y0][x0], t1, optimize=True)
+    L = np.einsum("eLMa,aUVh->eLMUVh", t4, L, optimize=True)
+    L = np.einsum("eLMUVh,pULSr->eMVhpSr", L, A, optimize=True)
+    L = np.einsum("eMVhpSr,qVMTs->ehpSrqTs", L, np.conj(A), optimize=True)
+    CB = np.einsum("ge,kSTg->ekST", C[3][y0][x0], t3, optimize=True)
+    left = np.einsum("ehpSrqTs,ekST->hrskpq", L, CB, optimize=True)
+    u1 = _split(T[0][y0][x1], 1, D)   # [l, u, u', r]
+    t2 = _split(T[1][y0][x1], 1, D)   # [u, r, r', d]
+    b3 = _split(T[2][y0][x1], 1, D)   # [r, d, d', l]
+    # right half: (T1 C2) T2, open B and conj(B), then (C3 T3)
+    R = np.einsum("hUVc,cf->hUVf", u1, C[1][y0][x1], optimize=True)
+    R = np.einsum("hUVf,fRSg->hUVRSg", R, t2, optimize=True)
+    R = np.einsum("hUVRSg,pUlXR->hVSgplX", R, B, optimize=True)
+    R = np.einsum("hVSgplX,qVmYS->hgplXqmY", R, np.conj(B), optimize=True)
+    CB = np.einsum("gi,iXYk->gXYk", C[2][y0][x1], b3, optimize=True)
+    right = np.einsum("hgplXqmY,gXYk->hlmkpq", R, CB, optimize=True)
+    rho = np.einsum("hrskpq,hrskPQ->pPqQ", left, right, optimize=True)
+    d = A.shape[0]
+    rho = rho.reshape(d * d, d * d)
+    return rho / np.trace(rho)
+
+
+def _rotate_tensor(A: np.ndarray) -> np.ndarray:
+    """A[p,u,l,d,r] of the network rotated 90 degrees counter-clockwise."""
+    return np.ascontiguousarray(np.transpose(A, (0, 4, 1, 2, 3)))
+
+
+def bond_rdms(st: CTMState, tensors, pattern):
+    """All nearest-neighbour RDMs of the cell.
+
+    Returns dict with 'h' -> array [Ly, Lx, d^2, d^2] for bonds (x,y)-(x+1,y)
+    (left site first) and 'v' -> [Ly, Lx, d^2, d^2] for bonds (x,y)-(x,y+1)
+    (upper site first).  Vertical bonds are horizontal bonds of the network
+    rotated by 90 degrees counter-clockwise, where (x,y) -> (y, -x).
+    """
+    Lx, Ly = st.Lx, st.Ly
+    A_cell = [[tensors[pattern[y][x]] for x in range(Lx)] for y in range(Ly)]
+    d = A_cell[0][0].shape[0]
+    h = np.zeros((Ly, Lx, d * d, d * d), dtype=np.complex128)
+    v = np.zeros_like(h)
+    for y in range(Ly):
+        for x in range(Lx):
+            h[y, x] = rdm_horizontal(st, A_cell, x, y)
+    rst = rotate_k(st, 1)
+    rA = [[None] * Ly for _ in range(Lx)]
+    for yp in range(Lx):
+        for xp in range(Ly):
+            rA[yp][xp] = _rotate_tensor(A_cell[xp % Ly][(-yp) % Lx])
+    for y in range(Ly):
+        for x in range(Lx):
+            v[y, x] = rdm_horizontal(rst, rA, y, (-x) % Lx)
+    return {"h": h, "v": v}
+
+
+# ---------------------------------------------------------------------------
+# Ruby model in block-site form (App. A).  Block-site basis p = 4 b1 + 2 b2 + b3
+# (spin 1 most significant), b = 0 meaning sigma^z = +1.
+# ---------------------------------------------------------------------------
+def pauli_block_ops():
+    sx = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    sy = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+    sz = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+    I2 = np.eye(2, dtype=np.complex128)
+    ops = {}
+    for name, s in (("x", sx), ("y", sy), ("z", sz)):
+        for k in (1, 2, 3):
+            f = [I2, I2, I2]
+            f[k - 1] = s
+            ops[name + str(k)] = np.kron(np.kron(f[0], f[1]), f[2])
+    return ops
+
+
+def site_type(x: int, y: int) -> str:
+    """Checkerboard block-site type of the 2x2 cell (Sec. II.B): A when x+y even."""
+    return "A" if (x + y) % 2 == 0 else "B"
+
+
+def ruby_bond_hamiltonians(J):
+    """Bond operators (64x64, left/upper site first) of H_R = -sum J_a s^a s^a.
+
+    Each sigma^a sigma^a link of App. A carries -J_a.  Horizontal bond with the
+    A site on the left: H_r = h^x_{iA,jB}; with B on the left: H_l = 0 (the
+    trivial auxiliary bond).  Vertical bonds: H_u / H_d = (h_A + h_B)/2 + h^y,
+    where h_A = h_B = -Jz (z1 z2 + z1 z3 + z2 z3) and h^y couples the upper
+    site's spin 3 to the lower site's spin 2 by x and spin 2 to spin 1 by y
+    (the same form for A-over-B and B-over-A).
+    """
+    Jx, Jy, Jz = J
+    o = pauli_block_ops()
+    I8 = np.eye(8, dtype=np.complex128)
+    h_site = -Jz * (o["z1"] @ o["z2"] + o["z1"] @ o["z3"] + o["z2"] @ o["z3"])
+    H_r = -Jx * np.kron(o["x1"], o["x1"]) - Jy * np.kron(o["y3"], o["y3"])
+    H_l = np.zeros((64, 64), dtype=np.complex128)
+    H_v = 0.5 * (np.kron(h_site, I8) + np.kron(I8, h_site)) \
+        - Jx * np.kron(o["x3"], o["x2"]) - Jy * np.kron(o["y2"], o["y1"])
+    return {"H_r": H_r, "H_l": H_l, "H_u": H_v, "H_d": H_v.copy(), "h_site": h_site}
+
+
+def energy_per_spin(rdms, J, Lx: int, Ly: int) -> float:
+    """(1/(3 Lx Ly)) * sum over the cell's 2 Lx Ly bonds of Re tr(rho_b H_b)."""
+    H = ruby_bond_hamiltonians(J)
+    e = 0.0
+    for y in range(Ly):
+        for x in range(Lx):
+            Hh = H["H_r"] if site_type(x, y) == "A" else H["H_l"]
+            e += np.real(np.trace(rdms["h"][y, x] @ Hh))
+            Hv = H["H_u"] if site_type(x, y) == "A" else H["H_d"]
+            e += np.real(np.trace(rdms["v"][y, x] @ Hv))
+    return e / (3 * Lx * Ly)
+
+
+# ---------------------------------------------------------------------------
+# Sec. III: fidelity per site.  For a network with environment, the per-cell
+# "free energy" kappa = Z(cell) Z(corners) / (Z(columns only) Z(rows only)),
+# Eq. (fidelity) written with C1..C4, T (Fig. 4).
+# ---------------------------------------------------------------------------
+def _window_contract(st: CTMState, with_rows: bool, with_cols: bool) -> complex:
+    """Contract the environment window at (0,0) row by row.
+
+    with_cols: the Lx columns (T1 on top, T3 at the bottom, a's inside) are
+    present; with_rows: the Ly rows (T4 on the left, T2 on the right) are
+    present.  The four corners are always present.  The boundary array B
+    carries axes [vl, v_0 .. v_{n-1}, vr] (left bond, column bonds, right bond).
+    """
+    Lx, Ly = st.Lx, st.Ly
+    C, T, a = st.C, st.T, st.a
+    n = Lx if with_cols else 0
+    xr, yb = Lx - 1, Ly - 1
+    B = C[0][0][0]                                   # [vl, ht]
+    for x in range(n):
+        B = np.tensordot(B, T[0][0][x], axes=([B.ndim - 1], [0]))  # T1[l,d,r]
+    B = np.tensordot(B, C[1][0][xr], axes=([B.ndim - 1], [0]))     # C2[l,d]
+    for y in range(Ly if with_rows else 0):
+        B = np.tensordot(T[3][y][0], B, axes=([2], [0]))  # T4[d,r,u]: [vl', h, v.., vr]
+        for x in range(n):
+            B = np.tensordot(B, a[y][x], axes=([1 + x, 2 + x], [1, 0]))
+            B = np.moveaxis(B, [B.ndim - 2, B.ndim - 1], [1 + x, 2 + x])
+        B = np.tensordot(B, T[1][y][xr], axes=([1 + n, 2 + n], [1, 0]))  # T2[u,l,d]
+    B = np.tensordot(C[3][yb][0], B, axes=([1], [0]))    # C4[r,u]: [hb, v.., vr]
+    for x in range(n):
+        B = np.tensordot(B, T[2][yb][x], axes=([0, 1], [2, 1]))    # T3[r,u,l]
+        B = np.moveaxis(B, B.ndim - 1, 0)
+    return complex(np.einsum("hv,vh->", B, C[2][yb][xr]))  # C3[u,l]
+
+
+def partition_ratios(st: CTMState):
+    """(Z_cell, Z_00, Z_cols, Z_rows) for the window at (0,0)."""
+    return (_window_contract(st, True, True), _window_contract(st, False, False),
+            _window_contract(st, False, True), _window_contract(st, True, False))
+
+
+def kappa(st: CTMState) -> complex:
+    """Per-cell kappa = Z_cell Z_00 / (Z_cols Z_rows)."""
+    Zc, Z00, Zcol, Zrow = partition_ratios(st)
+    return Zc * Z00 / (Zcol * Zrow)
+
+
+def fidelity(k12: complex, k11: complex, k22: complex, n_sites: int):
+    """Fidelity per block site d = |k12|^(1/n) / (|k11| |k22|)^(1/(2n)) and per
+    spin d^(1/3) (three spins per block site)."""
+    d_block = np.exp((np.log(abs(k12)) - 0.5 * (np.log(abs(k11)) + np.log(abs(k22)))) / n_sites)
+    return float(d_block), float(d_block ** (1.0 / 3.0))
+
+
+# ---------------------------------------------------------------------------
+# Sec. IV: boundary density operator.  sigma_R = ring of N_v tensors T2 at
+# column x, sigma_L = ring of N_v tensors T4 at column x+1 (Fig. "cylinder" b),
+# both read as D^Nv x D^Nv operators (ket index rows, bra index columns).
+# ---------------------------------------------------------------------------
+def ring_sigma(st: CTMState, which: str, x: int, Nv: int) -> np.ndarray:
+    Lx, Ly, D = st.Lx, st.Ly, st.D
+    if Nv % Ly:
+        raise ValueError("Nv must be a multiple of the cell height")
+    if which == "R":
+        ts = [_split(st.T[1][i % Ly][x % Lx], 1, D) for i in range(Nv)]  # [u, k, b, d]
+    else:
+        ts = [np.transpose(_split(st.T[3][i % Ly][(x + 1) % Lx], 1, D), (3, 1, 2, 0)) for i in range(Nv)]
+    R = ts[0]  # [c0, K, B, c1]
+    for t in ts[1:]:
+        R = np.einsum("aKBc,ckbe->aKkBbe", R, t, optimize=True)
+        s = R.shape
+        R = R.reshape(s[0], s[1] * s[2], s[3] * s[4], s[5])
+    return np.einsum("aKBa->KB", R, optimize=True)
+
+
+def boundary_spectrum(st: CTMState, x: int, Nv: int):
+    """Eigenvalues of sigma_L^T sigma_R normalised to sum 1, descending.
+
+    Computed through the similar Hermitian operator sqrt(sigma_L^T) sigma_R
+    sqrt(sigma_L^T) (Eq. "rho" and the spectrum identity that follows it),
+    after Hermitising both sigma's and clamping negative eigenvalues of
+    sigma_L^T to zero.
+    """
+    sL = ring_sigma(st, "L", x, Nv)
+    sR = ring_sigma(st, "R", x, Nv)
+    # overall phases of the rings are gauge: fix them so the traces are real positive
+    sL = sL * np.exp(-1j * np.angle(np.trace(sL)))
+    sR = sR * np.exp(-1j * np.angle(np.trace(sR)))
+    sL = 0.5 * (sL + sL.conj().T)
+    sR = 0.5 * (sR + sR.conj().T)
+    w, V = np.linalg.eigh(sL.T)
+    w = np.clip(w, 0.0, None)
+    W = (V * np.sqrt(w)[None, :]) @ V.conj().T
+    H = W @ sR @ W
+    H = 0.5 * (H + H.conj().T)
+    lam = np.linalg.eigvalsh(H)[::-1]
+    return lam / lam.sum()
+
+
+def entropy(lam: np.ndarray) -> float:
+    """Von Neumann entropy -sum lam ln lam over the positive eigenvalues."""
+    p = lam[lam > 0]
+    return float(-np.sum(p * np.log(p)))

@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs shared by the FP64 oracle and the CUDA library tests.
+
+This module holds no CTM arithmetic: it only draws numbers.  Every value comes
+from SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) used as a counter-based generator:
+
+    z  = seed + (n + 1) * 0x9E3779B97F4A7C15          (mod 2^64)
+    z  = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9
+    z  = (z ^ (z >> 27)) * 0x94D049BB133111EB
+    out = z ^ (z >> 31)
+
+`uniform53(seed, n)` = (out >> 11) * 2^-53 in [0, 1), an exact double.  Normal
+deviates use the Box-Muller transform on two consecutive uniforms.
+
+Workloads (the PEPS tensors of the paper's Sec. II.A, A[p,u,l,d,r], d = 2^3 = 8
+for a three-spin block site of the ruby lattice, Sec. II.B):
+
+* ``random_real``: iid N(0,1) entries, then divided by max |A| (per tensor).
+* ``product_plus_noise``: the all-spins-up product state (A[0,0,0,0,0] = 1,
+  p = 0 meaning sigma^z = +1 on all three spins) plus ``eps`` times iid complex
+  normal noise with Re, Im ~ N(0, 1/2) on every entry.
+
+Tensor ``t`` of a workload with seed ``s`` draws from stream ``s * 16 + t``.
+
+The randomized range finder of the projector step needs a test matrix Omega;
+``omega`` draws it with uniform [-1, 1) real and imaginary parts (exact
+doubles, so the CUDA library's own SplitMix64 copy reproduces it bit for bit).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for counters ``n`` (uint64 array) of stream ``seed``."""
+    n = np.asarray(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed % (1 << 64)) + (n + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform53(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """``count`` exact doubles in [0, 1) from counters offset .. offset+count-1."""
+    n = np.arange(offset, offset + count, dtype=np.uint64)
+    return (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, count: int) -> np.ndarray:
+    """``count`` iid N(0,1) deviates (Box-Muller on uniform pairs)."""
+    u = uniform53(seed, 2 * count)
+    u1 = 1.0 - u[0::2]  # in (0, 1]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def random_real(seed: int, tid: int, d: int, D: int) -> np.ndarray:
+    """A[p,u,l,d,r] real, iid N(0,1), normalised to max-abs 1."""
+    A = normal(seed * 16 + tid, d * D ** 4).reshape(d, D, D, D, D)
+    return A / np.max(np.abs(A))
+
+
+def product_plus_noise(seed: int, tid: int, d: int, D: int, eps: float = 0.1) -> np.ndarray:
+    """All-up product state plus eps * complex normal noise (E|z|^2 = 1)."""
+    n = d * D ** 4
+    g = normal(seed * 16 + tid, 2 * n)
+    noise = (g[:n] + 1j * g[n:]) * np.sqrt(0.5)
+    A = eps * noise.reshape(d, D, D, D, D)
+    A[0, 0, 0, 0, 0] += 1.0
+    return A
+
+
+def omega(seed: int, rows: int, cols: int) -> np.ndarray:
+    """Range-finder test matrix, rows x cols complex, Re/Im uniform in [-1, 1).
+
+    Entry (i, j) uses counters 2*(i*cols + j) (real) and 2*(i*cols + j) + 1
+    (imaginary) of stream ``seed``.
+    """
+    u = uniform53(seed, 2 * rows * cols)
+    re = 2.0 * u[0::2] - 1.0
+    im = 2.0 * u[1::2] - 1.0
+    return (re + 1j * im).reshape(rows, cols)
+
+
+# ---------------------------------------------------------------------------
+# Named workloads.  Each returns (tensors, pattern, Lx, Ly, d, D, chi, J).
+# pattern[y][x] is the tensor id at cell position (x, y).
+# ---------------------------------------------------------------------------
+
+def workload(name: str, seed: int = 0, D: int | None = None, chi: int | None = None):
+    """Return a dict describing one of the paper-shaped synthetic workloads.
+
+    ``cfg1_real_d8_D2_chi16``      4 real tensors, d=8, D=2, chi=16, J=(1,1,1)
+    ``cfg2_c128_d8_D4_chi64``      4 complex product+noise tensors, D=4, chi=64, J=(1,1,0.5)
+    ``cfg3_c128_d8_D5_chi100``     as cfg2 with D=5, chi=100
+    ``cfg5_c128_d8_D6_chi144``     as cfg2 with D=6, chi=144
+    D / chi may be overridden to build scaled-down variants of the same recipe.
+    """
+    d = 8
+    if name.startswith("cfg1"):
+        D = D or 2
+        chi = chi or 16
+        tensors = [random_real(seed, t, d, D) for t in range(4)]
+        J = (1.0, 1.0, 1.0)
+    elif name.startswith(("cfg2", "cfg3", "cfg5")):
+        D = D or {"cfg2": 4, "cfg3": 5, "cfg5": 6}[name[:4]]
+        chi = chi or {"cfg2": 64, "cfg3": 100, "cfg5": 144}[name[:4]]
+        tensors = [product_plus_noise(seed, t, d, D) for t in range(4)]
+        J = (1.0, 1.0, 0.5)
+    else:
+        raise ValueError(f"unknown workload {name}")
+    return {
+        "tensors": tensors,
+        "pattern": [[0, 1], [2, 3]],
+        "Lx": 2,
+        "Ly": 2,
+        "d": d,
+        "D": D,
+        "chi": chi,
+        "J": J,
+        "seed": seed,
+    }

@@ -1,0 +1,499 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula: each compares the oracle with a
+closed form (Onsager's solution of the 2D Ising model, product states), a
+brute-force contraction written here independently, or an invariance of the
+exact network (gauge, lattice symmetry, the spectrum identity of Sec. IV).
+"""
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.linalg as sla
+import scipy.special as ss
+
+import oracle as O
+import synth
+
+
+# ---------------------------------------------------------------------------
+# helpers (independent of the oracle's contraction code)
+# ---------------------------------------------------------------------------
+def ising_tensor(beta):
+    """d=2, D=2 PEPS whose norm network is the classical Ising model at beta:
+    A_s[u,l,d,r] = W_su W_sl W_sd W_sr with W = sqrt(B(beta/2)), so each bond of
+    the double layer carries B(beta/2)_{ss'}^2 = exp(beta s s')."""
+    B = np.array([[np.exp(beta / 2), np.exp(-beta / 2)], [np.exp(-beta / 2), np.exp(beta / 2)]])
+    W = np.real(sla.sqrtm(B))
+    return np.einsum("pu,pl,pd,pr->puldr", W, W, W, W)
+
+
+def onsager_minus_beta_f(beta):
+    """-beta f per site of the square-lattice Ising model (J = 1), Onsager 1944,
+    with the inner angular integral done in closed form."""
+    c2, s = np.cosh(2 * beta) ** 2, np.sinh(2 * beta)
+
+    def f(t):
+        c = c2 - s * np.cos(t)
+        return np.log((c + np.sqrt(c * c - s * s)) / 2)
+
+    val, _ = si.quad(f, 0, 2 * np.pi, epsabs=1e-14, epsrel=1e-14, limit=400)
+    return np.log(2) + val / (4 * np.pi)
+
+
+def onsager_nn_corr(beta):
+    """<s_i s_j> on a nearest-neighbour bond, closed form with the complete
+    elliptic integral K of modulus k = 2 sinh(2b)/cosh^2(2b)."""
+    k = 2 * np.sinh(2 * beta) / np.cosh(2 * beta) ** 2
+    return (0.5 + (2 * np.tanh(2 * beta) ** 2 - 1) * ss.ellipk(k * k) / np.pi) / np.tanh(2 * beta)
+
+
+def random_tensors(seed, n, d, D, cplx=True):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        A = rng.standard_normal((d, D, D, D, D))
+        if cplx:
+            A = A + 1j * rng.standard_normal((d, D, D, D, D))
+        out.append(A / np.abs(A).max())
+    return out
+
+
+def brute_force_rdm(tensors, pattern, xs, ys, open_sites):
+    """Reduced density matrix of ``open_sites`` in the finite patch of sites
+    xs x ys (ranges), every outer virtual leg traced ket against bra, by plain
+    row-by-row contraction of the ket/bra layers (D legs kept separate)."""
+    Ly, Lx = len(pattern), len(pattern[0])
+    D = tensors[0].shape[1]
+    d = tensors[0].shape[0]
+    W = len(xs)
+    # state axes: [(k_x, b_x) for each column x] + open legs (p, p') in order;
+    # the top legs are traced: only k == b survives.
+    state = np.ones([D, D] * W)
+    for x in range(W):
+        state = state * np.eye(D).reshape([1] * (2 * x) + [D, D] + [1] * (2 * (W - x - 1)))
+    n_open = 0
+    for y in ys:
+        # horizontal ket/bra bond entering from the left: traced
+        h = np.eye(D)  # axes (k, b)
+        cur = np.einsum("...,kb->...kb", state, h)  # [col legs..., open..., hk, hb]
+        for ix, x in enumerate(xs):
+            A = tensors[pattern[y % Ly][x % Lx]]
+            op = (x, y) in open_sites
+            # axes of cur: column legs (2W), open legs (2 n_open), hk, hb
+            ncol = 2 * W
+            nopen = 2 * n_open
+            ku, bu = 2 * ix, 2 * ix + 1
+            hk, hb = ncol + nopen, ncol + nopen + 1
+            if op:
+                ket = A
+                bra = np.conj(A)
+                # contract ket: A[p,u,l,d,r] with (u=ku, l=hk)
+                cur = np.tensordot(cur, ket, axes=([ku, hk], [1, 2]))  # appends p, d, r
+                # remaining axes shift: remove ku and hk
+                bu2 = bu - 1
+                hb2 = hb - 2
+                cur = np.tensordot(cur, bra, axes=([bu2, hb2], [1, 2]))  # appends p', d', r'
+            else:
+                # sum_p A conj(A): contract ket with the physical index shared
+                cur = np.tensordot(cur, A, axes=([ku, hk], [1, 2]))  # appends p, d, r
+                bu2 = bu - 1
+                hb2 = hb - 2
+                cur = np.tensordot(cur, np.conj(A), axes=([bu2, hb2, cur.ndim - 3], [1, 2, 0]))  # appends d', r'
+            # reorder: new column legs (d, d') into position ix, open (p,p') appended, (r, r') last
+            nd = cur.ndim
+            if op:
+                # tail axes: p, d, r, p', d', r'
+                p, dk, rk, pb, db, rb = range(nd - 6, nd)
+                rest = list(range(nd - 6))
+                # rest holds: column legs except ix (2W-2), open legs, nothing else
+                cols = rest[:2 * ix] + [dk, db] + rest[2 * ix:2 * W - 2]
+                opens = rest[2 * W - 2:] + [p, pb]
+                cur = np.transpose(cur, cols + opens + [rk, rb])
+            else:
+                dk, rk, db, rb = range(nd - 4, nd)
+                rest = list(range(nd - 4))
+                cols = rest[:2 * ix] + [dk, db] + rest[2 * ix:2 * W - 2]
+                opens = rest[2 * W - 2:]
+                cur = np.transpose(cur, cols + opens + [rk, rb])
+            if op:
+                n_open += 1
+        # right boundary traced
+        state = np.einsum("...kb,kb->...", cur, np.eye(D))
+    # bottom legs traced
+    for x in range(W):
+        state = np.einsum("kb...,kb->...", state, np.eye(D))
+    # state axes: open legs in order of appearance (p1, p1', p2, p2', ...)
+    rho = state
+    if n_open == 2:
+        rho = np.transpose(rho, (0, 2, 1, 3)).reshape(d * d, d * d)
+    else:
+        rho = rho.reshape(d, d)
+    return rho / np.trace(rho)
+
+
+# ---------------------------------------------------------------------------
+# a1: double layer (Fig. 3a)
+# ---------------------------------------------------------------------------
+def test_double_layer_hermitian_and_norm():
+    A = random_tensors(1, 1, 3, 2)[0]
+    a = O.double_layer(A)
+    D = 2
+    a8 = a.reshape([D] * 8)  # u u' l l' d d' r r'
+    # swapping ket and bra on every leg conjugates a
+    assert np.allclose(a8, np.conj(np.transpose(a8, (1, 0, 3, 2, 5, 4, 7, 6))), atol=1e-14)
+    # tracing every leg ket against bra gives the squared norm of A
+    tr = np.einsum("aabbccdd->", a8)
+    assert abs(tr - np.vdot(A, A)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# lattice rotation (relabelling only)
+# ---------------------------------------------------------------------------
+def test_rotation_is_a_relabelling():
+    ts = random_tensors(2, 4, 2, 2)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 2, 8)
+    st4 = O.rotate_k(st, 4)
+    for j in range(4):
+        for y in range(2):
+            for x in range(2):
+                assert np.array_equal(st4.C[j][y][x], st.C[j][y][x])
+                assert np.array_equal(st4.T[j][y][x], st.T[j][y][x])
+    # trace initialisation commutes with rotating the tensors themselves
+    rot = lambda A: np.transpose(A, (0, 4, 1, 2, 3))
+    r1 = O.rotate(st)
+    rpat_tensors = [rot(ts[pat[x % 2][(-y) % 2]]) for y in range(2) for x in range(2)]
+    rst = O.make_state(rpat_tensors, [[0, 1], [2, 3]], 2, 8)
+    for j in range(4):
+        for y in range(2):
+            for x in range(2):
+                assert np.allclose(r1.C[j][y][x], rst.C[j][y][x], atol=1e-14)
+                assert np.allclose(r1.T[j][y][x], rst.T[j][y][x], atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Whole CTM + kappa + RDMs on a correlated network: 2D classical Ising model
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_ising_free_energy_and_bond_correlation(beta):
+    A = ising_tensor(beta)
+    st = O.make_state([A], [[0]], 2, 16)
+    st, n, _ = O.ctm_converge(st, O.CTMOptions(chi=16, proj="svd", cutoff=1e-12), 1e-9, 80)
+    lnk = np.log(abs(O.kappa(st)))
+    assert abs(lnk - onsager_minus_beta_f(beta)) < 1e-10
+    r = O.bond_rdms(st, [A], [[0]])
+    zz = np.array([1.0, -1.0, -1.0, 1.0])
+    for key in ("h", "v"):
+        corr = np.real(np.diag(r[key][0, 0])) @ zz
+        assert abs(corr - onsager_nn_corr(beta)) < 1e-9
+
+
+def test_ising_fidelity_closed_form():
+    """Overlap of Ising PEPS at b1 and b2 is the Ising model at (b1+b2)/2, so
+    d = Z((b1+b2)/2) / sqrt(Z(b1) Z(b2)) per site (Sec. III with Onsager)."""
+    b1, b2 = 0.25, 0.35
+    A1, A2 = ising_tensor(b1), ising_tensor(b2)
+    opt = O.CTMOptions(chi=16, proj="svd", cutoff=1e-12)
+    ks = []
+    for ta, tb in ((A1, A2), (A1, A1), (A2, A2)):
+        st = O.make_state([ta], [[0]], 2, 16, mixed_with=[tb])
+        st, _, _ = O.ctm_converge(st, opt, 1e-9, 80)
+        ks.append(O.kappa(st))
+    d_block, _ = O.fidelity(ks[0], ks[1], ks[2], 1)
+    exact = np.exp(onsager_minus_beta_f((b1 + b2) / 2)
+                   - 0.5 * (onsager_minus_beta_f(b1) + onsager_minus_beta_f(b2)))
+    assert abs(d_block - exact) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# D = 1 product states: the environment is exact and everything is closed form
+# ---------------------------------------------------------------------------
+def product_tensors(seed, n=4, d=8):
+    rng = np.random.default_rng(seed)
+    phis = [rng.standard_normal(d) + 1j * rng.standard_normal(d) for _ in range(n)]
+    return phis, [phi.reshape(d, 1, 1, 1, 1) for phi in phis]
+
+
+# ruby bonds of one 2x2 cell as (site1, spin1, site2, spin2, alpha), sites given
+# as (x, y); written from App. A: triangle z-links inside every block site,
+# inter-block x/y links on the right bond of an A site and on vertical bonds.
+def ruby_links():
+    links = []
+    sites = [(0, 0), (1, 0), (0, 1), (1, 1)]
+    for s in sites:
+        links += [(s, 1, s, 2, "z"), (s, 1, s, 3, "z"), (s, 2, s, 3, "z")]
+    for (x, y) in sites:
+        t = "A" if (x + y) % 2 == 0 else "B"
+        right = ((x + 1) % 2, y)
+        below = (x, (y + 1) % 2)
+        if t == "A":
+            links += [((x, y), 1, right, 1, "x"), ((x, y), 3, right, 3, "y")]
+        # vertical: upper spin 3 -- lower spin 2 by x, upper 2 -- lower 1 by y
+        links += [((x, y), 3, below, 2, "x"), ((x, y), 2, below, 1, "y")]
+    return links
+
+
+def spin_expect(phi, k, alpha):
+    """<phi| sigma^alpha on spin k |phi> / <phi|phi> for a block-site vector."""
+    s = {"x": np.array([[0, 1], [1, 0]]), "y": np.array([[0, -1j], [1j, 0]]), "z": np.diag([1, -1])}[alpha]
+    psi = phi.reshape(2, 2, 2)
+    out = np.tensordot(s, psi, axes=([1], [k - 1]))
+    out = np.moveaxis(out, 0, k - 1)
+    return np.real(np.vdot(psi, out) / np.vdot(psi, psi))
+
+
+def pair_expect(phi, k1, k2, alpha):
+    """<phi| sigma^alpha_k1 sigma^alpha_k2 |phi> / <phi|phi> inside one block site."""
+    s = {"x": np.array([[0, 1], [1, 0]]), "y": np.array([[0, -1j], [1j, 0]]), "z": np.diag([1, -1])}[alpha]
+    psi = phi.reshape(2, 2, 2)
+    out = psi
+    for k in (k1, k2):
+        out = np.moveaxis(np.tensordot(s, out, axes=([1], [k - 1])), 0, k - 1)
+    return np.real(np.vdot(psi, out) / np.vdot(psi, psi))
+
+
+def test_product_state_rdm_and_energy_closed_form():
+    phis, ts = product_tensors(3)
+    pat = [[0, 1], [2, 3]]
+    J = (0.7, 1.3, 0.9)
+    st = O.make_state(ts, pat, 1, 2)
+    opt = O.CTMOptions(chi=2, proj="svd")
+    for _ in range(2):
+        st = O.sweep(st, opt)
+    r = O.bond_rdms(st, ts, pat)
+    rho1 = [np.outer(p, p.conj()) / np.vdot(p, p) for p in phis]
+    for y in range(2):
+        for x in range(2):
+            exp_h = np.kron(rho1[pat[y][x]], rho1[pat[y][(x + 1) % 2]])
+            exp_v = np.kron(rho1[pat[y][x]], rho1[pat[(y + 1) % 2][x]])
+            assert np.allclose(r["h"][y, x], exp_h, atol=1e-13)
+            assert np.allclose(r["v"][y, x], exp_v, atol=1e-13)
+    e = O.energy_per_spin(r, J, 2, 2)
+    Jd = {"x": J[0], "y": J[1], "z": J[2]}
+    site_phi = {(x, y): phis[pat[y][x]] for x in range(2) for y in range(2)}
+    links = ruby_links()
+    assert len(links) == 24  # 12 spins, four-valent lattice
+    def term(s1, k1, s2, k2, al):
+        if s1 == s2:  # two spins of the same block site
+            return pair_expect(site_phi[s1], k1, k2, al)
+        return spin_expect(site_phi[s1], k1, al) * spin_expect(site_phi[s2], k2, al)
+    e_exact = sum(-Jd[l[4]] * term(*l) for l in links) / 12
+    assert abs(e - e_exact) < 1e-13
+
+
+def test_all_up_energy_is_minus_Jz():
+    d = 8
+    A = np.zeros((d, 1, 1, 1, 1))
+    A[0] = 1.0
+    st = O.make_state([A] * 4, [[0, 1], [2, 3]], 1, 1)
+    st = O.sweep(st, O.CTMOptions(chi=1, proj="svd"))
+    r = O.bond_rdms(st, [A] * 4, [[0, 1], [2, 3]])
+    assert abs(O.energy_per_spin(r, (1.0, 1.0, 0.37), 2, 2) + 0.37) < 1e-14
+
+
+def test_product_state_fidelity_closed_form():
+    phis1, t1 = product_tensors(5)
+    phis2, t2 = product_tensors(6)
+    pat = [[0, 1], [2, 3]]
+    opt = O.CTMOptions(chi=1, proj="svd")
+    ks = []
+    for a, b in ((t1, t2), (t1, t1), (t2, t2)):
+        st = O.make_state(a, pat, 1, 1, mixed_with=b)
+        st = O.sweep(st, opt)
+        ks.append(O.kappa(st))
+    d_block, d_spin = O.fidelity(*ks, 4)
+    ov = [abs(np.vdot(q, p)) / (np.linalg.norm(p) * np.linalg.norm(q)) for p, q in zip(phis1, phis2)]
+    exact = np.prod(ov) ** 0.25
+    assert abs(d_block - exact) < 1e-13
+    assert abs(d_spin - exact ** (1 / 3)) < 1e-13
+    st = O.make_state(t1, pat, 1, 1, mixed_with=t1)
+    st = O.sweep(st, opt)
+    k = O.kappa(st)
+    assert abs(O.fidelity(k, k, k, 4)[0] - 1.0) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Untruncated moves equal the exact contraction of the finite patch
+# ---------------------------------------------------------------------------
+def test_trace_init_rdm_equals_bruteforce_patch():
+    ts = random_tensors(7, 4, 2, 2)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 2, 4)
+    A_cell = [[ts[pat[y][x]] for x in range(2)] for y in range(2)]
+    rho = O.rdm_horizontal(st, A_cell, 0, 0)
+    ref = brute_force_rdm(ts, pat, range(-1, 3), range(-1, 2), [(0, 0), (1, 0)])
+    assert np.allclose(rho, ref, atol=1e-13)
+
+
+def test_untruncated_column_absorption_equals_bruteforce_patch():
+    """2x2 cell, four tensors: absorbing column 0 without truncation gives the
+    environment of the patch one column wider (bond (1,0)-(2,0))."""
+    ts = random_tensors(8, 4, 4, 2)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 2, 64)
+    st = O.left_move(st, O.CTMOptions(chi=64, proj="svd", cutoff=1e-14), columns=[0])
+    A_cell = [[ts[pat[y][x]] for x in range(2)] for y in range(2)]
+    rho = O.rdm_horizontal(st, A_cell, 1, 0)
+    ref = brute_force_rdm(ts, pat, range(-1, 4), range(-1, 2), [(1, 0), (2, 0)])
+    assert np.allclose(rho, ref, atol=1e-9)
+
+
+@pytest.mark.parametrize("direction", ["L", "R", "U", "D"])
+def test_untruncated_move_equals_bruteforce_patch(direction):
+    """1x1 cell: one move in each direction widens the patch on that side."""
+    ts = random_tensors(9, 1, 4, 2)
+    st = O.make_state(ts, [[0]], 2, 64)
+    st = O.move(st, direction, O.CTMOptions(chi=64, proj="svd", cutoff=1e-14))
+    rho = O.rdm_horizontal(st, [[ts[0]]], 0, 0)
+    xs = {"L": range(-2, 3), "R": range(-1, 4)}.get(direction, range(-1, 3))
+    ys = {"U": range(-2, 2), "D": range(-1, 3)}.get(direction, range(-1, 2))
+    ref = brute_force_rdm(ts, [[0]], xs, ys, [(0, 0), (1, 0)])
+    assert np.allclose(rho, ref, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Invariances of the exact network
+# ---------------------------------------------------------------------------
+def random_unitary(rng, n):
+    q, r = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+def test_unitary_gauge_invariance():
+    ts = random_tensors(10, 4, 8, 2)
+    pat = [[0, 1], [2, 3]]
+    rng = np.random.default_rng(11)
+    g = [t.copy() for t in ts]
+    for y in range(2):
+        for x in range(2):
+            U = random_unitary(rng, 2)  # bond (x,y) -> (x+1,y)
+            L, R = pat[y][x], pat[y][(x + 1) % 2]
+            g[L] = np.einsum("puldr,rs->pulds", g[L], U)
+            g[R] = np.einsum("sl,puldr->pusdr", U.conj().T, g[R])
+            V = random_unitary(rng, 2)  # bond (x,y) -> (x,y+1)
+            T_, B_ = pat[y][x], pat[(y + 1) % 2][x]
+            g[T_] = np.einsum("puldr,ds->pulsr", g[T_], V)
+            g[B_] = np.einsum("su,puldr->psldr", V.conj().T, g[B_])
+    opt = O.CTMOptions(chi=12, proj="svd")
+    res = []
+    for tens in (ts, g):
+        st = O.make_state(tens, pat, 2, 12)
+        for _ in range(3):
+            st = O.sweep(st, opt)
+        r = O.bond_rdms(st, tens, pat)
+        res.append((O.corner_spectra(st), r, O.energy_per_spin(r, (1, 1, 1), 2, 2)))
+    assert np.allclose(res[0][0], res[1][0], atol=1e-10)
+    assert np.allclose(res[0][1]["h"], res[1][1]["h"], atol=1e-10)
+    assert np.allclose(res[0][1]["v"], res[1][1]["v"], atol=1e-10)
+    assert abs(res[0][2] - res[1][2]) < 1e-12
+
+
+def c4v_symmetrize(A):
+    rot = lambda t: np.transpose(t, (0, 4, 1, 2, 3))       # (u,l,d,r) -> (r,u,l,d)
+    ref = lambda t: np.transpose(t, (0, 1, 4, 3, 2))       # swap l <-> r
+    out = np.zeros_like(A)
+    t = A
+    for _ in range(4):
+        out = out + t + ref(t)
+        t = rot(t)
+    return out / 8
+
+
+def test_c4v_symmetric_tensor_gives_symmetric_environment():
+    A = c4v_symmetrize(random_tensors(12, 1, 2, 2, cplx=False)[0])
+    st = O.make_state([A], [[0]], 2, 12)
+    opt = O.CTMOptions(chi=12, proj="svd")
+    st, _, _ = O.ctm_converge(st, opt, 1e-11, 200)
+    s = O.corner_spectra(st)
+    nz = s[0, 0, 0] > 1e-8
+    for j in range(1, 4):
+        assert np.allclose(s[j, 0, 0][nz], s[0, 0, 0][nz], atol=1e-10)
+    r = O.bond_rdms(st, [A], [[0]])
+    assert np.allclose(r["h"], r["v"], atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Projectors: the randomized range finder is exact once it spans everything,
+# and converges to the exact truncated SVD with more subspace iterations.
+# ---------------------------------------------------------------------------
+def test_rsvd_full_span_equals_svd():
+    ts = random_tensors(13, 4, 8, 2)
+    pat = [[0, 1], [2, 3]]
+    chi = 4
+    K = chi * 4
+    es = []
+    for proj, over in (("svd", 0), ("rsvd", 16)):
+        opt = O.CTMOptions(chi=chi, proj=proj, oversample=over, omega=synth.omega(1, K, chi + over))
+        st = O.make_state(ts, pat, 2, chi)
+        for _ in range(3):
+            st = O.sweep(st, opt)
+        es.append(O.energy_per_spin(O.bond_rdms(st, ts, pat), (1, 1, 1), 2, 2))
+    assert abs(es[0] - es[1]) < 1e-12
+
+
+def test_rsvd_converges_to_svd_with_power_iterations():
+    rng = np.random.default_rng(4)
+    n, k = 120, 30
+    U = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+    V = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+    s = 0.8 ** np.arange(n)
+    X = (U * s) @ V.conj().T
+    opt = O.CTMOptions(chi=20, proj="rsvd", oversample=10, power=6, omega=synth.omega(2, n, k))
+    Ur, sr, Vr = O.truncated_svd(X, opt)
+    assert np.allclose(sr[:20], s[:20], rtol=1e-12)
+    # the kept left subspace matches
+    Pr = Ur[:, :20] @ Ur[:, :20].conj().T
+    Pe = U[:, :20] @ U[:, :20].conj().T
+    assert np.linalg.norm(Pr - Pe) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Sec. IV: boundary density operator
+# ---------------------------------------------------------------------------
+def test_spectrum_identity_of_eq_rho():
+    """spec(sigma_L^T sigma_R) = spec(sqrt(sigma_L^T) sigma_R sqrt(sigma_L^T))
+    for Hermitian positive sigma's (the identity used after Eq. rho)."""
+    rng = np.random.default_rng(5)
+    n = 16
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    sL, sR = G @ G.conj().T, H @ H.conj().T
+    ev = np.sort(np.real(np.linalg.eigvals(sL.T @ sR)))[::-1]
+    w, V = np.linalg.eigh(sL.T)
+    Wh = (V * np.sqrt(w)) @ V.conj().T
+    ev2 = np.sort(np.linalg.eigvalsh(Wh @ sR @ Wh))[::-1]
+    assert np.allclose(ev, ev2, rtol=1e-10)
+
+
+def test_ring_sigma_at_trace_init_is_column_of_sites():
+    ts = random_tensors(14, 4, 2, 2)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 2, 4)
+    D = 2
+    # T2[0, y] at trace init = site (1, y) with its right leg traced
+    sR = O.ring_sigma(st, "R", 0, 2)
+    a = [O.double_layer(ts[pat[y][1]]).reshape(D, D, D, D, D, D, D, D) for y in range(2)]
+    # sites (1,0), (1,1) stacked on a periodic column of height 2, right legs traced,
+    # left legs open (ket k, bra b); T's are normalised, so compare up to scale.
+    ref = np.einsum("aAkKbBrr,bBlLaAss->klKL", a[0], a[1]).reshape(4, 4)
+    # st tensors are padded/normalised copies: compare the normalised operators
+    assert np.allclose(sR / np.linalg.norm(sR), ref / np.linalg.norm(ref), atol=1e-13)
+
+
+def test_product_state_boundary_entropy_is_zero():
+    _, ts = product_tensors(15)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 1, 1)
+    st = O.sweep(st, O.CTMOptions(chi=1, proj="svd"))
+    lam = O.boundary_spectrum(st, 0, 2)
+    assert np.allclose(lam, [1.0]) and abs(O.entropy(lam)) < 1e-15
+
+
+def test_hamiltonian_terms_hermitian_and_trivial_bond():
+    H = O.ruby_bond_hamiltonians((0.3, 0.5, 0.7))
+    for k in ("H_r", "H_u", "H_d"):
+        assert np.allclose(H[k], H[k].conj().T)
+    assert not np.any(H["H_l"])
+    # each Pauli-product term is traceless: trace of every bond operator vanishes
+    for k in ("H_r", "H_u", "H_d"):
+        assert abs(np.trace(H[k])) < 1e-12
