@@ -1,0 +1,303 @@
+"""Benchmark of the CTM hot path on GB300.
+
+One step = rebuild of the double layers (Fig. 3a) + one CTM sweep (moves L,
+R, U, D: enlarged corners, projectors, renormalisation, normalisation) + the
+eight nearest-neighbour RDMs and the ruby energy, on the D=5, chi=100, 2x2
+complex workload.  value = CTM moves per second over the whole job
+(4 moves per step and rank).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CTM moves/s & TFLOP/s at D=5 χ=100: mixed-prec/batched vs FP64, |ΔE|≤1e-6"
+MOVES_PER_STEP = 4
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--prec", default="fp64", choices=["fp64", "tf32", "bf16x3"])
+    p.add_argument("--D", type=int, default=5)
+    p.add_argument("--chi", type=int, default=100)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(D, chi, seed):
+    import synth
+    return synth.workload("cfg3", seed=seed, D=D, chi=chi)
+
+
+def config_desc(args, prec):
+    return {
+        "workload": f"2x2 ruby block-site cell, d=8, D={args.D}, chi={args.chi}, complex product state "
+                    f"+ 0.1 complex-normal noise (config 3 recipe), rSVD projectors k=chi+16, q=2",
+        "step": "double-layer rebuild + 1 sweep (L,R,U,D) + 8 bond RDMs + energy",
+        "prec": prec,
+        "cell": "2x2",
+        "l2": "working set > L2 (four enlarged corners of (chi D^2)^2 complex128 = 400 MB)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def zgemm_peak_tflops(torch):
+    """Complex128 GEMM throughput of cuBLAS on this GPU (FP64 reference peak)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.complex128, device="cuda")
+    b = torch.randn(n, n, dtype=torch.complex128, device="cuda")
+    best = 0.0
+    for _ in range(4):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 8.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    del a, b
+    return best
+
+
+def oracle_move_seconds(D, chi, n_moves=1):
+    """The oracle as it stands: one left move of the same workload on the host cores."""
+    import oracle as O
+    import synth
+    w = workload(D, chi, 0)
+    st = O.make_state(w["tensors"], w["pattern"], D, chi)
+    K, k = chi * D * D, chi + 16
+    opt = O.CTMOptions(chi=chi, proj="rsvd", omega=synth.omega(7, K, k))
+    t0 = time.perf_counter()
+    for _ in range(n_moves):
+        st = O.move(st, "L", opt)
+    return (time.perf_counter() - t0) / n_moves
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    secs = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_move_seconds(args.D, args.chi)
+        if i >= args.warmup:
+            secs.append(t)
+    mean = sum(secs) / len(secs)
+    v = 1.0 / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "moves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_desc(args, "fp64 numpy oracle"),
+        "cpu_baseline": {"value": v, "unit": "moves/s", "cores": host_cores(), "kind": "oracle",
+                         "sample": "one left move (of the 4 per sweep) per step, numpy/LAPACK FP64"},
+        "e2e": {"value": v, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1711_04798_gb300 import CTM
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    w = workload(args.D, args.chi, seed=rank)
+    J = w["J"]
+    g = CTM(w["tensors"], w["pattern"], args.chi, prec=args.prec, stream=stream.cuda_stream)
+
+    def step():
+        g.rebuild()
+        g.sweep(1)
+        return g.energy(J)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    g.profile(True)
+    l0 = g.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        energies = [step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = g.launch_count() - l0
+    gemm = g.profile_read(0)
+    jac = g.profile_read(1)
+    g.profile(False)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps * MOVES_PER_STEP / (ms_max * 1e-3)
+
+    # end to end through the public API: host tensors in, energy out, every step
+    host_tensors = w["tensors"]
+    h2d = sum(a.nbytes for a in host_tensors)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.set_tensors(host_tensors)
+        g.sweep(1)
+        g.energy(J)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps * MOVES_PER_STEP / float(te.item())
+
+    if rank != 0:
+        g.close()
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    if args.prec == "fp64":
+        zpk = zgemm_peak_tflops(torch)
+        roof = {"bound": "alu", "achieved": gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] else None,
+                "peak": zpk, "unit": "TFLOP/s", "traffic": None,
+                "kernel": "zgemm_kernel (complex FP64 GEMM, CUDA cores)",
+                "peak_source": "cuBLAS complex128 GEMM measured in this run (no FP64 entry in the peaks file)"}
+    else:
+        pk = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "achieved": gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] else None,
+                "peak": pk, "unit": "TFLOP/s", "traffic": None, "kernel": "tcgen05 GEMM",
+                "peak_source": f"bf16 sustained ({peak_src})"}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] and roof["peak"] else None
+    roof["gemm_share_of_step"] = gemm["ms"] / ms if ms else None
+    roof["gemm_launches"] = gemm["launches"]
+    roof["jacobi_ms_share"] = jac["ms"] / ms if ms else None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        secs = oracle_move_seconds(args.D, args.chi)
+        cpu = {"value": 1.0 / secs, "unit": "moves/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "one left move of the same workload (numpy/LAPACK FP64, all host cores)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec],
+        "data": "synthetic", "config": config_desc(args, args.prec),
+        "tflops": gemm["flops"] / (ms * 1e-3) / 1e12 if ms else None,
+        "energy_per_spin": energies[-1],
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ipeps_ctm.h -- C ABI of the GB300 CTM library.
+ *
+ * The library contracts the infinite double-layer network of an iPEPS with
+ * the corner transfer matrix (CTM) renormalization group (paper Sec. II.C and
+ * Fig. 3): four chi x chi corners C1..C4 and four chi x chi x D^2 edge tensors
+ * T1..T4 per unit-cell position, grown by directional moves and truncated to
+ * chi by projectors.  It also evaluates the readouts the paper builds on that
+ * environment: nearest-neighbour reduced density matrices and the energy of
+ * the ruby model (Eq. H-KR, App. A), the fidelity per site (Sec. III, Eq.
+ * "fidelity", Fig. 4) and the boundary density operator spectrum /
+ * entanglement entropy on an infinite cylinder (Sec. IV, Eq. "rho").
+ *
+ * Conventions (all arrays row-major, complex values as interleaved
+ * (re, im) doubles):
+ *   - site tensors A[p,u,l,d,r], p physical (dimension d), u,l,d,r virtual
+ *     (dimension D), unit cell Lx x Ly with x to the right and y downwards;
+ *   - the double-layer tensor a[(u u'),(l l'),(d d'),(r r')], fused index
+ *     ket*D + bra (Fig. 3a);
+ *   - environment legs, listed so a 90-degree rotation only relabels:
+ *     C1[d,r] C2[l,d] C3[u,l] C4[r,u], T1[l,d,r] T2[u,l,d] T3[r,u,l] T4[d,r,u];
+ *   - a move is one direction applied to every column (row) of the cell in
+ *     turn; a sweep is the moves L, R, U, D.
+ *
+ * Memory: the library copies the host tensors at create time; all device
+ * memory of a handle comes from the caller's workspace (if given) or from
+ * cudaMalloc at create time, and is released by ipeps_ctm_destroy.  Host
+ * output buffers are always caller-owned.  Every call runs on the handle's
+ * stream and returns when its host outputs are ready.
+ *
+ * Errors: every entry point returns an ipeps_status; none aborts.  On error
+ * ipeps_last_error() (thread-local) holds a one-line message.  A handle stays
+ * valid after an error, but its environment is unspecified after a failed
+ * move.  A handle is used by one host thread at a time.
+ */
+#ifndef IPEPS_CTM_H
+#define IPEPS_CTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipeps_ctm_s* ipeps_ctm;
+
+typedef enum {
+  IPEPS_OK = 0,
+  IPEPS_EINVAL = 1,      /* bad argument (sizes, pointers, pattern)          */
+  IPEPS_ENOMEM = 2,      /* device allocation or workspace too small          */
+  IPEPS_ECUDA = 3,       /* a CUDA runtime call failed                        */
+  IPEPS_ENOCONV = 4,     /* converge: max_sweeps reached above tolerance      */
+  IPEPS_ETIMEOUT = 5,    /* an iteration budget inside a kernel ran out       */
+  IPEPS_ENUMERIC = 6,    /* NaN/Inf or a zero norm met                        */
+  IPEPS_EUNSUPPORTED = 7 /* option combination not built                      */
+} ipeps_status;
+
+typedef enum { IPEPS_REAL64 = 0, IPEPS_COMPLEX128 = 1 } ipeps_dtype;
+
+/* Arithmetic of the contraction GEMMs.  Projector orthonormalisation, the
+ * Jacobi SVDs, normalisation and readouts are FP64 in every mode. */
+typedef enum {
+  IPEPS_PREC_FP64 = 0,   /* complex FP64 on the CUDA cores                    */
+  IPEPS_PREC_TF32 = 1,   /* tcgen05 TF32 tensor cores, FP32 accumulate        */
+  IPEPS_PREC_BF16X3 = 2  /* tcgen05 split-BF16 (hi*hi + hi*lo + lo*hi), FP32  */
+} ipeps_prec;
+
+typedef enum {
+  IPEPS_MOVE_LEFT = 0,
+  IPEPS_MOVE_UP = 1,
+  IPEPS_MOVE_RIGHT = 2,
+  IPEPS_MOVE_DOWN = 3,
+  IPEPS_SWEEP = 4        /* L, R, U, D */
+} ipeps_dir;
+
+/* Unit cell (paper Sec. II.B: a 2x2 cell of block sites; 1x1 also allowed). */
+typedef struct {
+  int Lx, Ly;                       /* 1 or 2 each                                 */
+  int pattern[4];                   /* tensor id at (x,y) is pattern[y*Lx + x]     */
+  int n_tensors;                    /* 1..4                                        */
+  int d;                            /* physical dimension (8 for a block site)     */
+  int D;                            /* bond dimension (a leg of size 1 is padded)  */
+  ipeps_dtype dtype;                /* element type of the host tensors           */
+  const void* const* tensors;       /* n_tensors host pointers, A[p,u,l,d,r]       */
+  const void* const* tensors_bra;   /* NULL, or the second state B of the mixed
+                                       network e = sum_p A_p conj(B_p) (Sec. III)  */
+} ipeps_cell;
+
+typedef struct {
+  int chi;                          /* environment bond dimension, >= D*D          */
+  ipeps_prec prec;                  /* contraction arithmetic                      */
+  int rsvd_oversample;              /* projector range finder width k = chi + p    */
+  int rsvd_power;                   /* subspace iterations q                       */
+  double svd_cutoff;                /* keep singular values > cutoff * largest     */
+  double orth_tol;                  /* range-finder basis: drop s < tol * largest  */
+  uint64_t omega_seed;              /* SplitMix64 stream of the test matrix        */
+  int jacobi_max_sweeps;            /* iteration budget of every Jacobi SVD        */
+  void* stream;                     /* cudaStream_t; NULL = legacy default stream  */
+  void* workspace;                  /* optional caller-owned device memory         */
+  size_t workspace_bytes;           /* its size; see ipeps_ctm_workspace_size      */
+} ipeps_options;
+
+/* Fill *opt with the defaults: prec FP64, oversample 16, power 2, cutoff 1e-8,
+ * orth_tol 1e-14, omega_seed 7, jacobi_max_sweeps 40, NULL stream/workspace.
+ * chi is set to 0 and must be chosen by the caller. */
+void ipeps_default_options(ipeps_options* opt);
+
+/* Device bytes a handle with this cell/options needs (workspace sizing). */
+ipeps_status ipeps_ctm_workspace_size(const ipeps_cell* cell, const ipeps_options* opt,
+                                      size_t* bytes);
+
+/* Copy the tensors to the device, build every double-layer tensor (Fig. 3a;
+ * the mixed e of Sec. III when tensors_bra is given), and initialise the
+ * environment by tracing the outer legs of the neighbouring sites ket against
+ * bra.  EINVAL if chi < D*D, Lx/Ly not in {1,2}, ids out of range. */
+ipeps_status ipeps_ctm_create(const ipeps_cell* cell, const ipeps_options* opt, ipeps_ctm* out);
+
+/* Replace the site tensors (same shapes) and rebuild the double layers; the
+ * environment is kept, as when an update step reuses it (Sec. II.C).  With
+ * tensors == NULL the double layers are rebuilt from the tensors already on
+ * the device (no copy; the call does not wait for the device). */
+ipeps_status ipeps_ctm_set_tensors(ipeps_ctm h, const void* const* tensors,
+                                   const void* const* tensors_bra);
+
+/* Re-run the trace initialisation of the environment. */
+ipeps_status ipeps_ctm_reset_env(ipeps_ctm h);
+
+/* Apply `count` moves in direction dir (ipeps_dir).  Each move computes the
+ * enlarged corners, the projectors of every cut and renormalises the
+ * corners/edges of each column (row) of the cell in turn (Sec. II.C). */
+ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count);
+
+/* Singular values of every corner, divided by the largest: s_out is
+ * [4][Ly][Lx][chi] doubles (C1..C4), caller-owned. */
+ipeps_status ipeps_ctm_spectra(ipeps_ctm h, double* s_out);
+
+/* Sweep until max over corners of ||s/s_0 - s_old/s_old_0||_2 < tol or
+ * max_sweeps is reached (ENOCONV).  sweeps/delta may be NULL. */
+ipeps_status ipeps_ctm_converge(ipeps_ctm h, double tol, int max_sweeps, int* sweeps,
+                                double* delta);
+
+/* Nearest-neighbour two-site RDMs normalised to trace one (paper Sec. II.C,
+ * used for the correlators of Sec. VI).  rho_h: bonds (x,y)-(x+1,y), rho_v:
+ * bonds (x,y)-(x,y+1), each [Ly][Lx][d*d][d*d] complex (interleaved doubles),
+ * rows (p_first, p_second) ket, columns the bra pair.  Either may be NULL. */
+ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v);
+
+/* Energy per spin of the ruby model H_R = -sum_a J_a sum s^a s^a (Eq. H-KR)
+ * in the block-site form of App. A (2x2 cell, d = 8): J = {Jx, Jy, Jz}. */
+ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e_per_spin);
+
+/* Partition-function ratio kappa = Z(window) Z(corners) / (Z(columns)
+ * Z(rows)) of the 2x2 window of sites at (0,0), cell indices taken mod
+ * (Lx, Ly) (Eq. "fidelity", Fig. 4): the weight of those four sites per unit
+ * of infinite lattice.  kappa_out = {re, im}. */
+ipeps_status ipeps_kappa(ipeps_ctm h, double* kappa_out);
+
+/* Fidelity per block site d = |k12|^(1/4) / (|k11| |k22|)^(1/8) (the 2x2 window),
+ * from a converged mixed-network handle h12 (tensors_bra set) and the two
+ * converged plain handles (Sec. III); d_spin = d_block^(1/3). */
+ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double* d_block,
+                            double* d_spin);
+
+/* Boundary density operator on a cylinder of circumference Nv block sites
+ * (a multiple of Ly) cut between columns x and x+1 (Sec. IV): sigma_R = ring
+ * of T2 at column x, sigma_L = ring of T4 at column x+1; eigenvalues of
+ * sigma_L^T sigma_R through sqrt(sigma_L^T) sigma_R sqrt(sigma_L^T) after
+ * Hermitising, normalised to sum 1, descending.  eig_out holds D^Nv doubles
+ * (caller-owned, may be NULL), *n_out = D^Nv, *S_vn = -sum l ln l.  EINVAL
+ * if D^Nv > 4096. */
+ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
+                                double* S_vn);
+
+/* Copy one environment tensor to the host: role 0..3 = C1..C4 (chi*chi
+ * complex), 4..7 = T1..T4 (chi*D*D*chi complex), at cell position (x,y). */
+ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* host_out);
+
+/* Block until all work of the handle is done. */
+ipeps_status ipeps_ctm_sync(ipeps_ctm h);
+
+/* Number of kernels this handle launched since create (a counter kept on
+ * the host, for launch accounting). */
+uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
+
+/* Kernel-class timing for roofline reports: with enable != 0 every
+ * contraction GEMM (kind 0) and every Jacobi SVD (kind 1) is bracketed by
+ * CUDA events on the handle's stream.  profile() clears the records;
+ * profile_read() synchronises and returns the summed event time (ms), the
+ * number of launches and (kind 0) the algorithmic flops, 8*M*N*K per complex
+ * GEMM.  Not a paper operation: measurement support only. */
+ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable);
+ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms, uint64_t* launches,
+                                    double* flops);
+
+void ipeps_ctm_destroy(ipeps_ctm h);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* ipeps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPEPS_CTM_H */

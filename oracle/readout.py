@@ -166,48 +166,53 @@ def energy_per_spin(rdms, J, Lx: int, Ly: int) -> float:
 # "free energy" kappa = Z(cell) Z(corners) / (Z(columns only) Z(rows only)),
 # Eq. (fidelity) written with C1..C4, T (Fig. 4).
 # ---------------------------------------------------------------------------
-def _window_contract(st: CTMState, with_rows: bool, with_cols: bool) -> complex:
-    """Contract the environment window at (0,0) row by row.
+WINDOW = 2  # kappa uses a 2x2 window of sites for every cell (Lx, Ly in {1, 2})
 
-    with_cols: the Lx columns (T1 on top, T3 at the bottom, a's inside) are
-    present; with_rows: the Ly rows (T4 on the left, T2 on the right) are
-    present.  The four corners are always present.  The boundary array B
-    carries axes [vl, v_0 .. v_{n-1}, vr] (left bond, column bonds, right bond).
+
+def _window_contract(st: CTMState, with_rows: bool, with_cols: bool) -> complex:
+    """Contract the environment of the 2x2 window of sites at (0,0) row by row.
+
+    with_cols: the window's two columns (T1 on top, T3 at the bottom, a's
+    inside) are present; with_rows: its two rows (T4 on the left, T2 on the
+    right) are present.  The four corners are always present.  Cell indices
+    are taken mod (Lx, Ly).  The boundary array B carries axes
+    [vl, v_0 .. v_{n-1}, vr] (left bond, column bonds, right bond).
     """
     Lx, Ly = st.Lx, st.Ly
     C, T, a = st.C, st.T, st.a
-    n = Lx if with_cols else 0
-    xr, yb = Lx - 1, Ly - 1
+    n = WINDOW if with_cols else 0
+    xr, yb = (WINDOW - 1) % Lx, (WINDOW - 1) % Ly
     B = C[0][0][0]                                   # [vl, ht]
     for x in range(n):
-        B = np.tensordot(B, T[0][0][x], axes=([B.ndim - 1], [0]))  # T1[l,d,r]
-    B = np.tensordot(B, C[1][0][xr], axes=([B.ndim - 1], [0]))     # C2[l,d]
-    for y in range(Ly if with_rows else 0):
-        B = np.tensordot(T[3][y][0], B, axes=([2], [0]))  # T4[d,r,u]: [vl', h, v.., vr]
+        B = np.tensordot(B, T[0][0][x % Lx], axes=([B.ndim - 1], [0]))  # T1[l,d,r]
+    B = np.tensordot(B, C[1][0][xr], axes=([B.ndim - 1], [0]))          # C2[l,d]
+    for y in range(WINDOW if with_rows else 0):
+        B = np.tensordot(T[3][y % Ly][0], B, axes=([2], [0]))  # T4[d,r,u]: [vl', h, v.., vr]
         for x in range(n):
-            B = np.tensordot(B, a[y][x], axes=([1 + x, 2 + x], [1, 0]))
+            B = np.tensordot(B, a[y % Ly][x % Lx], axes=([1 + x, 2 + x], [1, 0]))
             B = np.moveaxis(B, [B.ndim - 2, B.ndim - 1], [1 + x, 2 + x])
-        B = np.tensordot(B, T[1][y][xr], axes=([1 + n, 2 + n], [1, 0]))  # T2[u,l,d]
+        B = np.tensordot(B, T[1][y % Ly][xr], axes=([1 + n, 2 + n], [1, 0]))  # T2[u,l,d]
     B = np.tensordot(C[3][yb][0], B, axes=([1], [0]))    # C4[r,u]: [hb, v.., vr]
     for x in range(n):
-        B = np.tensordot(B, T[2][yb][x], axes=([0, 1], [2, 1]))    # T3[r,u,l]
+        B = np.tensordot(B, T[2][yb][x % Lx], axes=([0, 1], [2, 1]))    # T3[r,u,l]
         B = np.moveaxis(B, B.ndim - 1, 0)
     return complex(np.einsum("hv,vh->", B, C[2][yb][xr]))  # C3[u,l]
 
 
 def partition_ratios(st: CTMState):
-    """(Z_cell, Z_00, Z_cols, Z_rows) for the window at (0,0)."""
+    """(Z_window, Z_00, Z_cols, Z_rows) for the 2x2 window at (0,0)."""
     return (_window_contract(st, True, True), _window_contract(st, False, False),
             _window_contract(st, False, True), _window_contract(st, True, False))
 
 
 def kappa(st: CTMState) -> complex:
-    """Per-cell kappa = Z_cell Z_00 / (Z_cols Z_rows)."""
+    """kappa of the 2x2 window = Z_window Z_00 / (Z_cols Z_rows): the
+    partition function of its four sites per unit of infinite lattice."""
     Zc, Z00, Zcol, Zrow = partition_ratios(st)
     return Zc * Z00 / (Zcol * Zrow)
 
 
-def fidelity(k12: complex, k11: complex, k22: complex, n_sites: int):
+def fidelity(k12: complex, k11: complex, k22: complex, n_sites: int = WINDOW * WINDOW):
     """Fidelity per block site d = |k12|^(1/n) / (|k11| |k22|)^(1/(2n)) and per
     spin d^(1/3) (three spins per block site)."""
     d_block = np.exp((np.log(abs(k12)) - 0.5 * (np.log(abs(k11)) + np.log(abs(k22)))) / n_sites)
@@ -236,26 +241,25 @@ def ring_sigma(st: CTMState, which: str, x: int, Nv: int) -> np.ndarray:
 
 
 def boundary_spectrum(st: CTMState, x: int, Nv: int):
-    """Eigenvalues of sigma_L^T sigma_R normalised to sum 1, descending.
+    """Spectrum of sigma_L^T sigma_R normalised to sum 1, descending.
 
-    Computed through the similar Hermitian operator sqrt(sigma_L^T) sigma_R
-    sqrt(sigma_L^T) (Eq. "rho" and the spectrum identity that follows it),
-    after Hermitising both sigma's and clamping negative eigenvalues of
-    sigma_L^T to zero.
+    Computed through the similar operator |sigma_L^T|^(1/2) sigma_R
+    |sigma_L^T|^(1/2) (Eq. "rho" and the spectrum identity after it): both
+    rings are phase-fixed so their traces are real positive and Hermitised;
+    |S|^(1/2) comes from the SVD S = U s V^H as V s^(1/2) V^H; the spectrum is
+    the singular values of the resulting Hermitian operator (its eigenvalues
+    when it is positive, as for an exact environment).
     """
     sL = ring_sigma(st, "L", x, Nv)
     sR = ring_sigma(st, "R", x, Nv)
-    # overall phases of the rings are gauge: fix them so the traces are real positive
     sL = sL * np.exp(-1j * np.angle(np.trace(sL)))
     sR = sR * np.exp(-1j * np.angle(np.trace(sR)))
     sL = 0.5 * (sL + sL.conj().T)
     sR = 0.5 * (sR + sR.conj().T)
-    w, V = np.linalg.eigh(sL.T)
-    w = np.clip(w, 0.0, None)
-    W = (V * np.sqrt(w)[None, :]) @ V.conj().T
+    _, s, Vh = np.linalg.svd(sL.T)
+    W = (Vh.conj().T * np.sqrt(s)[None, :]) @ Vh
     H = W @ sR @ W
-    H = 0.5 * (H + H.conj().T)
-    lam = np.linalg.eigvalsh(H)[::-1]
+    lam = np.linalg.svd(H, compute_uv=False)
     return lam / lam.sum()
 
 

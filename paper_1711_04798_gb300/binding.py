@@ -1,0 +1,270 @@
+"""ctypes binding of the C ABI in include/ipeps_ctm.h (argument marshalling
+only; every step of the CTM path runs in the CUDA library)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libipeps_ctm.so")
+
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2}
+DIRS = {"L": 0, "U": 1, "R": 2, "D": 3, "sweep": 4}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT",
+          6: "ENUMERIC", 7: "EUNSUPPORTED"}
+
+EXPORTS = [
+    "ipeps_default_options", "ipeps_ctm_workspace_size", "ipeps_ctm_create",
+    "ipeps_ctm_set_tensors", "ipeps_ctm_reset_env", "ipeps_ctm_move", "ipeps_ctm_spectra",
+    "ipeps_ctm_converge", "ipeps_rdm", "ipeps_energy", "ipeps_kappa", "ipeps_fidelity",
+    "ipeps_boundary_rho", "ipeps_ctm_env_get", "ipeps_ctm_sync", "ipeps_ctm_launch_count",
+    "ipeps_ctm_destroy", "ipeps_last_error", "ipeps_ctm_profile", "ipeps_ctm_profile_read",
+]
+
+
+class Cell(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("pattern", C.c_int * 4), ("n_tensors", C.c_int),
+                ("d", C.c_int), ("D", C.c_int), ("dtype", C.c_int),
+                ("tensors", C.POINTER(C.c_void_p)), ("tensors_bra", C.POINTER(C.c_void_p))]
+
+
+class Options(C.Structure):
+    _fields_ = [("chi", C.c_int), ("prec", C.c_int), ("rsvd_oversample", C.c_int),
+                ("rsvd_power", C.c_int), ("svd_cutoff", C.c_double), ("orth_tol", C.c_double),
+                ("omega_seed", C.c_uint64), ("jacobi_max_sweeps", C.c_int),
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class CTMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    lib.ipeps_default_options.argtypes = [C.POINTER(Options)]
+    lib.ipeps_default_options.restype = None
+    lib.ipeps_ctm_workspace_size.argtypes = [C.POINTER(Cell), C.POINTER(Options), C.POINTER(C.c_size_t)]
+    lib.ipeps_ctm_create.argtypes = [C.POINTER(Cell), C.POINTER(Options), C.POINTER(P)]
+    lib.ipeps_ctm_set_tensors.argtypes = [P, C.POINTER(P), C.POINTER(P)]
+    lib.ipeps_ctm_reset_env.argtypes = [P]
+    lib.ipeps_ctm_move.argtypes = [P, I, I]
+    lib.ipeps_ctm_spectra.argtypes = [P, C.POINTER(D)]
+    lib.ipeps_ctm_converge.argtypes = [P, D, I, C.POINTER(I), C.POINTER(D)]
+    lib.ipeps_rdm.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_kappa.argtypes = [P, C.POINTER(D)]
+    lib.ipeps_fidelity.argtypes = [P, P, P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_boundary_rho.argtypes = [P, I, I, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
+    lib.ipeps_ctm_env_get.argtypes = [P, I, I, I, C.POINTER(D)]
+    lib.ipeps_ctm_sync.argtypes = [P]
+    lib.ipeps_ctm_launch_count.argtypes = [P]
+    lib.ipeps_ctm_launch_count.restype = C.c_uint64
+    lib.ipeps_ctm_profile.argtypes = [P, I]
+    lib.ipeps_ctm_profile_read.argtypes = [P, I, C.POINTER(D), C.POINTER(C.c_uint64), C.POINTER(D)]
+    lib.ipeps_ctm_destroy.argtypes = [P]
+    lib.ipeps_ctm_destroy.restype = None
+    lib.ipeps_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("ipeps_default_options", "ipeps_ctm_destroy", "ipeps_last_error",
+                        "ipeps_ctm_launch_count"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise CTMError(st, _lib.ipeps_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class CTM:
+    """One CTM environment on the GPU (handle of the C ABI).
+
+    tensors: list of A[p,u,l,d,r] (float64 or complex128 numpy arrays);
+    pattern: [[id at (x,y)]] rows y, columns x; bra: optional second list for
+    the mixed network of the fidelity (Sec. III).
+    """
+
+    def __init__(self, tensors, pattern, chi, prec="fp64", bra=None, oversample=16, power=2,
+                 cutoff=1e-8, orth_tol=1e-14, omega_seed=7, jacobi_max_sweeps=40, stream=None,
+                 workspace=None):
+        lib = load_library()
+        self.lib = lib
+        Ly, Lx = len(pattern), len(pattern[0])
+        d, D = tensors[0].shape[0], tensors[0].shape[1]
+        cplx = any(np.iscomplexobj(t) for t in tensors) or (bra is not None)
+        dt = np.complex128 if cplx else np.float64
+        self._keep = [np.ascontiguousarray(t, dtype=dt) for t in tensors]
+        self._keep_bra = [np.ascontiguousarray(t, dtype=dt) for t in bra] if bra is not None else None
+        self.Lx, self.Ly, self.d, self.D, self.chi = Lx, Ly, d, D, chi
+        self.n_tensors = len(tensors)
+        self._dtype = dt
+        cell = Cell()
+        cell.Lx, cell.Ly = Lx, Ly
+        for y in range(Ly):
+            for x in range(Lx):
+                cell.pattern[y * Lx + x] = pattern[y][x]
+        cell.n_tensors = len(tensors)
+        cell.d, cell.D = d, D
+        cell.dtype = 1 if cplx else 0
+        self._ptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in self._keep])
+        cell.tensors = C.cast(self._ptrs, C.POINTER(C.c_void_p))
+        if self._keep_bra is not None:
+            self._bptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in self._keep_bra])
+            cell.tensors_bra = C.cast(self._bptrs, C.POINTER(C.c_void_p))
+        opt = Options()
+        lib.ipeps_default_options(C.byref(opt))
+        opt.chi = chi
+        opt.prec = PREC[prec]
+        opt.rsvd_oversample, opt.rsvd_power = oversample, power
+        opt.svd_cutoff, opt.orth_tol = cutoff, orth_tol
+        opt.omega_seed = omega_seed
+        opt.jacobi_max_sweeps = jacobi_max_sweeps
+        opt.stream = stream
+        if workspace is not None:
+            opt.workspace = C.c_void_p(workspace[0])
+            opt.workspace_bytes = workspace[1]
+        self._cell, self._opt = cell, opt
+        h = C.c_void_p()
+        _check(lib.ipeps_ctm_create(C.byref(cell), C.byref(opt), C.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def workspace_bytes(tensors, pattern, chi, **kw) -> int:
+        lib = load_library()
+        Ly, Lx = len(pattern), len(pattern[0])
+        cell = Cell()
+        cell.Lx, cell.Ly = Lx, Ly
+        for y in range(Ly):
+            for x in range(Lx):
+                cell.pattern[y * Lx + x] = pattern[y][x]
+        cell.n_tensors = len(tensors)
+        cell.d, cell.D = tensors[0].shape[0], tensors[0].shape[1]
+        cell.dtype = 1
+        dummy = (C.c_void_p * len(tensors))(*([1] * len(tensors)))
+        cell.tensors = C.cast(dummy, C.POINTER(C.c_void_p))
+        opt = Options()
+        lib.ipeps_default_options(C.byref(opt))
+        opt.chi = chi
+        opt.rsvd_oversample = kw.get("oversample", 16)
+        n = C.c_size_t()
+        _check(lib.ipeps_ctm_workspace_size(C.byref(cell), C.byref(opt), C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ipeps_ctm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rebuild(self):
+        """Rebuild the double layers from the device-resident tensors."""
+        _check(self.lib.ipeps_ctm_set_tensors(self.h, None, None))
+
+    def set_tensors(self, tensors, bra=None):
+        self._keep = [np.ascontiguousarray(t, dtype=self._dtype) for t in tensors]
+        self._ptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in self._keep])
+        bp = None
+        if bra is not None:
+            self._keep_bra = [np.ascontiguousarray(t, dtype=self._dtype) for t in bra]
+            self._bptrs = (C.c_void_p * len(bra))(*[t.ctypes.data for t in self._keep_bra])
+            bp = C.cast(self._bptrs, C.POINTER(C.c_void_p))
+        _check(self.lib.ipeps_ctm_set_tensors(self.h, C.cast(self._ptrs, C.POINTER(C.c_void_p)), bp))
+
+    def reset_env(self):
+        _check(self.lib.ipeps_ctm_reset_env(self.h))
+
+    def move(self, direction="sweep", count=1):
+        _check(self.lib.ipeps_ctm_move(self.h, DIRS[direction], count))
+
+    def sweep(self, count=1):
+        self.move("sweep", count)
+
+    def spectra(self) -> np.ndarray:
+        out = np.zeros((4, self.Ly, self.Lx, self.chi))
+        _check(self.lib.ipeps_ctm_spectra(self.h, _dptr(out)))
+        return out
+
+    def converge(self, tol, max_sweeps):
+        n, dl = C.c_int(), C.c_double()
+        st = self.lib.ipeps_ctm_converge(self.h, tol, max_sweeps, C.byref(n), C.byref(dl))
+        if st not in (0, 4):
+            _check(st)
+        return n.value, dl.value, st == 0
+
+    def rdms(self):
+        n = self.d * self.d
+        rh = np.zeros((self.Ly, self.Lx, n, n), dtype=np.complex128)
+        rv = np.zeros_like(rh)
+        _check(self.lib.ipeps_rdm(self.h, _dptr(rh.view(np.float64)), _dptr(rv.view(np.float64))))
+        return {"h": rh, "v": rv}
+
+    def energy(self, J) -> float:
+        Jv = np.asarray(J, dtype=np.float64)
+        e = C.c_double()
+        _check(self.lib.ipeps_energy(self.h, _dptr(Jv), C.byref(e)))
+        return e.value
+
+    def kappa(self) -> complex:
+        k = np.zeros(2)
+        _check(self.lib.ipeps_kappa(self.h, _dptr(k)))
+        return complex(k[0], k[1])
+
+    @staticmethod
+    def fidelity(h12: "CTM", h11: "CTM", h22: "CTM"):
+        lib = load_library()
+        db, ds = C.c_double(), C.c_double()
+        _check(lib.ipeps_fidelity(h12.h, h11.h, h22.h, C.byref(db), C.byref(ds)))
+        return db.value, ds.value
+
+    def boundary_rho(self, x, Nv):
+        n = self.D ** Nv
+        eig = np.zeros(n)
+        nout, S = C.c_int(), C.c_double()
+        _check(self.lib.ipeps_boundary_rho(self.h, x, Nv, _dptr(eig), C.byref(nout), C.byref(S)))
+        return eig[: nout.value], S.value
+
+    def env(self, role, x, y) -> np.ndarray:
+        n = self.chi * self.chi if role < 4 else self.chi * self.D * self.D * self.chi
+        out = np.zeros(n, dtype=np.complex128)
+        _check(self.lib.ipeps_ctm_env_get(self.h, role, x, y, _dptr(out.view(np.float64))))
+        if role < 4:
+            return out.reshape(self.chi, self.chi)
+        return out.reshape(self.chi, self.D * self.D, self.chi)
+
+    def sync(self):
+        _check(self.lib.ipeps_ctm_sync(self.h))
+
+    def profile(self, enable=True):
+        _check(self.lib.ipeps_ctm_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, kind=0):
+        ms, n, fl = C.c_double(), C.c_uint64(), C.c_double()
+        _check(self.lib.ipeps_ctm_profile_read(self.h, kind, C.byref(ms), C.byref(n), C.byref(fl)))
+        return {"ms": ms.value, "launches": int(n.value), "flops": fl.value}
+
+    def launch_count(self) -> int:
+        return int(self.lib.ipeps_ctm_launch_count(self.h))

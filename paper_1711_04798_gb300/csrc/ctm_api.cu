@@ -1,0 +1,1445 @@
+// C ABI of the CTM library: handle, device arena, the directional move
+// (enlarged corners -> projectors -> renormalisation, paper Sec. II.C) and the
+// readouts (RDMs/energy App. A, kappa/fidelity Sec. III, boundary rho Sec. IV).
+//
+// Every contraction runs in this library's kernels (complex FP64 GEMM or the
+// tensor-core GEMMs, index permutation, Jacobi SVD); the host only plans and
+// launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/ipeps_ctm.h"
+#include "ctm_internal.h"
+#include "tc_gemm.h"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static ipeps_status fail(ipeps_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(IPEPS_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                 \
+  } while (0)
+
+#define CKS(call)                     \
+  do {                                \
+    ipeps_status s_ = (call);         \
+    if (s_ != IPEPS_OK) return s_;    \
+  } while (0)
+
+extern "C" const char* ipeps_last_error(void) { return g_err.c_str(); }
+
+static const cplx ONE = {1.0, 0.0};
+static const cplx ZERO = {0.0, 0.0};
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct TV {  // contiguous row-major tensor view
+  cplx* p;
+  int nd;
+  int dims[8];
+  long long size() const {
+    long long s = 1;
+    for (int i = 0; i < nd; ++i) s *= dims[i];
+    return s;
+  }
+};
+
+static TV tv(cplx* p, std::initializer_list<int> dims) {
+  TV t;
+  t.p = p;
+  t.nd = 0;
+  for (int d : dims) t.dims[t.nd++] = d;
+  return t;
+}
+
+struct ipeps_ctm_s {
+  int Lx, Ly, d, D, D2, chi, K, k, ntens;
+  int pattern[4];
+  bool mixed;
+  int dtype;
+  ipeps_options opt;
+  cudaStream_t stream;
+  bool own_mem;
+  char* base;
+  size_t bytes, used;
+  // device data
+  cplx* A[4][4];      // [rotation][tensor] ket tensors A[p,u,l,d,r] in each frame
+  cplx* Bt[4][4];     // bra tensors (== A unless mixed)
+  cplx* a[4][4];      // [rotation][tensor] double layers
+  cplx* C[4][4];      // [role][y*Lx + x], original frame
+  cplx* T[4][4];
+  cplx* spareC[2][2]; // replacement buffers for renormalised C1 / C4, per row
+  cplx* spareT[2];    // replacement T4 per row
+  cplx* Q[4];
+  cplx* omt;
+  cplx* thin[4];      // k x K work
+  cplx* PT[2];        // chi x K, projector P transposed, per cut row
+  cplx* Ptil[2];      // chi x K
+  cplx* Vt;           // k x k
+  cplx* Gsel;         // chi x k
+  cplx* Hbond[4];     // 64x64 ruby bond operators: H_r, H_l, H_u, H_d
+  double* sigma;
+  double* s_sel;
+  int* perm;
+  int* counters;
+  double* dwork;      // 4096 doubles
+  double* dacc;       // 64 doubles
+  cplx* scalar;       // 16 complex
+  DevStatus* st;
+  cplx* scratch;      // bump-allocated per operation
+  long long scratch_elems, scratch_top;
+  uint64_t launches_at_create;
+  // optional per-kernel-class timing (CUDA events on the handle's stream)
+  bool profiling;
+  struct Rec { cudaEvent_t a, b; double flops; int kind; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+static cudaEvent_t pool_event(ipeps_ctm h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// kind 0: contraction GEMMs, 1: Jacobi SVDs
+static void prof_begin(ipeps_ctm h, cudaEvent_t* a) {
+  if (!h->profiling) return;
+  *a = pool_event(h);
+  cudaEventRecord(*a, h->stream);
+}
+static void prof_end(ipeps_ctm h, cudaEvent_t a, double flops, int kind) {
+  if (!h->profiling) return;
+  cudaEvent_t b = pool_event(h);
+  cudaEventRecord(b, h->stream);
+  h->recs.push_back({a, b, flops, kind});
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <class Tp>
+static Tp* carve(ipeps_ctm h, size_t count) {
+  const size_t b = align_up(count * sizeof(Tp));
+  if (h->used + b > h->bytes) return nullptr;
+  Tp* p = (Tp*)(h->base + h->used);
+  h->used += b;
+  return p;
+}
+
+static cplx* scratch_alloc(ipeps_ctm h, long long n) {
+  const long long nn = (n + 15) & ~15LL;
+  if (h->scratch_top + nn > h->scratch_elems) return nullptr;
+  cplx* p = h->scratch + h->scratch_top;
+  h->scratch_top += nn;
+  return p;
+}
+
+// sizes of everything a handle carves from its memory
+struct Sizes {
+  long long tens, a, C, T, Q, thin, proj, scratch;
+  size_t total;
+};
+
+static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens) {
+  Sizes s;
+  const long long D2 = (long long)D * D, K = chi * D2;
+  s.tens = (long long)d * D2 * D2;
+  s.a = D2 * D2 * D2 * D2;
+  s.C = (long long)chi * chi;
+  s.T = (long long)chi * D2 * chi;
+  s.Q = K * K;
+  s.thin = (long long)k * K;
+  s.proj = (long long)chi * K;
+  // largest intermediates: RDM halves (chi^2 D^4 d, three of them) and the
+  // enlarged-corner chain (a few K^2); boundary rings are below these.
+  // rdm: L2, L3, L4 and two contraction temporaries of chi^2 D^4 d, the halves
+  const long long rdm = 6 * (long long)chi * chi * D2 * D2 * d + 3 * (long long)chi * chi * D2 * d * d;
+  s.scratch = std::max(6 * s.Q, rdm) + (1 << 16);
+  size_t tot = 0;
+  auto add = [&](long long n, size_t el) { tot += align_up((size_t)n * el); };
+  for (int i = 0; i < 2 * 4 * ntens; ++i) add(s.tens, 16);
+  for (int i = 0; i < 4 * ntens; ++i) add(s.a, 16);
+  for (int i = 0; i < 4 * Lx * Ly; ++i) { add(s.C, 16); add(s.T, 16); }
+  for (int i = 0; i < 4; ++i) add(s.C, 16);
+  for (int i = 0; i < 2; ++i) add(s.T, 16);
+  for (int i = 0; i < 4; ++i) add(s.Q, 16);
+  add(s.thin, 16);
+  for (int i = 0; i < 4; ++i) add(s.thin, 16);
+  for (int i = 0; i < 4; ++i) add(s.proj, 16);
+  add((long long)k * k, 16);
+  add((long long)chi * k, 16);
+  for (int i = 0; i < 4; ++i) add(64 * 64, 16);
+  add(std::max(k, 4096), 8);
+  add(std::max(k, 4096), 8);
+  add(std::max(k, 4096), 4);
+  add(2, 4);
+  add(4096, 8);
+  add(64, 8);
+  add(16, 16);
+  add(1, sizeof(DevStatus));
+  add(s.scratch, 16);
+  s.total = tot + 4096;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// frames: frame f is the network rotated f times by 90 degrees counter-
+// clockwise; environment role j of frame f is role (j+f) mod 4 of frame 0.
+// ---------------------------------------------------------------------------
+static void frame_dims(ipeps_ctm h, int f, int* Lx, int* Ly) {
+  *Lx = (f & 1) ? h->Ly : h->Lx;
+  *Ly = (f & 1) ? h->Lx : h->Ly;
+}
+
+// frame-f coordinates -> frame-0 coordinates
+static void to_orig(ipeps_ctm h, int f, int x, int y, int* ox, int* oy) {
+  int lx, ly;
+  frame_dims(h, f, &lx, &ly);
+  x = ((x % lx) + lx) % lx;
+  y = ((y % ly) + ly) % ly;
+  for (int g = f; g > 0; --g) {
+    // frame g (dims lx, ly) -> frame g-1 (dims ly, lx): x_prev = -y, y_prev = x
+    const int plx = ly, ply = lx;
+    const int nx = ((-y) % plx + plx) % plx, ny = x % ply;
+    x = nx;
+    y = ny;
+    lx = plx;
+    ly = ply;
+  }
+  *ox = x;
+  *oy = y;
+}
+
+static int cell_index(ipeps_ctm h, int f, int x, int y) {
+  int ox, oy;
+  to_orig(h, f, x, y, &ox, &oy);
+  return oy * h->Lx + ox;
+}
+
+static cplx*& envC(ipeps_ctm h, int f, int j, int x, int y) {
+  return h->C[(j + f) & 3][cell_index(h, f, x, y)];
+}
+static cplx*& envT(ipeps_ctm h, int f, int j, int x, int y) {
+  return h->T[(j + f) & 3][cell_index(h, f, x, y)];
+}
+static int tensor_id(ipeps_ctm h, int f, int x, int y) {
+  return h->pattern[cell_index(h, f, x, y)];
+}
+static cplx* site_a(ipeps_ctm h, int f, int x, int y) { return h->a[f][tensor_id(h, f, x, y)]; }
+
+// ---------------------------------------------------------------------------
+// contraction planner: C[labels] = alpha * A[labels] B[labels], every label of
+// C appearing in exactly one operand, shared labels summed (transpose/permute
+// into GEMM form, one complex GEMM, permute out if needed).
+// ---------------------------------------------------------------------------
+struct Plan {
+  std::string la, lb, lc;
+};
+
+static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cplx* A, long long lda,
+                                      int opA, const cplx* B, long long ldb, int opB, cplx* C,
+                                      long long ldc, cplx alpha);
+
+static ipeps_status gemm_dispatch(ipeps_ctm h, int M, int N, int K, const cplx* A, long long lda,
+                                  int opA, const cplx* B, long long ldb, int opB, cplx* C,
+                                  long long ldc, cplx alpha) {
+  cudaEvent_t a = nullptr;
+  prof_begin(h, &a);
+  ipeps_status st = gemm_dispatch_raw(h, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha);
+  prof_end(h, a, 8.0 * (double)M * (double)N * (double)K, 0);
+  return st;
+}
+
+static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cplx* A, long long lda,
+                                      int opA, const cplx* B, long long ldb, int opB, cplx* C,
+                                      long long ldc, cplx alpha) {
+  if (h->opt.prec != IPEPS_PREC_FP64) {
+    cudaError_t e = tc_zgemm(h->stream, (int)h->opt.prec, M, N, K, alpha, A, lda, opA, B, ldb,
+                             opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top);
+    if (e == cudaErrorNotSupported) return fail(IPEPS_EUNSUPPORTED, "tensor-core GEMM unavailable for this shape");
+    CK(e);
+    return IPEPS_OK;
+  }
+  CK(zgemm(h->stream, M, N, K, alpha, A, lda, opA, B, ldb, opB, ZERO, C, ldc));
+  return IPEPS_OK;
+}
+
+static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV B, bool conjB,
+                             TV C, cplx alpha = ONE) {
+  std::string s(spec);
+  const size_t c1 = s.find(','), ar = s.find("->");
+  if (c1 == std::string::npos || ar == std::string::npos)
+    return fail(IPEPS_EINVAL, "bad contraction spec %s", spec);
+  std::string la = s.substr(0, c1), lb = s.substr(c1 + 1, ar - c1 - 1), lc = s.substr(ar + 2);
+  if ((int)la.size() != A.nd || (int)lb.size() != B.nd || (int)lc.size() != C.nd)
+    return fail(IPEPS_EINVAL, "rank mismatch in %s", spec);
+  auto dimA = [&](char c) { return A.dims[la.find(c)]; };
+  auto dimB = [&](char c) { return B.dims[lb.find(c)]; };
+  std::string fa, fb, kc;
+  for (char c : la) (lb.find(c) == std::string::npos ? fa : kc) += c;
+  for (char c : lb)
+    if (la.find(c) == std::string::npos) fb += c;
+  for (char c : kc)
+    if (dimA(c) != dimB(c)) return fail(IPEPS_EINVAL, "dim mismatch on %c in %s", c, spec);
+  for (char c : lc)
+    if (la.find(c) == std::string::npos && lb.find(c) == std::string::npos)
+      return fail(IPEPS_EINVAL, "output label %c not in inputs (%s)", c, spec);
+  if (fa.size() + fb.size() != lc.size()) return fail(IPEPS_EINVAL, "batch labels unsupported: %s", spec);
+
+  // output order: C = [fa', fb'] directly, or [fb', fa'] with the operands swapped
+  bool swap = false, direct = false;
+  std::string Mo, No;
+  {
+    std::string head = lc.substr(0, fa.size()), tail = lc.substr(fa.size());
+    std::string sh = head, sf = fa;
+    std::sort(sh.begin(), sh.end());
+    std::sort(sf.begin(), sf.end());
+    if (sh == sf) {
+      direct = true;
+      Mo = head;
+      No = tail;
+    } else {
+      std::string head2 = lc.substr(0, fb.size()), tail2 = lc.substr(fb.size());
+      std::string s2 = head2, sfb = fb;
+      std::sort(s2.begin(), s2.end());
+      std::sort(sfb.begin(), sfb.end());
+      if (s2 == sfb) {
+        direct = true;
+        swap = true;
+        Mo = tail2;   // rows of the A-side product are A's free labels ...
+        No = head2;   // ... but C is stored [fb, fa]: compute C = B' A'
+      } else {
+        Mo = fa;
+        No = fb;
+      }
+    }
+  }
+  long long M = 1, N = 1, Kd = 1;
+  for (char c : fa) M *= dimA(c);
+  for (char c : fb) N *= dimB(c);
+  for (char c : kc) Kd *= dimA(c);
+
+  const long long mark = h->scratch_top;
+  // arrange one operand as [free..., k...] (op N) or [k..., free...] (op T)
+  auto arrange = [&](TV X, const std::string& lx, bool cj, const std::string& fo,
+                     const std::string& ko, const cplx** out, long long* ld, int* op) -> ipeps_status {
+    long long fdim = 1, kdim = 1;
+    for (char c : fo) fdim *= X.dims[lx.find(c)];
+    for (char c : ko) kdim *= X.dims[lx.find(c)];
+    if (lx == fo + ko) {
+      *out = X.p; *ld = kdim; *op = OP_N | (cj ? OP_CONJ : 0);
+      return IPEPS_OK;
+    }
+    if (lx == ko + fo) {
+      *out = X.p; *ld = fdim; *op = OP_T | (cj ? OP_CONJ : 0);
+      return IPEPS_OK;
+    }
+    std::string want = fo + ko;
+    int perm[8];
+    for (size_t i = 0; i < want.size(); ++i) perm[i] = (int)lx.find(want[i]);
+    cplx* t = scratch_alloc(h, X.size());
+    if (!t) return fail(IPEPS_ENOMEM, "scratch exhausted in %s", spec);
+    CK(permute(h->stream, X.p, t, X.nd, X.dims, perm, cj, ONE));
+    *out = t; *ld = kdim; *op = OP_N;
+    return IPEPS_OK;
+  };
+  // choose the contracted-label order from an operand that is already in GEMM form
+  auto is_form = [](const std::string& lx, const std::string& f, const std::string& k) {
+    return lx == f + k || lx == k + f;
+  };
+  std::string ko = kc;  // order as in A
+  {
+    std::string kb;
+    for (char c : lb)
+      if (la.find(c) != std::string::npos) kb += c;
+    // prefer the order that leaves an operand untouched
+    if (!is_form(la, swap ? Mo : Mo, kc) && !is_form(la, Mo, kc)) {
+      if (is_form(lb, No, kb)) ko = kb;
+    }
+    if (!is_form(la, Mo, ko) && is_form(lb, No, kb)) ko = kb;
+  }
+  const cplx *pa, *pb;
+  long long lda, ldb;
+  int opa, opb;
+  CKS(arrange(A, la, conjA, Mo, ko, &pa, &lda, &opa));
+  // B must be [ko, No] (op N) or [No, ko] (op T); arrange() returns [No, ko] forms
+  {
+    long long fdim = 1, kdim = 1;
+    for (char c : No) fdim *= dimB(c);
+    for (char c : ko) kdim *= dimB(c);
+    if (lb == ko + No) {
+      pb = B.p; ldb = fdim; opb = OP_N | (conjB ? OP_CONJ : 0);
+    } else if (lb == No + ko) {
+      pb = B.p; ldb = kdim; opb = OP_T | (conjB ? OP_CONJ : 0);
+    } else {
+      std::string want = ko + No;
+      int perm[8];
+      for (size_t i = 0; i < want.size(); ++i) perm[i] = (int)lb.find(want[i]);
+      cplx* t = scratch_alloc(h, B.size());
+      if (!t) return fail(IPEPS_ENOMEM, "scratch exhausted in %s", spec);
+      CK(permute(h->stream, B.p, t, B.nd, B.dims, perm, conjB, ONE));
+      pb = t; ldb = fdim; opb = OP_N;
+    }
+  }
+  if (direct && !swap) {
+    CKS(gemm_dispatch(h, (int)M, (int)N, (int)Kd, pa, lda, opa, pb, ldb, opb, C.p, N, alpha));
+  } else if (direct && swap) {
+    // C[No, Mo] = (A' B')^T = B'^T A'^T
+    auto flip = [](int op) { return op ^ OP_T; };
+    CKS(gemm_dispatch(h, (int)N, (int)M, (int)Kd, pb, ldb, flip(opb), pa, lda, flip(opa), C.p, M, alpha));
+  } else {
+    cplx* t = scratch_alloc(h, M * N);
+    if (!t) return fail(IPEPS_ENOMEM, "scratch exhausted in %s", spec);
+    CKS(gemm_dispatch(h, (int)M, (int)N, (int)Kd, pa, lda, opa, pb, ldb, opb, t, N, ONE));
+    // t has labels Mo+No; permute to lc
+    std::string have = Mo + No;
+    int dims[8], perm[8];
+    for (size_t i = 0; i < have.size(); ++i)
+      dims[i] = la.find(have[i]) != std::string::npos ? dimA(have[i]) : dimB(have[i]);
+    for (size_t i = 0; i < lc.size(); ++i) perm[i] = (int)have.find(lc[i]);
+    CK(permute(h->stream, t, C.p, (int)have.size(), dims, perm, false, alpha));
+  }
+  h->scratch_top = mark;
+  return IPEPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host tables: ruby bond operators of App. A (block-site basis p = 4b1+2b2+b3,
+// b = 0 meaning sigma^z = +1), each sigma^a sigma^a link weighted by -J_a.
+// ---------------------------------------------------------------------------
+struct CM {  // small dense complex matrix on the host
+  int n;
+  std::vector<double> re, im;
+  explicit CM(int n_) : n(n_), re(n_ * n_, 0.0), im(n_ * n_, 0.0) {}
+};
+
+static CM kron(const CM& A, const CM& B) {
+  CM R(A.n * B.n);
+  for (int i = 0; i < A.n; ++i)
+    for (int j = 0; j < A.n; ++j)
+      for (int k = 0; k < B.n; ++k)
+        for (int l = 0; l < B.n; ++l) {
+          const int r = i * B.n + k, c = j * B.n + l;
+          const double ar = A.re[i * A.n + j], ai = A.im[i * A.n + j];
+          const double br = B.re[k * B.n + l], bi = B.im[k * B.n + l];
+          R.re[r * R.n + c] = ar * br - ai * bi;
+          R.im[r * R.n + c] = ar * bi + ai * br;
+        }
+  return R;
+}
+
+static CM matmul(const CM& A, const CM& B) {
+  CM R(A.n);
+  for (int i = 0; i < A.n; ++i)
+    for (int j = 0; j < A.n; ++j) {
+      double sr = 0, si = 0;
+      for (int k = 0; k < A.n; ++k) {
+        const double ar = A.re[i * A.n + k], ai = A.im[i * A.n + k];
+        const double br = B.re[k * A.n + j], bi = B.im[k * A.n + j];
+        sr += ar * br - ai * bi;
+        si += ar * bi + ai * br;
+      }
+      R.re[i * A.n + j] = sr;
+      R.im[i * A.n + j] = si;
+    }
+  return R;
+}
+
+static void axpy(CM& Y, double a, const CM& X) {
+  for (size_t i = 0; i < Y.re.size(); ++i) {
+    Y.re[i] += a * X.re[i];
+    Y.im[i] += a * X.im[i];
+  }
+}
+
+// sigma^alpha on spin k (1..3) of a block site, 8x8
+static CM spin_op(char alpha, int k) {
+  CM s(2), I2(2);
+  I2.re[0] = I2.re[3] = 1.0;
+  if (alpha == 'x') { s.re[1] = s.re[2] = 1.0; }
+  if (alpha == 'y') { s.im[1] = -1.0; s.im[2] = 1.0; }
+  if (alpha == 'z') { s.re[0] = 1.0; s.re[3] = -1.0; }
+  const CM& f1 = k == 1 ? s : I2;
+  const CM& f2 = k == 2 ? s : I2;
+  const CM& f3 = k == 3 ? s : I2;
+  return kron(kron(f1, f2), f3);
+}
+
+static void ruby_bonds(const double J[3], CM* Hr, CM* Hv) {
+  CM I8(8);
+  for (int i = 0; i < 8; ++i) I8.re[i * 8 + i] = 1.0;
+  CM hs(8);
+  axpy(hs, -J[2], matmul(spin_op('z', 1), spin_op('z', 2)));
+  axpy(hs, -J[2], matmul(spin_op('z', 1), spin_op('z', 3)));
+  axpy(hs, -J[2], matmul(spin_op('z', 2), spin_op('z', 3)));
+  *Hr = CM(64);
+  axpy(*Hr, -J[0], kron(spin_op('x', 1), spin_op('x', 1)));
+  axpy(*Hr, -J[1], kron(spin_op('y', 3), spin_op('y', 3)));
+  *Hv = CM(64);
+  axpy(*Hv, 0.5, kron(hs, I8));
+  axpy(*Hv, 0.5, kron(I8, hs));
+  axpy(*Hv, -J[0], kron(spin_op('x', 3), spin_op('x', 2)));
+  axpy(*Hv, -J[1], kron(spin_op('y', 2), spin_op('y', 1)));
+}
+
+// ---------------------------------------------------------------------------
+// create / destroy
+// ---------------------------------------------------------------------------
+extern "C" void ipeps_default_options(ipeps_options* o) {
+  memset(o, 0, sizeof *o);
+  o->chi = 0;
+  o->prec = IPEPS_PREC_FP64;
+  o->rsvd_oversample = 16;
+  o->rsvd_power = 2;
+  o->svd_cutoff = 1e-8;
+  o->orth_tol = 1e-14;
+  o->omega_seed = 7;
+  o->jacobi_max_sweeps = 40;
+}
+
+static ipeps_status validate(const ipeps_cell* c, const ipeps_options* o) {
+  if (!c || !o) return fail(IPEPS_EINVAL, "null cell or options");
+  if (c->Lx < 1 || c->Lx > 2 || c->Ly < 1 || c->Ly > 2) return fail(IPEPS_EINVAL, "Lx, Ly must be 1 or 2");
+  if (c->n_tensors < 1 || c->n_tensors > 4) return fail(IPEPS_EINVAL, "n_tensors must be 1..4");
+  for (int i = 0; i < c->Lx * c->Ly; ++i)
+    if (c->pattern[i] < 0 || c->pattern[i] >= c->n_tensors) return fail(IPEPS_EINVAL, "pattern id out of range");
+  if (c->d < 1 || c->d > 64 || c->D < 1 || c->D > 12) return fail(IPEPS_EINVAL, "d in 1..64, D in 1..12");
+  if (c->dtype != IPEPS_REAL64 && c->dtype != IPEPS_COMPLEX128) return fail(IPEPS_EINVAL, "bad dtype");
+  if (!c->tensors) return fail(IPEPS_EINVAL, "null tensors");
+  if (o->chi < c->D * c->D) return fail(IPEPS_EINVAL, "chi (%d) must be >= D*D (%d)", o->chi, c->D * c->D);
+  if (o->chi > 1024) return fail(IPEPS_EINVAL, "chi > 1024");
+  if (o->rsvd_oversample < 0 || o->rsvd_power < 0) return fail(IPEPS_EINVAL, "bad rsvd options");
+  if (o->chi + o->rsvd_oversample > 1024) return fail(IPEPS_EINVAL, "chi + oversample > 1024");
+  if (o->prec < IPEPS_PREC_FP64 || o->prec > IPEPS_PREC_BF16X3) return fail(IPEPS_EINVAL, "bad prec");
+  if (o->jacobi_max_sweeps < 1) return fail(IPEPS_EINVAL, "jacobi_max_sweeps >= 1");
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_workspace_size(const ipeps_cell* c, const ipeps_options* o,
+                                                 size_t* bytes) {
+  CKS(validate(c, o));
+  if (!bytes) return fail(IPEPS_EINVAL, "null bytes");
+  Sizes s = plan_sizes(c->Lx, c->Ly, c->d, c->D, o->chi, o->chi + o->rsvd_oversample, c->n_tensors);
+  *bytes = s.total;
+  return IPEPS_OK;
+}
+
+static ipeps_status build_layers(ipeps_ctm h) {
+  // rotated site tensors: A'[p,u,l,d,r] = A[p,l,d,r,u] per counter-clockwise turn
+  const int dims5[5] = {h->d, h->D, h->D, h->D, h->D};
+  const int rot5[5] = {0, 4, 1, 2, 3};
+  for (int t = 0; t < h->ntens; ++t) {
+    for (int f = 1; f < 4; ++f) {
+      CK(permute(h->stream, h->A[f - 1][t], h->A[f][t], 5, dims5, rot5, false, ONE));
+      CK(permute(h->stream, h->Bt[f - 1][t], h->Bt[f][t], 5, dims5, rot5, false, ONE));
+    }
+    CK(double_layer(h->stream, h->A[0][t], h->Bt[0][t], h->a[0][t], h->d, h->D));
+    for (int f = 1; f < 4; ++f) CK(rotate_a(h->stream, h->a[f - 1][t], h->a[f][t], h->D2));
+  }
+  return IPEPS_OK;
+}
+
+static ipeps_status trace_init_env(ipeps_ctm h) {
+  // role -> neighbouring site offset (frame 0)
+  static const int off[8][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}, {0, -1}, {1, 0}, {0, 1}, {-1, 0}};
+  for (int y = 0; y < h->Ly; ++y)
+    for (int x = 0; x < h->Lx; ++x)
+      for (int r = 0; r < 8; ++r) {
+        const int sx = ((x + off[r][0]) % h->Lx + h->Lx) % h->Lx;
+        const int sy = ((y + off[r][1]) % h->Ly + h->Ly) % h->Ly;
+        const cplx* a = h->a[0][h->pattern[sy * h->Lx + sx]];
+        cplx* out = r < 4 ? h->C[r][y * h->Lx + x] : h->T[r - 4][y * h->Lx + x];
+        CK(trace_init_tensor(h->stream, a, out, r, h->D, h->chi));
+        const long long n = r < 4 ? (long long)h->chi * h->chi : (long long)h->chi * h->D2 * h->chi;
+        CK(normalize(h->stream, out, n, h->dwork, h->st));
+      }
+  return IPEPS_OK;
+}
+
+static ipeps_status upload_one(ipeps_ctm h, const void* src, cplx* dst, std::vector<double>& buf);
+
+static ipeps_status check_status(ipeps_ctm h) {
+  DevStatus st;
+  CK(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st.nonfinite) return fail(IPEPS_ENUMERIC, "non-finite or zero norm met (%d times)", st.nonfinite);
+  if (st.jacobi_unconverged)
+    return fail(IPEPS_ETIMEOUT, "%d Jacobi SVDs hit the sweep budget", st.jacobi_unconverged);
+  return IPEPS_OK;
+}
+
+static ipeps_status reset_status(ipeps_ctm h) {
+  CK(cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream));
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_options* o, ipeps_ctm* out) {
+  CKS(validate(c, o));
+  if (!out) return fail(IPEPS_EINVAL, "null out");
+  ipeps_ctm h = new ipeps_ctm_s();
+  memset(h, 0, sizeof *h);
+  h->Lx = c->Lx; h->Ly = c->Ly; h->d = c->d; h->D = c->D; h->D2 = c->D * c->D;
+  h->chi = o->chi; h->K = o->chi * h->D2; h->k = o->chi + o->rsvd_oversample;
+  h->ntens = c->n_tensors;
+  for (int i = 0; i < 4; ++i) h->pattern[i] = i < c->Lx * c->Ly ? c->pattern[i] : 0;
+  h->mixed = c->tensors_bra != nullptr;
+  h->dtype = c->dtype;
+  h->opt = *o;
+  h->stream = (cudaStream_t)o->stream;
+  Sizes sz = plan_sizes(h->Lx, h->Ly, h->d, h->D, h->chi, h->k, h->ntens);
+  if (o->workspace) {
+    if (o->workspace_bytes < sz.total) {
+      delete h;
+      return fail(IPEPS_ENOMEM, "workspace too small: %zu < %zu bytes", o->workspace_bytes, sz.total);
+    }
+    h->base = (char*)o->workspace;
+    h->bytes = o->workspace_bytes;
+    h->own_mem = false;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&h->base, sz.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(IPEPS_ENOMEM, "cudaMalloc(%zu) failed: %s", sz.total, cudaGetErrorString(e));
+    }
+    h->bytes = sz.total;
+    h->own_mem = true;
+  }
+  h->used = 0;
+  bool ok = true;
+  auto need = [&](void* p) { if (!p) ok = false; };
+  for (int f = 0; f < 4; ++f)
+    for (int t = 0; t < h->ntens; ++t) {
+      need(h->A[f][t] = carve<cplx>(h, sz.tens));
+      need(h->Bt[f][t] = carve<cplx>(h, sz.tens));
+      need(h->a[f][t] = carve<cplx>(h, sz.a));
+    }
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < h->Lx * h->Ly; ++i) {
+      need(h->C[j][i] = carve<cplx>(h, sz.C));
+      need(h->T[j][i] = carve<cplx>(h, sz.T));
+    }
+  for (int i = 0; i < 2; ++i) {
+    need(h->spareC[0][i] = carve<cplx>(h, sz.C));
+    need(h->spareC[1][i] = carve<cplx>(h, sz.C));
+    need(h->spareT[i] = carve<cplx>(h, sz.T));
+  }
+  for (int i = 0; i < 4; ++i) need(h->Q[i] = carve<cplx>(h, sz.Q));
+  need(h->omt = carve<cplx>(h, sz.thin));
+  for (int i = 0; i < 4; ++i) need(h->thin[i] = carve<cplx>(h, sz.thin));
+  for (int i = 0; i < 2; ++i) {
+    need(h->PT[i] = carve<cplx>(h, sz.proj));
+    need(h->Ptil[i] = carve<cplx>(h, sz.proj));
+  }
+  need(h->Vt = carve<cplx>(h, (size_t)h->k * h->k));
+  need(h->Gsel = carve<cplx>(h, (size_t)h->chi * h->k));
+  for (int i = 0; i < 4; ++i) need(h->Hbond[i] = carve<cplx>(h, 64 * 64));
+  need(h->sigma = carve<double>(h, std::max(h->k, 4096)));
+  need(h->s_sel = carve<double>(h, std::max(h->k, 4096)));
+  need(h->perm = carve<int>(h, std::max(h->k, 4096)));
+  need(h->counters = carve<int>(h, 2));
+  need(h->dwork = carve<double>(h, 4096));
+  need(h->dacc = carve<double>(h, 64));
+  need(h->scalar = carve<cplx>(h, 16));
+  need(h->st = carve<DevStatus>(h, 1));
+  need(h->scratch = carve<cplx>(h, sz.scratch));
+  h->scratch_elems = sz.scratch;
+  h->scratch_top = 0;
+  if (!ok) {
+    if (h->own_mem) cudaFree(h->base);
+    delete h;
+    return fail(IPEPS_ENOMEM, "arena layout exceeded (internal)");
+  }
+  h->launches_at_create = launch_counter();
+  ipeps_status st = IPEPS_OK;
+  // host -> device copies of the tensors (real inputs promoted to complex)
+  std::vector<double> buf;
+  for (int t = 0; t < h->ntens && st == IPEPS_OK; ++t) {
+    const void* ket = c->tensors[t];
+    const void* bra = h->mixed ? c->tensors_bra[t] : c->tensors[t];
+    if (!ket || !bra) { st = fail(IPEPS_EINVAL, "null tensor pointer %d", t); break; }
+    st = upload_one(h, ket, h->A[0][t], buf);
+    if (st == IPEPS_OK) st = upload_one(h, bra, h->Bt[0][t], buf);
+  }
+  if (st == IPEPS_OK) st = reset_status(h);
+  if (st == IPEPS_OK) st = build_layers(h);
+  if (st == IPEPS_OK) {
+    cudaError_t e = fill_omega_t(h->stream, h->omt, h->k, h->K, o->omega_seed);
+    if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "omega: %s", cudaGetErrorString(e));
+  }
+  if (st == IPEPS_OK) st = trace_init_env(h);
+  if (st == IPEPS_OK) st = check_status(h);
+  if (st != IPEPS_OK) {
+    if (h->own_mem) cudaFree(h->base);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& r : h->recs) {
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+  h->profiling = enable != 0;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms,
+                                               uint64_t* launches, double* flops) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  CK(cudaStreamSynchronize(h->stream));
+  double ms = 0, fl = 0;
+  uint64_t n = 0;
+  for (auto& r : h->recs) {
+    if (r.kind != kind) continue;
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    fl += r.flops;
+    ++n;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = n;
+  if (flops) *flops = fl;
+  return IPEPS_OK;
+}
+
+extern "C" void ipeps_ctm_destroy(ipeps_ctm h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  if (h->own_mem) cudaFree(h->base);
+  delete h;
+}
+
+extern "C" ipeps_status ipeps_ctm_sync(ipeps_ctm h) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  CK(cudaStreamSynchronize(h->stream));
+  return IPEPS_OK;
+}
+
+extern "C" uint64_t ipeps_ctm_launch_count(ipeps_ctm h) {
+  return h ? launch_counter() - h->launches_at_create : 0;
+}
+
+static ipeps_status upload_one(ipeps_ctm h, const void* src, cplx* dst, std::vector<double>& buf) {
+  const long long n = (long long)h->d * h->D2 * h->D2;
+  const double* sp = (const double*)src;
+  if (h->dtype == IPEPS_REAL64) {  // host-side promotion of real inputs
+    buf.resize(2 * n);
+    for (long long i = 0; i < n; ++i) { buf[2 * i] = sp[i]; buf[2 * i + 1] = 0.0; }
+    sp = buf.data();
+  }
+  CK(cudaMemcpyAsync(dst, sp, n * sizeof(cplx), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));  // the staging buffer is reused
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_set_tensors(ipeps_ctm h, const void* const* tensors,
+                                              const void* const* tensors_bra) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (!tensors) {  // rebuild the double layers from the device-resident tensors
+    CKS(build_layers(h));
+    return IPEPS_OK;
+  }
+  if ((tensors_bra != nullptr) != h->mixed) return fail(IPEPS_EINVAL, "bra tensors must match create");
+  std::vector<double> buf;
+  for (int t = 0; t < h->ntens; ++t) {
+    if (!tensors[t] || (h->mixed && !tensors_bra[t])) return fail(IPEPS_EINVAL, "null tensor %d", t);
+    CKS(upload_one(h, tensors[t], h->A[0][t], buf));
+    CKS(upload_one(h, h->mixed ? tensors_bra[t] : tensors[t], h->Bt[0][t], buf));
+  }
+  CKS(build_layers(h));
+  CK(cudaStreamSynchronize(h->stream));
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_reset_env(ipeps_ctm h) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  CKS(reset_status(h));
+  CKS(trace_init_env(h));
+  return check_status(h);
+}
+
+// ---------------------------------------------------------------------------
+// the move
+// ---------------------------------------------------------------------------
+// Enlarged corners of the plaquette with upper-left site (x,y) in frame f:
+//   Q1[(d_T4,d_a),(r_T1,r_a)]  Q2[(l_T1,l_a),(d_T2,d_a)]
+//   Q3[(u_T2,u_a),(l_T3,l_a)]  Q4[(u_T4,u_a),(r_T3,r_a)]
+static ipeps_status enlarged_corners(ipeps_ctm h, int f, int x, int y) {
+  const int c = h->chi, D2 = h->D2;
+  const long long entry = h->scratch_top;
+  cplx* w1 = scratch_alloc(h, (long long)c * D2 * c);
+  cplx* w2 = scratch_alloc(h, (long long)h->K * h->K);
+  if (!w1 || !w2) return fail(IPEPS_ENOMEM, "scratch exhausted (corners)");
+  const long long mark = h->scratch_top;
+  // Q1 = ((C1 T1) T4) a
+  CKS(contract(h, "ab,bcr->acr", tv(envC(h, f, 0, x, y), {c, c}), false,
+               tv(envT(h, f, 0, x, y), {c, D2, c}), false, tv(w1, {c, D2, c})));
+  CKS(contract(h, "dea,acr->decr", tv(envT(h, f, 3, x, y), {c, D2, c}), false, tv(w1, {c, D2, c}),
+               false, tv(w2, {c, D2, D2, c})));
+  CKS(contract(h, "decr,ceDR->dDrR", tv(w2, {c, D2, D2, c}), false,
+               tv(site_a(h, f, x, y), {D2, D2, D2, D2}), false, tv(h->Q[0], {c, D2, c, D2})));
+  h->scratch_top = mark;
+  // Q2 = ((T1 C2) T2) a
+  CKS(contract(h, "Ltg,gh->Lth", tv(envT(h, f, 0, x + 1, y), {c, D2, c}), false,
+               tv(envC(h, f, 1, x + 1, y), {c, c}), false, tv(w1, {c, D2, c})));
+  CKS(contract(h, "Lth,hmE->LtmE", tv(w1, {c, D2, c}), false, tv(envT(h, f, 1, x + 1, y), {c, D2, c}),
+               false, tv(w2, {c, D2, D2, c})));
+  CKS(contract(h, "LtmE,tKem->LKEe", tv(w2, {c, D2, D2, c}), false,
+               tv(site_a(h, f, x + 1, y), {D2, D2, D2, D2}), false, tv(h->Q[1], {c, D2, c, D2})));
+  h->scratch_top = mark;
+  // Q3 = ((T2 C3) T3) a
+  CKS(contract(h, "Umh,hg->Umg", tv(envT(h, f, 1, x + 1, y + 1), {c, D2, c}), false,
+               tv(envC(h, f, 2, x + 1, y + 1), {c, c}), false, tv(w1, {c, D2, c})));
+  CKS(contract(h, "Umg,gtL->UmtL", tv(w1, {c, D2, c}), false,
+               tv(envT(h, f, 2, x + 1, y + 1), {c, D2, c}), false, tv(w2, {c, D2, D2, c})));
+  CKS(contract(h, "UmtL,uKtm->UuLK", tv(w2, {c, D2, D2, c}), false,
+               tv(site_a(h, f, x + 1, y + 1), {D2, D2, D2, D2}), false, tv(h->Q[2], {c, D2, c, D2})));
+  h->scratch_top = mark;
+  // Q4 = ((C4 T4) T3) a
+  CKS(contract(h, "gh,hmU->gmU", tv(envC(h, f, 3, x, y + 1), {c, c}), false,
+               tv(envT(h, f, 3, x, y + 1), {c, D2, c}), false, tv(w1, {c, D2, c})));
+  CKS(contract(h, "gmU,Rtg->mUtR", tv(w1, {c, D2, c}), false, tv(envT(h, f, 2, x, y + 1), {c, D2, c}),
+               false, tv(w2, {D2, c, D2, c})));
+  CKS(contract(h, "mUtR,umtr->UuRr", tv(w2, {D2, c, D2, c}), false,
+               tv(site_a(h, f, x, y + 1), {D2, D2, D2, D2}), false, tv(h->Q[3], {c, D2, c, D2})));
+  h->scratch_top = entry;
+  return IPEPS_OK;
+}
+
+// thin (k x K, row-major = transposed K x k) times one corner
+static ipeps_status thin_mul(ipeps_ctm h, const cplx* in, int opin, cplx* out, const cplx* Qm, int opQ,
+                             int rows) {
+  return gemm_dispatch(h, rows, h->K, h->K, in, h->K, opin, Qm, h->K, opQ, out, h->K, ONE);
+}
+
+// Yt = In * Q3 * Q4^T * Q1 * Q2      (the transpose of X * In^T)
+static ipeps_status apply_XT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
+  CKS(thin_mul(h, in, OP_N, h->thin[2], h->Q[2], OP_N, rows));
+  CKS(thin_mul(h, h->thin[2], OP_N, h->thin[3], h->Q[3], OP_T, rows));
+  CKS(thin_mul(h, h->thin[3], OP_N, h->thin[2], h->Q[0], OP_N, rows));
+  CKS(thin_mul(h, h->thin[2], OP_N, out, h->Q[1], OP_N, rows));
+  return IPEPS_OK;
+}
+// Zt = In * Q2^H * Q1^H * conj(Q4) * Q3^H   (the transpose of X^H * In^T)
+static ipeps_status apply_XHT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
+  CKS(thin_mul(h, in, OP_N, h->thin[2], h->Q[1], OP_H, rows));
+  CKS(thin_mul(h, h->thin[2], OP_N, h->thin[3], h->Q[0], OP_H, rows));
+  CKS(thin_mul(h, h->thin[3], OP_N, h->thin[2], h->Q[3], OP_C, rows));
+  CKS(thin_mul(h, h->thin[2], OP_N, out, h->Q[2], OP_H, rows));
+  return IPEPS_OK;
+}
+
+static ipeps_status orth(ipeps_ctm h, cplx* G) {
+  cudaEvent_t a = nullptr;
+  prof_begin(h, &a);
+  CK(jacobi_rows(h->stream, G, h->k, h->K, h->K, nullptr, h->sigma, h->opt.jacobi_max_sweeps,
+                 h->dwork, h->counters, h->st));
+  prof_end(h, a, 0.0, 1);
+  CK(orth_rows_finish(h->stream, G, h->k, h->K, h->K, h->sigma, h->opt.orth_tol));
+  return IPEPS_OK;
+}
+
+// Projectors of the left cut of plaquette (x,y): PT = P^T, Ptil (both chi x K).
+static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx* Ptil) {
+  CKS(enlarged_corners(h, f, x, y));
+  const int k = h->k, K = h->K, chi = h->chi;
+  cplx* Qt = h->thin[0];
+  cplx* Zt = h->thin[1];
+  CKS(apply_XT(h, h->omt, Qt, k));
+  CKS(orth(h, Qt));
+  for (int it = 0; it < h->opt.rsvd_power; ++it) {
+    CKS(apply_XHT(h, Qt, Zt, k));
+    CKS(orth(h, Zt));
+    CKS(apply_XT(h, Zt, Qt, k));
+    CKS(orth(h, Qt));
+  }
+  // W = X^H Q (K x k) stored as Wt; its SVD W = U_w S V_w^H gives X ~ (Q V_w) S U_w^H
+  CKS(apply_XHT(h, Qt, Zt, k));
+  CK(jacobi_rows(h->stream, Zt, k, K, K, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
+                 h->counters, h->st));
+  CK(select_top(h->stream, h->sigma, k, chi, h->opt.svd_cutoff, h->perm, h->s_sel));
+  // V_chi^T rows = selected columns of U_w (normalised rows of Wt)
+  cplx* Vt_chi = h->thin[2];
+  CK(gather_rows(h->stream, Zt, K, Vt_chi, K, h->perm, h->sigma, chi, K, true));
+  // U_chi^T = (V_w[:, sel])^T Q^T
+  CK(gather_rows(h->stream, h->Vt, k, h->Gsel, k, h->perm, h->sigma, chi, k, false));
+  cplx* Ut_chi = h->thin[3];
+  CKS(gemm_dispatch(h, chi, K, k, h->Gsel, k, OP_N, Qt, K, OP_N, Ut_chi, K, ONE));
+  // P^T = S^-1/2 V^T Q3 Q4^T
+  CKS(thin_mul(h, Vt_chi, OP_N, Zt, h->Q[2], OP_N, chi));
+  CKS(thin_mul(h, Zt, OP_N, PT, h->Q[3], OP_T, chi));
+  CK(scale_rows_isqrt(h->stream, PT, chi, K, K, h->s_sel));
+  // Ptil = S^-1/2 U^H Q2^T Q1^T
+  CKS(thin_mul(h, Ut_chi, OP_C, Zt, h->Q[1], OP_T, chi));
+  CKS(thin_mul(h, Zt, OP_N, Ptil, h->Q[0], OP_T, chi));
+  CK(scale_rows_isqrt(h->stream, Ptil, chi, K, K, h->s_sel));
+  return IPEPS_OK;
+}
+
+static ipeps_status left_move(ipeps_ctm h, int f) {
+  int Lx, Ly;
+  frame_dims(h, f, &Lx, &Ly);
+  const int c = h->chi, D2 = h->D2;
+  for (int x = 0; x < Lx; ++x) {
+    for (int y = 0; y < Ly; ++y) CKS(projectors(h, f, x, y, h->PT[y], h->Ptil[y]));
+    for (int y = 0; y < Ly; ++y) {
+      const int ym = (y - 1 + Ly) % Ly;
+      cplx* w1 = scratch_alloc(h, (long long)c * D2 * c);
+      cplx* w2 = scratch_alloc(h, (long long)c * D2 * c * D2);
+      if (!w1 || !w2) return fail(IPEPS_ENOMEM, "scratch exhausted (absorb)");
+      // C1'[n,r] = sum P[(a,s),n] (C1 T1)[a,s,r]
+      CKS(contract(h, "ab,bsr->asr", tv(envC(h, f, 0, x, y), {c, c}), false,
+                   tv(envT(h, f, 0, x, y), {c, D2, c}), false, tv(w1, {c, D2, c})));
+      CKS(contract(h, "nas,asr->nr", tv(h->PT[ym], {c, c, D2}), false, tv(w1, {c, D2, c}), false,
+                   tv(h->spareC[0][y], {c, c})));
+      // T4'[b,r,a] = sum P[(e,h),b] T4[e,m,f] a[g,m,h,r] Ptil[a,(f,g)]
+      CKS(contract(h, "emf,beh->mfhb", tv(envT(h, f, 3, x, y), {c, D2, c}), false,
+                   tv(h->PT[y], {c, c, D2}), false, tv(w2, {D2, c, D2, c})));
+      cplx* w3 = scratch_alloc(h, (long long)c * D2 * c * D2);
+      if (!w3) return fail(IPEPS_ENOMEM, "scratch exhausted (absorb)");
+      CKS(contract(h, "mfhb,gmhr->fbgr", tv(w2, {D2, c, D2, c}), false,
+                   tv(site_a(h, f, x, y), {D2, D2, D2, D2}), false, tv(w3, {c, c, D2, D2})));
+      CKS(contract(h, "fbgr,afg->bra", tv(w3, {c, c, D2, D2}), false, tv(h->Ptil[ym], {c, c, D2}),
+                   false, tv(h->spareT[y], {c, D2, c})));
+      // C4'[r,a] = sum (C4 T3)[r,s,u] Ptil[a,(u,s)]
+      CKS(contract(h, "gu,rsg->rsu", tv(envC(h, f, 3, x, y), {c, c}), false,
+                   tv(envT(h, f, 2, x, y), {c, D2, c}), false, tv(w1, {c, D2, c})));
+      CKS(contract(h, "rsu,aus->ra", tv(w1, {c, D2, c}), false, tv(h->Ptil[y], {c, c, D2}), false,
+                   tv(h->spareC[1][y], {c, c})));
+      h->scratch_top = 0;
+      CK(normalize(h->stream, h->spareC[0][y], (long long)c * c, h->dwork, h->st));
+      CK(normalize(h->stream, h->spareT[y], (long long)c * D2 * c, h->dwork, h->st));
+      CK(normalize(h->stream, h->spareC[1][y], (long long)c * c, h->dwork, h->st));
+    }
+    // install the renormalised tensors at column x+1 (pointer swap, no copies)
+    for (int y = 0; y < Ly; ++y) {
+      std::swap(envC(h, f, 0, x + 1, y), h->spareC[0][y]);
+      std::swap(envT(h, f, 3, x + 1, y), h->spareT[y]);
+      std::swap(envC(h, f, 3, x + 1, y), h->spareC[1][y]);
+    }
+  }
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (dir < 0 || dir > 4 || count < 0) return fail(IPEPS_EINVAL, "bad dir/count");
+  CKS(reset_status(h));
+  static const int sweep[4] = {IPEPS_MOVE_LEFT, IPEPS_MOVE_RIGHT, IPEPS_MOVE_UP, IPEPS_MOVE_DOWN};
+  for (int n = 0; n < count; ++n) {
+    if (dir == IPEPS_SWEEP) {
+      for (int i = 0; i < 4; ++i) CKS(left_move(h, sweep[i]));
+    } else {
+      CKS(left_move(h, dir));
+    }
+  }
+  return check_status(h);
+}
+
+// ---------------------------------------------------------------------------
+// spectra / convergence
+// ---------------------------------------------------------------------------
+static ipeps_status spectra_device(ipeps_ctm h, double* host) {
+  const int c = h->chi;
+  cplx* w = scratch_alloc(h, (long long)c * c);
+  if (!w) return fail(IPEPS_ENOMEM, "scratch exhausted (spectra)");
+  const int ncell = h->Lx * h->Ly;
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < ncell; ++i) {
+      CK(cudaMemcpyAsync(w, h->C[j][i], (size_t)c * c * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+      CK(jacobi_rows(h->stream, w, c, c, c, nullptr, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
+                     h->counters, h->st));
+      CK(select_top(h->stream, h->sigma, c, c, 0.0, h->perm, h->s_sel));
+      CK(cudaMemcpyAsync(host + (size_t)(j * ncell + i) * c, h->s_sel, c * sizeof(double),
+                         cudaMemcpyDeviceToHost, h->stream));
+    }
+  h->scratch_top = 0;
+  CK(cudaStreamSynchronize(h->stream));
+  for (int q = 0; q < 4 * ncell; ++q) {
+    double* s = host + (size_t)q * c;
+    const double s0 = s[0];
+    if (s0 > 0)
+      for (int a = 0; a < c; ++a) s[a] /= s0;
+  }
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_ctm_spectra(ipeps_ctm h, double* s_out) {
+  if (!h || !s_out) return fail(IPEPS_EINVAL, "null argument");
+  CKS(reset_status(h));
+  CKS(spectra_device(h, s_out));
+  return check_status(h);
+}
+
+extern "C" ipeps_status ipeps_ctm_converge(ipeps_ctm h, double tol, int max_sweeps, int* sweeps,
+                                           double* delta) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  const size_t n = (size_t)4 * h->Lx * h->Ly * h->chi;
+  std::vector<double> s_old(n), s_new(n);
+  CKS(ipeps_ctm_spectra(h, s_old.data()));
+  double dl = INFINITY;
+  int it = 0;
+  while (it < max_sweeps) {
+    CKS(ipeps_ctm_move(h, IPEPS_SWEEP, 1));
+    ++it;
+    CKS(ipeps_ctm_spectra(h, s_new.data()));
+    dl = 0.0;
+    for (size_t q = 0; q < n / h->chi; ++q) {
+      double acc = 0.0;
+      for (int a = 0; a < h->chi; ++a) {
+        const double t = s_new[q * h->chi + a] - s_old[q * h->chi + a];
+        acc += t * t;
+      }
+      dl = std::max(dl, sqrt(acc));
+    }
+    s_old.swap(s_new);
+    if (dl < tol) break;
+  }
+  if (sweeps) *sweeps = it;
+  if (delta) *delta = dl;
+  if (!(dl < tol)) return fail(IPEPS_ENOCONV, "not converged after %d sweeps (delta %.3e)", it, dl);
+  return IPEPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// RDMs and energy (frame f horizontal bond (x,y)-(x+1,y))
+// ---------------------------------------------------------------------------
+static ipeps_status rdm_horizontal(ipeps_ctm h, int f, int x, int y, cplx* rho) {
+  const int c = h->chi, D = h->D, d = h->d;
+  const cplx* Aa = h->A[f][tensor_id(h, f, x, y)];
+  const cplx* Ab = h->A[f][tensor_id(h, f, x + 1, y)];
+  const long long big = (long long)c * c * D * D * D * D * d;
+  cplx* L2 = scratch_alloc(h, (long long)c * c * D * D * D * D);
+  cplx* L3 = scratch_alloc(h, big);
+  cplx* L4 = scratch_alloc(h, big);
+  cplx* left = scratch_alloc(h, (long long)c * c * D * D * d * d);
+  cplx* right = scratch_alloc(h, (long long)c * c * D * D * d * d);
+  cplx* small = scratch_alloc(h, (long long)c * c * D * D);
+  if (!L2 || !L3 || !L4 || !left || !right || !small) return fail(IPEPS_ENOMEM, "scratch exhausted (rdm)");
+  // left half
+  CKS(contract(h, "ab,bUVh->aUVh", tv(envC(h, f, 0, x, y), {c, c}), false,
+               tv(envT(h, f, 0, x, y), {c, D, D, c}), false, tv(small, {c, D, D, c})));
+  CKS(contract(h, "eLMa,aUVh->eLMUVh", tv(envT(h, f, 3, x, y), {c, D, D, c}), false,
+               tv(small, {c, D, D, c}), false, tv(L2, {c, D, D, D, D, c})));
+  CKS(contract(h, "eLMUVh,pULSr->eMVhpSr", tv(L2, {c, D, D, D, D, c}), false,
+               tv((cplx*)Aa, {d, D, D, D, D}), false, tv(L3, {c, D, D, c, d, D, D})));
+  CKS(contract(h, "ge,kSTg->ekST", tv(envC(h, f, 3, x, y), {c, c}), false,
+               tv(envT(h, f, 2, x, y), {c, D, D, c}), false, tv(small, {c, c, D, D})));
+  CKS(contract(h, "eMVhpSr,ekST->MVhprkT", tv(L3, {c, D, D, c, d, D, D}), false,
+               tv(small, {c, c, D, D}), false, tv(L4, {D, D, c, d, D, c, D})));
+  CKS(contract(h, "MVhprkT,qVMTs->hrskpq", tv(L4, {D, D, c, d, D, c, D}), false,
+               tv((cplx*)Aa, {d, D, D, D, D}), true, tv(left, {c, D, D, c, d, d})));
+  // right half
+  CKS(contract(h, "hUVc,cf->hUVf", tv(envT(h, f, 0, x + 1, y), {c, D, D, c}), false,
+               tv(envC(h, f, 1, x + 1, y), {c, c}), false, tv(small, {c, D, D, c})));
+  CKS(contract(h, "hUVf,fRSg->hUVRSg", tv(small, {c, D, D, c}), false,
+               tv(envT(h, f, 1, x + 1, y), {c, D, D, c}), false, tv(L2, {c, D, D, D, D, c})));
+  CKS(contract(h, "hUVRSg,pUlXR->hVSgplX", tv(L2, {c, D, D, D, D, c}), false,
+               tv((cplx*)Ab, {d, D, D, D, D}), false, tv(L3, {c, D, D, c, d, D, D})));
+  CKS(contract(h, "gi,iXYk->gXYk", tv(envC(h, f, 2, x + 1, y), {c, c}), false,
+               tv(envT(h, f, 2, x + 1, y), {c, D, D, c}), false, tv(small, {c, D, D, c})));
+  CKS(contract(h, "hVSgplX,gXYk->hVSplYk", tv(L3, {c, D, D, c, d, D, D}), false,
+               tv(small, {c, D, D, c}), false, tv(L4, {c, D, D, d, D, D, c})));
+  CKS(contract(h, "hVSplYk,qVmYS->hlmkpq", tv(L4, {c, D, D, d, D, D, c}), false,
+               tv((cplx*)Ab, {d, D, D, D, D}), true, tv(right, {c, D, D, c, d, d})));
+  CKS(contract(h, "hrskpq,hrskPQ->pPqQ", tv(left, {c, D, D, c, d, d}), false,
+               tv(right, {c, D, D, c, d, d}), false, tv(rho, {d, d, d, d})));
+  CK(trace_normalize(h->stream, rho, d * d, h->dwork));
+  h->scratch_top = 0;
+  return IPEPS_OK;
+}
+
+// all bond RDMs into device buffers rh, rv ([Ly][Lx][d^2][d^2] each)
+static ipeps_status all_rdms(ipeps_ctm h, cplx* rh, cplx* rv) {
+  const long long n2 = (long long)h->d * h->d * h->d * h->d;
+  for (int y = 0; y < h->Ly; ++y)
+    for (int x = 0; x < h->Lx; ++x) {
+      const long long o = (long long)(y * h->Lx + x) * n2;
+      if (rh) CKS(rdm_horizontal(h, 0, x, y, rh + o));
+      // vertical bond (x,y)-(x,y+1) is horizontal in frame 1 at (y, -x)
+      if (rv) CKS(rdm_horizontal(h, 1, y, -x, rv + o));
+    }
+  return IPEPS_OK;
+}
+
+static ipeps_status rdm_buffers(ipeps_ctm h, cplx** rh, cplx** rv) {
+  const long long n2 = (long long)h->d * h->d * h->d * h->d * h->Lx * h->Ly;
+  // keep the RDMs at the top of the scratch arena, below the per-bond work
+  *rh = h->scratch + h->scratch_elems - 2 * n2;
+  *rv = *rh + n2;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  CKS(reset_status(h));
+  cplx *rh, *rv;
+  CKS(rdm_buffers(h, &rh, &rv));
+  const long long n2 = (long long)h->d * h->d * h->d * h->d * h->Lx * h->Ly;
+  const long long save = h->scratch_elems;
+  h->scratch_elems -= 2 * n2;
+  ipeps_status st = all_rdms(h, rho_h ? rh : nullptr, rho_v ? rv : nullptr);
+  h->scratch_elems = save;
+  CKS(st);
+  if (rho_h) CK(cudaMemcpyAsync(rho_h, rh, n2 * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+  if (rho_v) CK(cudaMemcpyAsync(rho_v, rv, n2 * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_status(h);
+}
+
+static ipeps_status upload_bonds(ipeps_ctm h, const double J[3]) {
+  CM Hr(64), Hv(64);
+  ruby_bonds(J, &Hr, &Hv);
+  std::vector<double> buf(2 * 64 * 64);
+  const CM* mats[4] = {&Hr, nullptr, &Hv, &Hv};  // H_r, H_l (= 0), H_u, H_d
+  for (int m = 0; m < 4; ++m) {
+    for (int i = 0; i < 64 * 64; ++i) {
+      buf[2 * i] = mats[m] ? mats[m]->re[i] : 0.0;
+      buf[2 * i + 1] = mats[m] ? mats[m]->im[i] : 0.0;
+    }
+    CK(cudaMemcpyAsync(h->Hbond[m], buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e) {
+  if (!h || !J || !e) return fail(IPEPS_EINVAL, "null argument");
+  if (h->d != 8 || h->Lx != 2 || h->Ly != 2)
+    return fail(IPEPS_EINVAL, "the ruby energy needs a 2x2 cell of d = 8 block sites");
+  CKS(reset_status(h));
+  CKS(upload_bonds(h, J));
+  cplx *rh, *rv;
+  CKS(rdm_buffers(h, &rh, &rv));
+  const long long n2 = 64LL * 64 * 4;
+  const long long save = h->scratch_elems;
+  h->scratch_elems -= 2 * n2;
+  ipeps_status st = all_rdms(h, rh, rv);
+  h->scratch_elems = save;
+  CKS(st);
+  CK(cudaMemsetAsync(h->dacc, 0, sizeof(double), h->stream));
+  for (int y = 0; y < 2; ++y)
+    for (int x = 0; x < 2; ++x) {
+      const bool siteA = ((x + y) % 2) == 0;
+      const long long o = (long long)(y * 2 + x) * 64 * 64;
+      CK(trace_product(h->stream, rh + o, h->Hbond[siteA ? 0 : 1], 64, h->dacc, 0, 1.0 / 12.0));
+      CK(trace_product(h->stream, rv + o, h->Hbond[siteA ? 2 : 3], 64, h->dacc, 0, 1.0 / 12.0));
+    }
+  CK(cudaMemcpyAsync(e, h->dacc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_status(h);
+}
+
+// ---------------------------------------------------------------------------
+// kappa (Sec. III): window at (0,0) contracted row by row, labels generated
+// ---------------------------------------------------------------------------
+struct Lab {
+  int next = 0;
+  char fresh() {
+    static const char pool[] = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ";
+    return pool[(next++) % 52];
+  }
+};
+
+// The 2x2 window of sites at (0,0) (cell indices mod Lx, Ly), contracted with
+// its environment.  rows/cols select which of the window's two rows (T4 ..
+// T2) and two columns (T1 .. T3) are present; the corners always are.  The
+// full window (rows and cols) is the trace of the ring of enlarged corners,
+// sum_{i,k} (Q1 Q2)[i,k] (Q4 Q3^T)[i,k]; the others are contracted row by row.
+static ipeps_status window_contract(ipeps_ctm h, bool rows, bool cols, cplx* result) {
+  const int c = h->chi, D2 = h->D2, Lx = h->Lx, Ly = h->Ly, W = 2;
+  const long long mark = h->scratch_top;
+  if (rows && cols) {
+    CKS(enlarged_corners(h, 0, 0, 0));
+    const long long K = h->K;
+    cplx* Rup = scratch_alloc(h, K * K);
+    cplx* Rdn = scratch_alloc(h, K * K);
+    if (!Rup || !Rdn) return fail(IPEPS_ENOMEM, "scratch exhausted (kappa)");
+    CKS(gemm_dispatch(h, (int)K, (int)K, (int)K, h->Q[0], K, OP_N, h->Q[1], K, OP_N, Rup, K, ONE));
+    CKS(gemm_dispatch(h, (int)K, (int)K, (int)K, h->Q[3], K, OP_N, h->Q[2], K, OP_T, Rdn, K, ONE));
+    TV out; out.p = result; out.nd = 0;
+    CKS(contract(h, "ik,ik->", tv(Rup, {(int)K, (int)K}), false, tv(Rdn, {(int)K, (int)K}), false, out));
+    h->scratch_top = mark;
+    return IPEPS_OK;
+  }
+  const int n = cols ? W : 0;
+  const int xr = (W - 1) % Lx, yb = (W - 1) % Ly;
+  auto Cp = [&](int role, int x, int y) { return h->C[role][(y % Ly) * Lx + (x % Lx)]; };
+  auto Tp = [&](int role, int x, int y) { return h->T[role][(y % Ly) * Lx + (x % Lx)]; };
+  Lab L;
+  std::string bl;
+  std::vector<int> bd;
+  const long long cap = (long long)c * D2 * D2 * c + (long long)c * c * D2;
+  cplx* cur = scratch_alloc(h, cap);
+  cplx* nxt = scratch_alloc(h, cap);
+  if (!cur || !nxt) return fail(IPEPS_ENOMEM, "scratch exhausted (kappa)");
+  auto view = [&](cplx* p, const std::vector<int>& dims) {
+    TV t; t.p = p; t.nd = (int)dims.size();
+    for (int i = 0; i < t.nd; ++i) t.dims[i] = dims[i];
+    return t;
+  };
+  auto step = [&](cplx* op, const std::string& lop, const std::vector<int>& dop,
+                  const std::string& lout) -> ipeps_status {
+    std::vector<int> dout;
+    long long sz = 1;
+    for (char ch : lout) {
+      size_t p = bl.find(ch);
+      dout.push_back(p != std::string::npos ? bd[p] : dop[lop.find(ch)]);
+      sz *= dout.back();
+    }
+    if (sz > cap) return fail(IPEPS_ENOMEM, "kappa intermediate too large");
+    std::string spec = bl + "," + lop + "->" + lout;
+    CKS(contract(h, spec.c_str(), view(cur, bd), false, view(op, dop), false, view(nxt, dout)));
+    std::swap(cur, nxt);
+    bl = lout;
+    bd = dout;
+    return IPEPS_OK;
+  };
+  {  // top: C1 [vl, h]
+    char vl = L.fresh(), hh = L.fresh();
+    CK(cudaMemcpyAsync(cur, Cp(0, 0, 0), (size_t)c * c * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+    bl = std::string() + vl + hh;
+    bd = {c, c};
+  }
+  for (int x = 0; x < n; ++x) {  // T1[l, d, r]
+    char v = L.fresh(), hn = L.fresh();
+    CKS(step(Tp(0, x, 0), std::string() + bl.back() + v + hn, {c, D2, c}, bl.substr(0, bl.size() - 1) + v + hn));
+  }
+  {  // C2[l, d]
+    char vr = L.fresh();
+    CKS(step(Cp(1, xr, 0), std::string() + bl.back() + vr, {c, c}, bl.substr(0, bl.size() - 1) + vr));
+  }
+  for (int y = 0; y < (rows ? W : 0); ++y) {  // rows only when there are no columns
+    char dn = L.fresh(), hr = L.fresh();
+    CKS(step(Tp(3, 0, y), std::string() + dn + hr + bl[0], {c, D2, c}, std::string() + dn + hr + bl.substr(1)));
+    char hx = bl[1], vr = bl[2], dd = L.fresh();
+    CKS(step(Tp(1, xr, y), std::string() + vr + hx + dd, {c, D2, c}, bl.substr(0, 1) + dd));
+  }
+  {  // C4[r, u]
+    char hb = L.fresh();
+    CKS(step(Cp(3, 0, yb), std::string() + hb + bl[0], {c, c}, std::string() + hb + bl.substr(1)));
+  }
+  for (int x = 0; x < n; ++x) {  // T3[r, u, l]
+    char hb = bl[0], vx = bl[1], rr = L.fresh();
+    CKS(step(Tp(2, x, yb), std::string() + rr + vx + hb, {c, D2, c}, std::string() + rr + bl.substr(2)));
+  }
+  {  // C3[u=vr, l=hb] -> scalar
+    std::string lop = std::string() + bl[1] + bl[0];
+    std::string spec = bl + "," + lop + "->";
+    TV out; out.p = result; out.nd = 0;
+    CKS(contract(h, spec.c_str(), view(cur, bd), false, tv(Cp(2, xr, yb), {c, c}), false, out));
+  }
+  h->scratch_top = mark;
+  return IPEPS_OK;
+}
+
+static ipeps_status kappa_host(ipeps_ctm h, double* kre, double* kim) {
+  CKS(window_contract(h, true, true, h->scalar + 0));
+  CKS(window_contract(h, false, false, h->scalar + 1));
+  CKS(window_contract(h, false, true, h->scalar + 2));
+  CKS(window_contract(h, true, false, h->scalar + 3));
+  cplx z[4];
+  CK(cudaMemcpyAsync(z, h->scalar, sizeof z, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  // kappa = Z_cell Z_00 / (Z_cols Z_rows)
+  const double nr = z[0].x * z[1].x - z[0].y * z[1].y, ni = z[0].x * z[1].y + z[0].y * z[1].x;
+  const double dr = z[2].x * z[3].x - z[2].y * z[3].y, di = z[2].x * z[3].y + z[2].y * z[3].x;
+  const double den = dr * dr + di * di;
+  if (!(den > 0)) return fail(IPEPS_ENUMERIC, "zero partition ratio denominator");
+  *kre = (nr * dr + ni * di) / den;
+  *kim = (ni * dr - nr * di) / den;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_kappa(ipeps_ctm h, double* k) {
+  if (!h || !k) return fail(IPEPS_EINVAL, "null argument");
+  CKS(reset_status(h));
+  CKS(kappa_host(h, k, k + 1));
+  return check_status(h);
+}
+
+extern "C" ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double* d_block,
+                                       double* d_spin) {
+  if (!h12 || !h11 || !h22) return fail(IPEPS_EINVAL, "null handle");
+  if (h12->Lx != h11->Lx || h12->Ly != h11->Ly || h22->Lx != h11->Lx || h22->Ly != h11->Ly)
+    return fail(IPEPS_EINVAL, "cells differ");
+  double k[3][2];
+  CKS(ipeps_kappa(h12, k[0]));
+  CKS(ipeps_kappa(h11, k[1]));
+  CKS(ipeps_kappa(h22, k[2]));
+  const int ns = 4;  // sites of the 2x2 window kappa is taken on
+  const double l12 = log(hypot(k[0][0], k[0][1])), l11 = log(hypot(k[1][0], k[1][1]));
+  const double l22 = log(hypot(k[2][0], k[2][1]));
+  const double db = exp((l12 - 0.5 * (l11 + l22)) / ns);
+  if (d_block) *d_block = db;
+  if (d_spin) *d_spin = pow(db, 1.0 / 3.0);
+  return IPEPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// boundary density operator (Sec. IV)
+// ---------------------------------------------------------------------------
+// half ring of `len` edge tensors starting at row y0 of column xc in role
+// `role` (T2: [u,(k,b),d] going down; T4: [d,(k,b),u] going down) -> out
+// [c_first, K, B, c_last] with K, B the fused ket / bra multi-indices.
+static ipeps_status half_ring(ipeps_ctm h, int role, int xc, int y0, int len, cplx* out, cplx* tmp) {
+  const int c = h->chi, D = h->D;
+  auto Tptr = [&](int i) { return h->T[role][((y0 + i) % h->Ly) * h->Lx + xc]; };
+  long long Kd = D;
+  // first tensor as [c0, k, b, c1]
+  if (role == 1) {
+    CK(cudaMemcpyAsync(out, Tptr(0), (size_t)c * D * D * c * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    const int dims[4] = {c, D, D, c};
+    const int perm[4] = {3, 1, 2, 0};
+    CK(permute(h->stream, Tptr(0), out, 4, dims, perm, false, ONE));
+  }
+  for (int i = 1; i < len; ++i) {
+    // R[a, K, B, c] T[c, k, b, e] -> [a, K, k, B, b, e]
+    if (role == 1)
+      CKS(contract(h, "aKBc,ckbe->aKkBbe", tv(out, {c, (int)Kd, (int)Kd, c}), false,
+                   tv(Tptr(i), {c, D, D, c}), false, tv(tmp, {c, (int)Kd, D, (int)Kd, D, c})));
+    else
+      CKS(contract(h, "aKBc,ekbc->aKkBbe", tv(out, {c, (int)Kd, (int)Kd, c}), false,
+                   tv(Tptr(i), {c, D, D, c}), false, tv(tmp, {c, (int)Kd, D, (int)Kd, D, c})));
+    Kd *= D;
+    CK(cudaMemcpyAsync(out, tmp, (size_t)c * Kd * Kd * c * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return IPEPS_OK;
+}
+
+static ipeps_status ring_sigma(ipeps_ctm h, int role, int xc, int Nv, cplx* sigma) {
+  const int c = h->chi, D = h->D;
+  const int h1 = Nv / 2, h2 = Nv - h1;
+  long long K1 = 1, K2 = 1;
+  for (int i = 0; i < h1; ++i) K1 *= D;
+  for (int i = 0; i < h2; ++i) K2 *= D;
+  cplx* H1 = scratch_alloc(h, (long long)c * K1 * K1 * c);
+  cplx* H2 = scratch_alloc(h, (long long)c * K2 * K2 * c);
+  cplx* tmp = scratch_alloc(h, (long long)c * K2 * K2 * c);
+  if (!H1 || !H2 || !tmp) return fail(IPEPS_ENOMEM, "scratch exhausted (ring)");
+  if (h1 > 0) CKS(half_ring(h, role, xc, 0, h1, H1, tmp));
+  CKS(half_ring(h, role, xc, h1, h2, H2, tmp));
+  if (h1 == 0) {
+    // single tensor ring: trace its two chi legs
+    return fail(IPEPS_EINVAL, "Nv must be >= 2");
+  }
+  // sigma[(K1 K2),(B1 B2)] = sum_{a,m} H1[a,K1,B1,m] H2[m,K2,B2,a]
+  CKS(contract(h, "aKBm,mLEa->KLBE", tv(H1, {c, (int)K1, (int)K1, c}), false,
+               tv(H2, {c, (int)K2, (int)K2, c}), false, tv(sigma, {(int)K1, (int)K2, (int)K1, (int)K2})));
+  return IPEPS_OK;
+}
+
+namespace bnd {
+void launch_phase_herm(cudaStream_t s, cplx* S, int n, bool transpose_out, double* work);
+void launch_spectrum_finish(cudaStream_t s, const double* sigma, int n, double* lam, double* S_vn);
+void launch_scale_cols(cudaStream_t s, cplx* G, int n, const double* sigma);
+}  // namespace bnd
+
+extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
+                                           double* S_vn) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
+  long long n = 1;
+  for (int i = 0; i < Nv; ++i) n *= h->D;
+  if (n > 4096) return fail(IPEPS_EINVAL, "D^Nv = %lld > 4096", n);
+  CKS(reset_status(h));
+  const int nn = (int)n;
+  const long long mark = h->scratch_top;
+  cplx* sL = scratch_alloc(h, n * n);
+  cplx* sR = scratch_alloc(h, n * n);
+  cplx* G = scratch_alloc(h, n * n);
+  cplx* Hm = scratch_alloc(h, n * n);
+  cplx* Vt = scratch_alloc(h, n * n);
+  if (!sL || !sR || !G || !Hm || !Vt) return fail(IPEPS_ENOMEM, "scratch exhausted (boundary rho)");
+  const long long inner = h->scratch_top;
+  const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
+  CKS(ring_sigma(h, 3, xl, Nv, sL));
+  h->scratch_top = inner;
+  CKS(ring_sigma(h, 1, xr, Nv, sR));
+  h->scratch_top = inner;
+  // phase-fix by the trace, Hermitise; sL is replaced by sigma_L^T
+  bnd::launch_phase_herm(h->stream, sL, nn, true, h->dwork);
+  bnd::launch_phase_herm(h->stream, sR, nn, false, h->dwork);
+  count_launch(2);
+  CK(cudaGetLastError());
+  // |sigma_L^T|^(1/2) factor: Jacobi on the rows of sigma_L^T gives rows
+  // lambda_i w_i^H; G = (rows)^H scaled by sigma_i^(-1/2) column-wise.
+  CK(cudaMemcpyAsync(G, sL, n * n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+  CK(jacobi_rows(h->stream, G, nn, nn, nn, nullptr, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
+                 h->counters, h->st));
+  // Gm = G^H (n x n), columns scaled
+  {
+    const int dims[2] = {nn, nn}, perm[2] = {1, 0};
+    CK(permute(h->stream, G, Hm, 2, dims, perm, true, ONE));
+  }
+  bnd::launch_scale_cols(h->stream, Hm, nn, h->sigma);
+  count_launch();
+  CK(cudaGetLastError());
+  // H = Gm^H sR Gm
+  CK(zgemm(h->stream, nn, nn, nn, ONE, sR, nn, OP_N, Hm, nn, OP_N, ZERO, G, nn));
+  CK(zgemm(h->stream, nn, nn, nn, ONE, Hm, nn, OP_H, G, nn, OP_N, ZERO, Vt, nn));
+  CK(jacobi_rows(h->stream, Vt, nn, nn, nn, nullptr, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
+                 h->counters, h->st));
+  bnd::launch_spectrum_finish(h->stream, h->sigma, nn, h->s_sel, h->dacc);
+  count_launch();
+  CK(cudaGetLastError());
+  if (eig_out) CK(cudaMemcpyAsync(eig_out, h->s_sel, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  double S = 0;
+  CK(cudaMemcpyAsync(&S, h->dacc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->scratch_top = mark;
+  if (n_out) *n_out = nn;
+  if (S_vn) *S_vn = S;
+  return check_status(h);
+}
+
+extern "C" ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* out) {
+  if (!h || !out) return fail(IPEPS_EINVAL, "null argument");
+  if (role < 0 || role > 7 || x < 0 || x >= h->Lx || y < 0 || y >= h->Ly)
+    return fail(IPEPS_EINVAL, "bad role/position");
+  const long long n = role < 4 ? (long long)h->chi * h->chi : (long long)h->chi * h->D2 * h->chi;
+  const cplx* src = role < 4 ? h->C[role][y * h->Lx + x] : h->T[role - 4][y * h->Lx + x];
+  CK(cudaMemcpyAsync(out, src, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return IPEPS_OK;
+}

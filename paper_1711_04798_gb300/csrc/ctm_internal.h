@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+typedef double2 cplx;  // (re, im), 16-byte aligned
+
+// ---------------------------------------------------------------------------
+// error plumbing: every launcher returns cudaError_t; the API layer converts.
+// ---------------------------------------------------------------------------
+struct DevStatus {
+  // written by kernels that can run out of an iteration budget
+  int jacobi_unconverged;  // number of Jacobi calls that hit the sweep budget
+  int nonfinite;           // a NaN/Inf met in a norm
+};
+
+// ---------------------------------------------------------------------------
+// GEMM operand ops (row-major storage):
+//   A op N: element (m,k) at A[m*lda + k];  op T: at A[k*lda + m]
+//   B op N: element (k,n) at B[k*ldb + n];  op T: at B[n*ldb + k]
+//   OP_C flag conjugates the element.
+// ---------------------------------------------------------------------------
+enum { OP_N = 0, OP_T = 1, OP_CONJ = 2, OP_C = OP_N | OP_CONJ, OP_H = OP_T | OP_CONJ };
+
+struct GemmBatch {
+  int count;
+  long long sA, sB, sC;  // element strides between batch entries
+};
+
+// C[M,N] = alpha * opA(A) opB(B) + beta * C   (complex FP64, CUDA cores)
+cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
+                  int opA, const cplx* B, long long ldb, int opB, cplx beta, cplx* C,
+                  long long ldc, GemmBatch batch = {1, 0, 0, 0});
+
+// out = alpha * (conj?) permute(in): out axis i is in axis perm[i].
+cudaError_t permute(cudaStream_t s, const cplx* in, cplx* out, int nd, const int* in_dims,
+                    const int* perm, bool conj, cplx alpha);
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+cudaError_t double_layer(cudaStream_t s, const cplx* A, const cplx* B, cplx* a, int d, int D);
+cudaError_t rotate_a(cudaStream_t s, const cplx* a, cplx* out, int D2);
+// trace init of one environment tensor from a double-layer tensor (role 0..7)
+cudaError_t trace_init_tensor(cudaStream_t s, const cplx* a, cplx* out, int role, int D, int chi);
+// x *= 1/||x||_F (FP64 reduction); work holds >= 1024 doubles
+cudaError_t normalize(cudaStream_t s, cplx* x, long long n, double* work, DevStatus* st);
+cudaError_t fill_omega_t(cudaStream_t s, cplx* omt, int k, int K, uint64_t seed);
+cudaError_t set_zero(cudaStream_t s, cplx* x, long long n);
+
+// One-sided (Hestenes) Jacobi on the n rows of G (row length m, row stride ldg):
+// rotates row pairs until mutually orthogonal; optional Vt (n x n) accumulates the
+// same rotations starting from the identity.  sigma[i] = ||row i|| on return.
+cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
+                        double* sigma, int max_sweeps, double* work, int* counters,
+                        DevStatus* st);
+// rows of G scaled to unit norm where sigma > tol*max(sigma), zero otherwise
+cudaError_t orth_rows_finish(cudaStream_t s, cplx* G, int n, int m, long long ldg,
+                             const double* sigma, double tol);
+// descending selection of the top chi of sigma[0..n) above cutoff*max:
+// perm[0..chi) (or -1), s_sel[0..chi) (or 0)
+cudaError_t select_top(cudaStream_t s, const double* sigma, int n, int chi, double cutoff,
+                       int* perm, double* s_sel);
+// out[a, :] = scale_a * in[perm[a], :] (row length m); scale_a = 1/sigma[perm[a]] if
+// normalize_by_sigma, else 1; rows with perm[a] < 0 are zero.
+cudaError_t gather_rows(cudaStream_t s, const cplx* in, long long ldi, cplx* out,
+                        long long ldo, const int* perm, const double* sigma, int rows, int m,
+                        bool normalize_by_sigma);
+// rows a < chi of X scaled by s_sel[a]^(-1/2) (0 where s_sel == 0)
+cudaError_t scale_rows_isqrt(cudaStream_t s, cplx* X, int rows, int m, long long ld,
+                             const double* s_sel);
+// out = sum_{ij} rho[i,j] * H[j,i]  (real part), accumulated with weight w into acc[idx]
+cudaError_t trace_product(cudaStream_t s, const cplx* rho, const cplx* H, int n, double* acc,
+                          int idx, double w);
+cudaError_t trace_normalize(cudaStream_t s, cplx* rho, int n, double* work);
+cudaError_t copy_to_complex(cudaStream_t s, const double* in, cplx* out, long long n);
+
+// launch accounting (host counter incremented by every launcher)
+void count_launch(int n = 1);
+uint64_t launch_counter();

@@ -1,0 +1,135 @@
+"""GPU (CUDA library, through the C ABI) against the FP64 oracle on the same
+seeded inputs.  FP64 path tolerance: 1e-10 relative on energies and RDM
+elements, and on corner spectra s_i/s_0 above 1e-8 (1e-8 absolute)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_common import gpu_ctm, oracle_options, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _oracle_run(w, chi, moves, **kw):
+    st = O.make_state(w["tensors"], w["pattern"], w["D"], chi)
+    opt = oracle_options(chi, w["D"], **kw)
+    for m in moves:
+        st = O.sweep(st, opt) if m == "sweep" else O.move(st, m, opt)
+    return st
+
+
+def _compare_rdms(g, st, w, tol=TOL):
+    r_gpu = g.rdms()
+    r_ref = O.bond_rdms(st, w["tensors"], w["pattern"])
+    for key in ("h", "v"):
+        assert rel_err(r_gpu[key], r_ref[key]) < tol, key
+
+
+def _compare_spectra(g, st, floor=1e-8, tol=1e-8):
+    s_gpu = g.spectra()
+    s_ref = O.corner_spectra(st)
+    mask = s_ref > floor
+    assert np.max(np.abs(s_gpu - s_ref)[mask]) < tol
+
+
+def test_trace_init_environment_matches():
+    w = synth.workload("cfg1", seed=3)
+    g = gpu_ctm(w["tensors"], w["pattern"], 8)
+    st = O.make_state(w["tensors"], w["pattern"], w["D"], 8)
+    for role in range(8):
+        for y in range(2):
+            for x in range(2):
+                ref = st.C[role][y][x] if role < 4 else st.T[role - 4][y][x]
+                assert np.max(np.abs(g.env(role, x, y) - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("direction", ["L", "R", "U", "D"])
+def test_single_move_each_direction(direction):
+    w = synth.workload("cfg1", seed=1, chi=12)
+    g = gpu_ctm(w["tensors"], w["pattern"], 12)
+    g.move(direction, 1)
+    st = _oracle_run(w, 12, [direction])
+    _compare_rdms(g, st, w)
+    _compare_spectra(g, st)
+
+
+def test_cfg1_twenty_sweeps_energy_rdms_spectra():
+    """Config 1: real d=8, D=2, chi=16, 20 sweeps, J=(1,1,1)."""
+    w = synth.workload("cfg1", seed=0)
+    g = gpu_ctm(w["tensors"], w["pattern"], 16)
+    g.sweep(20)
+    st = _oracle_run(w, 16, ["sweep"] * 20)
+    e_ref = O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2)
+    e_gpu = g.energy(w["J"])
+    assert abs(e_gpu - e_ref) < TOL * abs(e_ref)
+    _compare_rdms(g, st, w)
+    _compare_spectra(g, st)
+
+
+def test_cfg2_recipe_scaled_complex():
+    """Config-2 recipe (complex product state + 0.1 noise) at D=3, chi=18."""
+    w = synth.workload("cfg2", seed=2, D=3, chi=18)
+    g = gpu_ctm(w["tensors"], w["pattern"], 18)
+    g.sweep(3)
+    st = _oracle_run(w, 18, ["sweep"] * 3)
+    e_ref = O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2)
+    assert abs(g.energy(w["J"]) - e_ref) < TOL * abs(e_ref)
+    _compare_rdms(g, st, w)
+    _compare_spectra(g, st)
+
+
+def test_ising_onsager_on_gpu():
+    from test_oracle_pins import ising_tensor, onsager_minus_beta_f
+    beta = 0.3
+    A = ising_tensor(beta)
+    g = gpu_ctm([A], [[0]], 16, cutoff=1e-12)
+    g.sweep(30)
+    assert abs(np.log(abs(g.kappa())) / 4 - onsager_minus_beta_f(beta)) < 1e-9
+
+
+def test_kappa_and_fidelity_match_oracle():
+    w1 = synth.workload("cfg2", seed=4, D=2, chi=8)
+    w2 = synth.workload("cfg2", seed=5, D=2, chi=8)
+    t1, t2, pat = w1["tensors"], w2["tensors"], w1["pattern"]
+    hs = [gpu_ctm(t1, pat, 8, bra=t2), gpu_ctm(t1, pat, 8), gpu_ctm(t2, pat, 8)]
+    ks_ref = []
+    for a, b in ((t1, t2), (t1, t1), (t2, t2)):
+        st = O.make_state(a, pat, 2, 8, mixed_with=b)
+        opt = oracle_options(8, 2)
+        for _ in range(4):
+            st = O.sweep(st, opt)
+        ks_ref.append(O.kappa(st))
+    for hnd in hs:
+        hnd.sweep(4)
+    for hnd, kr in zip(hs, ks_ref):
+        assert abs(hnd.kappa() - kr) < TOL * abs(kr)
+    from paper_1711_04798_gb300 import CTM
+    d_gpu = CTM.fidelity(*hs)
+    d_ref = O.fidelity(*ks_ref)
+    assert abs(d_gpu[0] - d_ref[0]) < TOL and abs(d_gpu[1] - d_ref[1]) < TOL
+
+
+@pytest.mark.parametrize("Nv", [2, 4])
+def test_boundary_rho_matches_oracle(Nv):
+    w = synth.workload("cfg2", seed=6, D=2, chi=8)
+    g = gpu_ctm(w["tensors"], w["pattern"], 8)
+    g.sweep(3)
+    st = _oracle_run(w, 8, ["sweep"] * 3)
+    lam_gpu, S_gpu = g.boundary_rho(0, Nv)
+    lam_ref = O.boundary_spectrum(st, 0, Nv)
+    assert np.max(np.abs(lam_gpu - lam_ref)) < 1e-10
+    assert abs(S_gpu - O.entropy(lam_ref)) < 1e-10
+
+
+def test_errors_are_reported_not_fatal():
+    from paper_1711_04798_gb300 import CTMError
+    w = synth.workload("cfg1", seed=0)
+    with pytest.raises(CTMError):
+        gpu_ctm(w["tensors"], w["pattern"], 3)  # chi < D^2
+    g = gpu_ctm(w["tensors"], w["pattern"], 8)
+    with pytest.raises(CTMError):
+        g.boundary_rho(0, 3)  # not a multiple of Ly
+    g.sweep(1)  # the handle is still usable

@@ -179,7 +179,7 @@ def test_ising_free_energy_and_bond_correlation(beta):
     A = ising_tensor(beta)
     st = O.make_state([A], [[0]], 2, 16)
     st, n, _ = O.ctm_converge(st, O.CTMOptions(chi=16, proj="svd", cutoff=1e-12), 1e-9, 80)
-    lnk = np.log(abs(O.kappa(st)))
+    lnk = np.log(abs(O.kappa(st))) / 4  # 2x2 window
     assert abs(lnk - onsager_minus_beta_f(beta)) < 1e-10
     r = O.bond_rdms(st, [A], [[0]])
     zz = np.array([1.0, -1.0, -1.0, 1.0])
@@ -199,7 +199,7 @@ def test_ising_fidelity_closed_form():
         st = O.make_state([ta], [[0]], 2, 16, mixed_with=[tb])
         st, _, _ = O.ctm_converge(st, opt, 1e-9, 80)
         ks.append(O.kappa(st))
-    d_block, _ = O.fidelity(ks[0], ks[1], ks[2], 1)
+    d_block, _ = O.fidelity(ks[0], ks[1], ks[2])
     exact = np.exp(onsager_minus_beta_f((b1 + b2) / 2)
                    - 0.5 * (onsager_minus_beta_f(b1) + onsager_minus_beta_f(b2)))
     assert abs(d_block - exact) < 1e-10
@@ -301,7 +301,7 @@ def test_product_state_fidelity_closed_form():
         st = O.make_state(a, pat, 1, 1, mixed_with=b)
         st = O.sweep(st, opt)
         ks.append(O.kappa(st))
-    d_block, d_spin = O.fidelity(*ks, 4)
+    d_block, d_spin = O.fidelity(*ks)
     ov = [abs(np.vdot(q, p)) / (np.linalg.norm(p) * np.linalg.norm(q)) for p, q in zip(phis1, phis2)]
     exact = np.prod(ov) ** 0.25
     assert abs(d_block - exact) < 1e-13
@@ -309,7 +309,7 @@ def test_product_state_fidelity_closed_form():
     st = O.make_state(t1, pat, 1, 1, mixed_with=t1)
     st = O.sweep(st, opt)
     k = O.kappa(st)
-    assert abs(O.fidelity(k, k, k, 4)[0] - 1.0) < 1e-14
+    assert abs(O.fidelity(k, k, k)[0] - 1.0) < 1e-14
 
 
 # ---------------------------------------------------------------------------
