@@ -195,6 +195,26 @@ ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms, uin
 
 void ipeps_ctm_destroy(ipeps_ctm h);
 
+/* Corner spectrum without any device allocation (the paper has no
+ * counterpart: this is an interface for callers that cannot call cudaMalloc,
+ * e.g. a process whose device memory is owned entirely by another allocator,
+ * or a loop that must not take the device synchronisation of cudaMalloc /
+ * cudaFree).  C_dev: device pointer to one chi x chi complex corner matrix
+ * (interleaved doubles, row-major, read only); s_dev: device pointer to chi
+ * doubles receiving its singular values in descending order divided by the
+ * largest (zeros where the matrix has none) -- the same values
+ * ipeps_ctm_spectra returns for a corner.  stream: cudaStream_t (NULL =
+ * default stream); the call returns when s_dev is written.
+ * All intermediates live in one fixed device array of about 1 MiB inside
+ * the library (every GPU that loads the library holds it until exit), so
+ * chi is limited to 1..256; larger chi returns EINVAL.  The first call on
+ * each device looks up that array's address with that device current; make
+ * the first call before any stream capture.  All calls share the array: two
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and give wrong results.  Errors: EINVAL (null pointer, chi out of range),
+ * ECUDA, ETIMEOUT (Jacobi sweep budget), with ipeps_last_error(). */
+ipeps_status ipeps_corner_spectrum_noalloc(const double* C_dev, int chi, double* s_dev, void* stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char* ipeps_last_error(void);
 

@@ -49,6 +49,8 @@ static ipeps_status fail(ipeps_status st, const char* fmt, ...) {
 
 extern "C" const char* ipeps_last_error(void) { return g_err.c_str(); }
 
+void set_last_error_message(const char* msg) { g_err = msg; }
+
 static const cplx ONE = {1.0, 0.0};
 static const cplx ZERO = {0.0, 0.0};
 
