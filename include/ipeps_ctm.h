@@ -92,7 +92,8 @@ typedef struct {
   ipeps_prec prec;                  /* contraction arithmetic                      */
   int rsvd_oversample;              /* projector range finder width k = chi + p    */
   int rsvd_power;                   /* subspace iterations q                       */
-  double svd_cutoff;                /* keep singular values > cutoff * largest     */
+  double svd_cutoff;                /* keep singular values > cutoff * largest;
+                                       <= 0: 1e-8 (FP64), 1e-6 (BF16X3), 1e-5 (TF32) */
   double orth_tol;                  /* range-finder basis: drop s < tol * largest  */
   uint64_t omega_seed;              /* SplitMix64 stream of the test matrix        */
   int jacobi_max_sweeps;            /* iteration budget of every Jacobi SVD        */
@@ -101,7 +102,7 @@ typedef struct {
   size_t workspace_bytes;           /* its size; see ipeps_ctm_workspace_size      */
 } ipeps_options;
 
-/* Fill *opt with the defaults: prec FP64, oversample 16, power 2, cutoff 1e-8,
+/* Fill *opt with the defaults: prec FP64, oversample 16, power 2, cutoff 0 (automatic),
  * orth_tol 1e-14, omega_seed 7, jacobi_max_sweeps 40, NULL stream/workspace.
  * chi is set to 0 and must be chosen by the caller. */
 void ipeps_default_options(ipeps_options* opt);
@@ -194,6 +195,16 @@ ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms, uin
                                     double* flops);
 
 void ipeps_ctm_destroy(ipeps_ctm h);
+
+/* Complex GEMM building block of every contraction, for unit tests: C = opA(A)
+ * opB(B) with M x N output, complex interleaved doubles in host memory
+ * (row-major; op 0 = N, 1 = T, 2 = conj, 3 = conj-transpose, so that opA(A)
+ * is M x K and A is stored M x K for op 0/2 and K x M for op 1/3).  prec as
+ * ipeps_prec: FP64 CUDA-core kernel or the tcgen05 TF32 / split-BF16 kernel
+ * (with its operand packing and split-K reduction).  Allocates and frees its
+ * own device buffers; synchronises the device. */
+ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
+                         double* C);
 
 /* Corner spectrum without any device allocation (the paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc,

@@ -104,7 +104,7 @@ class CTM:
     """
 
     def __init__(self, tensors, pattern, chi, prec="fp64", bra=None, oversample=16, power=2,
-                 cutoff=1e-8, orth_tol=1e-14, omega_seed=7, jacobi_max_sweeps=40, stream=None,
+                 cutoff=0.0, orth_tol=1e-14, omega_seed=7, jacobi_max_sweeps=40, stream=None,
                  workspace=None):
         lib = load_library()
         self.lib = lib

@@ -48,7 +48,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
             if l.strip():
                 print(l)
     tmp = LIB + ".tmp"
-    cmd = [nv, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcuda"]
+    cmd = [nv, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -169,7 +169,7 @@ struct Sizes {
   size_t total;
 };
 
-static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens) {
+static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens, int prec) {
   Sizes s;
   const long long D2 = (long long)D * D, K = chi * D2;
   s.tens = (long long)d * D2 * D2;
@@ -184,6 +184,8 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens)
   // rdm: L2, L3, L4 and two contraction temporaries of chi^2 D^4 d, the halves
   const long long rdm = 6 * (long long)chi * chi * D2 * D2 * d + 3 * (long long)chi * chi * D2 * d * d;
   s.scratch = std::max(6 * s.Q, rdm) + (1 << 16);
+  // packed tensor-core operands (padded to 128 x 256 tiles) and split-K partials
+  if (prec != IPEPS_PREC_FP64) s.scratch = s.scratch * 3 / 2 + (1 << 22);
   size_t tot = 0;
   auto add = [&](long long n, size_t el) { tot += align_up((size_t)n * el); };
   for (int i = 0; i < 2 * 4 * ntens; ++i) add(s.tens, 16);
@@ -282,7 +284,8 @@ static ipeps_status gemm_dispatch(ipeps_ctm h, int M, int N, int K, const cplx* 
 static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cplx* A, long long lda,
                                       int opA, const cplx* B, long long ldb, int opB, cplx* C,
                                       long long ldc, cplx alpha) {
-  if (h->opt.prec != IPEPS_PREC_FP64) {
+  // small products (a few tiles of zero padding would dominate) stay FP64
+  if (h->opt.prec != IPEPS_PREC_FP64 && M >= 64 && N >= 32 && K >= 32) {
     cudaError_t e = tc_zgemm(h->stream, (int)h->opt.prec, M, N, K, alpha, A, lda, opA, B, ldb,
                              opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top);
     if (e == cudaErrorNotSupported) return fail(IPEPS_EUNSUPPORTED, "tensor-core GEMM unavailable for this shape");
@@ -520,7 +523,7 @@ extern "C" void ipeps_default_options(ipeps_options* o) {
   o->prec = IPEPS_PREC_FP64;
   o->rsvd_oversample = 16;
   o->rsvd_power = 2;
-  o->svd_cutoff = 1e-8;
+  o->svd_cutoff = 0.0;  // automatic by precision
   o->orth_tol = 1e-14;
   o->omega_seed = 7;
   o->jacobi_max_sweeps = 40;
@@ -548,7 +551,7 @@ extern "C" ipeps_status ipeps_ctm_workspace_size(const ipeps_cell* c, const ipep
                                                  size_t* bytes) {
   CKS(validate(c, o));
   if (!bytes) return fail(IPEPS_EINVAL, "null bytes");
-  Sizes s = plan_sizes(c->Lx, c->Ly, c->d, c->D, o->chi, o->chi + o->rsvd_oversample, c->n_tensors);
+  Sizes s = plan_sizes(c->Lx, c->Ly, c->d, c->D, o->chi, o->chi + o->rsvd_oversample, c->n_tensors, o->prec);
   *bytes = s.total;
   return IPEPS_OK;
 }
@@ -594,6 +597,10 @@ static ipeps_status check_status(ipeps_ctm h) {
   if (st.nonfinite) return fail(IPEPS_ENUMERIC, "non-finite or zero norm met (%d times)", st.nonfinite);
   if (st.jacobi_unconverged)
     return fail(IPEPS_ETIMEOUT, "%d Jacobi SVDs hit the sweep budget", st.jacobi_unconverged);
+  if (h->opt.prec != IPEPS_PREC_FP64) {
+    const int n = tc_take_errors();
+    if (n) return fail(IPEPS_ETIMEOUT, "%d tensor-core GEMM waits timed out", n);
+  }
   return IPEPS_OK;
 }
 
@@ -614,8 +621,10 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   h->mixed = c->tensors_bra != nullptr;
   h->dtype = c->dtype;
   h->opt = *o;
+  if (!(h->opt.svd_cutoff > 0.0))  // automatic: above the noise floor of the contraction arithmetic
+    h->opt.svd_cutoff = o->prec == IPEPS_PREC_FP64 ? 1e-8 : (o->prec == IPEPS_PREC_BF16X3 ? 1e-6 : 1e-5);
   h->stream = (cudaStream_t)o->stream;
-  Sizes sz = plan_sizes(h->Lx, h->Ly, h->d, h->D, h->chi, h->k, h->ntens);
+  Sizes sz = plan_sizes(h->Lx, h->Ly, h->d, h->D, h->chi, h->k, h->ntens, o->prec);
   if (o->workspace) {
     if (o->workspace_bytes < sz.total) {
       delete h;
@@ -1444,4 +1453,37 @@ extern "C" ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, d
   CK(cudaMemcpyAsync(out, src, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return IPEPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stand-alone complex GEMM (building block, host buffers) for unit tests
+// ---------------------------------------------------------------------------
+extern "C" ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA, const double* B,
+                                    int opB, double* C) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return fail(IPEPS_EINVAL, "bad GEMM arguments");
+  if (prec < 0 || prec > 2 || opA < 0 || opA > 3 || opB < 0 || opB > 3) return fail(IPEPS_EINVAL, "bad prec/op");
+  const size_t na = (size_t)M * K, nb = (size_t)K * N, nc = (size_t)M * N;
+  const size_t scratch_elems = 4 * (na + nb) + 8 * nc + (1 << 20);
+  cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dS = nullptr;
+  ipeps_status st = IPEPS_OK;
+  auto cleanup = [&]() { cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dS); };
+  cudaError_t e = cudaMalloc(&dA, na * sizeof(cplx));
+  if (e == cudaSuccess) e = cudaMalloc(&dB, nb * sizeof(cplx));
+  if (e == cudaSuccess) e = cudaMalloc(&dC, nc * sizeof(cplx));
+  if (e == cudaSuccess && prec) e = cudaMalloc(&dS, scratch_elems * sizeof(cplx));
+  if (e == cudaSuccess) e = cudaMemcpy(dA, A, na * sizeof(cplx), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dB, B, nb * sizeof(cplx), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cleanup(); return fail(IPEPS_ECUDA, "zgemm setup: %s", cudaGetErrorString(e)); }
+  const long long lda = (opA & OP_T) ? M : K, ldb = (opB & OP_T) ? K : N;
+  if (prec == 0) e = zgemm(0, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, ZERO, dC, N);
+  else e = tc_zgemm(0, prec, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, dC, N, dS, (long long)scratch_elems, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(C, dC, nc * sizeof(cplx), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "zgemm: %s", cudaGetErrorString(e));
+  if (st == IPEPS_OK && prec) {
+    const int n = tc_take_errors();
+    if (n) st = fail(IPEPS_ETIMEOUT, "%d tensor-core GEMM waits timed out", n);
+  }
+  cleanup();
+  return st;
 }

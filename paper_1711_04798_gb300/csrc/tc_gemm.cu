@@ -1,6 +1,443 @@
+// Tensor-core GEMM of the precision form (sm_103a, tcgen05 + TMA + TMEM).
+//
+// A complex GEMM C = alpha opA(A) opB(B) (complex128 storage) runs as one real
+// GEMM through the real embedding
+//     Ar[m, 2k+c]      = (Re, Im)[c] of A[m,k]                       (M x 2K)
+//     Br^T[2n+b, 2k+a] = [[Re, Im], [-Im, Re]][a][b] of B[k,n]        (2N x 2K)
+//     Cr[m, 2n+b]      = (Re, Im)[b] of C[m,n]
+// Both packed operands are K-major, in TF32 (one array) or in BF16 hi/lo
+// pairs (x = hi + lo, three products hi*hi + hi*lo + lo*hi accumulated in
+// FP32 in tensor memory).  One CTA computes a 128 x 256 tile of Cr: warp 0
+// issues the TMA loads (128-byte swizzle), warp 1 issues tcgen05.mma, all four
+// warps drain the accumulator with tcgen05.ld.  Thin products (few output
+// tiles) split K over the grid's z dimension into FP32 partials, summed in a
+// fixed order by a second kernel.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
 #include "tc_gemm.h"
 
-cudaError_t tc_zgemm(cudaStream_t, int, int, int, int, cplx, const cplx*, long long, int, const cplx*,
-                     long long, int, cplx*, long long, cplx*, long long, long long) {
+namespace {
+
+constexpr int BM = 128, BN = 256, NTHREADS = 128;
+constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
+
+__device__ int g_tc_errors;  // timeouts of bounded waits (read by tc_take_errors)
+
+template <int PREC>
+struct Cfg {
+  static constexpr int ELEM = PREC == PREC_TF32 ? 4 : 2;
+  static constexpr int BK = 128 / ELEM;                 // elements per k-block (128 bytes)
+  static constexpr int NOPS = PREC == PREC_TF32 ? 1 : 2;
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = PREC == PREC_TF32 ? 4 : 2;
+  static constexpr int UMMA_K = PREC == PREC_TF32 ? 8 : 16;  // K of one MMA
+  static constexpr int KSTEPS = BK / UMMA_K;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  // instruction descriptor: FP32 accumulate, K-major A and B, N = 256, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | ((PREC == PREC_TF32 ? 2u : 1u) << 7) |
+                                    ((PREC == PREC_TF32 ? 2u : 1u) << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// wait for phase `parity` of the barrier; false after WAIT_CYCLES
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+template <int PREC>
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+  if (PREC == PREC_TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(Cfg<PREC>::IDESC), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(Cfg<PREC>::IDESC), "r"(accum)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                   const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+                   int kb_total, int kb_per_split, int M, int Nr, cplx alpha, cplx* __restrict__ C,
+                   long long ldc, float* __restrict__ partial, int Nrp, long long pstride) {
+  using K_ = Cfg<PREC>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + K_::STAGES * K_::STAGE_BYTES);
+  uint64_t* empty = full + K_::STAGES;
+  uint64_t* accb = empty + K_::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accb + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y, split = blockIdx.z;
+  const int kb0 = split * kb_per_split;
+  const int nkb = min(kb_total, kb0 + kb_per_split) - kb0;  // >= 1 by construction
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < K_::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: one k-block per stage
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % K_::STAGES, r = i / K_::STAGES;
+      if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
+        atomicAdd(&g_tc_errors, 1);
+        break;
+      }
+      unsigned char* st = smem + s * K_::STAGE_BYTES;
+      mbar_expect_tx(&full[s], K_::STAGE_BYTES);
+      const int kx = (kb0 + i) * K_::BK;
+      tma_load_2d(st, &mA0, &full[s], kx, m_tile * BM);
+      if (K_::NOPS == 2) tma_load_2d(st + K_::A_BYTES, &mA1, &full[s], kx, m_tile * BM);
+      tma_load_2d(st + K_::NOPS * K_::A_BYTES, &mB0, &full[s], kx, n_tile * BN);
+      if (K_::NOPS == 2)
+        tma_load_2d(st + K_::NOPS * K_::A_BYTES + K_::B_BYTES, &mB1, &full[s], kx, n_tile * BN);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % K_::STAGES, r = i / K_::STAGES;
+      if (!mbar_wait(&full[s], r & 1)) {
+        atomicAdd(&g_tc_errors, 1);
+        break;
+      }
+      fence_after();
+      const uint32_t base = smem_u32(smem + s * K_::STAGE_BYTES);
+      const uint32_t a0 = base, a1 = base + K_::A_BYTES;
+      const uint32_t b0 = base + K_::NOPS * K_::A_BYTES, b1 = b0 + K_::B_BYTES;
+#pragma unroll
+      for (int j = 0; j < K_::KSTEPS; ++j) {
+        const uint32_t ko = j * 32;  // bytes of one MMA's K inside the 128-byte row
+        const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
+        umma<PREC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), acc);
+        if (K_::NOPS == 2) {
+          umma<PREC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
+          umma<PREC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+        }
+      }
+      umma_commit(&empty[s]);  // frees the stage when these MMAs are done
+    }
+    umma_commit(accb);
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+  const bool ready = mbar_wait(accb, 0);
+  if (!ready && lane == 0) atomicAdd(&g_tc_errors, 1);
+  __syncwarp();
+  fence_after();
+  if (ready) {
+    const int row = m_tile * BM + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(trow + c0, v);
+      const int col = n_tile * BN + c0;  // real column
+      if (partial) {
+        float4* dst = (float4*)(partial + split * pstride + (long long)row * Nrp + col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else if (row < M) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (col + 2 * t < Nr) {
+            const double re = v[2 * t], im = v[2 * t + 1];
+            C[(long long)row * ldc + (col >> 1) + t] =
+                make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// C[m,n] = alpha * sum_z P[z][m][2n .. 2n+1]  (fixed summation order)
+__global__ void splitk_reduce_kernel(const float* __restrict__ P, int S, long long pstride, int Nrp, int M,
+                                     int N, cplx alpha, cplx* __restrict__ C, long long ldc) {
+  const long long total = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / N), n = (int)(e % N);
+    double re = 0.0, im = 0.0;
+    for (int z = 0; z < S; ++z) {
+      const float2 p = *(const float2*)(P + z * pstride + (long long)m * Nrp + 2 * n);
+      re += p.x;
+      im += p.y;
+    }
+    C[(long long)m * ldc + n] = make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+  }
+}
+
+__device__ __forceinline__ cplx load_op(const cplx* X, long long ld, int op, int r, int c) {
+  // element (r, c) of the operand in its GEMM role (A: (m,k); B: (k,n))
+  cplx v = (op & OP_T) ? X[(long long)c * ld + r] : X[(long long)r * ld + c];
+  if (op & OP_CONJ) v.y = -v.y;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return u;
+}
+
+// Ar[m, kr], padded to Mp x Krp (K-major)
+template <int PREC>
+__global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int Krp,
+                              void* __restrict__ o0, void* __restrict__ o1) {
+  const long long total = (long long)Mp * Krp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / Krp), kr = (int)(e % Krp);
+    double x = 0.0;
+    if (m < M && kr < 2 * K) {
+      const cplx v = load_op(A, lda, opA, m, kr >> 1);
+      x = (kr & 1) ? v.y : v.x;
+    }
+    if (PREC == PREC_TF32) {
+      ((uint32_t*)o0)[e] = to_tf32((float)x);
+    } else {
+      const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+      const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+      ((__nv_bfloat16*)o0)[e] = hi;
+      ((__nv_bfloat16*)o1)[e] = lo;
+    }
+  }
+}
+
+// Br^T[nr, kr] = [[Re, Im], [-Im, Re]][kr%2][nr%2] of B[kr/2, nr/2], padded to Nrp x Krp
+template <int PREC>
+__global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp, int Krp,
+                              void* __restrict__ o0, void* __restrict__ o1) {
+  const long long total = (long long)Nrp * Krp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nr = (int)(e / Krp), kr = (int)(e % Krp);
+    double x = 0.0;
+    if (nr < 2 * N && kr < 2 * K) {
+      const cplx v = load_op(B, ldb, opB, kr >> 1, nr >> 1);
+      const int a = kr & 1, b = nr & 1;
+      x = (a == b) ? v.x : (a == 0 ? v.y : -v.y);
+    }
+    if (PREC == PREC_TF32) {
+      ((uint32_t*)o0)[e] = to_tf32((float)x);
+    } else {
+      const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+      const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+      ((__nv_bfloat16*)o0)[e] = hi;
+      ((__nv_bfloat16*)o1)[e] = lo;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t get_encoder() {
+  if (g_encode) return cudaSuccess;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return cudaSuccess;
+}
+
+// K-major [rows x kcols] operand, box of box_rows x (128 bytes)
+cudaError_t make_map(CUtensorMap* map, void* base, int prec, long long rows, long long kcols, int box_rows) {
+  const bool tf = prec == PREC_TF32;
+  const cuuint64_t dims[2] = {(cuuint64_t)kcols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(kcols * (tf ? 4 : 2))};
+  const cuuint32_t box[2] = {(cuuint32_t)(tf ? 32 : 64), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)b;
+}
+
+template <int PREC>
+cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
+                const cplx* B, long long ldb, int opB, cplx* C, long long ldc, char* scratch, size_t scratch_bytes) {
+  using K_ = Cfg<PREC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, K_::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long Mp = (M + BM - 1) / BM * BM;
+  const long long Kr = 2LL * K, Krp = (Kr + K_::BK - 1) / K_::BK * K_::BK;
+  const long long Nr = 2LL * N, Nrp = (Nr + BN - 1) / BN * BN;
+  const int kb_total = (int)(Krp / K_::BK);
+  const long long tiles = (Mp / BM) * (Nrp / BN);
+  int S = 1;
+  if (tiles < 152) {
+    S = (int)((2 * 152 + tiles - 1) / tiles);
+    if (S > kb_total / 2) S = kb_total / 2;
+    if (S < 1) S = 1;
+  }
+  const int kps = (kb_total + S - 1) / S;
+  S = (kb_total + kps - 1) / kps;  // no empty split
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  const size_t abytes = al((size_t)Mp * Krp * K_::ELEM), bbytes = al((size_t)Nrp * Krp * K_::ELEM);
+  const size_t pbytes = S > 1 ? al((size_t)S * Mp * Nrp * 4) : 0;
+  char* p = (char*)(((uintptr_t)scratch + 1023) & ~(uintptr_t)1023);
+  const size_t need = K_::NOPS * (abytes + bbytes) + pbytes + 1024;
+  if (need > scratch_bytes) return cudaErrorMemoryAllocation;
+  char* a0 = p;
+  char* a1 = a0 + abytes;
+  char* b0 = a0 + K_::NOPS * abytes;
+  char* b1 = b0 + bbytes;
+  float* part = S > 1 ? (float*)(b0 + K_::NOPS * bbytes) : nullptr;
+  pack_a_kernel<PREC><<<grid_for(Mp * Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)Mp, (int)Krp, a0, a1);
+  pack_b_kernel<PREC><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
+  count_launch(2);
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mA0, mA1, mB0, mB1;
+  if ((e = make_map(&mA0, a0, PREC, Mp, Krp, BM)) != cudaSuccess) return e;
+  if ((e = make_map(&mB0, b0, PREC, Nrp, Krp, BN)) != cudaSuccess) return e;
+  mA1 = mA0;
+  mB1 = mB0;
+  if (K_::NOPS == 2) {
+    if ((e = make_map(&mA1, a1, PREC, Mp, Krp, BM)) != cudaSuccess) return e;
+    if ((e = make_map(&mB1, b1, PREC, Nrp, Krp, BN)) != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)(Nrp / BN), (unsigned)(Mp / BM), (unsigned)S);
+  tc_gemm_kernel<PREC><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mB0, mB1, kb_total, kps, M, (int)Nr, alpha, C,
+                                                         ldc, part, (int)Nrp, (long long)Mp * Nrp);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (S > 1) {
+    splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, (long long)Mp * Nrp, (int)Nrp, M, N,
+                                                                    alpha, C, ldc);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
+                     int opA, const cplx* B, long long ldb, int opB, cplx* C, long long ldc, cplx* scratch,
+                     long long scratch_elems, long long scratch_top) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
+  char* base = (char*)(scratch + scratch_top);
+  const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
+  if (prec == PREC_TF32) return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, C, ldc, base, bytes);
+  if (prec == PREC_BF16X3) return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, C, ldc, base, bytes);
   return cudaErrorNotSupported;
+}
+
+int tc_take_errors() {
+  int n = 0;
+  cudaMemcpyFromSymbol(&n, g_tc_errors, sizeof n);
+  if (n) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_tc_errors, &z, sizeof z);
+  }
+  return n;
 }

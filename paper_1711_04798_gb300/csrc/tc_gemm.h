@@ -10,3 +10,7 @@
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A,
                      long long lda, int opA, const cplx* B, long long ldb, int opB, cplx* C,
                      long long ldc, cplx* scratch, long long scratch_elems, long long scratch_top);
+
+// number of bounded-wait timeouts inside tensor-core kernels since the last
+// call (resets the counter); synchronous.
+int tc_take_errors();

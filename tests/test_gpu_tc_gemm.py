@@ -1,0 +1,54 @@
+"""tcgen05 GEMM of the precision form (TF32, split-BF16 x3) against numpy's
+complex128 product, through ipeps_zgemm, on ragged shapes that span several
+tiles, the split-K path and every operand op.  The error bound is relative to
+sum_k |A_ik| |B_kj| (the scale of each output element): 2^-10 for TF32 inputs
+(two roundings to 11 bits), 2^-15 for the BF16 hi/lo split (each input kept
+to about 16 bits) plus FP32 accumulation."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-13, 1: 2.0 ** -10, 2: 2.0 ** -15}
+
+
+def _zgemm(prec, A, opA, B, opB, M, N, K):
+    from paper_1711_04798_gb300 import load_library
+    lib = load_library()
+    f = lib.ipeps_zgemm
+    P = ctypes.POINTER(ctypes.c_double)
+    f.argtypes = [ctypes.c_int] * 4 + [P, ctypes.c_int, P, ctypes.c_int, P]
+    f.restype = ctypes.c_int
+    C = np.zeros((M, N), dtype=np.complex128)
+    A = np.ascontiguousarray(A)
+    B = np.ascontiguousarray(B)
+    st = f(prec, M, N, K, A.ctypes.data_as(P), opA, B.ctypes.data_as(P), opB, C.ctypes.data_as(P))
+    assert st == 0, lib.ipeps_last_error()
+    return C
+
+
+def _op(X, op):
+    if op & 1:
+        X = X.T
+    if op & 2:
+        X = X.conj()
+    return X
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(130, 77, 300), (1, 1000, 700), (116, 600, 2500), (300, 129, 33)])
+@pytest.mark.parametrize("ops", [(0, 0), (1, 3), (2, 1)])
+def test_tc_gemm_matches_complex128(prec, shape, ops):
+    M, N, K = shape
+    rng = np.random.default_rng(M * 7 + N + K + prec)
+    opA, opB = ops
+    Ast = rng.standard_normal((K, M) if opA & 1 else (M, K)) + 1j * rng.standard_normal((K, M) if opA & 1 else (M, K))
+    Bst = rng.standard_normal((N, K) if opB & 1 else (K, N)) + 1j * rng.standard_normal((N, K) if opB & 1 else (K, N))
+    C = _zgemm(prec, Ast, opA, Bst, opB, M, N, K)
+    Aop, Bop = _op(Ast, opA), _op(Bst, opB)
+    ref = Aop @ Bop
+    scale = np.abs(Aop) @ np.abs(Bop)
+    err = np.max(np.abs(C - ref) / scale)
+    assert err < TOL[prec], err

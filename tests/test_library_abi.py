@@ -44,7 +44,7 @@ def test_argument_validation_without_gpu(lib):
     cell.tensors = ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p))
     opt = Options()
     lib.ipeps_default_options(ctypes.byref(opt))
-    assert abs(opt.svd_cutoff - 1e-8) < 1e-20 and opt.rsvd_oversample == 16
+    assert opt.svd_cutoff == 0.0 and opt.rsvd_oversample == 16  # 0: chosen by precision
     opt.chi = 8  # < D^2 = 16
     n = ctypes.c_size_t()
     assert lib.ipeps_ctm_workspace_size(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(n)) == 1
