@@ -32,7 +32,9 @@ def parse():
     p.add_argument("--steps", type=int, default=4)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="fp64", choices=["fp64", "tf32", "bf16x3"])
+    p.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3"])
+    p.add_argument("--no-fp64-check", action="store_true",
+                   help="skip the FP64 comparison run (moves/s and |dE| of the plain FP64 GPU path)")
     p.add_argument("--D", type=int, default=5)
     p.add_argument("--chi", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -264,6 +266,29 @@ def run_ours(args, rank, world, local_rank):
     roof["gemm_share_of_step"] = gemm["ms"] / ms if ms else None
     roof["gemm_launches"] = gemm["launches"]
     roof["jacobi_ms_share"] = jac["ms"] / ms if ms else None
+    roof["jacobi_calls"] = jac["launches"]
+    roof["jacobi_mean_sweeps"] = jac["flops"]
+    fp64_cmp = None
+    if args.prec != "fp64" and not args.no_fp64_check:
+        # the same number of sweeps from the trace initialisation, plain FP64 GPU path
+        n_sw = 2
+        gm = CTM(w["tensors"], w["pattern"], args.chi, prec=args.prec, stream=stream.cuda_stream)
+        gf = CTM(w["tensors"], w["pattern"], args.chi, prec="fp64", stream=stream.cuda_stream)
+        gm.sweep(n_sw)
+        em = gm.energy(J)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        gf.sweep(n_sw)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ef = gf.energy(J)
+        fp64_cmp = {"sweeps": n_sw, "fp64_moves_per_s": 4 * n_sw / (f0.elapsed_time(f1) * 1e-3),
+                    "energy_mixed": em, "energy_fp64": ef, "abs_dE": abs(em - ef),
+                    "speedup_vs_fp64": None}
+        fp64_cmp["speedup_vs_fp64"] = value / fp64_cmp["fp64_moves_per_s"]
+        gm.close()
+        gf.close()
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         secs = oracle_move_seconds(args.D, args.chi)
@@ -277,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic", "config": config_desc(args, args.prec),
         "tflops": gemm["flops"] / (ms * 1e-3) / 1e12 if ms else None,
         "energy_per_spin": energies[-1],
-        "roofline": roof, "cpu_baseline": cpu,
+        "roofline": roof, "cpu_baseline": cpu, "fp64_comparison": fp64_cmp,
         "e2e": {"value": e2e_value, "unit": "moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
         "gpu_launches": launches, "clocks": clk.summary(),
     }

@@ -189,7 +189,8 @@ uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
  * CUDA events on the handle's stream.  profile() clears the records;
  * profile_read() synchronises and returns the summed event time (ms), the
  * number of launches and (kind 0) the algorithmic flops, 8*M*N*K per complex
- * GEMM.  Not a paper operation: measurement support only. */
+ * GEMM, or (kind 1) the mean number of sweeps per Jacobi call.  Not a paper
+ * operation: measurement support only. */
 ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable);
 ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms, uint64_t* launches,
                                     double* flops);

@@ -115,6 +115,7 @@ struct ipeps_ctm_s {
   uint64_t launches_at_create;
   // optional per-kernel-class timing (CUDA events on the handle's stream)
   bool profiling;
+  long long jac_sweeps, jac_calls;  // accumulated while profiling
   struct Rec { cudaEvent_t a, b; double flops; int kind; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -203,7 +204,7 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   add(std::max(k, 4096), 8);
   add(std::max(k, 4096), 8);
   add(std::max(k, 4096), 4);
-  add(2, 4);
+  add(4, 4);
   add(4096, 8);
   add(64, 8);
   add(16, 16);
@@ -292,7 +293,8 @@ static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cp
     CK(e);
     return IPEPS_OK;
   }
-  CK(zgemm(h->stream, M, N, K, alpha, A, lda, opA, B, ldb, opB, ZERO, C, ldc));
+  CK(zgemm(h->stream, M, N, K, alpha, A, lda, opA, B, ldb, opB, ZERO, C, ldc, GemmBatch{1, 0, 0, 0},
+           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
   return IPEPS_OK;
 }
 
@@ -594,6 +596,10 @@ static ipeps_status check_status(ipeps_ctm h) {
   DevStatus st;
   CK(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->profiling) {
+    h->jac_sweeps += st.jacobi_sweeps;
+    h->jac_calls += st.jacobi_calls;
+  }
   if (st.nonfinite) return fail(IPEPS_ENUMERIC, "non-finite or zero norm met (%d times)", st.nonfinite);
   if (st.jacobi_unconverged)
     return fail(IPEPS_ETIMEOUT, "%d Jacobi SVDs hit the sweep budget", st.jacobi_unconverged);
@@ -674,7 +680,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   need(h->sigma = carve<double>(h, std::max(h->k, 4096)));
   need(h->s_sel = carve<double>(h, std::max(h->k, 4096)));
   need(h->perm = carve<int>(h, std::max(h->k, 4096)));
-  need(h->counters = carve<int>(h, 2));
+  need(h->counters = carve<int>(h, 4));
   need(h->dwork = carve<double>(h, 4096));
   need(h->dacc = carve<double>(h, 64));
   need(h->scalar = carve<cplx>(h, 16));
@@ -724,6 +730,7 @@ extern "C" ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable) {
   }
   h->recs.clear();
   h->profiling = enable != 0;
+  h->jac_sweeps = h->jac_calls = 0;
   return IPEPS_OK;
 }
 
@@ -741,6 +748,7 @@ extern "C" ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* to
     fl += r.flops;
     ++n;
   }
+  if (kind == 1) fl = h->jac_calls ? (double)h->jac_sweeps / (double)h->jac_calls : 0.0;
   if (total_ms) *total_ms = ms;
   if (launches) *launches = n;
   if (flops) *flops = fl;
@@ -889,39 +897,118 @@ static ipeps_status orth(ipeps_ctm h, cplx* G) {
   return IPEPS_OK;
 }
 
+// Precision form, one CholeskyQR pass on the k rows of `in` (length K):
+// G = conj(in) in^T (FP64), G = R^H R (dropped pivots below tol * max), out =
+// R^{-T} in (rows orthonormal on the kept directions, zero elsewhere).  R is
+// left in Rout (k x k) when given.
+static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Rout, double tol,
+                                bool apply = true) {
+  const int k = h->k, K = h->K;
+  const long long mark = h->scratch_top;
+  cplx* G = scratch_alloc(h, (long long)k * k);
+  cplx* W = scratch_alloc(h, (long long)k * k);
+  cplx* R = Rout ? Rout : scratch_alloc(h, (long long)k * k);
+  cplx* Ri = scratch_alloc(h, (long long)k * k);
+  if (!G || !W || !R || !Ri) return fail(IPEPS_ENOMEM, "scratch exhausted (cholqr)");
+  CK(zgemm(h->stream, k, k, K, ONE, in, K, OP_C, in, K, OP_T, ZERO, G, k, GemmBatch{1, 0, 0, 0},
+           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
+  CK(chol_drop(h->stream, G, W, R, k, tol));
+  if (apply) {
+    CK(tri_inv(h->stream, R, Ri, k));
+    // Q = Y R^{-1}  ->  Q^T = R^{-T} Y^T
+    CK(zgemm(h->stream, k, K, k, ONE, Ri, k, OP_T, in, K, OP_N, ZERO, out, K, GemmBatch{1, 0, 0, 0},
+             h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
+  }
+  h->scratch_top = mark;
+  return IPEPS_OK;
+}
+
+// Precision form orthonormalisation: CholeskyQR2 (directions below ~1e-7 of
+// the largest singular value dropped in the first pass).
+static ipeps_status orth_chol(ipeps_ctm h, cplx* Y, cplx* tmp) {
+  CKS(cholqr_pass(h, Y, tmp, nullptr, 1e-14));
+  CKS(cholqr_pass(h, tmp, Y, nullptr, 1e-14));
+  return IPEPS_OK;
+}
+
+// Precision form SVD of W (K x k, stored as the k rows Wt): W = Q R by
+// CholeskyQR2 (R = R2 R1, backward stable), one-sided Jacobi on the columns of
+// the k x k R (R V = U_R S), then out rows = (W v_i)^T = s_i u_i^T, sigma = s,
+// h->Vt rows = columns of V.
+static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
+  const int k = h->k, K = h->K;
+  const long long mark = h->scratch_top;
+  cplx* R1 = scratch_alloc(h, (long long)k * k);
+  cplx* R2 = scratch_alloc(h, (long long)k * k);
+  cplx* Rt = scratch_alloc(h, (long long)k * k);
+  if (!R1 || !R2 || !Rt) return fail(IPEPS_ENOMEM, "scratch exhausted (svd chol)");
+  CKS(cholqr_pass(h, Wt, out, R1, 1e-14));
+  CKS(cholqr_pass(h, out, nullptr, R2, 1e-14, false));  // only R2 is needed
+  // Rt = (R2 R1)^T: rows of Rt are the columns of R
+  CK(zgemm(h->stream, k, k, k, ONE, R1, k, OP_T, R2, k, OP_T, ZERO, Rt, k));
+  {
+    cudaEvent_t a = nullptr;
+    prof_begin(h, &a);
+    CK(jacobi_rows(h->stream, Rt, k, k, k, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
+                   h->counters, h->st));
+    prof_end(h, a, 0.0, 1);
+  }
+  // out = V^T Wt  (rows (W v_i)^T)
+  CK(zgemm(h->stream, k, K, k, ONE, h->Vt, k, OP_N, Wt, K, OP_N, ZERO, out, K, GemmBatch{1, 0, 0, 0},
+           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
+  CK(row_norms(h->stream, out, k, K, K, h->sigma));
+  h->scratch_top = mark;
+  return IPEPS_OK;
+}
+
 // Projectors of the left cut of plaquette (x,y): PT = P^T, Ptil (both chi x K).
 static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx* Ptil) {
   CKS(enlarged_corners(h, f, x, y));
   const int k = h->k, K = h->K, chi = h->chi;
+  const bool fp64 = h->opt.prec == IPEPS_PREC_FP64;
   cplx* Qt = h->thin[0];
   cplx* Zt = h->thin[1];
+  auto orth_any = [&](cplx* Y) -> ipeps_status {
+    return fp64 ? orth(h, Y) : orth_chol(h, Y, h->thin[2]);
+  };
   CKS(apply_XT(h, h->omt, Qt, k));
-  CKS(orth(h, Qt));
+  CKS(orth_any(Qt));
   for (int it = 0; it < h->opt.rsvd_power; ++it) {
     CKS(apply_XHT(h, Qt, Zt, k));
-    CKS(orth(h, Zt));
+    CKS(orth_any(Zt));
     CKS(apply_XT(h, Zt, Qt, k));
-    CKS(orth(h, Qt));
+    CKS(orth_any(Qt));
   }
   // W = X^H Q (K x k) stored as Wt; its SVD W = U_w S V_w^H gives X ~ (Q V_w) S U_w^H
   CKS(apply_XHT(h, Qt, Zt, k));
-  CK(jacobi_rows(h->stream, Zt, k, K, K, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                 h->counters, h->st));
+  cplx* Wrot;  // rows sigma_i u_i^T
+  if (fp64) {
+    cudaEvent_t a = nullptr;
+    prof_begin(h, &a);
+    CK(jacobi_rows(h->stream, Zt, k, K, K, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
+                   h->counters, h->st));
+    prof_end(h, a, 0.0, 1);
+    Wrot = Zt;
+  } else {
+    CKS(svd_rows_chol(h, Zt, h->thin[2]));
+    Wrot = h->thin[2];
+  }
+  cplx* Vt_chi = (Wrot == Zt) ? h->thin[2] : Zt;
+  cplx* Ut_chi = h->thin[3];
+  cplx* tmp = (Wrot == Zt) ? Zt : h->thin[2];  // free once Vt_chi has been gathered
   CK(select_top(h->stream, h->sigma, k, chi, h->opt.svd_cutoff, h->perm, h->s_sel));
-  // V_chi^T rows = selected columns of U_w (normalised rows of Wt)
-  cplx* Vt_chi = h->thin[2];
-  CK(gather_rows(h->stream, Zt, K, Vt_chi, K, h->perm, h->sigma, chi, K, true));
+  // V_chi^T rows = selected columns of U_w (normalised rows of Wrot)
+  CK(gather_rows(h->stream, Wrot, K, Vt_chi, K, h->perm, h->sigma, chi, K, true));
   // U_chi^T = (V_w[:, sel])^T Q^T
   CK(gather_rows(h->stream, h->Vt, k, h->Gsel, k, h->perm, h->sigma, chi, k, false));
-  cplx* Ut_chi = h->thin[3];
   CKS(gemm_dispatch(h, chi, K, k, h->Gsel, k, OP_N, Qt, K, OP_N, Ut_chi, K, ONE));
   // P^T = S^-1/2 V^T Q3 Q4^T
-  CKS(thin_mul(h, Vt_chi, OP_N, Zt, h->Q[2], OP_N, chi));
-  CKS(thin_mul(h, Zt, OP_N, PT, h->Q[3], OP_T, chi));
+  CKS(thin_mul(h, Vt_chi, OP_N, tmp, h->Q[2], OP_N, chi));
+  CKS(thin_mul(h, tmp, OP_N, PT, h->Q[3], OP_T, chi));
   CK(scale_rows_isqrt(h->stream, PT, chi, K, K, h->s_sel));
   // Ptil = S^-1/2 U^H Q2^T Q1^T
-  CKS(thin_mul(h, Ut_chi, OP_C, Zt, h->Q[1], OP_T, chi));
-  CKS(thin_mul(h, Zt, OP_N, Ptil, h->Q[0], OP_T, chi));
+  CKS(thin_mul(h, Ut_chi, OP_C, tmp, h->Q[1], OP_T, chi));
+  CKS(thin_mul(h, tmp, OP_N, Ptil, h->Q[0], OP_T, chi));
   CK(scale_rows_isqrt(h->stream, Ptil, chi, K, K, h->s_sel));
   return IPEPS_OK;
 }

@@ -16,6 +16,8 @@ struct DevStatus {
   // written by kernels that can run out of an iteration budget
   int jacobi_unconverged;  // number of Jacobi calls that hit the sweep budget
   int nonfinite;           // a NaN/Inf met in a norm
+  int jacobi_sweeps;       // sweeps used by all Jacobi calls (accounting)
+  int jacobi_calls;
 };
 
 // ---------------------------------------------------------------------------
@@ -31,10 +33,16 @@ struct GemmBatch {
   long long sA, sB, sC;  // element strides between batch entries
 };
 
-// C[M,N] = alpha * opA(A) opB(B) + beta * C   (complex FP64, CUDA cores)
+// C[M,N] = alpha * opA(A) opB(B) + beta * C   (complex FP64, CUDA cores).  With a
+// workspace, products with few output tiles split K (partials summed in order).
 cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                   int opA, const cplx* B, long long ldb, int opB, cplx beta, cplx* C,
-                  long long ldc, GemmBatch batch = {1, 0, 0, 0});
+                  long long ldc, GemmBatch batch = {1, 0, 0, 0}, cplx* work = nullptr,
+                  long long work_elems = 0);
+// sigma[i] = ||row i|| of G (n rows of length m, stride ldg)
+cudaError_t row_norms(cudaStream_t s, const cplx* G, int n, int m, long long ldg, double* sigma);
+// x <- conj(x)
+cudaError_t conj_inplace(cudaStream_t s, cplx* x, long long n);
 
 // out = alpha * (conj?) permute(in): out axis i is in axis perm[i].
 cudaError_t permute(cudaStream_t s, const cplx* in, cplx* out, int nd, const int* in_dims,
@@ -55,6 +63,8 @@ cudaError_t set_zero(cudaStream_t s, cplx* x, long long n);
 // One-sided (Hestenes) Jacobi on the n rows of G (row length m, row stride ldg):
 // rotates row pairs until mutually orthogonal; optional Vt (n x n) accumulates the
 // same rotations starting from the identity.  sigma[i] = ||row i|| on return.
+// counters: 4 ints of scratch (sweep counters and, for m <= 256, a grid barrier);
+// work: 1 double of scratch.
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
                         DevStatus* st);
@@ -78,6 +88,12 @@ cudaError_t trace_product(cudaStream_t s, const cplx* rho, const cplx* H, int n,
                           int idx, double w);
 cudaError_t trace_normalize(cudaStream_t s, cplx* rho, int n, double* work);
 cudaError_t copy_to_complex(cudaStream_t s, const double* in, cplx* out, long long n);
+
+// Cholesky with dropped pivots (d <= tol * max diagonal) of the Hermitian n x n G:
+// R upper triangular (dropped rows zero); work: n*n scratch.  One CTA.
+cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n, double tol);
+// inverse of upper-triangular R on its kept block (zero where R[i,i] == 0)
+cudaError_t tri_inv(cudaStream_t s, const cplx* R, cplx* Rinv, int n);
 
 // launch accounting (host counter incremented by every launcher)
 void count_launch(int n = 1);

@@ -269,10 +269,148 @@ __global__ void __launch_bounds__(JAC_THREADS)
     grid.sync();
     if (cnt == 0) {
       converged = true;
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->jacobi_sweeps, sweep + 1);
       break;
     }
   }
-  if (!converged && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->jacobi_unconverged, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&st->jacobi_calls, 1);
+    if (!converged) {
+      atomicAdd(&st->jacobi_unconverged, 1);
+      atomicAdd(&st->jacobi_sweeps, max_sweeps);
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi for short rows (m <= 256): one warp per row pair, one pair
+// per CTA, warp-shuffle reductions only, and a light generation barrier
+// between rounds (bounded spin; all CTAs are co-resident by cooperative launch).
+// ---------------------------------------------------------------------------
+constexpr long long BARRIER_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
+                                             unsigned& my_gen) {
+  __syncwarp();
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence();
+    const unsigned g0 = my_gen;
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicExch((unsigned*)gen, g0 + 1);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (clock64() - t0 > BARRIER_WAIT_CYCLES) { ok = false; break; }
+      }
+    }
+    __threadfence();
+  }
+  my_gen += 1;
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  __syncwarp();
+  return ok;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(32)
+    jacobi_small_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt,
+                        int max_sweeps, double tol, int* counters, double* fro2, unsigned* bar,
+                        DevStatus* st) {
+  const int lane = threadIdx.x;
+  unsigned my_gen = 0;
+  const unsigned nb = gridDim.x;
+  bool alive = true;
+  {
+    double v = 0.0;
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+      for (int t = lane; t < m; t += 32) {
+        const cplx x = G[(long long)i * ldg + t];
+        v += x.x * x.x + x.y * x.y;
+      }
+    v = warp_sum(v);
+    if (lane == 0) atomicAdd(fro2, v);
+  }
+  alive = grid_barrier(bar, bar + 1, nb, my_gen);
+  const double negligible = *((volatile double*)fro2) * 1e-30;
+  const int np = (n + 1) & ~1;
+  const int rounds = np - 1, npairs = np / 2;
+  bool converged = false;
+  int sweep = 0;
+  for (; sweep < max_sweeps && alive; ++sweep) {
+    for (int r = 0; r < rounds && alive; ++r) {
+      for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+        int i, j;
+        if (p == 0) {
+          i = np - 1;
+          j = r;
+        } else {
+          i = (r + p) % rounds;
+          j = (r - p + rounds) % rounds;
+        }
+        if (i > j) { const int t = i; i = j; j = t; }
+        if (j >= n) continue;
+        cplx* gi = G + (long long)i * ldg;
+        cplx* gj = G + (long long)j * ldg;
+        double al = 0.0, be = 0.0, gr = 0.0, gim = 0.0;
+        for (int t = lane; t < m; t += 32) {
+          const cplx x = gi[t], y = gj[t];
+          al += x.x * x.x + x.y * x.y;
+          be += y.x * y.x + y.y * y.y;
+          gr += x.x * y.x + x.y * y.y;
+          gim += x.x * y.y - x.y * y.x;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gim = warp_sum(gim);
+        const double g = hypot(gr, gim);
+        if (al > negligible && be > negligible && g > tol * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          const cplx ph = make_double2(gr / g, -gim / g);
+          for (int q = lane; q < m; q += 32) {
+            const cplx x = gi[q], y = cmul(gj[q], ph);
+            gi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+            gj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+          }
+          if (Vt) {
+            cplx* vi = Vt + (long long)i * n;
+            cplx* vj = Vt + (long long)j * n;
+            for (int q = lane; q < n; q += 32) {
+              const cplx x = vi[q], y = cmul(vj[q], ph);
+              vi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+              vj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+            }
+          }
+          if (lane == 0) atomicAdd(&counters[sweep & 1], 1);
+        }
+      }
+      alive = grid_barrier(bar, bar + 1, nb, my_gen);
+    }
+    if (!alive) break;
+    const int cnt = *((volatile int*)&counters[sweep & 1]);
+    if (blockIdx.x == 0 && lane == 0) counters[(sweep + 1) & 1] = 0;
+    alive = grid_barrier(bar, bar + 1, nb, my_gen);
+    if (cnt == 0) {
+      converged = true;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && lane == 0) {
+    atomicAdd(&st->jacobi_calls, 1);
+    atomicAdd(&st->jacobi_sweeps, converged ? sweep + 1 : max_sweeps);
+    if (!converged) atomicAdd(&st->jacobi_unconverged, 1);
+  }
 }
 
 __global__ void row_norms_kernel(const cplx* __restrict__ G, int n, int m, long long ldg,
@@ -412,6 +550,12 @@ __global__ void trace_normalize_kernel(cplx* rho, int n) {
   for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) rho[e] = cmul(rho[e], inv);
 }
 
+__global__ void conj_kernel(cplx* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i].y = -x[i].y;
+}
+
 __global__ void to_complex_kernel(const double* in, cplx* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -479,7 +623,27 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(work, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
-  if (n >= 2) {
+  if (n >= 2 && m <= 256 && n <= 2 * 1024) {
+    // counters[2..3] hold the barrier (count, generation)
+    e = cudaMemsetAsync(counters + 2, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    static int max_small = 0;
+    if (max_small == 0) {
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_small_kernel, 32, 0);
+      max_small = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int npairs = ((n + 1) & ~1) / 2;
+    int grid = npairs < max_small ? npairs : max_small;
+    double tol = (double)m * 2.220446049250313e-16;
+    unsigned* bar = (unsigned*)(counters + 2);
+    void* args[] = {&G, &n, &m, &ldg, &Vt, &max_sweeps, &tol, &counters, &work, &bar, &st};
+    e = cudaLaunchCooperativeKernel((const void*)jacobi_small_kernel, dim3(grid), dim3(32), args, 0, s);
+    count_launch();
+    if (e != cudaSuccess) return e;
+  } else if (n >= 2) {
     static int max_coresident = 0;
     if (max_coresident == 0) {
       int dev = 0, sms = 0, per_sm = 0;
@@ -549,6 +713,18 @@ cudaError_t trace_normalize(cudaStream_t s, cplx* rho, int n, double* work) {
 
 cudaError_t copy_to_complex(cudaStream_t s, const double* in, cplx* out, long long n) {
   to_complex_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t row_norms(cudaStream_t s, const cplx* G, int n, int m, long long ldg, double* sigma) {
+  row_norms_kernel<<<n < 1024 ? n : 1024, 256, 0, s>>>(G, n, m, ldg, sigma);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t conj_inplace(cudaStream_t s, cplx* x, long long n) {
+  conj_kernel<<<grid_for(n), 256, 0, s>>>(x, n);
   count_launch();
   return cudaGetLastError();
 }

@@ -11,6 +11,8 @@ uint64_t launch_counter() { return g_launches.load(); }
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr cplx ONE_C = {1.0, 0.0};
+constexpr cplx ZERO_C = {0.0, 0.0};
 
 __device__ __forceinline__ cplx ld_op(const cplx* p, bool cj) {
   cplx v = *p;
@@ -25,17 +27,27 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
                                                    int opA, const cplx* __restrict__ B,
                                                    long long ldb, int opB, cplx beta,
                                                    cplx* __restrict__ C, long long ldc,
-                                                   long long sA, long long sB, long long sC) {
+                                                   long long sA, long long sB, long long sC,
+                                                   int ksplit) {
   __shared__ cplx As[BK][BM + 1];
   __shared__ cplx Bs[BK][BN + 1];
   const long long bz = blockIdx.z;
-  A += bz * sA;
-  B += bz * sB;
-  C += bz * sC;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool tA = opA & OP_T, cA = opA & OP_CONJ;
   const bool tB = opB & OP_T, cB = opB & OP_CONJ;
+  if (ksplit > 0) {
+    // split-K: entry z sums k in [z*ksplit, min(K, (z+1)*ksplit)) into its own C slice
+    const long long kb = bz * (long long)ksplit;
+    A += tA ? kb * lda : kb;
+    B += tB ? kb : kb * ldb;
+    K = (int)min((long long)ksplit, (long long)K - kb);
+    C += bz * sC;
+  } else {
+    A += bz * sA;
+    B += bz * sB;
+    C += bz * sC;
+  }
   double cr[4][4], ci[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -101,6 +113,29 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
   }
 }
 
+// C = alpha * sum_z W[z] (+ beta C), fixed summation order
+__global__ void splitk_sum_kernel(const cplx* __restrict__ W, int S, int M, int N, cplx alpha, cplx beta,
+                                  cplx* __restrict__ C, long long ldc) {
+  const long long total = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    double r = 0.0, im = 0.0;
+    for (int z = 0; z < S; ++z) {
+      r += W[z * total + e].x;
+      im += W[z * total + e].y;
+    }
+    const int m = (int)(e / N), n = (int)(e % N);
+    cplx* cp = C + (long long)m * ldc + n;
+    double orr = alpha.x * r - alpha.y * im, oi = alpha.x * im + alpha.y * r;
+    if (beta.x != 0.0 || beta.y != 0.0) {
+      const cplx o = *cp;
+      orr += beta.x * o.x - beta.y * o.y;
+      oi += beta.x * o.y + beta.y * o.x;
+    }
+    *cp = make_double2(orr, oi);
+  }
+}
+
 struct PermParams {
   int nd;
   long long odims[8];
@@ -127,15 +162,32 @@ __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ o
 
 cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                   int opA, const cplx* B, long long ldb, int opB, cplx beta, cplx* C,
-                  long long ldc, GemmBatch batch) {
+                  long long ldc, GemmBatch batch, cplx* work, long long work_elems) {
   if (M <= 0 || N <= 0 || batch.count <= 0) return cudaSuccess;
-  if (K <= 0) {
-    // C = beta*C: handled by a zero-K GEMM pass (the loop body never runs)
+  const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  // few output tiles and a long K: split K over the grid (FP64 throughput needs every SM)
+  if (batch.count == 1 && work && tiles < 152 && K >= 4 * BK) {
+    long long S = (2 * 152 + tiles - 1) / tiles;
+    if (S > K / (2 * BK)) S = K / (2 * BK);
+    if (S > 64) S = 64;
+    if (S * M * N > work_elems) S = work_elems / ((long long)M * N);
+    if (S >= 2) {
+      const int ksplit = (int)((K + S - 1) / S);
+      S = (K + ksplit - 1) / ksplit;
+      dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (unsigned)S);
+      zgemm_kernel<<<grid, NT, 0, s>>>(M, N, K, ONE_C, A, lda, opA, B, ldb, opB, ZERO_C, work, N, 0, 0,
+                                       (long long)M * N, ksplit);
+      long long blocks = ((long long)M * N + 255) / 256;
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      splitk_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(work, (int)S, M, N, alpha, beta, C, ldc);
+      count_launch(2);
+      return cudaGetLastError();
+    }
   }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch.count);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   zgemm_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,
-                                   batch.sA, batch.sB, batch.sC);
+                                   batch.sA, batch.sB, batch.sC, 0);
   count_launch();
   return cudaGetLastError();
 }
