@@ -95,6 +95,8 @@ struct ipeps_ctm_s {
   cplx* spareC[2][2]; // replacement buffers for renormalised C1 / C4, per row
   cplx* spareT[2];    // replacement T4 per row
   cplx* Q[4];
+  TcPacked Qp[4][2];  // precision form: corners packed once per cut, [op N, op T]
+  void* Qpmem[4][2];
   cplx* omt;
   cplx* thin[4];      // k x K work
   cplx* PT[2];        // chi x K, projector P transposed, per cut row
@@ -195,6 +197,8 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   for (int i = 0; i < 4; ++i) add(s.C, 16);
   for (int i = 0; i < 2; ++i) add(s.T, 16);
   for (int i = 0; i < 4; ++i) add(s.Q, 16);
+  if (prec != IPEPS_PREC_FP64)
+    for (int i = 0; i < 8; ++i) tot += align_up(tc_packed_bytes(prec, (int)K, (int)K));
   add(s.thin, 16);
   for (int i = 0; i < 4; ++i) add(s.thin, 16);
   for (int i = 0; i < 4; ++i) add(s.proj, 16);
@@ -286,7 +290,7 @@ static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cp
                                       int opA, const cplx* B, long long ldb, int opB, cplx* C,
                                       long long ldc, cplx alpha) {
   // small products (a few tiles of zero padding would dominate) stay FP64
-  if (h->opt.prec != IPEPS_PREC_FP64 && M >= 64 && N >= 32 && K >= 32) {
+  if (h->opt.prec != IPEPS_PREC_FP64 && M >= 64 && N >= 32 && K >= 16) {
     cudaError_t e = tc_zgemm(h->stream, (int)h->opt.prec, M, N, K, alpha, A, lda, opA, B, ldb,
                              opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top);
     if (e == cudaErrorNotSupported) return fail(IPEPS_EUNSUPPORTED, "tensor-core GEMM unavailable for this shape");
@@ -668,6 +672,9 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
     need(h->spareT[i] = carve<cplx>(h, sz.T));
   }
   for (int i = 0; i < 4; ++i) need(h->Q[i] = carve<cplx>(h, sz.Q));
+  if (o->prec != IPEPS_PREC_FP64)
+    for (int i = 0; i < 4; ++i)
+      for (int v = 0; v < 2; ++v) need(h->Qpmem[i][v] = carve<char>(h, tc_packed_bytes(o->prec, h->K, h->K)));
   need(h->omt = carve<cplx>(h, sz.thin));
   for (int i = 0; i < 4; ++i) need(h->thin[i] = carve<cplx>(h, sz.thin));
   for (int i = 0; i < 2; ++i) {
@@ -870,8 +877,38 @@ static ipeps_status thin_mul(ipeps_ctm h, const cplx* in, int opin, cplx* out, c
   return gemm_dispatch(h, rows, h->K, h->K, in, h->K, opin, Qm, h->K, opQ, out, h->K, ONE);
 }
 
+// precision form: in (op opin) times the pre-packed corner q in variant v
+// (0: Q, 1: Q^T); the result is conjugated when conj_out.
+static ipeps_status thin_mul_packed(ipeps_ctm h, const cplx* in, int opin, cplx* out, int q, int v, int rows,
+                                    bool conj_out) {
+  cudaEvent_t a = nullptr;
+  prof_begin(h, &a);
+  cudaError_t e = tc_zgemm_packed(h->stream, (int)h->opt.prec, rows, ONE, in, h->K, opin, h->Qp[q][v], out, h->K,
+                                  conj_out, h->scratch, h->scratch_elems, h->scratch_top);
+  prof_end(h, a, 8.0 * (double)rows * (double)h->K * (double)h->K, 0);
+  CK(e);
+  return IPEPS_OK;
+}
+
+static ipeps_status pack_corners(ipeps_ctm h) {
+  for (int q = 0; q < 4; ++q)
+    for (int v = 0; v < 2; ++v)
+      CK(tc_pack_b(h->stream, (int)h->opt.prec, h->Q[q], h->K, v ? OP_T : OP_N, h->K, h->K, h->Qpmem[q][v],
+                   &h->Qp[q][v]));
+  return IPEPS_OK;
+}
+
+static bool packed_path(ipeps_ctm h) { return h->opt.prec != IPEPS_PREC_FP64; }
+
 // Yt = In * Q3 * Q4^T * Q1 * Q2      (the transpose of X * In^T)
 static ipeps_status apply_XT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
+  if (packed_path(h)) {
+    CKS(thin_mul_packed(h, in, OP_N, h->thin[2], 2, 0, rows, false));
+    CKS(thin_mul_packed(h, h->thin[2], OP_N, h->thin[3], 3, 1, rows, false));
+    CKS(thin_mul_packed(h, h->thin[3], OP_N, h->thin[2], 0, 0, rows, false));
+    CKS(thin_mul_packed(h, h->thin[2], OP_N, out, 1, 0, rows, false));
+    return IPEPS_OK;
+  }
   CKS(thin_mul(h, in, OP_N, h->thin[2], h->Q[2], OP_N, rows));
   CKS(thin_mul(h, h->thin[2], OP_N, h->thin[3], h->Q[3], OP_T, rows));
   CKS(thin_mul(h, h->thin[3], OP_N, h->thin[2], h->Q[0], OP_N, rows));
@@ -879,7 +916,15 @@ static ipeps_status apply_XT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
   return IPEPS_OK;
 }
 // Zt = In * Q2^H * Q1^H * conj(Q4) * Q3^H   (the transpose of X^H * In^T)
+//    = conj( conj(In) * Q2^T * Q1^T * Q4 * Q3^T )
 static ipeps_status apply_XHT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
+  if (packed_path(h)) {
+    CKS(thin_mul_packed(h, in, OP_C, h->thin[2], 1, 1, rows, false));
+    CKS(thin_mul_packed(h, h->thin[2], OP_N, h->thin[3], 0, 1, rows, false));
+    CKS(thin_mul_packed(h, h->thin[3], OP_N, h->thin[2], 3, 0, rows, false));
+    CKS(thin_mul_packed(h, h->thin[2], OP_N, out, 2, 1, rows, true));
+    return IPEPS_OK;
+  }
   CKS(thin_mul(h, in, OP_N, h->thin[2], h->Q[1], OP_H, rows));
   CKS(thin_mul(h, h->thin[2], OP_N, h->thin[3], h->Q[0], OP_H, rows));
   CKS(thin_mul(h, h->thin[3], OP_N, h->thin[2], h->Q[3], OP_C, rows));
@@ -925,7 +970,14 @@ static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Ro
 
 // Precision form orthonormalisation: CholeskyQR2 (directions below ~1e-7 of
 // the largest singular value dropped in the first pass).
-static ipeps_status orth_chol(ipeps_ctm h, cplx* Y, cplx* tmp) {
+static ipeps_status orth_chol(ipeps_ctm h, cplx* Y, cplx* tmp, bool twice) {
+  if (!twice) {
+    // intermediate bases of the subspace iteration only need to stay well
+    // conditioned: one pass (orthogonality ~ eps cond^2 below the dropped 1e-7)
+    CKS(cholqr_pass(h, Y, tmp, nullptr, 1e-14));
+    CK(cudaMemcpyAsync(Y, tmp, (size_t)h->k * h->K * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+    return IPEPS_OK;
+  }
   CKS(cholqr_pass(h, Y, tmp, nullptr, 1e-14));
   CKS(cholqr_pass(h, tmp, Y, nullptr, 1e-14));
   return IPEPS_OK;
@@ -966,18 +1018,20 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   CKS(enlarged_corners(h, f, x, y));
   const int k = h->k, K = h->K, chi = h->chi;
   const bool fp64 = h->opt.prec == IPEPS_PREC_FP64;
+  if (!fp64) CKS(pack_corners(h));
   cplx* Qt = h->thin[0];
   cplx* Zt = h->thin[1];
-  auto orth_any = [&](cplx* Y) -> ipeps_status {
-    return fp64 ? orth(h, Y) : orth_chol(h, Y, h->thin[2]);
+  auto orth_any = [&](cplx* Y, bool last) -> ipeps_status {
+    return fp64 ? orth(h, Y) : orth_chol(h, Y, h->thin[2], last);
   };
+  const int q = h->opt.rsvd_power;
   CKS(apply_XT(h, h->omt, Qt, k));
-  CKS(orth_any(Qt));
-  for (int it = 0; it < h->opt.rsvd_power; ++it) {
+  CKS(orth_any(Qt, q == 0));
+  for (int it = 0; it < q; ++it) {
     CKS(apply_XHT(h, Qt, Zt, k));
-    CKS(orth_any(Zt));
+    CKS(orth_any(Zt, false));
     CKS(apply_XT(h, Zt, Qt, k));
-    CKS(orth_any(Qt));
+    CKS(orth_any(Qt, it == q - 1));
   }
   // W = X^H Q (K x k) stored as Wt; its SVD W = U_w S V_w^H gives X ~ (Q V_w) S U_w^H
   CKS(apply_XHT(h, Qt, Zt, k));
@@ -1002,13 +1056,22 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   // U_chi^T = (V_w[:, sel])^T Q^T
   CK(gather_rows(h->stream, h->Vt, k, h->Gsel, k, h->perm, h->sigma, chi, k, false));
   CKS(gemm_dispatch(h, chi, K, k, h->Gsel, k, OP_N, Qt, K, OP_N, Ut_chi, K, ONE));
-  // P^T = S^-1/2 V^T Q3 Q4^T
-  CKS(thin_mul(h, Vt_chi, OP_N, tmp, h->Q[2], OP_N, chi));
-  CKS(thin_mul(h, tmp, OP_N, PT, h->Q[3], OP_T, chi));
+  // P^T = S^-1/2 V^T Q3 Q4^T ;  Ptil = S^-1/2 U^H Q2^T Q1^T
+  if (!fp64) {
+    CKS(thin_mul_packed(h, Vt_chi, OP_N, tmp, 2, 0, chi, false));
+    CKS(thin_mul_packed(h, tmp, OP_N, PT, 3, 1, chi, false));
+  } else {
+    CKS(thin_mul(h, Vt_chi, OP_N, tmp, h->Q[2], OP_N, chi));
+    CKS(thin_mul(h, tmp, OP_N, PT, h->Q[3], OP_T, chi));
+  }
   CK(scale_rows_isqrt(h->stream, PT, chi, K, K, h->s_sel));
-  // Ptil = S^-1/2 U^H Q2^T Q1^T
-  CKS(thin_mul(h, Ut_chi, OP_C, tmp, h->Q[1], OP_T, chi));
-  CKS(thin_mul(h, tmp, OP_N, Ptil, h->Q[0], OP_T, chi));
+  if (!fp64) {
+    CKS(thin_mul_packed(h, Ut_chi, OP_C, tmp, 1, 1, chi, false));
+    CKS(thin_mul_packed(h, tmp, OP_N, Ptil, 0, 1, chi, false));
+  } else {
+    CKS(thin_mul(h, Ut_chi, OP_C, tmp, h->Q[1], OP_T, chi));
+    CKS(thin_mul(h, tmp, OP_N, Ptil, h->Q[0], OP_T, chi));
+  }
   CK(scale_rows_isqrt(h->stream, Ptil, chi, K, K, h->s_sel));
   return IPEPS_OK;
 }

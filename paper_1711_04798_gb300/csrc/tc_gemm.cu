@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                    int kb_total, int kb_per_split, int M, int Nr, cplx alpha, cplx* __restrict__ C,
-                   long long ldc, float* __restrict__ partial, int Nrp, long long pstride) {
+                   long long ldc, float* __restrict__ partial, int Nrp, long long pstride, int conj_out) {
   using K_ = Cfg<PREC>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -231,8 +231,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int t = 0; t < 8; ++t) {
           if (col + 2 * t < Nr) {
             const double re = v[2 * t], im = v[2 * t + 1];
-            C[(long long)row * ldc + (col >> 1) + t] =
-                make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+            const double orr = alpha.x * re - alpha.y * im, oi = alpha.x * im + alpha.y * re;
+            C[(long long)row * ldc + (col >> 1) + t] = make_double2(orr, conj_out ? -oi : oi);
           }
         }
       }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // C[m,n] = alpha * sum_z P[z][m][2n .. 2n+1]  (fixed summation order)
 __global__ void splitk_reduce_kernel(const float* __restrict__ P, int S, long long pstride, int Nrp, int M,
-                                     int N, cplx alpha, cplx* __restrict__ C, long long ldc) {
+                                     int N, cplx alpha, cplx* __restrict__ C, long long ldc, int conj_out) {
   const long long total = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -258,7 +258,8 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ P, int S, long lo
       re += p.x;
       im += p.y;
     }
-    C[(long long)m * ldc + n] = make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+    const double oi = alpha.x * im + alpha.y * re;
+    C[(long long)m * ldc + n] = make_double2(alpha.x * re - alpha.y * im, conj_out ? -oi : oi);
   }
 }
 
@@ -324,6 +325,47 @@ __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB
   }
 }
 
+// Br^T[nr, kr] for an op-N (or op-C) operand B[k, n] (row-major, k x n):
+// 32 x 32 complex tiles through shared memory so reads run along n and
+// writes along kr (the plain kernel would read with stride ldb).
+template <int PREC>
+__global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int conj, int N, int K, int Nrp,
+                                 int Krp, void* __restrict__ o0, void* __restrict__ o1) {
+  __shared__ cplx tile[32][33];
+  const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i, n = n0 + threadIdx.x;
+    cplx v = make_double2(0.0, 0.0);
+    if (k < K && n < N) {
+      v = B[(long long)k * ldb + n];
+      if (conj) v.y = -v.y;
+    }
+    tile[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 64; r += blockDim.y) {
+    const int nr = 2 * n0 + r;
+    if (nr >= Nrp) continue;
+    const int nl = r >> 1, b = r & 1;
+    for (int c = threadIdx.x; c < 64; c += 32) {
+      const int kr = 2 * k0 + c;
+      if (kr >= Krp) continue;
+      const int kl = c >> 1, a = c & 1;
+      const cplx v = tile[kl][nl];
+      const double x = (a == b) ? v.x : (a == 0 ? v.y : -v.y);
+      const long long e = (long long)nr * Krp + kr;
+      if (PREC == PREC_TF32) {
+        ((uint32_t*)o0)[e] = to_tf32((float)x);
+      } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+        const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+        ((__nv_bfloat16*)o0)[e] = hi;
+        ((__nv_bfloat16*)o1)[e] = lo;
+      }
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 cudaError_t get_encoder() {
@@ -358,8 +400,30 @@ unsigned grid_for(long long n) {
 }
 
 template <int PREC>
+cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, int N, int K, long long Nrp,
+                       long long Krp, void* b0, void* b1) {
+  if (opB & OP_T) {
+    pack_b_kernel<PREC><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
+  } else {
+    dim3 grid((unsigned)((Nrp / 2 + 31) / 32), (unsigned)((Krp / 2 + 31) / 32));
+    pack_b_tr_kernel<PREC><<<grid, dim3(32, 8), 0, s>>>(B, ldb, (opB & OP_CONJ) ? 1 : 0, N, K, (int)Nrp, (int)Krp,
+                                                        b0, b1);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int PREC>
+void padded(int N, int K, long long* Nrp, long long* Krp) {
+  using K_ = Cfg<PREC>;
+  *Krp = (2LL * K + K_::BK - 1) / K_::BK * K_::BK;
+  *Nrp = (2LL * N + BN - 1) / BN * BN;
+}
+
+template <int PREC>
 cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
-                const cplx* B, long long ldb, int opB, cplx* C, long long ldc, char* scratch, size_t scratch_bytes) {
+                const cplx* B, long long ldb, int opB, const TcPacked* pre, cplx* C, long long ldc, bool conj_out,
+                char* scratch, size_t scratch_bytes) {
   using K_ = Cfg<PREC>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -368,8 +432,9 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     attr_set = true;
   }
   const long long Mp = (M + BM - 1) / BM * BM;
-  const long long Kr = 2LL * K, Krp = (Kr + K_::BK - 1) / K_::BK * K_::BK;
-  const long long Nr = 2LL * N, Nrp = (Nr + BN - 1) / BN * BN;
+  long long Nrp, Krp;
+  padded<PREC>(N, K, &Nrp, &Krp);
+  const long long Nr = 2LL * N;
   const int kb_total = (int)(Krp / K_::BK);
   const long long tiles = (Mp / BM) * (Nrp / BN);
   int S = 1;
@@ -381,7 +446,8 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   const int kps = (kb_total + S - 1) / S;
   S = (kb_total + kps - 1) / kps;  // no empty split
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-  const size_t abytes = al((size_t)Mp * Krp * K_::ELEM), bbytes = al((size_t)Nrp * Krp * K_::ELEM);
+  const size_t abytes = al((size_t)Mp * Krp * K_::ELEM);
+  const size_t bbytes = pre ? 0 : al((size_t)Nrp * Krp * K_::ELEM);
   const size_t pbytes = S > 1 ? al((size_t)S * Mp * Nrp * 4) : 0;
   char* p = (char*)(((uintptr_t)scratch + 1023) & ~(uintptr_t)1023);
   const size_t need = K_::NOPS * (abytes + bbytes) + pbytes + 1024;
@@ -392,10 +458,16 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   char* b1 = b0 + bbytes;
   float* part = S > 1 ? (float*)(b0 + K_::NOPS * bbytes) : nullptr;
   pack_a_kernel<PREC><<<grid_for(Mp * Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)Mp, (int)Krp, a0, a1);
-  pack_b_kernel<PREC><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
-  count_launch(2);
-  cudaError_t e = get_encoder();
-  if (e != cudaSuccess) return e;
+  count_launch();
+  cudaError_t e;
+  if (pre) {
+    if (pre->prec != PREC || pre->N != N || pre->K != K) return cudaErrorInvalidValue;
+    b0 = (char*)pre->b0;
+    b1 = (char*)pre->b1;
+  } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, Nrp, Krp, b0, b1)) != cudaSuccess) {
+    return e;
+  }
+  if ((e = get_encoder()) != cudaSuccess) return e;
   CUtensorMap mA0, mA1, mB0, mB1;
   if ((e = make_map(&mA0, a0, PREC, Mp, Krp, BM)) != cudaSuccess) return e;
   if ((e = make_map(&mB0, b0, PREC, Nrp, Krp, BN)) != cudaSuccess) return e;
@@ -407,12 +479,12 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   }
   dim3 grid((unsigned)(Nrp / BN), (unsigned)(Mp / BM), (unsigned)S);
   tc_gemm_kernel<PREC><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mB0, mB1, kb_total, kps, M, (int)Nr, alpha, C,
-                                                         ldc, part, (int)Nrp, (long long)Mp * Nrp);
+                                                         ldc, part, (int)Nrp, (long long)Mp * Nrp, conj_out ? 1 : 0);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (S > 1) {
     splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, (long long)Mp * Nrp, (int)Nrp, M, N,
-                                                                    alpha, C, ldc);
+                                                                    alpha, C, ldc, conj_out ? 1 : 0);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -427,8 +499,58 @@ cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, 
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
-  if (prec == PREC_TF32) return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, C, ldc, base, bytes);
-  if (prec == PREC_BF16X3) return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, C, ldc, base, bytes);
+  if (prec == PREC_TF32)
+    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes);
+  if (prec == PREC_BF16X3)
+    return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes);
+  return cudaErrorNotSupported;
+}
+
+size_t tc_packed_bytes(int prec, int N, int K) {
+  long long Nrp, Krp;
+  if (prec == PREC_TF32) {
+    padded<PREC_TF32>(N, K, &Nrp, &Krp);
+    return (size_t)Nrp * Krp * 4 + 2048;
+  }
+  padded<PREC_BF16X3>(N, K, &Nrp, &Krp);
+  return 2 * ((size_t)Nrp * Krp * 2 + 1024) + 2048;
+}
+
+cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, int opB, int N, int K, void* mem,
+                      TcPacked* out) {
+  long long Nrp, Krp;
+  char* p = (char*)(((uintptr_t)mem + 1023) & ~(uintptr_t)1023);
+  out->prec = prec;
+  out->N = N;
+  out->K = K;
+  if (prec == PREC_TF32) {
+    padded<PREC_TF32>(N, K, &Nrp, &Krp);
+    out->b0 = p;
+    out->b1 = p;
+    return pack_b_any<PREC_TF32>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1);
+  }
+  if (prec == PREC_BF16X3) {
+    padded<PREC_BF16X3>(N, K, &Nrp, &Krp);
+    const size_t half = ((size_t)Nrp * Krp * 2 + 1023) & ~(size_t)1023;
+    out->b0 = p;
+    out->b1 = p + half;
+    return pack_b_any<PREC_BF16X3>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1);
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const cplx* A, long long lda, int opA,
+                            const TcPacked& B, cplx* C, long long ldc, bool conj_out, cplx* scratch,
+                            long long scratch_elems, long long scratch_top) {
+  if (M <= 0) return cudaSuccess;
+  char* base = (char*)(scratch + scratch_top);
+  const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
+  if (prec == PREC_TF32)
+    return run<PREC_TF32>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out, base,
+                          bytes);
+  if (prec == PREC_BF16X3)
+    return run<PREC_BF16X3>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out,
+                            base, bytes);
   return cudaErrorNotSupported;
 }
 

@@ -11,6 +11,22 @@ cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, 
                      long long lda, int opA, const cplx* B, long long ldb, int opB, cplx* C,
                      long long ldc, cplx* scratch, long long scratch_elems, long long scratch_top);
 
+// A B-role operand (op(B) is K x N complex) packed once as Br^T (2N x 2K real,
+// K-major, padded), reusable across products.
+struct TcPacked {
+  int prec;
+  long long N, K;
+  void* b0;  // TF32 values, or BF16 hi
+  void* b1;  // BF16 lo (== b0 for TF32)
+};
+size_t tc_packed_bytes(int prec, int N, int K);
+cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, int opB, int N, int K, void* mem,
+                      TcPacked* out);
+// C = alpha opA(A) B  (or its complex conjugate when conj_out), B pre-packed
+cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const cplx* A, long long lda, int opA,
+                            const TcPacked& B, cplx* C, long long ldc, bool conj_out, cplx* scratch,
+                            long long scratch_elems, long long scratch_top);
+
 // number of bounded-wait timeouts inside tensor-core kernels since the last
 // call (resets the counter); synchronous.
 int tc_take_errors();

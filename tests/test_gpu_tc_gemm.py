@@ -39,7 +39,7 @@ def _op(X, op):
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("shape", [(130, 77, 300), (1, 1000, 700), (116, 600, 2500), (300, 129, 33)])
-@pytest.mark.parametrize("ops", [(0, 0), (1, 3), (2, 1)])
+@pytest.mark.parametrize("ops", [(0, 0), (1, 3), (2, 1), (3, 2)])
 def test_tc_gemm_matches_complex128(prec, shape, ops):
     M, N, K = shape
     rng = np.random.default_rng(M * 7 + N + K + prec)
