@@ -76,6 +76,26 @@ static TV tv(cplx* p, std::initializer_list<int> dims) {
   return t;
 }
 
+// Resources of one projector computation.  The two cuts of a unit-cell
+// column are independent; the second one runs on its own stream with its own
+// copy of these buffers, swapped into the handle while it is being enqueued.
+struct Lane {
+  cudaStream_t stream;
+  cplx* Q[4];
+  TcPacked Qp[4][2];
+  void* Qpmem[4][2];
+  cplx* thin[4];
+  cplx* Vt;
+  cplx* Gsel;
+  double* sigma;
+  double* s_sel;
+  int* perm;
+  int* counters;
+  double* dwork;
+  cplx* scratch;
+  long long scratch_elems, scratch_top;
+};
+
 struct ipeps_ctm_s {
   int Lx, Ly, d, D, D2, chi, K, k, ntens;
   int pattern[4];
@@ -115,6 +135,9 @@ struct ipeps_ctm_s {
   cplx* scratch;      // bump-allocated per operation
   long long scratch_elems, scratch_top;
   uint64_t launches_at_create;
+  bool has_alt;       // second lane available (Ly or Lx == 2)
+  Lane alt;
+  cudaEvent_t ev_fork, ev_join;
   // optional per-kernel-class timing (CUDA events on the handle's stream)
   bool profiling;
   long long jac_sweeps, jac_calls;  // accumulated while profiling
@@ -148,6 +171,29 @@ static void prof_end(ipeps_ctm h, cudaEvent_t a, double flops, int kind) {
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// swap the handle's active projector resources with the second lane
+static void swap_lane(ipeps_ctm h) {
+  std::swap(h->stream, h->alt.stream);
+  for (int i = 0; i < 4; ++i) {
+    std::swap(h->Q[i], h->alt.Q[i]);
+    std::swap(h->thin[i], h->alt.thin[i]);
+    for (int v = 0; v < 2; ++v) {
+      std::swap(h->Qp[i][v], h->alt.Qp[i][v]);
+      std::swap(h->Qpmem[i][v], h->alt.Qpmem[i][v]);
+    }
+  }
+  std::swap(h->Vt, h->alt.Vt);
+  std::swap(h->Gsel, h->alt.Gsel);
+  std::swap(h->sigma, h->alt.sigma);
+  std::swap(h->s_sel, h->alt.s_sel);
+  std::swap(h->perm, h->alt.perm);
+  std::swap(h->counters, h->alt.counters);
+  std::swap(h->dwork, h->alt.dwork);
+  std::swap(h->scratch, h->alt.scratch);
+  std::swap(h->scratch_elems, h->alt.scratch_elems);
+  std::swap(h->scratch_top, h->alt.scratch_top);
+}
 
 template <class Tp>
 static Tp* carve(ipeps_ctm h, size_t count) {
@@ -214,6 +260,18 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   add(16, 16);
   add(1, sizeof(DevStatus));
   add(s.scratch, 16);
+  // second projector lane (the other cut of a column runs concurrently)
+  for (int i = 0; i < 4; ++i) add(s.Q, 16);
+  if (prec != IPEPS_PREC_FP64)
+    for (int i = 0; i < 8; ++i) tot += align_up(tc_packed_bytes(prec, (int)K, (int)K));
+  for (int i = 0; i < 4; ++i) add(s.thin, 16);
+  add((long long)k * k, 16);
+  add((long long)chi * k, 16);
+  add(std::max(k, 4096), 8);
+  add(std::max(k, 4096), 8);
+  add(std::max(k, 4096), 4);
+  add(4, 4);
+  add(4096, 8);
   s.total = tot + 4096;
   return s;
 }
@@ -695,6 +753,18 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   need(h->scratch = carve<cplx>(h, sz.scratch));
   h->scratch_elems = sz.scratch;
   h->scratch_top = 0;
+  for (int i = 0; i < 4; ++i) need(h->alt.Q[i] = carve<cplx>(h, sz.Q));
+  if (o->prec != IPEPS_PREC_FP64)
+    for (int i = 0; i < 4; ++i)
+      for (int v = 0; v < 2; ++v) need(h->alt.Qpmem[i][v] = carve<char>(h, tc_packed_bytes(o->prec, h->K, h->K)));
+  for (int i = 0; i < 4; ++i) need(h->alt.thin[i] = carve<cplx>(h, sz.thin));
+  need(h->alt.Vt = carve<cplx>(h, (size_t)h->k * h->k));
+  need(h->alt.Gsel = carve<cplx>(h, (size_t)h->chi * h->k));
+  need(h->alt.sigma = carve<double>(h, std::max(h->k, 4096)));
+  need(h->alt.s_sel = carve<double>(h, std::max(h->k, 4096)));
+  need(h->alt.perm = carve<int>(h, std::max(h->k, 4096)));
+  need(h->alt.counters = carve<int>(h, 4));
+  need(h->alt.dwork = carve<double>(h, 4096));
   if (!ok) {
     if (h->own_mem) cudaFree(h->base);
     delete h;
@@ -702,6 +772,11 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   }
   h->launches_at_create = launch_counter();
   ipeps_status st = IPEPS_OK;
+  h->has_alt = false;
+  if (cudaStreamCreateWithFlags(&h->alt.stream, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess)
+    h->has_alt = true;
   // host -> device copies of the tensors (real inputs promoted to complex)
   std::vector<double> buf;
   for (int t = 0; t < h->ntens && st == IPEPS_OK; ++t) {
@@ -770,6 +845,12 @@ extern "C" void ipeps_ctm_destroy(ipeps_ctm h) {
     cudaEventDestroy(r.b);
   }
   for (auto e : h->pool) cudaEventDestroy(e);
+  if (h->has_alt) {
+    cudaStreamSynchronize(h->alt.stream);
+    cudaStreamDestroy(h->alt.stream);
+    cudaEventDestroy(h->ev_fork);
+    cudaEventDestroy(h->ev_join);
+  }
   if (h->own_mem) cudaFree(h->base);
   delete h;
 }
@@ -1081,7 +1162,30 @@ static ipeps_status left_move(ipeps_ctm h, int f) {
   frame_dims(h, f, &Lx, &Ly);
   const int c = h->chi, D2 = h->D2;
   for (int x = 0; x < Lx; ++x) {
-    for (int y = 0; y < Ly; ++y) CKS(projectors(h, f, x, y, h->PT[y], h->Ptil[y]));
+    if (Ly == 2 && h->has_alt) {
+      // fork: cut y = 0 on the handle's stream, cut y = 1 on the second lane
+      const long long full = h->scratch_elems, half = (full / 2) & ~1023LL;
+      CK(cudaEventRecord(h->ev_fork, h->stream));
+      CK(cudaStreamWaitEvent(h->alt.stream, h->ev_fork, 0));
+      h->scratch_elems = half;
+      h->alt.scratch = h->scratch + half;
+      h->alt.scratch_elems = full - half;
+      h->alt.scratch_top = 0;
+      ipeps_status s0 = projectors(h, f, x, 0, h->PT[0], h->Ptil[0]);
+      ipeps_status s1 = IPEPS_OK;
+      if (s0 == IPEPS_OK) {
+        swap_lane(h);
+        s1 = projectors(h, f, x, 1, h->PT[1], h->Ptil[1]);
+        swap_lane(h);
+      }
+      h->scratch_elems = full;
+      CK(cudaEventRecord(h->ev_join, h->alt.stream));
+      CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+      CKS(s0);
+      CKS(s1);
+    } else {
+      for (int y = 0; y < Ly; ++y) CKS(projectors(h, f, x, y, h->PT[y], h->Ptil[y]));
+    }
     for (int y = 0; y < Ly; ++y) {
       const int ym = (y - 1 + Ly) % Ly;
       cplx* w1 = scratch_alloc(h, (long long)c * D2 * c);
