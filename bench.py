@@ -38,6 +38,10 @@ def parse():
     p.add_argument("--D", type=int, default=5)
     p.add_argument("--chi", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="single", choices=["single", "scan"],
+                   help="single: one D=5 chi=100 instance; scan: 64-instance batched phase-diagram scan")
+    p.add_argument("--instances", type=int, default=64)
+    p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
 
 
@@ -313,6 +317,114 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+SCAN_DESC = ("batched scan: {n} independent instances on the line Jx=Jy=(2-Jz)/2, Jz_k=2k/{n1}; "
+             "D_k in {{3,4,5}} and chi_k in {{32,48,64,100}} round-robin (r = seed mod 12); 2x2 cell, d=8, "
+             "complex product state + 0.1 complex-normal noise per instance")
+
+
+def run_scan(args, rank, world, local_rank):
+    """Batched scan: every instance advanced by one graph launch per sweep."""
+    import torch
+    import synth
+    from paper_1711_04798_gb300 import Batch, CTM
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    insts = synth.scan(seed=rank, n=args.instances)
+    t0 = time.perf_counter()
+    b = Batch(insts, tune=not args.no_tune, prec=args.prec)
+    create_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b.sweep(1)  # captures the sweep graph
+    capture_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup - 1, 0)):
+        b.sweep(1)
+    s = torch.cuda.ExternalStream(b.stream())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = b.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(s)
+        for _ in range(args.steps):
+            b.sweep(1)
+        e1.record(s)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = b.launch_count() - l0
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    n = len(insts)
+    value = world * n * MOVES_PER_STEP * args.steps / (ms_max * 1e-3)
+    energies = b.energies([i["J"] for i in insts])
+    tuning = b.tuning()
+    b.close()
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    # one representative per (D, chi) class, one sweep each, run alone:
+    # sequential estimates for the same precision and for the plain FP64 path
+    classes = {}
+    for i in insts:
+        classes.setdefault((i["D"], i["chi"]), []).append(i)
+    stream = torch.cuda.current_stream()
+    seq_prec = seq_fp64 = 0.0
+    dE = 0.0
+    per_class = []
+    for (D, chi), members in sorted(classes.items()):
+        rep = members[0]
+        times, es = {}, {}
+        for prec in (args.prec, "fp64"):
+            g = CTM(rep["tensors"], rep["pattern"], chi, prec=prec, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            g.sweep(1)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            times[prec] = f0.elapsed_time(f1) * 1e-3
+            es[prec] = g.energy(rep["J"])
+            g.close()
+        seq_prec += len(members) * times[args.prec]
+        seq_fp64 += len(members) * times["fp64"]
+        dE = max(dE, abs(es[args.prec] - es["fp64"]))
+        per_class.append({"D": D, "chi": chi, "count": len(members), "sweep_s_" + args.prec: times[args.prec],
+                          "sweep_s_fp64": times["fp64"], "abs_dE_1sweep": abs(es[args.prec] - es["fp64"])})
+    seq_prec_rate = n * MOVES_PER_STEP / seq_prec
+    seq_fp64_rate = n * MOVES_PER_STEP / seq_fp64
+    line = {
+        "metric": METRIC, "value": value, "unit": "instance-moves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": SCAN_DESC.format(n=n, n1=n - 1), "step": "one sweep (L,R,U,D) of every instance",
+                   "prec": args.prec, "autotune": not args.no_tune,
+                   "l2": "working set > L2 (the enlarged corners of all instances, tens of GB)"},
+        "scan": {"instances": n, "create_s": create_s, "first_sweep_with_capture_s": capture_s,
+                 "tuned_shapes": len(tuning),
+                 "tuned_speedup_vs_default": (sum(t["default_us"] for t in tuning) / sum(t["us"] for t in tuning))
+                 if tuning else None,
+                 "sequential_same_prec_inst_moves_per_s": seq_prec_rate,
+                 "sequential_fp64_inst_moves_per_s": seq_fp64_rate,
+                 "speedup_vs_sequential_same_prec": value / seq_prec_rate,
+                 "speedup_vs_sequential_fp64": value / seq_fp64_rate,
+                 "max_abs_dE_vs_fp64_one_sweep": dE, "classes": per_class,
+                 "energy_range": [float(min(energies)), float(max(energies))]},
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -320,6 +432,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "scan":
+        run_scan(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

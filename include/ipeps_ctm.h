@@ -227,6 +227,68 @@ ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA
  * ECUDA, ETIMEOUT (Jacobi sweep budget), with ipeps_last_error(). */
 ipeps_status ipeps_corner_spectrum_noalloc(const double* C_dev, int chi, double* s_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched scan: n independent instances (e.g. the coupling points of a
+ * phase-diagram scan, Sec. VI, each with its own tensors, D and chi) advanced
+ * together.  Each instance is an ordinary handle with its own device memory
+ * (allocated at create) and its own stream; a batch move is captured once per
+ * direction as one CUDA graph with one branch per instance and replayed, so
+ * one graph launch advances every instance and the GPU overlaps their small
+ * contractions.  Tensor-core products take the tile shape (128 x 128 or
+ * 128 x 256 output tiles) and K-split count chosen per product shape by the
+ * library's autotuner.
+ * ------------------------------------------------------------------------- */
+typedef struct ipeps_batch_s* ipeps_batch;
+
+/* Create the n instances: cells[i], opts[i] as for ipeps_ctm_create (the
+ * stream and workspace fields are ignored: the batch owns one stream per
+ * instance and each instance allocates its own memory).  With tune != 0 the
+ * autotuner times every candidate tile choice of every distinct tensor-core
+ * product shape during one sweep of each instance (cuts in sequence), after
+ * which each environment is re-initialised by the trace initialisation; with
+ * tune == 0 the default choice applies.  Errors: as ipeps_ctm_create, with
+ * the failing instance named in ipeps_last_error(); nothing is left allocated
+ * on error. */
+ipeps_status ipeps_batch_create(int n, const ipeps_cell* cells, const ipeps_options* opts, int tune,
+                                ipeps_batch* out);
+
+/* `count` moves (ipeps_dir, IPEPS_SWEEP = L, R, U, D) of every instance.  The
+ * first call per direction captures the graph; every call replays it `count`
+ * times and returns when all instances are done.  Each instance computes
+ * exactly what ipeps_ctm_move computes on it.  Errors: the first failing
+ * instance's status (ETIMEOUT, ENUMERIC, ...), named in ipeps_last_error(). */
+ipeps_status ipeps_batch_move(ipeps_batch b, int dir, int count);
+
+/* Energy per spin of every instance (as ipeps_energy), J = n x {Jx, Jy, Jz},
+ * e_out = n doubles; both caller-owned host arrays. */
+ipeps_status ipeps_batch_energy(ipeps_batch b, const double* J, double* e_out);
+
+/* Instance i as a handle for every single-instance readout (spectra, RDMs,
+ * kappa, boundary rho, env_get).  Owned by the batch: do not destroy it; do
+ * not move it while a batch move of the same batch is in flight.  NULL if i is
+ * out of range. */
+ipeps_ctm ipeps_batch_instance(ipeps_batch b, int i);
+
+/* Autotuner table: number of product shapes tuned, and entry i as fields =
+ * {prec, M, N, K, n-tile width, K splits} (M x N x K the complex product) and
+ * us = {time of the chosen tile, time of the default choice} in microseconds. */
+int ipeps_batch_tuning_size(ipeps_batch b);
+ipeps_status ipeps_batch_tuning_entry(ipeps_batch b, int i, int fields[6], double us[2]);
+
+/* Kernels the batch launched since create (graph replays count every kernel
+ * inside the graph). */
+uint64_t ipeps_batch_launch_count(ipeps_batch b);
+
+/* Block until all work of the batch is done. */
+ipeps_status ipeps_batch_sync(ipeps_batch b);
+
+/* The batch's own stream (cudaStream_t, owned by the batch): the graph of
+ * every batch move is launched on it, so events recorded on it before and
+ * after ipeps_batch_move bracket the whole move on the device. */
+void* ipeps_batch_stream(ipeps_batch b);
+
+void ipeps_batch_destroy(ipeps_batch b);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char* ipeps_last_error(void);
 

@@ -21,6 +21,9 @@ EXPORTS = [
     "ipeps_ctm_converge", "ipeps_rdm", "ipeps_energy", "ipeps_kappa", "ipeps_fidelity",
     "ipeps_boundary_rho", "ipeps_ctm_env_get", "ipeps_ctm_sync", "ipeps_ctm_launch_count",
     "ipeps_ctm_destroy", "ipeps_last_error", "ipeps_ctm_profile", "ipeps_ctm_profile_read",
+    "ipeps_batch_create", "ipeps_batch_move", "ipeps_batch_energy", "ipeps_batch_instance",
+    "ipeps_batch_tuning_size", "ipeps_batch_tuning_entry", "ipeps_batch_launch_count",
+    "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream",
 ]
 
 
@@ -78,9 +81,24 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_ctm_destroy.argtypes = [P]
     lib.ipeps_ctm_destroy.restype = None
     lib.ipeps_last_error.restype = C.c_char_p
+    lib.ipeps_batch_create.argtypes = [I, C.POINTER(Cell), C.POINTER(Options), I, C.POINTER(P)]
+    lib.ipeps_batch_move.argtypes = [P, I, I]
+    lib.ipeps_batch_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_batch_instance.argtypes = [P, I]
+    lib.ipeps_batch_instance.restype = P
+    lib.ipeps_batch_tuning_size.argtypes = [P]
+    lib.ipeps_batch_tuning_entry.argtypes = [P, I, C.POINTER(I), C.POINTER(D)]
+    lib.ipeps_batch_launch_count.argtypes = [P]
+    lib.ipeps_batch_launch_count.restype = C.c_uint64
+    lib.ipeps_batch_sync.argtypes = [P]
+    lib.ipeps_batch_stream.argtypes = [P]
+    lib.ipeps_batch_stream.restype = P
+    lib.ipeps_batch_destroy.argtypes = [P]
+    lib.ipeps_batch_destroy.restype = None
     for name in EXPORTS:
         if name not in ("ipeps_default_options", "ipeps_ctm_destroy", "ipeps_last_error",
-                        "ipeps_ctm_launch_count"):
+                        "ipeps_ctm_launch_count", "ipeps_batch_instance", "ipeps_batch_launch_count",
+                        "ipeps_batch_destroy", "ipeps_batch_stream"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -93,6 +111,48 @@ def _check(st: int):
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _make_cell(tensors, pattern, bra=None):
+    """ipeps_cell for the host tensors (kept alive by the returned tuple)."""
+    Ly, Lx = len(pattern), len(pattern[0])
+    d, D = tensors[0].shape[0], tensors[0].shape[1]
+    cplx = any(np.iscomplexobj(t) for t in tensors) or (bra is not None)
+    dt = np.complex128 if cplx else np.float64
+    keep = [np.ascontiguousarray(t, dtype=dt) for t in tensors]
+    keep_bra = [np.ascontiguousarray(t, dtype=dt) for t in bra] if bra is not None else None
+    cell = Cell()
+    cell.Lx, cell.Ly = Lx, Ly
+    for y in range(Ly):
+        for x in range(Lx):
+            cell.pattern[y * Lx + x] = pattern[y][x]
+    cell.n_tensors = len(tensors)
+    cell.d, cell.D = d, D
+    cell.dtype = 1 if cplx else 0
+    ptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in keep])
+    cell.tensors = C.cast(ptrs, C.POINTER(C.c_void_p))
+    bptrs = None
+    if keep_bra is not None:
+        bptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in keep_bra])
+        cell.tensors_bra = C.cast(bptrs, C.POINTER(C.c_void_p))
+    return cell, (keep, keep_bra, ptrs, bptrs, dt)
+
+
+def _make_options(lib, chi, prec="fp64", oversample=16, power=2, cutoff=0.0, orth_tol=1e-14,
+                  omega_seed=7, jacobi_max_sweeps=40, stream=None, workspace=None):
+    opt = Options()
+    lib.ipeps_default_options(C.byref(opt))
+    opt.chi = chi
+    opt.prec = PREC[prec]
+    opt.rsvd_oversample, opt.rsvd_power = oversample, power
+    opt.svd_cutoff, opt.orth_tol = cutoff, orth_tol
+    opt.omega_seed = omega_seed
+    opt.jacobi_max_sweeps = jacobi_max_sweeps
+    opt.stream = stream
+    if workspace is not None:
+        opt.workspace = C.c_void_p(workspace[0])
+        opt.workspace_bytes = workspace[1]
+    return opt
 
 
 class CTM:
@@ -108,44 +168,30 @@ class CTM:
                  workspace=None):
         lib = load_library()
         self.lib = lib
-        Ly, Lx = len(pattern), len(pattern[0])
-        d, D = tensors[0].shape[0], tensors[0].shape[1]
-        cplx = any(np.iscomplexobj(t) for t in tensors) or (bra is not None)
-        dt = np.complex128 if cplx else np.float64
-        self._keep = [np.ascontiguousarray(t, dtype=dt) for t in tensors]
-        self._keep_bra = [np.ascontiguousarray(t, dtype=dt) for t in bra] if bra is not None else None
-        self.Lx, self.Ly, self.d, self.D, self.chi = Lx, Ly, d, D, chi
-        self.n_tensors = len(tensors)
-        self._dtype = dt
-        cell = Cell()
-        cell.Lx, cell.Ly = Lx, Ly
-        for y in range(Ly):
-            for x in range(Lx):
-                cell.pattern[y * Lx + x] = pattern[y][x]
-        cell.n_tensors = len(tensors)
-        cell.d, cell.D = d, D
-        cell.dtype = 1 if cplx else 0
-        self._ptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in self._keep])
-        cell.tensors = C.cast(self._ptrs, C.POINTER(C.c_void_p))
-        if self._keep_bra is not None:
-            self._bptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in self._keep_bra])
-            cell.tensors_bra = C.cast(self._bptrs, C.POINTER(C.c_void_p))
-        opt = Options()
-        lib.ipeps_default_options(C.byref(opt))
-        opt.chi = chi
-        opt.prec = PREC[prec]
-        opt.rsvd_oversample, opt.rsvd_power = oversample, power
-        opt.svd_cutoff, opt.orth_tol = cutoff, orth_tol
-        opt.omega_seed = omega_seed
-        opt.jacobi_max_sweeps = jacobi_max_sweeps
-        opt.stream = stream
-        if workspace is not None:
-            opt.workspace = C.c_void_p(workspace[0])
-            opt.workspace_bytes = workspace[1]
+        self._borrowed = False
+        cell, keep = _make_cell(tensors, pattern, bra)
+        self._keep, self._keep_bra, self._ptrs, self._bptrs, self._dtype = keep
+        self._set_meta(tensors, pattern, chi)
+        opt = _make_options(lib, chi, prec, oversample, power, cutoff, orth_tol, omega_seed,
+                            jacobi_max_sweeps, stream, workspace)
         self._cell, self._opt = cell, opt
         h = C.c_void_p()
         _check(lib.ipeps_ctm_create(C.byref(cell), C.byref(opt), C.byref(h)))
         self.h = h
+
+    def _set_meta(self, tensors, pattern, chi):
+        self.Ly, self.Lx = len(pattern), len(pattern[0])
+        self.d, self.D, self.chi = tensors[0].shape[0], tensors[0].shape[1], chi
+        self.n_tensors = len(tensors)
+
+    @classmethod
+    def _borrow(cls, lib, h, tensors, pattern, chi, dtype):
+        """A view of a handle owned elsewhere (a batch instance)."""
+        self = cls.__new__(cls)
+        self.lib, self.h, self._borrowed = lib, h, True
+        self._set_meta(tensors, pattern, chi)
+        self._dtype = dtype
+        return self
 
     @staticmethod
     def workspace_bytes(tensors, pattern, chi, **kw) -> int:
@@ -171,7 +217,8 @@ class CTM:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.ipeps_ctm_destroy(self.h)
+            if not getattr(self, "_borrowed", False):
+                self.lib.ipeps_ctm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -268,3 +315,81 @@ class CTM:
 
     def launch_count(self) -> int:
         return int(self.lib.ipeps_ctm_launch_count(self.h))
+
+
+class Batch:
+    """Independent CTM instances advanced together (ipeps_batch_*): one CUDA
+    graph launch per move over all instances, tensor-core tiles from the
+    library's autotuner.
+
+    instances: list of dicts with keys tensors, pattern, chi (and optionally
+    bra); every option of CTM (prec, oversample, ...) applies to all of them.
+    """
+
+    def __init__(self, instances, tune=True, **kw):
+        lib = load_library()
+        self.lib = lib
+        n = len(instances)
+        cells = (Cell * n)()
+        opts = (Options * n)()
+        self._keep = []
+        for i, inst in enumerate(instances):
+            cell, keep = _make_cell(inst["tensors"], inst["pattern"], inst.get("bra"))
+            cells[i] = cell
+            self._keep.append(keep)
+            opts[i] = _make_options(lib, inst["chi"], **kw)
+        h = C.c_void_p()
+        _check(lib.ipeps_batch_create(n, cells, opts, 1 if tune else 0, C.byref(h)))
+        self.h = h
+        self.n = n
+        self._views = [CTM._borrow(lib, C.c_void_p(lib.ipeps_batch_instance(h, i)), inst["tensors"],
+                                   inst["pattern"], inst["chi"], self._keep[i][4])
+                       for i, inst in enumerate(instances)]
+
+    def move(self, direction="sweep", count=1):
+        _check(self.lib.ipeps_batch_move(self.h, DIRS[direction], count))
+
+    def sweep(self, count=1):
+        self.move("sweep", count)
+
+    def energies(self, J) -> np.ndarray:
+        Jv = np.ascontiguousarray(np.broadcast_to(np.asarray(J, dtype=np.float64), (self.n, 3)))
+        e = np.zeros(self.n)
+        _check(self.lib.ipeps_batch_energy(self.h, _dptr(Jv), _dptr(e)))
+        return e
+
+    def instance(self, i) -> CTM:
+        return self._views[i]
+
+    def tuning(self):
+        out = []
+        f = (C.c_int * 6)()
+        us = (C.c_double * 2)()
+        for i in range(self.lib.ipeps_batch_tuning_size(self.h)):
+            _check(self.lib.ipeps_batch_tuning_entry(self.h, i, f, us))
+            out.append({"prec": f[0], "M": f[1], "N": f[2], "K": f[3], "bn": f[4], "splits": f[5],
+                        "us": us[0], "default_us": us[1]})
+        return out
+
+    def sync(self):
+        _check(self.lib.ipeps_batch_sync(self.h))
+
+    def launch_count(self) -> int:
+        return int(self.lib.ipeps_batch_launch_count(self.h))
+
+    def stream(self) -> int:
+        """cudaStream_t the batch launches its graphs on."""
+        return int(self.lib.ipeps_batch_stream(self.h) or 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for v in self._views:
+                v.h = None
+            self.lib.ipeps_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -136,7 +136,9 @@ struct ipeps_ctm_s {
   long long scratch_elems, scratch_top;
   uint64_t launches_at_create;
   bool has_alt;       // second lane available (Ly or Lx == 2)
+  bool no_alt;        // run the two cuts of a column one after the other
   Lane alt;
+  TcTuner* tuner;     // tile choices of the tensor-core products (not owned), or null
   cudaEvent_t ev_fork, ev_join;
   // optional per-kernel-class timing (CUDA events on the handle's stream)
   bool profiling;
@@ -350,7 +352,7 @@ static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cp
   // small products (a few tiles of zero padding would dominate) stay FP64
   if (h->opt.prec != IPEPS_PREC_FP64 && M >= 64 && N >= 32 && K >= 16) {
     cudaError_t e = tc_zgemm(h->stream, (int)h->opt.prec, M, N, K, alpha, A, lda, opA, B, ldb,
-                             opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top);
+                             opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top, h->tuner);
     if (e == cudaErrorNotSupported) return fail(IPEPS_EUNSUPPORTED, "tensor-core GEMM unavailable for this shape");
     CK(e);
     return IPEPS_OK;
@@ -965,7 +967,7 @@ static ipeps_status thin_mul_packed(ipeps_ctm h, const cplx* in, int opin, cplx*
   cudaEvent_t a = nullptr;
   prof_begin(h, &a);
   cudaError_t e = tc_zgemm_packed(h->stream, (int)h->opt.prec, rows, ONE, in, h->K, opin, h->Qp[q][v], out, h->K,
-                                  conj_out, h->scratch, h->scratch_elems, h->scratch_top);
+                                  conj_out, h->scratch, h->scratch_elems, h->scratch_top, h->tuner);
   prof_end(h, a, 8.0 * (double)rows * (double)h->K * (double)h->K, 0);
   CK(e);
   return IPEPS_OK;
@@ -1162,7 +1164,7 @@ static ipeps_status left_move(ipeps_ctm h, int f) {
   frame_dims(h, f, &Lx, &Ly);
   const int c = h->chi, D2 = h->D2;
   for (int x = 0; x < Lx; ++x) {
-    if (Ly == 2 && h->has_alt) {
+    if (Ly == 2 && h->has_alt && !h->no_alt) {
       // fork: cut y = 0 on the handle's stream, cut y = 1 on the second lane
       const long long full = h->scratch_elems, half = (full / 2) & ~1023LL;
       CK(cudaEventRecord(h->ev_fork, h->stream));
@@ -1215,30 +1217,47 @@ static ipeps_status left_move(ipeps_ctm h, int f) {
       CK(normalize(h->stream, h->spareT[y], (long long)c * D2 * c, h->dwork, h->st));
       CK(normalize(h->stream, h->spareC[1][y], (long long)c * c, h->dwork, h->st));
     }
-    // install the renormalised tensors at column x+1 (pointer swap, no copies)
+    // install the renormalised tensors at column x+1.  Device copies keep the
+    // buffer of every environment tensor fixed, so a captured CUDA graph of a
+    // move stays valid for every replay.
+    const size_t cb = (size_t)c * c * sizeof(cplx), tb = (size_t)c * D2 * c * sizeof(cplx);
     for (int y = 0; y < Ly; ++y) {
-      std::swap(envC(h, f, 0, x + 1, y), h->spareC[0][y]);
-      std::swap(envT(h, f, 3, x + 1, y), h->spareT[y]);
-      std::swap(envC(h, f, 3, x + 1, y), h->spareC[1][y]);
+      CK(cudaMemcpyAsync(envC(h, f, 0, x + 1, y), h->spareC[0][y], cb, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(envT(h, f, 3, x + 1, y), h->spareT[y], tb, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(envC(h, f, 3, x + 1, y), h->spareC[1][y], cb, cudaMemcpyDeviceToDevice, h->stream));
     }
   }
   return IPEPS_OK;
+}
+
+// Enqueue one move (or one sweep) on the handle's stream without waiting for
+// the device or reading its status: the work a batch captures in a graph.
+ipeps_status ctm_enqueue_move(ipeps_ctm h, int dir) {
+  static const int sweep[4] = {IPEPS_MOVE_LEFT, IPEPS_MOVE_RIGHT, IPEPS_MOVE_UP, IPEPS_MOVE_DOWN};
+  if (dir == IPEPS_SWEEP) {
+    for (int i = 0; i < 4; ++i) CKS(left_move(h, sweep[i]));
+    return IPEPS_OK;
+  }
+  return left_move(h, dir);
 }
 
 extern "C" ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
   if (dir < 0 || dir > 4 || count < 0) return fail(IPEPS_EINVAL, "bad dir/count");
   CKS(reset_status(h));
-  static const int sweep[4] = {IPEPS_MOVE_LEFT, IPEPS_MOVE_RIGHT, IPEPS_MOVE_UP, IPEPS_MOVE_DOWN};
-  for (int n = 0; n < count; ++n) {
-    if (dir == IPEPS_SWEEP) {
-      for (int i = 0; i < 4; ++i) CKS(left_move(h, sweep[i]));
-    } else {
-      CKS(left_move(h, dir));
-    }
-  }
+  for (int n = 0; n < count; ++n) CKS(ctm_enqueue_move(h, dir));
   return check_status(h);
 }
+
+// handle internals used by the batch module (batch.cu)
+cudaStream_t ctm_stream(ipeps_ctm h) { return h->stream; }
+ipeps_status ctm_reset_status(ipeps_ctm h) { return reset_status(h); }
+ipeps_status ctm_check_status(ipeps_ctm h) { return check_status(h); }
+ipeps_status ctm_reinit_env(ipeps_ctm h) { return trace_init_env(h); }
+void ctm_set_tuner(ipeps_ctm h, TcTuner* t) { h->tuner = t; }
+void ctm_set_sequential_cuts(ipeps_ctm h, bool on) { h->no_alt = on; }
+int ctm_chi(ipeps_ctm h) { return h->chi; }
+int ctm_bond_dim(ipeps_ctm h) { return h->D; }
 
 // ---------------------------------------------------------------------------
 // spectra / convergence

@@ -95,6 +95,9 @@ cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n,
 // inverse of upper-triangular R on its kept block (zero where R[i,i] == 0)
 cudaError_t tri_inv(cudaStream_t s, const cplx* R, cplx* Rinv, int n);
 
+// one-time queries of the kernels' launch limits; called before any stream capture
+cudaError_t kernels_init();
+
 // launch accounting (host counter incremented by every launcher)
 void count_launch(int n = 1);
 uint64_t launch_counter();

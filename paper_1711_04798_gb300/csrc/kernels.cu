@@ -610,6 +610,25 @@ cudaError_t set_zero(cudaStream_t s, cplx* x, long long n) {
   return cudaGetLastError();
 }
 
+// co-resident CTA limits of the cooperative Jacobi kernels (queried once)
+static int max_small = 0, max_coresident = 0;
+
+cudaError_t kernels_init() {
+  if (max_small > 0 && max_coresident > 0) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_small_kernel, 32, 0)) != cudaSuccess)
+    return e;
+  max_small = sms * (per_sm > 0 ? per_sm : 1);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_rows_kernel, JAC_THREADS, 0)) !=
+      cudaSuccess)
+    return e;
+  max_coresident = sms * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
+}
+
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
                         DevStatus* st) {
@@ -627,14 +646,7 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
     // counters[2..3] hold the barrier (count, generation)
     e = cudaMemsetAsync(counters + 2, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    static int max_small = 0;
-    if (max_small == 0) {
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_small_kernel, 32, 0);
-      max_small = sms * (per_sm > 0 ? per_sm : 1);
-    }
+    if ((e = kernels_init()) != cudaSuccess) return e;
     const int npairs = ((n + 1) & ~1) / 2;
     int grid = npairs < max_small ? npairs : max_small;
     double tol = (double)m * 2.220446049250313e-16;
@@ -644,14 +656,7 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
     count_launch();
     if (e != cudaSuccess) return e;
   } else if (n >= 2) {
-    static int max_coresident = 0;
-    if (max_coresident == 0) {
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_rows_kernel, JAC_THREADS, 0);
-      max_coresident = sms * (per_sm > 0 ? per_sm : 1);
-    }
+    if ((e = kernels_init()) != cudaSuccess) return e;
     const int npairs = ((n + 1) & ~1) / 2;
     int grid = npairs < max_coresident ? npairs : max_coresident;
     // m * eps: an orthogonality a computed dot product of length m always resolves

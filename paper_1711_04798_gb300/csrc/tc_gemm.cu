@@ -18,27 +18,35 @@
 
 #include "tc_gemm.h"
 
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
 namespace {
 
-constexpr int BM = 128, BN = 256, NTHREADS = 128;
+constexpr int BM = 128, NPAD = 256, NTHREADS = 128;  // N of every packed B operand padded to NPAD
 constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
 
 __device__ int g_tc_errors;  // timeouts of bounded waits (read by tc_take_errors)
 
-template <int PREC>
+// Tile configuration: 128 x BN output tile (BN = 128 or 256), 128-byte k-blocks,
+// as many pipeline stages as fit in ~192 KB of shared memory.
+template <int PREC, int BN_>
 struct Cfg {
+  static constexpr int BN = BN_;
   static constexpr int ELEM = PREC == PREC_TF32 ? 4 : 2;
   static constexpr int BK = 128 / ELEM;                 // elements per k-block (128 bytes)
   static constexpr int NOPS = PREC == PREC_TF32 ? 1 : 2;
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = PREC == PREC_TF32 ? 4 : 2;
+  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
   static constexpr int UMMA_K = PREC == PREC_TF32 ? 8 : 16;  // K of one MMA
   static constexpr int KSTEPS = BK / UMMA_K;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
-  // instruction descriptor: FP32 accumulate, K-major A and B, N = 256, M = 128
+  // instruction descriptor: FP32 accumulate, K-major A and B, N = BN, M = 128
   static constexpr uint32_t IDESC = (1u << 4) | ((PREC == PREC_TF32 ? 2u : 1u) << 7) |
                                     ((PREC == PREC_TF32 ? 2u : 1u) << 10) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -91,19 +99,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-template <int PREC>
+template <int PREC, uint32_t IDESC>
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
   if (PREC == PREC_TF32) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(Cfg<PREC>::IDESC), "r"(accum)
+        "l"(a), "l"(b), "r"(IDESC), "r"(accum)
         : "memory");
   } else {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(Cfg<PREC>::IDESC), "r"(accum)
+        "l"(a), "l"(b), "r"(IDESC), "r"(accum)
         : "memory");
   }
 }
@@ -128,13 +136,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int PREC>
+template <int PREC, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                    int kb_total, int kb_per_split, int M, int Nr, cplx alpha, cplx* __restrict__ C,
                    long long ldc, float* __restrict__ partial, int Nrp, long long pstride, int conj_out) {
-  using K_ = Cfg<PREC>;
+  using K_ = Cfg<PREC, BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + K_::STAGES * K_::STAGE_BYTES);
@@ -198,10 +206,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int j = 0; j < K_::KSTEPS; ++j) {
         const uint32_t ko = j * 32;  // bytes of one MMA's K inside the 128-byte row
         const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
-        umma<PREC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), acc);
+        umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), acc);
         if (K_::NOPS == 2) {
-          umma<PREC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
-          umma<PREC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
         }
       }
       umma_commit(&empty[s]);  // frees the stage when these MMAs are done
@@ -415,94 +423,258 @@ cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, in
 
 template <int PREC>
 void padded(int N, int K, long long* Nrp, long long* Krp) {
-  using K_ = Cfg<PREC>;
-  *Krp = (2LL * K + K_::BK - 1) / K_::BK * K_::BK;
-  *Nrp = (2LL * N + BN - 1) / BN * BN;
+  constexpr int BK = Cfg<PREC, 256>::BK;
+  *Krp = (2LL * K + BK - 1) / BK * BK;
+  *Nrp = (2LL * N + NPAD - 1) / NPAD * NPAD;
 }
 
-template <int PREC>
-cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
-                const cplx* B, long long ldb, int opB, const TcPacked* pre, cplx* C, long long ldc, bool conj_out,
-                char* scratch, size_t scratch_bytes) {
-  using K_ = Cfg<PREC>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, K_::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const long long Mp = (M + BM - 1) / BM * BM;
-  long long Nrp, Krp;
-  padded<PREC>(N, K, &Nrp, &Krp);
-  const long long Nr = 2LL * N;
-  const int kb_total = (int)(Krp / K_::BK);
-  const long long tiles = (Mp / BM) * (Nrp / BN);
+// Default tile choice: 256-wide tiles; a product with fewer output tiles than
+// SMs splits K until about two waves of CTAs exist.
+TcChoice heuristic(long long Mp, long long Nrp, int kb_total) {
+  const long long tiles = (Mp / BM) * (Nrp / 256);
   int S = 1;
   if (tiles < 152) {
     S = (int)((2 * 152 + tiles - 1) / tiles);
     if (S > kb_total / 2) S = kb_total / 2;
     if (S < 1) S = 1;
   }
+  return TcChoice{256, S};
+}
+
+// effective number of splits (every split gets at least one k-block)
+int eff_splits(int kb_total, int S) {
+  if (S < 1) S = 1;
+  if (S > kb_total) S = kb_total;
   const int kps = (kb_total + S - 1) / S;
-  S = (kb_total + kps - 1) / kps;  // no empty split
-  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-  const size_t abytes = al((size_t)Mp * Krp * K_::ELEM);
-  const size_t bbytes = pre ? 0 : al((size_t)Nrp * Krp * K_::ELEM);
-  const size_t pbytes = S > 1 ? al((size_t)S * Mp * Nrp * 4) : 0;
-  char* p = (char*)(((uintptr_t)scratch + 1023) & ~(uintptr_t)1023);
-  const size_t need = K_::NOPS * (abytes + bbytes) + pbytes + 1024;
-  if (need > scratch_bytes) return cudaErrorMemoryAllocation;
-  char* a0 = p;
-  char* a1 = a0 + abytes;
-  char* b0 = a0 + K_::NOPS * abytes;
-  char* b1 = b0 + bbytes;
-  float* part = S > 1 ? (float*)(b0 + K_::NOPS * bbytes) : nullptr;
-  pack_a_kernel<PREC><<<grid_for(Mp * Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)Mp, (int)Krp, a0, a1);
-  count_launch();
-  cudaError_t e;
-  if (pre) {
-    if (pre->prec != PREC || pre->N != N || pre->K != K) return cudaErrorInvalidValue;
-    b0 = (char*)pre->b0;
-    b1 = (char*)pre->b1;
-  } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, Nrp, Krp, b0, b1)) != cudaSuccess) {
-    return e;
+  return (kb_total + kps - 1) / kps;
+}
+
+// The packed operands of one product, ready for the main kernel.
+struct Operands {
+  void *a0, *a1, *b0, *b1;
+  long long Mp, Nrp, Krp;
+  int kb_total;
+};
+
+// one-time kernel attribute (dynamic shared memory above 48 KB)
+template <int PREC, int BN>
+cudaError_t ensure_attr() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PREC, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<PREC, BN>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
   }
+  return cudaSuccess;
+}
+
+template <int PREC, int BN>
+cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, cplx alpha, cplx* C, long long ldc,
+                        float* part, bool conj_out) {
+  using K_ = Cfg<PREC, BN>;
+  cudaError_t e;
+  if ((e = ensure_attr<PREC, BN>()) != cudaSuccess) return e;
   if ((e = get_encoder()) != cudaSuccess) return e;
   CUtensorMap mA0, mA1, mB0, mB1;
-  if ((e = make_map(&mA0, a0, PREC, Mp, Krp, BM)) != cudaSuccess) return e;
-  if ((e = make_map(&mB0, b0, PREC, Nrp, Krp, BN)) != cudaSuccess) return e;
+  if ((e = make_map(&mA0, o.a0, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
+  if ((e = make_map(&mB0, o.b0, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
   mA1 = mA0;
   mB1 = mB0;
   if (K_::NOPS == 2) {
-    if ((e = make_map(&mA1, a1, PREC, Mp, Krp, BM)) != cudaSuccess) return e;
-    if ((e = make_map(&mB1, b1, PREC, Nrp, Krp, BN)) != cudaSuccess) return e;
+    if ((e = make_map(&mA1, o.a1, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
+    if ((e = make_map(&mB1, o.b1, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)(Nrp / BN), (unsigned)(Mp / BM), (unsigned)S);
-  tc_gemm_kernel<PREC><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mB0, mB1, kb_total, kps, M, (int)Nr, alpha, C,
-                                                         ldc, part, (int)Nrp, (long long)Mp * Nrp, conj_out ? 1 : 0);
+  S = eff_splits(o.kb_total, S);
+  const int kps = (o.kb_total + S - 1) / S;
+  dim3 grid((unsigned)(o.Nrp / BN), (unsigned)(o.Mp / BM), (unsigned)S);
+  tc_gemm_kernel<PREC, BN><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mB0, mB1, o.kb_total, kps, M, 2 * N, alpha,
+                                                             C, ldc, S > 1 ? part : nullptr, (int)o.Nrp,
+                                                             o.Mp * o.Nrp, conj_out ? 1 : 0);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (S > 1) {
-    splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, (long long)Mp * Nrp, (int)Nrp, M, N,
-                                                                    alpha, C, ldc, conj_out ? 1 : 0);
+    splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, o.Mp * o.Nrp, (int)o.Nrp, M, N, alpha,
+                                                                    C, ldc, conj_out ? 1 : 0);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
+template <int PREC>
+cudaError_t launch_choice(cudaStream_t s, const Operands& o, TcChoice c, int M, int N, cplx alpha, cplx* C,
+                          long long ldc, float* part, bool conj_out) {
+  if (c.bn == 128) return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out);
+  return launch_main<PREC, 256>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// autotuner: shape -> tile choice, filled by timing every candidate once
+// ---------------------------------------------------------------------------
+struct TcTuner {
+  struct Key {
+    int prec, M, N, K;
+    bool operator<(const Key& o) const {
+      return std::tie(prec, M, N, K) < std::tie(o.prec, o.M, o.N, o.K);
+    }
+  };
+  struct Entry {
+    TcChoice choice;
+    double us, heuristic_us;
+    int candidates;
+  };
+  std::map<Key, Entry> table;
+  std::vector<Key> order;  // insertion order, for reporting
+  bool measuring = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+TcTuner* tc_tuner_create() {
+  TcTuner* t = new TcTuner();
+  if (cudaEventCreate(&t->e0) != cudaSuccess || cudaEventCreate(&t->e1) != cudaSuccess) {
+    delete t;
+    return nullptr;
+  }
+  return t;
+}
+
+void tc_tuner_destroy(TcTuner* t) {
+  if (!t) return;
+  if (t->e0) cudaEventDestroy(t->e0);
+  if (t->e1) cudaEventDestroy(t->e1);
+  delete t;
+}
+
+void tc_tuner_set_measuring(TcTuner* t, bool on) {
+  if (t) t->measuring = on;
+}
+
+int tc_tuner_size(const TcTuner* t) { return t ? (int)t->order.size() : 0; }
+
+bool tc_tuner_entry(const TcTuner* t, int i, int fields[6], double us[2]) {
+  if (!t || i < 0 || i >= (int)t->order.size()) return false;
+  const TcTuner::Key& k = t->order[i];
+  const TcTuner::Entry& e = t->table.at(k);
+  fields[0] = k.prec;
+  fields[1] = k.M;
+  fields[2] = k.N;
+  fields[3] = k.K;
+  fields[4] = e.choice.bn;
+  fields[5] = e.choice.splits;
+  us[0] = e.us;
+  us[1] = e.heuristic_us;
+  return true;
+}
+
+namespace {
+
+template <int PREC>
+cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
+                const cplx* B, long long ldb, int opB, const TcPacked* pre, cplx* C, long long ldc, bool conj_out,
+                char* scratch, size_t scratch_bytes, TcTuner* tuner) {
+  using K_ = Cfg<PREC, 256>;
+  Operands o;
+  o.Mp = (M + BM - 1) / BM * BM;
+  padded<PREC>(N, K, &o.Nrp, &o.Krp);
+  o.kb_total = (int)(o.Krp / K_::BK);
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  const size_t abytes = al((size_t)o.Mp * o.Krp * K_::ELEM);
+  const size_t bbytes = pre ? 0 : al((size_t)o.Nrp * o.Krp * K_::ELEM);
+  const size_t fixed = K_::NOPS * (abytes + bbytes) + 1024;
+  if (fixed > scratch_bytes) return cudaErrorMemoryAllocation;
+  const size_t part_room = scratch_bytes - fixed;
+  auto part_bytes = [&](int S) { return S > 1 ? al((size_t)S * o.Mp * o.Nrp * 4) : (size_t)0; };
+  char* p = (char*)(((uintptr_t)scratch + 1023) & ~(uintptr_t)1023);
+  o.a0 = p;
+  o.a1 = p + abytes;
+  o.b0 = p + K_::NOPS * abytes;
+  o.b1 = (char*)o.b0 + bbytes;
+  float* part = (float*)((char*)o.b0 + K_::NOPS * bbytes);
+
+  TcChoice choice = heuristic(o.Mp, o.Nrp, o.kb_total);
+  const TcTuner::Key key{PREC, M, N, K};
+  bool tune_now = false;
+  if (tuner) {
+    auto it = tuner->table.find(key);
+    if (it != tuner->table.end())
+      choice = it->second.choice;
+    else
+      tune_now = tuner->measuring;
+  }
+  if (part_bytes(eff_splits(o.kb_total, choice.splits)) > part_room) return cudaErrorMemoryAllocation;
+
+  pack_a_kernel<PREC><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp, o.a0, o.a1);
+  count_launch();
+  cudaError_t e;
+  if (pre) {
+    if (pre->prec != PREC || pre->N != N || pre->K != K) return cudaErrorInvalidValue;
+    o.b0 = pre->b0;
+    o.b1 = pre->b1;
+  } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, o.Nrp, o.Krp, o.b0, o.b1)) != cudaSuccess) {
+    return e;
+  }
+  if (tune_now) {
+    // time every candidate (best of two runs each) on the packed operands
+    auto time_one = [&](TcChoice c, double* us) -> cudaError_t {
+      double best = 1e30;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaError_t r;
+        if ((r = cudaEventRecord(tuner->e0, s)) != cudaSuccess) return r;
+        if ((r = launch_choice<PREC>(s, o, c, M, N, alpha, C, ldc, part, conj_out)) != cudaSuccess) return r;
+        if ((r = cudaEventRecord(tuner->e1, s)) != cudaSuccess) return r;
+        if ((r = cudaEventSynchronize(tuner->e1)) != cudaSuccess) return r;
+        float ms = 0;
+        if ((r = cudaEventElapsedTime(&ms, tuner->e0, tuner->e1)) != cudaSuccess) return r;
+        best = std::min(best, 1e3 * (double)ms);
+      }
+      *us = best;
+      return cudaSuccess;
+    };
+    TcTuner::Entry ent{choice, 0.0, 0.0, 0};
+    if ((e = time_one(choice, &ent.heuristic_us)) != cudaSuccess) return e;
+    ent.us = ent.heuristic_us;
+    ent.candidates = 1;
+    static const int bns[2] = {128, 256};
+    static const int splits[7] = {1, 2, 4, 8, 12, 16, 32};
+    for (int bn : bns)
+      for (int S0 : splits) {
+        const int S = eff_splits(o.kb_total, S0);
+        if (S != S0 && S0 != 1) continue;        // duplicate of a smaller split count
+        if (S > 1 && o.kb_total / S < 2) continue;  // splits of a single k-block
+        if (part_bytes(S) > part_room) continue;
+        const TcChoice c{bn, S};
+        if (c.bn == ent.choice.bn && c.splits == eff_splits(o.kb_total, choice.splits)) continue;
+        double us = 0;
+        if ((e = time_one(c, &us)) != cudaSuccess) return e;
+        ++ent.candidates;
+        if (us < ent.us) {
+          ent.us = us;
+          ent.choice = c;
+        }
+      }
+    tuner->table[key] = ent;
+    tuner->order.push_back(key);
+    choice = ent.choice;
+  }
+  return launch_choice<PREC>(s, o, choice, M, N, alpha, C, ldc, part, conj_out);
+}
+
 }  // namespace
 
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                      int opA, const cplx* B, long long ldb, int opB, cplx* C, long long ldc, cplx* scratch,
-                     long long scratch_elems, long long scratch_top) {
+                     long long scratch_elems, long long scratch_top, TcTuner* tuner) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
   if (prec == PREC_TF32)
-    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes);
+    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes, tuner);
   if (prec == PREC_BF16X3)
-    return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes);
+    return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
+                            tuner);
   return cudaErrorNotSupported;
 }
 
@@ -541,17 +713,26 @@ cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, in
 
 cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const cplx* A, long long lda, int opA,
                             const TcPacked& B, cplx* C, long long ldc, bool conj_out, cplx* scratch,
-                            long long scratch_elems, long long scratch_top) {
+                            long long scratch_elems, long long scratch_top, TcTuner* tuner) {
   if (M <= 0) return cudaSuccess;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
   if (prec == PREC_TF32)
     return run<PREC_TF32>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out, base,
-                          bytes);
+                          bytes, tuner);
   if (prec == PREC_BF16X3)
     return run<PREC_BF16X3>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out,
-                            base, bytes);
+                            base, bytes, tuner);
   return cudaErrorNotSupported;
+}
+
+cudaError_t tc_init() {
+  cudaError_t e;
+  if ((e = ensure_attr<PREC_TF32, 128>()) != cudaSuccess) return e;
+  if ((e = ensure_attr<PREC_TF32, 256>()) != cudaSuccess) return e;
+  if ((e = ensure_attr<PREC_BF16X3, 128>()) != cudaSuccess) return e;
+  if ((e = ensure_attr<PREC_BF16X3, 256>()) != cudaSuccess) return e;
+  return get_encoder();
 }
 
 int tc_take_errors() {

@@ -7,9 +7,11 @@
 // operands are packed (permuted, converted, real-embedded) into `scratch`
 // above scratch_top.  Returns cudaErrorNotSupported when the precision or the
 // shape has no tensor-core kernel.
+struct TcTuner;
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A,
                      long long lda, int opA, const cplx* B, long long ldb, int opB, cplx* C,
-                     long long ldc, cplx* scratch, long long scratch_elems, long long scratch_top);
+                     long long ldc, cplx* scratch, long long scratch_elems, long long scratch_top,
+                     TcTuner* tuner = nullptr);
 
 // A B-role operand (op(B) is K x N complex) packed once as Br^T (2N x 2K real,
 // K-major, padded), reusable across products.
@@ -25,7 +27,30 @@ cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, in
 // C = alpha opA(A) B  (or its complex conjugate when conj_out), B pre-packed
 cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const cplx* A, long long lda, int opA,
                             const TcPacked& B, cplx* C, long long ldc, bool conj_out, cplx* scratch,
-                            long long scratch_elems, long long scratch_top);
+                            long long scratch_elems, long long scratch_top, TcTuner* tuner = nullptr);
+
+// Tile choice of one product: output tile 128 x bn (bn = 128 or 256 real
+// columns) and the number of K splits (FP32 partials summed in a fixed order).
+struct TcChoice {
+  int bn;
+  int splits;
+};
+
+// Autotuner table (shape -> tile choice).  Products run through a tuner use
+// its choice for their shape; while measuring, a shape not yet in the table is
+// timed with every candidate choice (CUDA events, synchronising) and the
+// fastest is recorded.  Without a tuner, or for unknown shapes when not
+// measuring, the default heuristic applies.  Not thread-safe.
+TcTuner* tc_tuner_create();
+void tc_tuner_destroy(TcTuner* t);
+void tc_tuner_set_measuring(TcTuner* t, bool on);
+int tc_tuner_size(const TcTuner* t);
+// entry i: fields = {prec, M, N, K, bn, splits}; us = {best time, default-choice time}
+bool tc_tuner_entry(const TcTuner* t, int i, int fields[6], double us[2]);
+
+// one-time setup (kernel attributes, driver entry point); called before any
+// stream capture so that captured products make no such calls.
+cudaError_t tc_init();
 
 // number of bounded-wait timeouts inside tensor-core kernels since the last
 // call (resets the counter); synchronous.

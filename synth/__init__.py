@@ -126,3 +126,24 @@ def workload(name: str, seed: int = 0, D: int | None = None, chi: int | None = N
         "J": J,
         "seed": seed,
     }
+
+
+def scan(seed: int = 0, n: int = 64, Ds=(3, 4, 5), chis=(32, 48, 64, 100)):
+    """The batched phase-diagram scan: ``n`` independent instances.
+
+    Instance k sits at Jz = 2k/(n-1) on the line Jx = Jy = (2 - Jz)/2 (the
+    paper's Jx = Jy scan, Sec. VI), with bond dimension Ds[(k + r) mod len(Ds)]
+    and environment dimension chis[(k + r) mod len(chis)], r = seed mod 12.
+    Its four tensors follow the product-plus-noise recipe with workload seed
+    seed * 64 + k.  Returns a list of dicts (tensors, pattern, D, chi, J).
+    """
+    r = seed % 12
+    out = []
+    for k in range(n):
+        Jz = 2.0 * k / max(n - 1, 1)
+        D = Ds[(k + r) % len(Ds)]
+        chi = chis[(k + r) % len(chis)]
+        tensors = [product_plus_noise(seed * 64 + k, t, 8, D) for t in range(4)]
+        out.append({"tensors": tensors, "pattern": [[0, 1], [2, 3]], "D": D, "chi": chi,
+                    "J": ((2.0 - Jz) / 2.0, (2.0 - Jz) / 2.0, Jz), "k": k})
+    return out
