@@ -24,6 +24,8 @@ __all__ = [
     "fidelity",
     "ring_sigma",
     "boundary_spectrum",
+    "boundary_spectrum_topk",
+    "fixed_rings",
     "entropy",
 ]
 
@@ -240,6 +242,35 @@ def ring_sigma(st: CTMState, which: str, x: int, Nv: int) -> np.ndarray:
     return np.einsum("aKBa->KB", R, optimize=True)
 
 
+def fixed_rings(st: CTMState, x: int, Nv: int):
+    """sigma_L and sigma_R of the cut between columns x and x+1 (rings of T4
+    and T2, Fig. "cylinder"), each multiplied by the phase that makes its trace
+    real positive and replaced by its Hermitian part."""
+    sL = ring_sigma(st, "L", x, Nv)
+    sR = ring_sigma(st, "R", x, Nv)
+    sL = sL * np.exp(-1j * np.angle(np.trace(sL)))
+    sR = sR * np.exp(-1j * np.angle(np.trace(sR)))
+    return 0.5 * (sL + sL.conj().T), 0.5 * (sR + sR.conj().T)
+
+
+def boundary_spectrum_topk(st: CTMState, x: int, Nv: int, k: int):
+    """The k largest eigenvalues of M = sigma_L^T sigma_R divided by tr M,
+    their entropy -sum lam ln lam and the weight 1 - sum lam they leave out.
+
+    Sec. IV: the spectrum of the boundary density operator is that of
+    sigma_L^T sigma_R (the identity after Eq. "rho"); for long cylinders only
+    its leading part is computed (iteratively, with the rings as structured
+    operators).  Written here as its plain definition: all eigenvalues of the
+    dense product (LAPACK), sorted by real part, the k largest kept; tr M is
+    the sum of all of them.
+    """
+    sL, sR = fixed_rings(st, x, Nv)
+    M = sL.T @ sR
+    ev = np.sort(np.real(np.linalg.eigvals(M)))[::-1]
+    lam = ev[:k] / np.real(np.trace(M))
+    return lam, entropy(lam), float(1.0 - lam.sum())
+
+
 def boundary_spectrum(st: CTMState, x: int, Nv: int):
     """Spectrum of sigma_L^T sigma_R normalised to sum 1, descending.
 
@@ -250,12 +281,7 @@ def boundary_spectrum(st: CTMState, x: int, Nv: int):
     the singular values of the resulting Hermitian operator (its eigenvalues
     when it is positive, as for an exact environment).
     """
-    sL = ring_sigma(st, "L", x, Nv)
-    sR = ring_sigma(st, "R", x, Nv)
-    sL = sL * np.exp(-1j * np.angle(np.trace(sL)))
-    sR = sR * np.exp(-1j * np.angle(np.trace(sR)))
-    sL = 0.5 * (sL + sL.conj().T)
-    sR = 0.5 * (sR + sR.conj().T)
+    sL, sR = fixed_rings(st, x, Nv)
     _, s, Vh = np.linalg.svd(sL.T)
     W = (Vh.conj().T * np.sqrt(s)[None, :]) @ Vh
     H = W @ sR @ W

@@ -489,6 +489,44 @@ def test_product_state_boundary_entropy_is_zero():
     assert np.allclose(lam, [1.0]) and abs(O.entropy(lam)) < 1e-15
 
 
+def _converged_state(seed, D, chi, sweeps):
+    w = synth.workload("cfg2", seed=seed, D=D, chi=chi)
+    st = O.make_state(w["tensors"], w["pattern"], D, chi)
+    opt = O.CTMOptions(chi=chi, proj="rsvd", omega=synth.omega(7, chi * D * D, chi + 16))
+    for _ in range(sweeps):
+        st = O.sweep(st, opt)
+    return st
+
+
+def test_topk_boundary_spectrum_equals_similar_operator_spectrum():
+    """The leading eigenvalues of sigma_L^T sigma_R (eig of the product) equal
+    the leading eigenvalues of |sigma_L^T|^(1/2) sigma_R |sigma_L^T|^(1/2)
+    (SVD route) when both rings are positive, as they are here."""
+    st = _converged_state(2, 2, 12, 6)
+    for Nv in (2, 4):
+        sL, sR = O.fixed_rings(st, 0, Nv)
+        assert np.linalg.eigvalsh(sL).min() > 0 and np.linalg.eigvalsh(sR).min() > 0
+        full = O.boundary_spectrum(st, 0, Nv)
+        n = len(full)
+        lam, S, rest = O.boundary_spectrum_topk(st, 0, Nv, n)
+        assert np.allclose(lam, full, rtol=1e-10, atol=1e-14) and abs(rest) < 1e-12
+        assert abs(S - O.entropy(full)) < 1e-10
+        k = n // 3
+        lk, Sk, restk = O.boundary_spectrum_topk(st, 0, Nv, k)
+        assert np.allclose(lk, full[:k], rtol=1e-10)
+        assert abs(restk - full[k:].sum()) < 1e-10
+        assert 0 < Sk < O.entropy(full)
+
+
+def test_topk_product_state_single_eigenvalue():
+    _, ts = product_tensors(15)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 1, 1)
+    st = O.sweep(st, O.CTMOptions(chi=1, proj="svd"))
+    lam, S, rest = O.boundary_spectrum_topk(st, 0, 2, 1)
+    assert np.allclose(lam, [1.0]) and abs(S) < 1e-15 and abs(rest) < 1e-14
+
+
 def test_hamiltonian_terms_hermitian_and_trivial_bond():
     H = O.ruby_bond_hamiltonians((0.3, 0.5, 0.7))
     for k in ("H_r", "H_u", "H_d"):
