@@ -38,8 +38,11 @@ def parse():
     p.add_argument("--D", type=int, default=5)
     p.add_argument("--chi", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "scan"],
-                   help="single: one D=5 chi=100 instance; scan: 64-instance batched phase-diagram scan")
+    p.add_argument("--workload", default="single", choices=["single", "scan", "cylinder"],
+                   help="single: one D=5 chi=100 instance; scan: 64-instance batched phase-diagram scan; "
+                        "cylinder: D=6 chi=144 environment, boundary spectrum at Nv = 2, 4, 6")
+    p.add_argument("--sweeps", type=int, default=12, help="cylinder: CTM sweeps before the readout")
+    p.add_argument("--topk", type=int, default=64, help="cylinder: leading eigenvalues at Nv = 6")
     p.add_argument("--instances", type=int, default=64)
     p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
@@ -425,6 +428,62 @@ def run_scan(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_cylinder(args, rank, world, local_rank):
+    """Config-5 readout: environment at D=6 chi=144, boundary spectrum and
+    entanglement entropy on cylinders of Nv = 2, 4 (dense) and 6 (Lanczos)."""
+    import torch
+    import synth
+    from paper_1711_04798_gb300 import CTM
+    torch.cuda.set_device(local_rank)
+    D = args.D if args.D != 5 else 6
+    chi = args.chi if args.chi != 100 else 144
+    w = synth.workload("cfg5", seed=rank, D=D, chi=chi)
+    stream = torch.cuda.current_stream()
+    g = CTM(w["tensors"], w["pattern"], chi, prec=args.prec, stream=stream.cuda_stream)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) * 1e-3
+
+    g.sweep(1)  # warm-up
+    with ClockSampler(local_rank) as clk:
+        _, ctm_s = timed(lambda: g.sweep(args.sweeps))
+        spectra = g.spectra()
+        readouts = []
+        for Nv in (2, 4):
+            (lam, S), t = timed(lambda: g.boundary_rho(0, Nv))
+            readouts.append({"Nv": Nv, "route": "dense", "dim": int(D ** Nv), "S_vn": S, "seconds": t,
+                             "lam_top4": [float(v) for v in lam[:4]]})
+        Nv = 6
+        k = min(args.topk, D ** Nv)
+        (lam, S, rest, nconv), t = timed(lambda: g.boundary_rho_topk(0, Nv, k, max_iter=min(8 * k, 1024),
+                                                                     tol=1e-8))
+        readouts.append({"Nv": Nv, "route": "lanczos", "dim": int(D ** Nv), "k": k, "converged": nconv,
+                         "S_vn_topk": S, "rest_weight": rest, "seconds": t,
+                         "lam_top4": [float(v) for v in lam[:4]]})
+    e = g.energy(w["J"])
+    g.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": 4 * args.sweeps / ctm_s, "unit": "moves/s", "n_gpus": world,
+        "steps": args.sweeps, "warmup": 1, "ms_per_step": 1e3 * ctm_s / args.sweeps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec], "data": "synthetic",
+        "config": {"workload": f"cylinder readout: 2x2 cell, d=8, D={D}, chi={chi}, complex product state + 0.1 "
+                               f"noise (config 5 recipe); {args.sweeps} sweeps then boundary rho at Nv=2,4,6",
+                   "prec": args.prec},
+        "readouts": readouts, "energy_per_spin": e,
+        "corner_spectrum_tail": float(np.min(spectra[spectra > 0])), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -434,6 +493,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "scan":
         run_scan(args, rank, world, local_rank)
+    elif args.workload == "cylinder":
+        run_cylinder(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -173,6 +173,29 @@ ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double*
 ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
                                 double* S_vn);
 
+/* Leading boundary spectrum for cylinders beyond the dense route (Sec. IV:
+ * for long circumferences only the leading eigenvalues of sigma_L^T sigma_R
+ * are computed, iteratively).  sigma_L and sigma_R (as in ipeps_boundary_rho,
+ * n = D^Nv) are built as dense n x n operators, each by one product of two
+ * half rings in the handle's contraction arithmetic (tensor cores in the
+ * precision forms), phase-fixed and Hermitised.  The k largest eigenvalues of
+ * M = sigma_L^T sigma_R then come from a Lanczos iteration in the sigma_R
+ * inner product <x,y> = x^H sigma_R y, in which M is self-adjoint when
+ * sigma_R is positive definite, with full reorthogonalisation, all in FP64;
+ * it stops when each of the k Ritz values has residual <= tol times the
+ * largest, or after max_iter steps.  The values are divided by tr M.
+ *   eig_out: k doubles, descending (caller-owned host; may be NULL);
+ *   *n_conv: how many of the k met tol (k when an invariant subspace was hit);
+ *   *S_vn = -sum lam ln lam over the k values; *rest = 1 - sum of the k.
+ * Device memory: allocated for the duration of the call (about 2 n^2 +
+ * chi^2 (D^Nv + 1.6 n) complex numbers for the two operators and the ring
+ * product) and freed before it returns.  Errors: EINVAL (Nv not a multiple of
+ * Ly or < 2, D^Nv > 200000, not 1 <= k <= max_iter <= min(1024, n), tol <= 0),
+ * ENOMEM, ENUMERIC (sigma_R not positive definite: a negative norm met),
+ * ETIMEOUT (Jacobi budget of the tridiagonal eigensolve). */
+ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int k, int max_iter, double tol,
+                                     double* eig_out, int* n_conv, double* S_vn, double* rest);
+
 /* Copy one environment tensor to the host: role 0..3 = C1..C4 (chi*chi
  * complex), 4..7 = T1..T4 (chi*D*D*chi complex), at cell position (x,y). */
 ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* host_out);
@@ -206,6 +229,14 @@ void ipeps_ctm_destroy(ipeps_ctm h);
  * own device buffers; synchronises the device. */
 ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
                          double* C);
+
+/* As ipeps_zgemm for the tensor-core precisions, with the tile choice fixed
+ * instead of the default: output tiles of 128 x bn real columns (bn = 128 or
+ * 256) and `splits` K splits (reduced to the number of 128-byte k-blocks if
+ * larger).  For unit tests of every choice the batch autotuner can make.
+ * EINVAL for prec FP64 or a bad choice. */
+ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K, const double* A, int opA,
+                              const double* B, int opB, double* C);
 
 /* Corner spectrum without any device allocation (the paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc,

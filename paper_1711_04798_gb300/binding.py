@@ -23,7 +23,7 @@ EXPORTS = [
     "ipeps_ctm_destroy", "ipeps_last_error", "ipeps_ctm_profile", "ipeps_ctm_profile_read",
     "ipeps_batch_create", "ipeps_batch_move", "ipeps_batch_energy", "ipeps_batch_instance",
     "ipeps_batch_tuning_size", "ipeps_batch_tuning_entry", "ipeps_batch_launch_count",
-    "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream",
+    "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
 ]
 
 
@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_fidelity.argtypes = [P, P, P, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_boundary_rho.argtypes = [P, I, I, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
     lib.ipeps_ctm_env_get.argtypes = [P, I, I, I, C.POINTER(D)]
+    lib.ipeps_boundary_rho_topk.argtypes = [P, I, I, I, I, D, C.POINTER(D), C.POINTER(I), C.POINTER(D),
+                                            C.POINTER(D)]
     lib.ipeps_ctm_sync.argtypes = [P]
     lib.ipeps_ctm_launch_count.argtypes = [P]
     lib.ipeps_ctm_launch_count.restype = C.c_uint64
@@ -293,6 +295,14 @@ class CTM:
         nout, S = C.c_int(), C.c_double()
         _check(self.lib.ipeps_boundary_rho(self.h, x, Nv, _dptr(eig), C.byref(nout), C.byref(S)))
         return eig[: nout.value], S.value
+
+    def boundary_rho_topk(self, x, Nv, k, max_iter=300, tol=1e-10):
+        """Leading k boundary-spectrum values (Lanczos); returns (lam, S, rest, n_conv)."""
+        lam = np.zeros(k)
+        nc, S, rest = C.c_int(), C.c_double(), C.c_double()
+        _check(self.lib.ipeps_boundary_rho_topk(self.h, x, Nv, k, max_iter, tol, _dptr(lam), C.byref(nc),
+                                                C.byref(S), C.byref(rest)))
+        return lam, S.value, rest.value, nc.value
 
     def env(self, role, x, y) -> np.ndarray:
         n = self.chi * self.chi if role < 4 else self.chi * self.D * self.D * self.chi

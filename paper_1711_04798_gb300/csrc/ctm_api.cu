@@ -1717,6 +1717,166 @@ extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* e
   return check_status(h);
 }
 
+// ---------------------------------------------------------------------------
+// Long cylinders (Sec. IV): the rings as dense operators built by one product
+// of two half rings laid out for it, and the leading spectrum by Lanczos.
+// ---------------------------------------------------------------------------
+// Half ring of `len` edge tensors (role T2 = 1 or T4 = 3) at column xc from
+// row y0 down, inner chi legs contracted, written in the layout the ring
+// product reads directly (no operand permutation):
+//   upper: out[K, B, a, m]  (a: open chi leg at the top, m: at the bottom)
+//   lower: out[a, m, K, B]  (m: open chi leg at the top, a: at the bottom)
+// K / B fuse the ket / bra legs of the len sites, the first site slowest.
+static ipeps_status half_ring_layout(ipeps_ctm h, int role, int xc, int y0, int len, bool upper, cplx* out) {
+  const int c = h->chi, D = h->D;
+  auto Tptr = [&](int i) { return h->T[role][((y0 + i) % h->Ly) * h->Lx + xc]; };
+  const long long mark = h->scratch_top;
+  // working form R[c0, K, B, c1] of the first tensor
+  cplx* cur = Tptr(0);
+  if (role != 1) {
+    cur = scratch_alloc(h, (long long)c * D * D * c);
+    if (!cur) return fail(IPEPS_ENOMEM, "scratch exhausted (half ring)");
+    const int dims[4] = {c, D, D, c}, perm[4] = {3, 1, 2, 0};
+    CK(permute(h->stream, Tptr(0), cur, 4, dims, perm, false, ONE));
+  }
+  long long Kd = D;
+  if (len == 1) {
+    const int dims[4] = {c, D, D, c};
+    const int pu[4] = {1, 2, 0, 3}, pl[4] = {3, 0, 1, 2};
+    CK(permute(h->stream, cur, out, 4, dims, upper ? pu : pl, false, ONE));
+    h->scratch_top = mark;
+    return IPEPS_OK;
+  }
+  const char* in_spec = role == 1 ? "aKBc,ckbe" : "aKBc,ekbc";
+  for (int i = 1; i < len; ++i) {
+    const TV R = tv(cur, {c, (int)Kd, (int)Kd, c});
+    const TV T = tv(Tptr(i), {c, D, D, c});
+    if (i < len - 1) {
+      cplx* nxt = scratch_alloc(h, (long long)c * Kd * D * Kd * D * c);
+      if (!nxt) return fail(IPEPS_ENOMEM, "scratch exhausted (half ring)");
+      CKS(contract(h, (std::string(in_spec) + "->aKkBbe").c_str(), R, false, T, false,
+                   tv(nxt, {c, (int)Kd, D, (int)Kd, D, c})));
+      cur = nxt;
+      Kd *= D;
+    } else if (upper) {
+      CKS(contract(h, (std::string(in_spec) + "->KkBbae").c_str(), R, false, T, false,
+                   tv(out, {(int)Kd, D, (int)Kd, D, c, c})));
+    } else {
+      CKS(contract(h, (std::string(in_spec) + "->eaKkBb").c_str(), R, false, T, false,
+                   tv(out, {c, c, (int)Kd, D, (int)Kd, D})));
+    }
+  }
+  h->scratch_top = mark;
+  return IPEPS_OK;
+}
+
+// sigma[(K1 K2), (B1 B2)] of the ring of Nv edge tensors (role, column xc):
+// t[(K1 B1), (K2 B2)] = H1[(K1 B1), (a m)] H2[(a m), (K2 B2)] in the handle's
+// contraction arithmetic, then one permutation into sigma.  Uses the handle's
+// scratch from its current top: t first, then the half rings and the
+// product's own work.  sigma must not overlap t.
+static ipeps_status ring_sigma_dense(ipeps_ctm h, int role, int xc, int Nv, cplx* sigma) {
+  const int c = h->chi, D = h->D;
+  const int h1 = Nv / 2, h2 = Nv - h1;
+  long long K1 = 1, K2 = 1;
+  for (int i = 0; i < h1; ++i) K1 *= D;
+  for (int i = 0; i < h2; ++i) K2 *= D;
+  const long long mark = h->scratch_top;
+  cplx* t = scratch_alloc(h, K1 * K1 * K2 * K2);
+  cplx* H1 = scratch_alloc(h, K1 * K1 * c * c);
+  cplx* H2 = scratch_alloc(h, K2 * K2 * c * c);
+  if (!t || !H1 || !H2) return fail(IPEPS_ENOMEM, "scratch exhausted (ring)");
+  CKS(half_ring_layout(h, role, xc, 0, h1, true, H1));
+  CKS(half_ring_layout(h, role, xc, h1, h2, false, H2));
+  CKS(gemm_dispatch(h, (int)(K1 * K1), (int)(K2 * K2), c * c, H1, (long long)c * c, OP_N, H2, K2 * K2, OP_N, t,
+                    K2 * K2, ONE));
+  const int dims[4] = {(int)K1, (int)K1, (int)K2, (int)K2}, perm[4] = {0, 2, 1, 3};
+  CK(permute(h->stream, t, sigma, 4, dims, perm, false, ONE));
+  h->scratch_top = mark;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int k, int max_iter, double tol,
+                                                double* eig_out, int* n_conv, double* S_vn, double* rest) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
+  long long n = 1;
+  for (int i = 0; i < Nv; ++i) {
+    n *= h->D;
+    if (n > 200000) return fail(IPEPS_EINVAL, "D^Nv above 200000");
+  }
+  if (k < 1 || max_iter < k || max_iter > 1024 || max_iter > n)
+    return fail(IPEPS_EINVAL, "need 1 <= k <= max_iter <= min(1024, D^Nv)");
+  if (!(tol > 0.0)) return fail(IPEPS_EINVAL, "tol must be positive");
+  CKS(reset_status(h));
+  const long long c2 = (long long)h->chi * h->chi;
+  long long K1 = 1, K2 = 1;
+  for (int i = 0; i < Nv / 2; ++i) K1 *= h->D;
+  for (int i = 0; i < Nv - Nv / 2; ++i) K2 *= h->D;
+  // region: [t | H1 | H2 | work of the half rings and of the ring product]
+  // while a ring is built; [. | sigma_R | Lanczos work] afterwards
+  const long long n2 = n * n;
+  // half rings: the last step's product output (chi^2 K^2) plus small
+  // intermediates; ring product: its packed tensor-core operands (~1.5 n chi^2)
+  const long long ring_work = std::max(c2 * std::max(K1 * K1, K2 * K2) * 5 / 4,
+                                       (long long)(1.6 * (double)n * (double)c2)) + (1LL << 24);
+  const long long ring_phase = n2 + c2 * (K1 * K1 + K2 * K2) + ring_work;
+  const long long krylov_phase = 2 * n2 + lanczos_work_elems(n, max_iter) + 1024;
+  const long long region_elems = std::max(ring_phase, krylov_phase);
+  cplx* mem = nullptr;
+  cudaError_t e = cudaMalloc((void**)&mem, (size_t)(n2 + region_elems) * sizeof(cplx));
+  if (e != cudaSuccess)
+    return fail(IPEPS_ENOMEM, "boundary rho: cudaMalloc of %.1f GB failed: %s",
+                (double)(n2 + region_elems) * 16e-9, cudaGetErrorString(e));
+  cplx* sL = mem;
+  cplx* region = mem + n2;
+  cplx* sR = region + n2;  // written over the dead half rings after the ring product
+  cplx* save_scratch = h->scratch;
+  const long long save_elems = h->scratch_elems, save_top = h->scratch_top;
+  h->scratch = region;
+  h->scratch_elems = region_elems;
+  h->scratch_top = 0;
+  const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
+  ipeps_status st = ring_sigma_dense(h, 3, xl, Nv, sL);
+  if (st == IPEPS_OK) st = ring_sigma_dense(h, 1, xr, Nv, sR);
+  h->scratch = save_scratch;
+  h->scratch_elems = save_elems;
+  h->scratch_top = save_top;
+  LanczosResult res{0, 0, 0, 0};
+  double out2[2] = {0.0, 0.0};
+  if (st == IPEPS_OK) {
+    // phase-fix by the trace, Hermitise; sL is replaced by sigma_L^T
+    bnd::launch_phase_herm(h->stream, sL, (int)n, true, h->dwork);
+    bnd::launch_phase_herm(h->stream, sR, (int)n, false, h->dwork);
+    count_launch(4);
+    cplx* work = region + 2 * n2;
+    const long long work_elems = region_elems - 2 * n2;
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = lanczos_leading(h->stream, sL, sR, n, k, max_iter, tol, h->opt.omega_seed ^ 0x5bd1e995ULL, work,
+                          work_elems, h->sigma, h->perm, h->s_sel, h->dwork, h->counters, h->st,
+                          h->opt.jacobi_max_sweeps, &res);
+    double2* partial = (double2*)work;
+    double2* trd = partial + 512;
+    double* lam = (double*)(trd + 1);
+    double* dout = lam + k + 1;
+    if (e == cudaSuccess) e = topk_finish(h->stream, sL, sR, n, h->s_sel, k, partial, trd, lam, dout);
+    if (e == cudaSuccess && eig_out)
+      e = cudaMemcpyAsync(eig_out, lam, k * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out2, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "boundary rho (Lanczos): %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(mem);
+  CKS(st);
+  if (res.indefinite) return fail(IPEPS_ENUMERIC, "sigma_R is not positive definite (negative norm in Lanczos)");
+  if (n_conv) *n_conv = res.converged;
+  if (S_vn) *S_vn = out2[0];
+  if (rest) *rest = out2[1];
+  return check_status(h);
+}
+
 extern "C" ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* out) {
   if (!h || !out) return fail(IPEPS_EINVAL, "null argument");
   if (role < 0 || role > 7 || x < 0 || x >= h->Lx || y < 0 || y >= h->Ly)
@@ -1731,12 +1891,29 @@ extern "C" ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, d
 // ---------------------------------------------------------------------------
 // stand-alone complex GEMM (building block, host buffers) for unit tests
 // ---------------------------------------------------------------------------
+static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
+                               double* C, const TcChoice* force);
+
 extern "C" ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA, const double* B,
                                     int opB, double* C) {
+  return zgemm_host(prec, M, N, K, A, opA, B, opB, C, nullptr);
+}
+
+extern "C" ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K, const double* A, int opA,
+                                         const double* B, int opB, double* C) {
+  if (prec != IPEPS_PREC_TF32 && prec != IPEPS_PREC_BF16X3) return fail(IPEPS_EINVAL, "tile choice needs TF32/BF16X3");
+  if ((bn != 128 && bn != 256) || splits < 1) return fail(IPEPS_EINVAL, "bad tile choice");
+  const TcChoice c{bn, splits};
+  return zgemm_host(prec, M, N, K, A, opA, B, opB, C, &c);
+}
+
+static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
+                               double* C, const TcChoice* force) {
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return fail(IPEPS_EINVAL, "bad GEMM arguments");
   if (prec < 0 || prec > 2 || opA < 0 || opA > 3 || opB < 0 || opB > 3) return fail(IPEPS_EINVAL, "bad prec/op");
   const size_t na = (size_t)M * K, nb = (size_t)K * N, nc = (size_t)M * N;
-  const size_t scratch_elems = 4 * (na + nb) + 8 * nc + (1 << 20);
+  const size_t scratch_elems = 4 * (na + nb) + 8 * nc + (force ? 4 * (size_t)force->splits * (nc + 256 * (size_t)M) : 0) +
+                               (1 << 20);
   cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dS = nullptr;
   ipeps_status st = IPEPS_OK;
   auto cleanup = [&]() { cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dS); };
@@ -1749,7 +1926,8 @@ extern "C" ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double*
   if (e != cudaSuccess) { cleanup(); return fail(IPEPS_ECUDA, "zgemm setup: %s", cudaGetErrorString(e)); }
   const long long lda = (opA & OP_T) ? M : K, ldb = (opB & OP_T) ? K : N;
   if (prec == 0) e = zgemm(0, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, ZERO, dC, N);
-  else e = tc_zgemm(0, prec, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, dC, N, dS, (long long)scratch_elems, 0);
+  else e = tc_zgemm(0, prec, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, dC, N, dS, (long long)scratch_elems, 0,
+                    nullptr, force);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(C, dC, nc * sizeof(cplx), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "zgemm: %s", cudaGetErrorString(e));

@@ -95,6 +95,32 @@ cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n,
 // inverse of upper-triangular R on its kept block (zero where R[i,i] == 0)
 cudaError_t tri_inv(cudaStream_t s, const cplx* R, cplx* Rinv, int n);
 
+// ---------------------------------------------------------------------------
+// Krylov readout of the boundary density operator (lanczos.cu)
+// ---------------------------------------------------------------------------
+struct LanczosResult {
+  int iters;       // Lanczos steps taken (size of the tridiagonal)
+  int converged;   // leading Ritz values with residual <= tol * largest
+  int breakdown;   // an invariant subspace was reached (Ritz values exact)
+  int indefinite;  // a negative B-norm met: B is not positive definite
+};
+// *out = sum conj(x) y over n entries (fixed order); partial: 512 double2
+cudaError_t zdotc_dev(cudaStream_t s, const cplx* x, const cplx* y, long long n, double2* partial, double2* out);
+// y = A x for a dense n x n row-major A
+cudaError_t zgemv_dense(cudaStream_t s, const cplx* A, long long n, const cplx* x, cplx* y);
+// complex elements of work lanczos_leading needs
+long long lanczos_work_elems(long long n, int max_iter);
+// Leading k eigenvalues of M = A B (A, B Hermitian, B positive definite) by
+// Lanczos in the B inner product with full reorthogonalisation; on return
+// s_sel[0..k) holds the Ritz values, descending (device), perm their indices.
+cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long long n, int k, int max_iter,
+                            double tol, uint64_t seed, cplx* work, long long work_elems, double* sigma, int* perm,
+                            double* s_sel, double* dwork, int* counters, DevStatus* st, int jac_sweeps,
+                            LanczosResult* res);
+// lam = theta / Re tr(A B) (k values) and out = {-sum lam ln lam, 1 - sum lam}
+cudaError_t topk_finish(cudaStream_t s, const cplx* A, const cplx* B, long long n, const double* theta, int k,
+                        double2* partial, double2* trd, double* lam, double* out);
+
 // one-time queries of the kernels' launch limits; called before any stream capture
 cudaError_t kernels_init();
 

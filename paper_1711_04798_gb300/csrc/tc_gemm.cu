@@ -574,7 +574,7 @@ namespace {
 template <int PREC>
 cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
                 const cplx* B, long long ldb, int opB, const TcPacked* pre, cplx* C, long long ldc, bool conj_out,
-                char* scratch, size_t scratch_bytes, TcTuner* tuner) {
+                char* scratch, size_t scratch_bytes, TcTuner* tuner, const TcChoice* force) {
   using K_ = Cfg<PREC, 256>;
   Operands o;
   o.Mp = (M + BM - 1) / BM * BM;
@@ -603,6 +603,11 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
       choice = it->second.choice;
     else
       tune_now = tuner->measuring;
+  }
+  if (force) {
+    if (force->bn != 128 && force->bn != 256) return cudaErrorInvalidValue;
+    choice = TcChoice{force->bn, eff_splits(o.kb_total, force->splits)};
+    tune_now = false;
   }
   if (part_bytes(eff_splits(o.kb_total, choice.splits)) > part_room) return cudaErrorMemoryAllocation;
 
@@ -666,15 +671,16 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
 
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                      int opA, const cplx* B, long long ldb, int opB, cplx* C, long long ldc, cplx* scratch,
-                     long long scratch_elems, long long scratch_top, TcTuner* tuner) {
+                     long long scratch_elems, long long scratch_top, TcTuner* tuner, const TcChoice* force) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
   if (prec == PREC_TF32)
-    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes, tuner);
+    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes, tuner,
+                          force);
   if (prec == PREC_BF16X3)
     return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
-                            tuner);
+                            tuner, force);
   return cudaErrorNotSupported;
 }
 
@@ -719,10 +725,10 @@ cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const c
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
   if (prec == PREC_TF32)
     return run<PREC_TF32>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out, base,
-                          bytes, tuner);
+                          bytes, tuner, nullptr);
   if (prec == PREC_BF16X3)
     return run<PREC_BF16X3>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out,
-                            base, bytes, tuner);
+                            base, bytes, tuner, nullptr);
   return cudaErrorNotSupported;
 }
 

@@ -8,10 +8,12 @@
 // above scratch_top.  Returns cudaErrorNotSupported when the precision or the
 // shape has no tensor-core kernel.
 struct TcTuner;
+struct TcChoice;
+// force: a fixed tile choice instead of the tuner's or the default one
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A,
                      long long lda, int opA, const cplx* B, long long ldb, int opB, cplx* C,
                      long long ldc, cplx* scratch, long long scratch_elems, long long scratch_top,
-                     TcTuner* tuner = nullptr);
+                     TcTuner* tuner = nullptr, const TcChoice* force = nullptr);
 
 // A B-role operand (op(B) is K x N complex) packed once as Br^T (2N x 2K real,
 // K-major, padded), reusable across products.

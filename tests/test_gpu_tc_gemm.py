@@ -52,3 +52,32 @@ def test_tc_gemm_matches_complex128(prec, shape, ops):
     scale = np.abs(Aop) @ np.abs(Bop)
     err = np.max(np.abs(C - ref) / scale)
     assert err < TOL[prec], err
+
+
+def _zgemm_tile(prec, bn, splits, A, opA, B, opB, M, N, K):
+    from paper_1711_04798_gb300 import load_library
+    lib = load_library()
+    f = lib.ipeps_zgemm_tile
+    P = ctypes.POINTER(ctypes.c_double)
+    f.argtypes = [ctypes.c_int] * 6 + [P, ctypes.c_int, P, ctypes.c_int, P]
+    f.restype = ctypes.c_int
+    C = np.zeros((M, N), dtype=np.complex128)
+    st = f(prec, bn, splits, M, N, K, np.ascontiguousarray(A).ctypes.data_as(P), opA,
+           np.ascontiguousarray(B).ctypes.data_as(P), opB, C.ctypes.data_as(P))
+    assert st == 0, lib.ipeps_last_error()
+    return C
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("bn", [128, 256])
+@pytest.mark.parametrize("splits", [1, 3, 8, 40])
+def test_every_tile_choice_matches_complex128(prec, bn, splits):
+    """Each (tile width, K split) the autotuner can pick gives the same product."""
+    M, N, K = 200, 333, 1500
+    rng = np.random.default_rng(bn + splits + 10 * prec)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))  # op T
+    C = _zgemm_tile(prec, bn, splits, A, 0, B, 1, M, N, K)
+    ref = A @ B.T
+    scale = np.abs(A) @ np.abs(B.T)
+    assert np.max(np.abs(C - ref) / scale) < TOL[prec]
