@@ -202,6 +202,7 @@ def run_ours(args, rank, world, local_rank):
     w = workload(args.D, args.chi, seed=rank)
     J = w["J"]
     g = CTM(w["tensors"], w["pattern"], args.chi, prec=args.prec, stream=stream.cuda_stream)
+    tuned = 0 if args.no_tune else g.autotune()
 
     def step():
         g.rebuild()
@@ -308,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec],
         "data": "synthetic", "config": config_desc(args, args.prec),
         "tflops": gemm["flops"] / (ms * 1e-3) / 1e12 if ms else None,
+        "autotuned_shapes": tuned,
         "energy_per_spin": energies[-1],
         "roofline": roof, "cpu_baseline": cpu, "fp64_comparison": fp64_cmp,
         "e2e": {"value": e2e_value, "unit": "moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},

@@ -132,6 +132,17 @@ ipeps_status ipeps_ctm_reset_env(ipeps_ctm h);
  * corners/edges of each column (row) of the cell in turn (Sec. II.C). */
 ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count);
 
+/* Autotune the tensor-core products of this handle: one sweep is run with
+ * every product shape timed under each candidate tile choice (128 x 128 or
+ * 128 x 256 output tiles, K splits) and the fastest recorded; later moves use
+ * the recorded choices (results change only by rounding).  The environment is
+ * restored afterwards (a temporary device copy of it is allocated for the
+ * call).  No-op for IPEPS_PREC_FP64.  ipeps_ctm_tuning_size: number of
+ * product shapes tuned.  Errors: ECUDA, ENOMEM-class CUDA failures, and any
+ * status of the tuning sweep. */
+ipeps_status ipeps_ctm_autotune(ipeps_ctm h);
+int ipeps_ctm_tuning_size(ipeps_ctm h);
+
 /* Singular values of every corner, divided by the largest: s_out is
  * [4][Ly][Lx][chi] doubles (C1..C4), caller-owned. */
 ipeps_status ipeps_ctm_spectra(ipeps_ctm h, double* s_out);

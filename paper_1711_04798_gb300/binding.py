@@ -24,6 +24,7 @@ EXPORTS = [
     "ipeps_batch_create", "ipeps_batch_move", "ipeps_batch_energy", "ipeps_batch_instance",
     "ipeps_batch_tuning_size", "ipeps_batch_tuning_entry", "ipeps_batch_launch_count",
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
+    "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile",
 ]
 
 
@@ -73,6 +74,8 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_fidelity.argtypes = [P, P, P, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_boundary_rho.argtypes = [P, I, I, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
     lib.ipeps_ctm_env_get.argtypes = [P, I, I, I, C.POINTER(D)]
+    lib.ipeps_ctm_autotune.argtypes = [P]
+    lib.ipeps_ctm_tuning_size.argtypes = [P]
     lib.ipeps_boundary_rho_topk.argtypes = [P, I, I, I, I, D, C.POINTER(D), C.POINTER(I), C.POINTER(D),
                                             C.POINTER(D)]
     lib.ipeps_ctm_sync.argtypes = [P]
@@ -251,6 +254,11 @@ class CTM:
 
     def sweep(self, count=1):
         self.move("sweep", count)
+
+    def autotune(self) -> int:
+        """Tile choices of the tensor-core products measured once; returns the number of shapes."""
+        _check(self.lib.ipeps_ctm_autotune(self.h))
+        return int(self.lib.ipeps_ctm_tuning_size(self.h))
 
     def spectra(self) -> np.ndarray:
         out = np.zeros((4, self.Ly, self.Lx, self.chi))

@@ -101,6 +101,9 @@ __global__ void tri_inv_kernel(const cplx* __restrict__ R, cplx* __restrict__ Ri
 }  // namespace
 
 cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n, double tol) {
+  cudaError_t e;
+  if ((e = kernels_init()) != cudaSuccess) return e;
+  if (chol_cluster_fits(n)) return chol_cluster(s, G, R, n, tol);
   chol_drop_kernel<<<1, 1024, 0, s>>>(G, work, R, n, tol);
   count_launch();
   return cudaGetLastError();

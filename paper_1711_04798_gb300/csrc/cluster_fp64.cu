@@ -1,0 +1,386 @@
+// FP64 pieces of the projector step on one thread-block cluster.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate per SM, so a
+// k x k Jacobi SVD or Cholesky factorisation on a single CTA is bound by one
+// SM's FP64 units, while spreading it over a grid pays a global-memory
+// barrier per step.  Here the rows are distributed over the CTAs of one
+// cluster (row i lives in the shared memory of CTA i mod csize), warps read
+// and write partner rows through distributed shared memory, and steps are
+// separated by the hardware cluster barrier.  The pair schedule and the
+// arithmetic are those of the grid-wide kernels (kernels.cu, cholqr.cu).
+#include <cooperative_groups.h>
+
+#include "ctm_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int CL_THREADS = 128;         // 4 warps per CTA
+constexpr int CL_SMEM = 200 * 1024;     // dynamic shared memory bound per CTA
+int g_csize = 0;                        // CTAs per cluster (16 if schedulable, else 8)
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void pair_of(int r, int p, int np, int rounds, int* i, int* j) {
+  int a, b;
+  if (p == 0) {
+    a = np - 1;
+    b = r;
+  } else {
+    a = (r + p) % rounds;
+    b = (r - p + rounds) % rounds;
+  }
+  if (a > b) { const int t = a; a = b; b = t; }
+  *i = a;
+  *j = b;
+}
+
+// One-sided Jacobi on the n rows of G (length m): rows and, with Vt, the rows
+// of the accumulated rotation (length n, from the identity) in the cluster's
+// shared memory.
+__global__ void __launch_bounds__(CL_THREADS)
+    jacobi_cluster_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt, int max_sweeps,
+                          double tol, double4* __restrict__ log, int* sweeps_used, DevStatus* st) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = CL_THREADS / 32;
+  const int R = (n + cs - 1) / cs;  // row slots per CTA
+  extern __shared__ cplx sm[];      // [R x m] rows of G, then [R x n] rows of Vt
+  __shared__ double s_fro;
+  __shared__ int s_rot;
+  cplx* gl = sm;
+  cplx* vl = sm + (long long)R * m;
+  double f = 0.0;
+  for (int l = 0; l < R; ++l) {
+    const int i = l * cs + rank;
+    if (i >= n) break;
+    for (int t = threadIdx.x; t < m; t += CL_THREADS) {
+      const cplx x = G[(long long)i * ldg + t];
+      gl[(long long)l * m + t] = x;
+      f += x.x * x.x + x.y * x.y;
+    }
+    if (Vt)
+      for (int t = threadIdx.x; t < n; t += CL_THREADS) vl[(long long)l * n + t] = make_double2(t == i ? 1.0 : 0.0, 0.0);
+  }
+  f = warp_sum(f);
+  __shared__ double s_w[CL_THREADS / 32];
+  if (lane == 0) s_w[warp] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nwarps; ++w) t += s_w[w];
+    s_fro = t;
+    s_rot = 0;
+  }
+  cl.sync();
+  double fro2 = 0.0;
+  for (int r = 0; r < cs; ++r) fro2 += *cl.map_shared_rank(&s_fro, r);
+  const double negligible = fro2 * 1e-30;
+  auto grow = [&](int i) { return cl.map_shared_rank(gl, i % cs) + (long long)(i / cs) * m; };
+  auto vrow = [&](int i) { return cl.map_shared_rank(vl, i % cs) + (long long)(i / cs) * n; };
+  const int np = (n + 1) & ~1;
+  const int rounds = np - 1, npairs = np / 2;
+  const int gw = rank * nwarps + warp, nw = cs * nwarps;
+  bool converged = false;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < rounds; ++r) {
+      for (int p = gw; p < npairs; p += nw) {
+        int i, j;
+        pair_of(r, p, np, rounds, &i, &j);
+        if (j >= n) {
+          if (log && lane == 0) log[((long long)sweep * rounds + r) * npairs + p] = make_double4(2.0, 0.0, 0.0, 0.0);
+          continue;
+        }
+        cplx* gi = grow(i);
+        cplx* gj = grow(j);
+        double al = 0.0, be = 0.0, gr = 0.0, gim = 0.0;
+        for (int t = lane; t < m; t += 32) {
+          const cplx x = gi[t], y = gj[t];
+          al += x.x * x.x + x.y * x.y;
+          be += y.x * y.x + y.y * y.y;
+          gr += x.x * y.x + x.y * y.y;
+          gim += x.x * y.y - x.y * y.x;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gim = warp_sum(gim);
+        // the rotation's scalars on one lane (FP64 divides and roots are
+        // costly here), broadcast to the warp
+        double c = 1.0, s = 0.0, phr = 1.0, phi = 0.0;
+        int rot = 0;
+        if (lane == 0) {
+          const double g = hypot(gr, gim);
+          if (al > negligible && be > negligible && g > tol * sqrt(al * be)) {
+            const double zeta = (be - al) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = c * t;
+            phr = gr / g;
+            phi = -gim / g;
+            rot = 1;
+          }
+        }
+        rot = __shfl_sync(0xffffffffu, rot, 0);
+        if (log && lane == 0)
+          log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4(c, s, phr, phi)
+                                                                  : make_double4(2.0, 0.0, 0.0, 0.0);
+        if (rot) {
+          c = __shfl_sync(0xffffffffu, c, 0);
+          s = __shfl_sync(0xffffffffu, s, 0);
+          const cplx ph = make_double2(__shfl_sync(0xffffffffu, phr, 0), __shfl_sync(0xffffffffu, phi, 0));
+          for (int q = lane; q < m; q += 32) {
+            const cplx x = gi[q], y = cmul(gj[q], ph);
+            gi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+            gj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+          }
+          if (Vt) {
+            cplx* vi = vrow(i);
+            cplx* vj = vrow(j);
+            for (int q = lane; q < n; q += 32) {
+              const cplx x = vi[q], y = cmul(vj[q], ph);
+              vi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+              vj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+            }
+          }
+          if (lane == 0) atomicAdd(&s_rot, 1);
+        }
+      }
+      cl.sync();
+    }
+    int total = 0;
+    for (int r = 0; r < cs; ++r) total += *cl.map_shared_rank(&s_rot, r);
+    cl.sync();  // every CTA has read every count
+    if (threadIdx.x == 0) s_rot = 0;
+    cl.sync();
+    if (total == 0) {
+      converged = true;
+      break;
+    }
+  }
+  for (int l = 0; l < R; ++l) {
+    const int i = l * cs + rank;
+    if (i >= n) break;
+    for (int t = threadIdx.x; t < m; t += CL_THREADS) G[(long long)i * ldg + t] = gl[(long long)l * m + t];
+    if (Vt)
+      for (int t = threadIdx.x; t < n; t += CL_THREADS) Vt[(long long)i * n + t] = vl[(long long)l * n + t];
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    if (sweeps_used) *sweeps_used = converged ? sweep + 1 : max_sweeps;
+    atomicAdd(&st->jacobi_calls, 1);
+    atomicAdd(&st->jacobi_sweeps, converged ? sweep + 1 : max_sweeps);
+    if (!converged) atomicAdd(&st->jacobi_unconverged, 1);
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// Vt (n x n) = the logged rotations applied to the identity, one CTA per
+// column q (columns are independent): thread p applies pair p of every round,
+// rounds in order, the column held in shared memory.  Rotation c = 2 marks a
+// pair that was not rotated.
+__global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4* __restrict__ log,
+                                     const int* __restrict__ sweeps_used) {
+  extern __shared__ cplx col[];
+  const int q = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = make_double2(i == q ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  const int sweeps = *sweeps_used;
+  const int np = (n + 1) & ~1;
+  const int rounds = np - 1, npairs = np / 2;
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int r = 0; r < rounds; ++r) {
+      const int p = threadIdx.x;
+      if (p < npairs) {
+        const double4 rec = log[((long long)sw * rounds + r) * npairs + p];
+        if (rec.x < 1.5) {
+          int i, j;
+          pair_of(r, p, np, rounds, &i, &j);
+          const double c = rec.x, s = rec.y;
+          const cplx x = col[i], y = cmul(col[j], make_double2(rec.z, rec.w));
+          col[i] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+          col[j] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Vt[(long long)i * n + q] = col[i];
+}
+
+// Right-looking Cholesky of the Hermitian n x n G (upper triangle used) with
+// dropped pivots (d <= tol * max diagonal: row of R zero): rows of the
+// working copy in the cluster's shared memory; at column j every CTA reads
+// row j from its owner and updates its own rows i > j.
+__global__ void __launch_bounds__(CL_THREADS)
+    chol_cluster_kernel(const cplx* __restrict__ G, cplx* __restrict__ Rout, int n, double tol) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
+  const int R = (n + cs - 1) / cs;
+  extern __shared__ cplx sm[];  // [R x n] rows of the working copy W
+  __shared__ double s_max;
+  double mx = 0.0;
+  for (int l = 0; l < R; ++l) {
+    const int i = l * cs + rank;
+    if (i >= n) break;
+    for (int t = threadIdx.x; t < n; t += CL_THREADS) sm[(long long)l * n + t] = G[(long long)i * n + t];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < R; ++l) {
+      const int i = l * cs + rank;
+      if (i >= n) break;
+      mx = fmax(mx, sm[(long long)l * n + i].x);
+    }
+    s_max = mx;
+  }
+  cl.sync();
+  double dmax = 0.0;
+  for (int r = 0; r < cs; ++r) dmax = fmax(dmax, *cl.map_shared_rank(&s_max, r));
+  const double thr = tol * dmax;
+  for (int j = 0; j < n; ++j) {
+    const cplx* wj = cl.map_shared_rank(sm, j % cs) + (long long)(j / cs) * n;
+    const double d = wj[j].x;
+    const bool keep = d > thr;
+    const double rjj = keep ? sqrt(d) : 0.0, inv = keep ? 1.0 / rjj : 0.0;
+    if (j % cs == rank) {
+      // row j of R (zero row for a dropped direction)
+      for (int l = threadIdx.x; l < n; l += CL_THREADS) {
+        cplx v = make_double2(0.0, 0.0);
+        if (keep && l >= j) {
+          const cplx g = wj[l];
+          v = make_double2(l == j ? rjj : g.x * inv, l == j ? 0.0 : g.y * inv);
+        }
+        Rout[(long long)j * n + l] = v;
+      }
+    }
+    if (keep) {
+      // own rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i
+      for (int l0 = 0; l0 < R; ++l0) {
+        const int i = l0 * cs + rank;
+        if (i >= n) break;
+        if (i <= j) continue;
+        const cplx gi = wj[i];
+        const cplx a = make_double2(gi.x * inv, gi.y * inv);
+        cplx* wi = sm + (long long)l0 * n;
+        for (int l = i + threadIdx.x; l < n; l += CL_THREADS) {
+          const cplx gl = wj[l];
+          const cplx b = make_double2(l == j ? rjj : gl.x * inv, l == j ? 0.0 : gl.y * inv);
+          wi[l].x -= a.x * b.x + a.y * b.y;
+          wi[l].y -= a.x * b.y - a.y * b.x;
+        }
+      }
+    }
+    cl.sync();
+  }
+}
+
+}  // namespace
+
+static cudaError_t cluster_init() {
+  if (g_csize) return cudaSuccess;
+  cudaError_t e;
+  const void* fns[2] = {(const void*)jacobi_cluster_kernel, (const void*)chol_cluster_kernel};
+  for (const void* f : fns) {
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, CL_SMEM)) != cudaSuccess) return e;
+  }
+  // 16 CTAs per cluster when the hardware can place such a cluster, else 8
+  int csize = 8;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 16;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(CL_THREADS);
+  cfg.dynamicSmemBytes = CL_SMEM;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)jacobi_cluster_kernel, &cfg) == cudaSuccess &&
+      nclusters >= 1)
+    csize = 16;
+  cudaGetLastError();  // a refused query leaves no error behind
+  g_csize = csize;
+  return cudaSuccess;
+}
+
+cudaError_t fp64_cluster_init() { return cluster_init(); }
+
+static cudaError_t launch_cluster(const void* fn, void** args, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = g_csize;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3(g_csize);
+  cfg.blockDim = dim3(CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+bool jacobi_cluster_fits(int n, int m, bool vt_in_smem) {
+  if (n < 32) return false;
+  if (cluster_init() != cudaSuccess) return false;
+  const long long R = (n + g_csize - 1) / g_csize;
+  return R * ((long long)m + (vt_in_smem ? n : 0)) * (long long)sizeof(cplx) <= CL_SMEM;
+}
+
+long long jacobi_log_elems(int n, int max_sweeps) {
+  const long long np = (n + 1) & ~1;
+  return (long long)max_sweeps * (np - 1) * (np / 2) * 2;  // one double4 = two complex slots per pair
+}
+
+cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
+                           DevStatus* st, cplx* rotlog, int* sweeps_used) {
+  cudaError_t e;
+  if ((e = cluster_init()) != cudaSuccess) return e;
+  const bool replay = Vt && rotlog && sweeps_used && n <= 2048;
+  cplx* Vin = replay ? nullptr : Vt;  // with a log, Vt is rebuilt afterwards across the GPU
+  double4* logp = replay ? (double4*)rotlog : nullptr;
+  int* su = replay ? sweeps_used : nullptr;
+  const long long R = (n + g_csize - 1) / g_csize;
+  const size_t smem = (size_t)(R * ((long long)m + (Vin ? n : 0)) * sizeof(cplx));
+  double tol = (double)m * 2.220446049250313e-16;
+  void* args[] = {&G, &n, &m, &ldg, &Vin, &max_sweeps, &tol, &logp, &su, &st};
+  e = launch_cluster((const void*)jacobi_cluster_kernel, args, smem, s);
+  count_launch();
+  if (e != cudaSuccess || !replay) return e;
+  const int npairs = ((n + 1) & ~1) / 2;
+  const int threads = (npairs + 31) / 32 * 32;
+  jacobi_replay_kernel<<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4*)rotlog, sweeps_used);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool chol_cluster_fits(int n) {
+  if (n < 32) return false;
+  if (cluster_init() != cudaSuccess) return false;
+  const long long R = (n + g_csize - 1) / g_csize;
+  return R * n * (long long)sizeof(cplx) <= CL_SMEM;
+}
+
+cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol) {
+  cudaError_t e;
+  if ((e = cluster_init()) != cudaSuccess) return e;
+  const long long rows = (n + g_csize - 1) / g_csize;
+  const size_t smem = (size_t)(rows * n * sizeof(cplx));
+  void* args[] = {&G, &R, &n, &tol};
+  e = launch_cluster((const void*)chol_cluster_kernel, args, smem, s);
+  count_launch();
+  return e;
+}

@@ -138,7 +138,8 @@ struct ipeps_ctm_s {
   bool has_alt;       // second lane available (Ly or Lx == 2)
   bool no_alt;        // run the two cuts of a column one after the other
   Lane alt;
-  TcTuner* tuner;     // tile choices of the tensor-core products (not owned), or null
+  TcTuner* tuner;     // tile choices of the tensor-core products, or null
+  bool own_tuner;     // created by ipeps_ctm_autotune (else owned by a batch)
   cudaEvent_t ev_fork, ev_join;
   // optional per-kernel-class timing (CUDA events on the handle's stream)
   bool profiling;
@@ -853,6 +854,7 @@ extern "C" void ipeps_ctm_destroy(ipeps_ctm h) {
     cudaEventDestroy(h->ev_fork);
     cudaEventDestroy(h->ev_join);
   }
+  if (h->own_tuner) tc_tuner_destroy(h->tuner);
   if (h->own_mem) cudaFree(h->base);
   delete h;
 }
@@ -1084,8 +1086,11 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
   {
     cudaEvent_t a = nullptr;
     prof_begin(h, &a);
+    const long long nlog = jacobi_log_elems(k, h->opt.jacobi_max_sweeps);
+    cplx* rotlog = scratch_alloc(h, nlog);
+    if (!rotlog) return fail(IPEPS_ENOMEM, "scratch exhausted (rotation log)");
     CK(jacobi_rows(h->stream, Rt, k, k, k, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                   h->counters, h->st));
+                   h->counters, h->st, rotlog, nlog));
     prof_end(h, a, 0.0, 1);
   }
   // out = V^T Wt  (rows (W v_i)^T)
@@ -1248,6 +1253,48 @@ extern "C" ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count) {
   for (int n = 0; n < count; ++n) CKS(ctm_enqueue_move(h, dir));
   return check_status(h);
 }
+
+extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (h->opt.prec == IPEPS_PREC_FP64) return IPEPS_OK;  // no tensor-core products to tune
+  CK(kernels_init());
+  CK(tc_init());
+  if (!h->tuner) {
+    h->tuner = tc_tuner_create();
+    if (!h->tuner) return fail(IPEPS_ECUDA, "tuner events");
+    h->own_tuner = true;
+  }
+  // snapshot of the environment, restored after the tuning sweep
+  const int ncell = h->Lx * h->Ly;
+  const size_t cb = (size_t)h->chi * h->chi * sizeof(cplx), tb = (size_t)h->chi * h->D2 * h->chi * sizeof(cplx);
+  char* snap = nullptr;
+  CK(cudaMalloc((void**)&snap, 4 * ncell * (cb + tb)));
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < ncell; ++i) {
+      CK(cudaMemcpyAsync(snap + (j * ncell + i) * (cb + tb), h->C[j][i], cb, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(snap + (j * ncell + i) * (cb + tb) + cb, h->T[j][i], tb, cudaMemcpyDeviceToDevice,
+                         h->stream));
+    }
+  tc_tuner_set_measuring(h->tuner, true);
+  h->no_alt = true;  // cuts in sequence: timings unperturbed by the other lane
+  ipeps_status st = reset_status(h);
+  if (st == IPEPS_OK) st = ctm_enqueue_move(h, IPEPS_SWEEP);
+  if (st == IPEPS_OK) st = check_status(h);
+  h->no_alt = false;
+  tc_tuner_set_measuring(h->tuner, false);
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < ncell; ++i) {
+      cudaMemcpyAsync(h->C[j][i], snap + (j * ncell + i) * (cb + tb), cb, cudaMemcpyDeviceToDevice, h->stream);
+      cudaMemcpyAsync(h->T[j][i], snap + (j * ncell + i) * (cb + tb) + cb, tb, cudaMemcpyDeviceToDevice, h->stream);
+    }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(snap);
+  CKS(st);
+  CK(e);
+  return IPEPS_OK;
+}
+
+extern "C" int ipeps_ctm_tuning_size(ipeps_ctm h) { return h ? tc_tuner_size(h->tuner) : 0; }
 
 // handle internals used by the batch module (batch.cu)
 cudaStream_t ctm_stream(ipeps_ctm h) { return h->stream; }

@@ -10,6 +10,38 @@
 typedef double2 cplx;  // (re, im), 16-byte aligned
 
 // ---------------------------------------------------------------------------
+// IEEE-754 binary64 <-> binary32 conversions and sign flips on the integer
+// pipe.  GB300 issues FP64 instructions (conversions included) at a small
+// fraction of its integer / FP32 rate, so data-movement kernels that touched
+// every element with one became bound by the FP64 unit.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+// binary64 -> binary32, mantissa truncated to 23 bits; |x| below 2^-126
+// becomes a signed zero, beyond the binary32 range an infinity (NaN too).
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+// binary32 -> binary64, exact for normal numbers (subnormals become zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long mant = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 255) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | mant));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | mant));
+}
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+#endif
+
+// ---------------------------------------------------------------------------
 // error plumbing: every launcher returns cudaError_t; the API layer converts.
 // ---------------------------------------------------------------------------
 struct DevStatus {
@@ -65,9 +97,11 @@ cudaError_t set_zero(cudaStream_t s, cplx* x, long long n);
 // same rotations starting from the identity.  sigma[i] = ||row i|| on return.
 // counters: 4 ints of scratch (sweep counters and, for m <= 256, a grid barrier);
 // work: 1 double of scratch.
+// rotlog (optional, jacobi_log_elems(n, max_sweeps) complex slots): lets the
+// cluster path rebuild Vt from logged rotations instead of holding it.
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
-                        DevStatus* st);
+                        DevStatus* st, cplx* rotlog = nullptr, long long rotlog_elems = 0);
 // rows of G scaled to unit norm where sigma > tol*max(sigma), zero otherwise
 cudaError_t orth_rows_finish(cudaStream_t s, cplx* G, int n, int m, long long ldg,
                              const double* sigma, double tol);
@@ -123,6 +157,19 @@ cudaError_t topk_finish(cudaStream_t s, const cplx* A, const cplx* B, long long 
 
 // one-time queries of the kernels' launch limits; called before any stream capture
 cudaError_t kernels_init();
+
+// FP64 Jacobi / Cholesky on one thread-block cluster (cluster_fp64.cu): rows
+// in distributed shared memory, hardware cluster barriers between steps.
+cudaError_t fp64_cluster_init();
+bool jacobi_cluster_fits(int n, int m, bool vt_in_smem);
+// With rotlog (jacobi_log_elems(n, max_sweeps) complex slots) and sweeps_used
+// (one int), Vt is not held in the cluster: the rotations are logged and
+// replayed onto the identity by one CTA per column afterwards.
+cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
+                           DevStatus* st, cplx* rotlog, int* sweeps_used);
+long long jacobi_log_elems(int n, int max_sweeps);
+bool chol_cluster_fits(int n);
+cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol);
 
 // launch accounting (host counter incremented by every launcher)
 void count_launch(int n = 1);

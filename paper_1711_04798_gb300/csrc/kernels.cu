@@ -626,14 +626,25 @@ cudaError_t kernels_init() {
       cudaSuccess)
     return e;
   max_coresident = sms * (per_sm > 0 ? per_sm : 1);
-  return cudaSuccess;
+  return fp64_cluster_init();
 }
 
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
-                        DevStatus* st) {
+                        DevStatus* st, cplx* rotlog, long long rotlog_elems) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
+  if ((e = kernels_init()) != cudaSuccess) return e;
+  const bool logged = Vt && rotlog && n <= 2048 && rotlog_elems >= jacobi_log_elems(n, max_sweeps);
+  if (jacobi_cluster_fits(n, m, Vt != nullptr && !logged)) {
+    // rows (and Vt unless logged) fit in one cluster's shared memory: no grid-wide barrier
+    if ((e = jacobi_cluster(s, G, n, m, ldg, Vt, max_sweeps, st, logged ? rotlog : nullptr,
+                            logged ? counters : nullptr)) != cudaSuccess)
+      return e;
+    row_norms_kernel<<<n < 1024 ? n : 1024, 256, 0, s>>>(G, n, m, ldg, sigma);
+    count_launch();
+    return cudaGetLastError();
+  }
   if (Vt) {
     init_identity_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(Vt, n);
     count_launch();

@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                    int kb_total, int kb_per_split, int M, int Nr, cplx alpha, cplx* __restrict__ C,
-                   long long ldc, float* __restrict__ partial, int Nrp, long long pstride, int conj_out) {
+                   long long ldc, float* __restrict__ partial, int Nrp, long long pstride, int conj_out,
+                   int unit_alpha) {
   using K_ = Cfg<PREC, BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -235,12 +236,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       } else if (row < M) {
+        if (unit_alpha) {
+          // alpha = 1: exact FP32 -> FP64 widening on the integer pipe
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          if (col + 2 * t < Nr) {
-            const double re = v[2 * t], im = v[2 * t + 1];
-            const double orr = alpha.x * re - alpha.y * im, oi = alpha.x * im + alpha.y * re;
-            C[(long long)row * ldc + (col >> 1) + t] = make_double2(orr, conj_out ? -oi : oi);
+          for (int t = 0; t < 8; ++t) {
+            if (col + 2 * t < Nr) {
+              const double re = f2d_bits(v[2 * t]), im = f2d_bits(v[2 * t + 1]);
+              C[(long long)row * ldc + (col >> 1) + t] = make_double2(re, conj_out ? neg_bits(im) : im);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            if (col + 2 * t < Nr) {
+              const double re = v[2 * t], im = v[2 * t + 1];
+              const double orr = alpha.x * re - alpha.y * im, oi = alpha.x * im + alpha.y * re;
+              C[(long long)row * ldc + (col >> 1) + t] = make_double2(orr, conj_out ? -oi : oi);
+            }
           }
         }
       }
@@ -255,11 +267,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // C[m,n] = alpha * sum_z P[z][m][2n .. 2n+1]  (fixed summation order)
 __global__ void splitk_reduce_kernel(const float* __restrict__ P, int S, long long pstride, int Nrp, int M,
-                                     int N, cplx alpha, cplx* __restrict__ C, long long ldc, int conj_out) {
+                                     int N, cplx alpha, cplx* __restrict__ C, long long ldc, int conj_out,
+                                     int unit_alpha) {
   const long long total = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(e / N), n = (int)(e % N);
+    if (unit_alpha) {
+      // FP32 sum of the partials (the products carry ~16 significant bits),
+      // widened to FP64 on the integer pipe
+      float re = 0.0f, im = 0.0f;
+      for (int z = 0; z < S; ++z) {
+        const float2 p = *(const float2*)(P + z * pstride + (long long)m * Nrp + 2 * n);
+        re += p.x;
+        im += p.y;
+      }
+      const double dr = f2d_bits(re), di = f2d_bits(im);
+      C[(long long)m * ldc + n] = make_double2(dr, conj_out ? neg_bits(di) : di);
+      continue;
+    }
     double re = 0.0, im = 0.0;
     for (int z = 0; z < S; ++z) {
       const float2 p = *(const float2*)(P + z * pstride + (long long)m * Nrp + 2 * n);
@@ -274,7 +300,7 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ P, int S, long lo
 __device__ __forceinline__ cplx load_op(const cplx* X, long long ld, int op, int r, int c) {
   // element (r, c) of the operand in its GEMM role (A: (m,k); B: (k,n))
   cplx v = (op & OP_T) ? X[(long long)c * ld + r] : X[(long long)r * ld + c];
-  if (op & OP_CONJ) v.y = -v.y;
+  if (op & OP_CONJ) v.y = neg_bits(v.y);
   return v;
 }
 
@@ -298,10 +324,11 @@ __global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA
       x = (kr & 1) ? v.y : v.x;
     }
     if (PREC == PREC_TF32) {
-      ((uint32_t*)o0)[e] = to_tf32((float)x);
+      ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
     } else {
-      const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
-      const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+      const float xf = d2f_bits(x);  // 23 mantissa bits: more than hi + lo keep
+      const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
       ((__nv_bfloat16*)o0)[e] = hi;
       ((__nv_bfloat16*)o1)[e] = lo;
     }
@@ -320,13 +347,14 @@ __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB
     if (nr < 2 * N && kr < 2 * K) {
       const cplx v = load_op(B, ldb, opB, kr >> 1, nr >> 1);
       const int a = kr & 1, b = nr & 1;
-      x = (a == b) ? v.x : (a == 0 ? v.y : -v.y);
+      x = (a == b) ? v.x : (a == 0 ? v.y : neg_bits(v.y));
     }
     if (PREC == PREC_TF32) {
-      ((uint32_t*)o0)[e] = to_tf32((float)x);
+      ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
     } else {
-      const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
-      const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+      const float xf = d2f_bits(x);  // 23 mantissa bits: more than hi + lo keep
+      const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
       ((__nv_bfloat16*)o0)[e] = hi;
       ((__nv_bfloat16*)o1)[e] = lo;
     }
@@ -346,7 +374,7 @@ __global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int 
     cplx v = make_double2(0.0, 0.0);
     if (k < K && n < N) {
       v = B[(long long)k * ldb + n];
-      if (conj) v.y = -v.y;
+      if (conj) v.y = neg_bits(v.y);
     }
     tile[i][threadIdx.x] = v;
   }
@@ -360,13 +388,14 @@ __global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int 
       if (kr >= Krp) continue;
       const int kl = c >> 1, a = c & 1;
       const cplx v = tile[kl][nl];
-      const double x = (a == b) ? v.x : (a == 0 ? v.y : -v.y);
+      const double x = (a == b) ? v.x : (a == 0 ? v.y : neg_bits(v.y));
       const long long e = (long long)nr * Krp + kr;
       if (PREC == PREC_TF32) {
-        ((uint32_t*)o0)[e] = to_tf32((float)x);
+        ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
       } else {
-        const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
-        const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+        const float xf = d2f_bits(x);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
         ((__nv_bfloat16*)o0)[e] = hi;
         ((__nv_bfloat16*)o1)[e] = lo;
       }
@@ -488,14 +517,15 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
   S = eff_splits(o.kb_total, S);
   const int kps = (o.kb_total + S - 1) / S;
   dim3 grid((unsigned)(o.Nrp / BN), (unsigned)(o.Mp / BM), (unsigned)S);
+  const int unit = alpha.x == 1.0 && alpha.y == 0.0;
   tc_gemm_kernel<PREC, BN><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mB0, mB1, o.kb_total, kps, M, 2 * N, alpha,
                                                              C, ldc, S > 1 ? part : nullptr, (int)o.Nrp,
-                                                             o.Mp * o.Nrp, conj_out ? 1 : 0);
+                                                             o.Mp * o.Nrp, conj_out ? 1 : 0, unit);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (S > 1) {
     splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, o.Mp * o.Nrp, (int)o.Nrp, M, N, alpha,
-                                                                    C, ldc, conj_out ? 1 : 0);
+                                                                    C, ldc, conj_out ? 1 : 0, unit);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

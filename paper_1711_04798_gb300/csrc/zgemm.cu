@@ -143,7 +143,7 @@ struct PermParams {
 };
 
 __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ out,
-                               long long total, PermParams p, int conj, cplx alpha) {
+                               long long total, PermParams p, int conj, cplx alpha, int unit) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long r = i, off = 0;
@@ -153,8 +153,12 @@ __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ o
       off += c * p.istr[a];
     }
     cplx v = in[off];
-    if (conj) v.y = -v.y;
-    out[i] = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
+    if (conj) v.y = neg_bits(v.y);
+    if (unit) {
+      out[i] = v;  // no FP64 arithmetic for the usual alpha = 1
+    } else {
+      out[i] = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
+    }
   }
 }
 
@@ -211,7 +215,8 @@ cudaError_t permute(cudaStream_t s, const cplx* in, cplx* out, int nd, const int
   if (total == 0) return cudaSuccess;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  permute_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, total, p, conj ? 1 : 0, alpha);
+  const int unit = alpha.x == 1.0 && alpha.y == 0.0;
+  permute_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, total, p, conj ? 1 : 0, alpha, unit);
   count_launch();
   return cudaGetLastError();
 }

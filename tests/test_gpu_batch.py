@@ -116,3 +116,24 @@ def test_batch_create_error_names_instance():
     with pytest.raises(CTMError) as ei:
         Batch(insts, tune=False, prec="fp64", **DEFAULTS)
     assert "instance 1" in str(ei.value) and ei.value.status == 1
+
+
+def test_single_handle_autotune_keeps_environment():
+    """ipeps_ctm_autotune restores the environment; tuned tiles change results only by rounding."""
+    from paper_1711_04798_gb300 import CTM
+    w = synth.workload("cfg2", seed=4, D=3, chi=16)
+    kw = dict(DEFAULTS, cutoff=1e-6, prec="bf16x3")
+    a = CTM(w["tensors"], w["pattern"], 16, **kw)
+    b = CTM(w["tensors"], w["pattern"], 16, **kw)
+    a.sweep(1)
+    b.sweep(1)
+    env_before = b.env(4, 0, 0)
+    n = b.autotune()
+    assert n > 0
+    assert np.array_equal(b.env(4, 0, 0), env_before)
+    a.sweep(2)
+    b.sweep(2)
+    assert abs(a.energy(w["J"]) - b.energy(w["J"])) < 1e-6
+    assert a.autotune() > 0 and CTM(w["tensors"], w["pattern"], 16, **dict(kw, prec="fp64")).autotune() == 0
+    a.close()
+    b.close()
