@@ -311,13 +311,12 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 }
 
 // Ar[m, kr], padded to Mp x Krp (K-major)
-template <int PREC>
+template <int PREC, typename Idx>
 __global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int Krp,
                               void* __restrict__ o0, void* __restrict__ o1) {
-  const long long total = (long long)Mp * Krp;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(e / Krp), kr = (int)(e % Krp);
+  const Idx total = (Idx)Mp * (Idx)Krp;
+  for (Idx e = (Idx)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (Idx)gridDim.x * blockDim.x) {
+    const int m = (int)(e / (Idx)Krp), kr = (int)(e - (Idx)m * (Idx)Krp);
     double x = 0.0;
     if (m < M && kr < 2 * K) {
       const cplx v = load_op(A, lda, opA, m, kr >> 1);
@@ -336,13 +335,12 @@ __global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA
 }
 
 // Br^T[nr, kr] = [[Re, Im], [-Im, Re]][kr%2][nr%2] of B[kr/2, nr/2], padded to Nrp x Krp
-template <int PREC>
+template <int PREC, typename Idx>
 __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp, int Krp,
                               void* __restrict__ o0, void* __restrict__ o1) {
-  const long long total = (long long)Nrp * Krp;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int nr = (int)(e / Krp), kr = (int)(e % Krp);
+  const Idx total = (Idx)Nrp * (Idx)Krp;
+  for (Idx e = (Idx)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (Idx)gridDim.x * blockDim.x) {
+    const int nr = (int)(e / (Idx)Krp), kr = (int)(e - (Idx)nr * (Idx)Krp);
     double x = 0.0;
     if (nr < 2 * N && kr < 2 * K) {
       const cplx v = load_op(B, ldb, opB, kr >> 1, nr >> 1);
@@ -440,7 +438,11 @@ template <int PREC>
 cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, int N, int K, long long Nrp,
                        long long Krp, void* b0, void* b1) {
   if (opB & OP_T) {
-    pack_b_kernel<PREC><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
+    if (Nrp * Krp < (1LL << 31))
+      pack_b_kernel<PREC, unsigned><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
+    else
+      pack_b_kernel<PREC, unsigned long long><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp,
+                                                                                   (int)Krp, b0, b1);
   } else {
     dim3 grid((unsigned)((Nrp / 2 + 31) / 32), (unsigned)((Krp / 2 + 31) / 32));
     pack_b_tr_kernel<PREC><<<grid, dim3(32, 8), 0, s>>>(B, ldb, (opB & OP_CONJ) ? 1 : 0, N, K, (int)Nrp, (int)Krp,
@@ -641,7 +643,12 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   }
   if (part_bytes(eff_splits(o.kb_total, choice.splits)) > part_room) return cudaErrorMemoryAllocation;
 
-  pack_a_kernel<PREC><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp, o.a0, o.a1);
+  if (o.Mp * o.Krp < (1LL << 31))
+    pack_a_kernel<PREC, unsigned><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp,
+                                                                         o.a0, o.a1);
+  else
+    pack_a_kernel<PREC, unsigned long long><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp,
+                                                                                   (int)o.Krp, o.a0, o.a1);
   count_launch();
   cudaError_t e;
   if (pre) {

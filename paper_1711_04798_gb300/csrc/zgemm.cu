@@ -149,15 +149,16 @@ struct PermParams {
   long long istr[8];
 };
 
+template <typename Idx>
 __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ out,
                                long long total, PermParams p, int conj, cplx alpha, int unit) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    long long r = i, off = 0;
+  for (Idx i = (Idx)blockIdx.x * (Idx)blockDim.x + threadIdx.x; i < (Idx)total; i += (Idx)gridDim.x * blockDim.x) {
+    Idx r = i, off = 0;
     for (int a = p.nd - 1; a >= 0; --a) {
-      const long long c = r % p.odims[a];
-      r /= p.odims[a];
-      off += c * p.istr[a];
+      const Idx d = (Idx)p.odims[a];
+      const Idx q = r / d;
+      off += (r - q * d) * (Idx)p.istr[a];
+      r = q;
     }
     cplx v = in[off];
     if (conj) v.y = neg_bits(v.y);
@@ -229,16 +230,29 @@ cudaError_t permute(cudaStream_t s, const cplx* in, cplx* out, int nd, const int
     istride[a] = acc;
     acc *= in_dims[a];
   }
+  // output axes that stay adjacent and in order in the input merge into one
+  // (fewer divisions per element)
+  p.nd = 0;
   for (int i = 0; i < nd; ++i) {
-    p.odims[i] = in_dims[perm[i]];
-    p.istr[i] = istride[perm[i]];
+    if (p.nd > 0 && perm[i] == perm[i - 1] + 1) {
+      p.odims[p.nd - 1] *= in_dims[perm[i]];
+      p.istr[p.nd - 1] = istride[perm[i]];
+    } else {
+      p.odims[p.nd] = in_dims[perm[i]];
+      p.istr[p.nd] = istride[perm[i]];
+      ++p.nd;
+    }
   }
   const long long total = acc;
   if (total == 0) return cudaSuccess;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   const int unit = alpha.x == 1.0 && alpha.y == 0.0;
-  permute_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, total, p, conj ? 1 : 0, alpha, unit);
+  if (total < (1LL << 31))  // 32-bit index arithmetic (offsets are below total)
+    permute_kernel<unsigned><<<(unsigned)blocks, 256, 0, s>>>(in, out, total, p, conj ? 1 : 0, alpha, unit);
+  else
+    permute_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, s>>>(in, out, total, p, conj ? 1 : 0, alpha,
+                                                                         unit);
   count_launch();
   return cudaGetLastError();
 }
