@@ -1083,7 +1083,8 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
   CKS(cholqr_pass(h, Wt, out, R1, 1e-14));
   CKS(cholqr_pass(h, out, nullptr, R2, 1e-14, false));  // only R2 is needed
   // Rt = (R2 R1)^T: rows of Rt are the columns of R
-  CK(zgemm(h->stream, k, k, k, ONE, R1, k, OP_T, R2, k, OP_T, ZERO, Rt, k));
+  CK(zgemm(h->stream, k, k, k, ONE, R1, k, OP_T, R2, k, OP_T, ZERO, Rt, k, GemmBatch{1, 0, 0, 0},
+           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, ZG_A_LOWER));
   {
     cudaEvent_t a = nullptr;
     prof_begin(h, &a);

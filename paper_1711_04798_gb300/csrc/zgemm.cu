@@ -179,19 +179,22 @@ cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A
   if ((flags & ZG_UPPER_TILES) && M != N) return cudaErrorInvalidValue;
   const long long tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   const long long tiles = (flags & ZG_UPPER_TILES) ? tm * (tm + 1) / 2 : tm * tn;
-  // Few output tiles: split K over the grid.  Every SM's FP64 units carry the
-  // product, so the split minimises (CTA waves over 152 SMs) x (k-tiles per
-  // CTA), with whole k-tiles per split; work of a lower-triangular A counted
-  // per tile row.
+  // Few output tiles: split K over the grid, whole k-tiles per split.  Every
+  // SM's FP64 units carry the product, and one 8-warp CTA per SM leaves them
+  // idle part of the time: measured on GB300, a lone CTA takes ~1.64x the time
+  // per k-tile of two co-resident ones.  Cost = k-tiles per CTA x (1.64 for a
+  // single wave of at most one CTA per SM, else the CTAs on the busiest SM).
   if (batch.count == 1 && work && tiles < 152 && K >= 2 * BK) {
     const long long kb = (K + BK - 1) / BK;
-    long long best_S = 1, best_cost = -1;
-    for (long long S = 1; S <= 64 && S <= kb; ++S) {
+    long long best_S = 1;
+    double best_cost = -1.0;
+    for (long long S = 1; S <= 160 && S <= kb; ++S) {
       const long long kps = (kb + S - 1) / S, Se = (kb + kps - 1) / kps;
       if (Se > 1 && Se * M * N > work_elems) break;
-      const long long waves = (tiles * Se + 151) / 152;
-      const long long cost = waves * kps * 16 + Se;  // small tie-break against many partials
-      if (best_cost < 0 || cost < best_cost) {
+      const long long ctas = tiles * Se;
+      const double per_sm = ctas <= 152 ? 1.64 : (double)((ctas + 151) / 152);
+      const double cost = (double)kps * per_sm + 1e-4 * (double)Se;  // tie-break: fewer partials
+      if (best_cost < 0.0 || cost < best_cost) {
         best_cost = cost;
         best_S = Se;
       }
