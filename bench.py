@@ -227,6 +227,7 @@ def run_ours(args, rank, world, local_rank):
     launches = g.launch_count() - l0
     gemm = g.profile_read(0)
     jac = g.profile_read(1)
+    f64g = g.profile_read(2)
     g.profile(False)
     t = torch.tensor([ms], device="cuda", dtype=torch.float64)
     if dist:
@@ -259,23 +260,34 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
     peaks, peak_src = measured_peaks()
+    zpk = zgemm_peak_tflops(torch)
+    zsrc = "cuBLAS complex128 GEMM measured in this run (no FP64 entry in the peaks file)"
+    classes = []
     if args.prec == "fp64":
-        zpk = zgemm_peak_tflops(torch)
-        roof = {"bound": "alu", "achieved": gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] else None,
-                "peak": zpk, "unit": "TFLOP/s", "traffic": None,
-                "kernel": "zgemm_kernel (complex FP64 GEMM, CUDA cores)",
-                "peak_source": "cuBLAS complex128 GEMM measured in this run (no FP64 entry in the peaks file)"}
+        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM, CUDA cores): contractions", "bound": "alu",
+                        "ms": gemm["ms"], "flops": gemm["flops"], "launches": gemm["launches"], "peak": zpk,
+                        "peak_source": zsrc})
     else:
-        pk = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "achieved": gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] else None,
-                "peak": pk, "unit": "TFLOP/s", "traffic": None, "kernel": "tcgen05 GEMM",
-                "peak_source": f"bf16 sustained ({peak_src})"}
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] and roof["peak"] else None
-    roof["gemm_share_of_step"] = gemm["ms"] / ms if ms else None
-    roof["gemm_launches"] = gemm["launches"]
-    roof["jacobi_ms_share"] = jac["ms"] / ms if ms else None
-    roof["jacobi_calls"] = jac["launches"]
-    roof["jacobi_mean_sweeps"] = jac["flops"]
+        classes.append({"kernel": "tc_gemm_kernel (tcgen05 " + args.prec + ") with operand packing: contractions",
+                        "bound": "tensor", "ms": gemm["ms"], "flops": gemm["flops"], "launches": gemm["launches"],
+                        "peak": peaks.get("bf16_tflops_sustained", 1700.0),
+                        "peak_source": f"bf16 sustained ({peak_src}); algorithmic flops (x3 executed for bf16x3)"})
+        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM): CholeskyQR Grams/applies of the projectors",
+                        "bound": "alu", "ms": f64g["ms"], "flops": f64g["flops"], "launches": f64g["launches"],
+                        "peak": zpk, "peak_source": zsrc})
+    for c in classes:
+        c["achieved"] = c["flops"] / (c["ms"] * 1e-3) / 1e12 if c["ms"] else None
+        c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
+        c["share_of_step"] = c["ms"] / ms if ms else None  # lanes overlap: shares can sum above 1
+        c["unit"] = "TFLOP/s"
+    dom = max(classes, key=lambda c: c["ms"])
+    roof = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"], "unit": "TFLOP/s",
+            "frac": dom["frac"], "traffic": None, "kernel": dom["kernel"], "peak_source": dom["peak_source"],
+            "dominant_by": "CUDA-event time of the kernel class inside the timed steps",
+            "by_class": [{k: c[k] for k in ("kernel", "bound", "achieved", "peak", "frac", "share_of_step",
+                                             "launches")} for c in classes],
+            "jacobi_ms_share": jac["ms"] / ms if ms else None, "jacobi_calls": jac["launches"],
+            "jacobi_mean_sweeps": jac["flops"]}
     fp64_cmp = None
     if args.prec != "fp64" and not args.no_fp64_check:
         # the same number of sweeps from the trace initialisation, plain FP64 GPU path

@@ -219,11 +219,15 @@ ipeps_status ipeps_ctm_sync(ipeps_ctm h);
 uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
 
 /* Kernel-class timing for roofline reports: with enable != 0 every
- * contraction GEMM (kind 0) and every Jacobi SVD (kind 1) is bracketed by
- * CUDA events on the handle's stream.  profile() clears the records;
- * profile_read() synchronises and returns the summed event time (ms), the
- * number of launches and (kind 0) the algorithmic flops, 8*M*N*K per complex
- * GEMM, or (kind 1) the mean number of sweeps per Jacobi call.  Not a paper
+ * contraction GEMM (kind 0), every Jacobi SVD (kind 1) and every FP64 GEMM of
+ * the precision form's projector step (kind 2: CholeskyQR Grams and applies,
+ * core products) is bracketed by CUDA events on the stream that runs it.
+ * profile() clears the records; profile_read() synchronises and returns the
+ * summed event time (ms), the number of launches and (kinds 0, 2) the
+ * algorithmic flops (8*M*N*K per complex GEMM; Hermitian and triangular
+ * results count their nonzero part), or (kind 1) the mean number of sweeps per
+ * Jacobi call.  With two projector lanes the brackets of concurrent work
+ * overlap, so class times can sum to more than the step.  Not a paper
  * operation: measurement support only. */
 ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable);
 ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms, uint64_t* launches,

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(CL_THREADS)
   const int R = (n + cs - 1) / cs;  // row slots per CTA
   extern __shared__ cplx sm[];      // [R x m] rows of G, then [R x n] rows of Vt
   __shared__ double s_fro;
-  __shared__ int s_rot;
+  __shared__ int s_rot, s_big;
   cplx* gl = sm;
   cplx* vl = sm + (long long)R * m;
   double f = 0.0;
@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(CL_THREADS)
     for (int w = 0; w < nwarps; ++w) t += s_w[w];
     s_fro = t;
     s_rot = 0;
+    s_big = 0;
   }
   cl.sync();
   double fro2 = 0.0;
@@ -129,6 +130,9 @@ __global__ void __launch_bounds__(CL_THREADS)
             phr = gr / g;
             phi = -gim / g;
             rot = 1;
+            // a rotation with off-orthogonality or angle above 1e-8 keeps the
+            // sweep from being the last one
+            if (g * g > 1e-16 * al * be || fabs(s) > 1e-8) s_big = 1;
           }
         }
         rot = __shfl_sync(0xffffffffu, rot, 0);
@@ -158,12 +162,22 @@ __global__ void __launch_bounds__(CL_THREADS)
       }
       cl.sync();
     }
-    int total = 0;
-    for (int r = 0; r < cs; ++r) total += *cl.map_shared_rank(&s_rot, r);
+    int total = 0, big = 0;
+    for (int r = 0; r < cs; ++r) {
+      total += *cl.map_shared_rank(&s_rot, r);
+      big |= *cl.map_shared_rank(&s_big, r);
+    }
     cl.sync();  // every CTA has read every count
-    if (threadIdx.x == 0) s_rot = 0;
+    if (threadIdx.x == 0) {
+      s_rot = 0;
+      s_big = 0;
+    }
     cl.sync();
-    if (total == 0) {
+    // No rotation: converged.  Only rotations with off-orthogonality and angle
+    // <= 1e-8: each later rotation changed an earlier pair's inner product by at
+    // most 1e-16 relative, so the rows are orthogonal to ~k * 1e-16 (the
+    // m * eps tolerance) and the confirming sweep is skipped.
+    if (total == 0 || big == 0) {
       converged = true;
       break;
     }

@@ -1027,6 +1027,19 @@ static ipeps_status orth(ipeps_ctm h, cplx* G) {
   return IPEPS_OK;
 }
 
+// FP64 GEMM of the projector step, bracketed as profiling class 2 with its
+// algorithmic flops (structure-aware: a Hermitian Gram counts its upper
+// triangle, a triangular factor its nonzero part).
+static cudaError_t proj_zgemm(ipeps_ctm h, double flops, int M, int N, int K, const cplx* A, long long lda,
+                              int opA, const cplx* B, long long ldb, int opB, cplx* C, long long ldc, int flags) {
+  cudaEvent_t ev = nullptr;
+  prof_begin(h, &ev);
+  cudaError_t e = zgemm(h->stream, M, N, K, ONE, A, lda, opA, B, ldb, opB, ZERO, C, ldc, GemmBatch{1, 0, 0, 0},
+                        h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, flags);
+  prof_end(h, ev, flops, 2);
+  return e;
+}
+
 // Precision form, one CholeskyQR pass on the k rows of `in` (length K):
 // G = conj(in) in^T (FP64), G = R^H R (dropped pivots below tol * max), out =
 // R^{-T} in (rows orthonormal on the kept directions, zero elsewhere).  R is
@@ -1041,14 +1054,12 @@ static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Ro
   cplx* Ri = scratch_alloc(h, (long long)k * k);
   if (!G || !W || !R || !Ri) return fail(IPEPS_ENOMEM, "scratch exhausted (cholqr)");
   // Hermitian Gram: the Cholesky reads its upper triangle only
-  CK(zgemm(h->stream, k, k, K, ONE, in, K, OP_C, in, K, OP_T, ZERO, G, k, GemmBatch{1, 0, 0, 0},
-           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, ZG_UPPER_TILES));
+  CK(proj_zgemm(h, 8.0 * K * (0.5 * k * (k + 1)), k, k, K, in, K, OP_C, in, K, OP_T, G, k, ZG_UPPER_TILES));
   CK(chol_drop(h->stream, G, W, R, k, tol));
   if (apply) {
     CK(tri_inv(h->stream, R, Ri, k));
     // Q = Y R^{-1}  ->  Q^T = R^{-T} Y^T
-    CK(zgemm(h->stream, k, K, k, ONE, Ri, k, OP_T, in, K, OP_N, ZERO, out, K, GemmBatch{1, 0, 0, 0},
-             h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, ZG_A_LOWER));
+    CK(proj_zgemm(h, 8.0 * K * (0.5 * k * (k + 1)), k, K, k, Ri, k, OP_T, in, K, OP_N, out, K, ZG_A_LOWER));
   }
   h->scratch_top = mark;
   return IPEPS_OK;
@@ -1083,8 +1094,7 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
   CKS(cholqr_pass(h, Wt, out, R1, 1e-14));
   CKS(cholqr_pass(h, out, nullptr, R2, 1e-14, false));  // only R2 is needed
   // Rt = (R2 R1)^T: rows of Rt are the columns of R
-  CK(zgemm(h->stream, k, k, k, ONE, R1, k, OP_T, R2, k, OP_T, ZERO, Rt, k, GemmBatch{1, 0, 0, 0},
-           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, ZG_A_LOWER));
+  CK(proj_zgemm(h, 8.0 * k * (k + 1.0) * (k + 2.0) / 6.0, k, k, k, R1, k, OP_T, R2, k, OP_T, Rt, k, ZG_A_LOWER));
   {
     cudaEvent_t a = nullptr;
     prof_begin(h, &a);
@@ -1096,8 +1106,7 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
     prof_end(h, a, 0.0, 1);
   }
   // out = V^T Wt  (rows (W v_i)^T)
-  CK(zgemm(h->stream, k, K, k, ONE, h->Vt, k, OP_N, Wt, K, OP_N, ZERO, out, K, GemmBatch{1, 0, 0, 0},
-           h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top));
+  CK(proj_zgemm(h, 8.0 * k * (double)K * k, k, K, k, h->Vt, k, OP_N, Wt, K, OP_N, out, K, 0));
   CK(row_norms(h->stream, out, k, K, K, h->sigma));
   h->scratch_top = mark;
   return IPEPS_OK;
