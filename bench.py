@@ -475,10 +475,16 @@ def run_cylinder(args, rank, world, local_rank):
                              "lam_top4": [float(v) for v in lam[:4]]})
         Nv = 6
         k = min(args.topk, D ** Nv)
+        g.profile(True)
         (lam, S, rest, nconv), t = timed(lambda: g.boundary_rho_topk(0, Nv, k, max_iter=min(8 * k, 1024),
                                                                      tol=1e-8))
+        ring, lz = g.profile_read(3), g.profile_read(4)
+        g.profile(False)
         readouts.append({"Nv": Nv, "route": "lanczos", "dim": int(D ** Nv), "k": k, "converged": nconv,
                          "S_vn_topk": S, "rest_weight": rest, "seconds": t,
+                         "ring_build_s": ring["ms"] * 1e-3,
+                         "ring_products_tflops": ring["flops"] / (ring["ms"] * 1e-3) / 1e12 if ring["ms"] else None,
+                         "lanczos_s": lz["ms"] * 1e-3, "lanczos_steps": int(lz["flops"]),
                          "lam_top4": [float(v) for v in lam[:4]]})
     e = g.energy(w["J"])
     g.close()

@@ -226,7 +226,9 @@ uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
  * summed event time (ms), the number of launches and (kinds 0, 2) the
  * algorithmic flops (8*M*N*K per complex GEMM; Hermitian and triangular
  * results count their nonzero part), or (kind 1) the mean number of sweeps per
- * Jacobi call.  With two projector lanes the brackets of concurrent work
+ * Jacobi call.  ipeps_boundary_rho_topk adds kind 3 (building both dense ring
+ * operators; flops: the two ring products, 16 n^2 chi^2) and kind 4 (the
+ * Lanczos iteration; "flops" holds its step count).  With two projector lanes the brackets of concurrent work
  * overlap, so class times can sum to more than the step.  Not a paper
  * operation: measurement support only. */
 ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable);

@@ -1895,8 +1895,11 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
   h->scratch_elems = region_elems;
   h->scratch_top = 0;
   const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
+  cudaEvent_t pr = nullptr;
+  prof_begin(h, &pr);
   ipeps_status st = ring_sigma_dense(h, 3, xl, Nv, sL);
   if (st == IPEPS_OK) st = ring_sigma_dense(h, 1, xr, Nv, sR);
+  prof_end(h, pr, 2.0 * 8.0 * (double)n * (double)n * (double)c2, 3);
   h->scratch = save_scratch;
   h->scratch_elems = save_elems;
   h->scratch_top = save_top;
@@ -1910,10 +1913,12 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
     cplx* work = region + 2 * n2;
     const long long work_elems = region_elems - 2 * n2;
     e = cudaGetLastError();
+    cudaEvent_t pl = nullptr;
+    prof_begin(h, &pl);
     if (e == cudaSuccess)
       e = lanczos_leading(h->stream, sL, sR, n, k, max_iter, tol, h->opt.omega_seed ^ 0x5bd1e995ULL, work,
-                          work_elems, h->sigma, h->perm, h->s_sel, h->dwork, h->counters, h->st,
-                          h->opt.jacobi_max_sweeps, &res);
+                          work_elems, h->s_sel, &res);
+    prof_end(h, pl, (double)res.iters, 4);
     double2* partial = (double2*)work;
     double2* trd = partial + 512;
     double* lam = (double*)(trd + 1);

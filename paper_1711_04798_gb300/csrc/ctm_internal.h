@@ -151,10 +151,9 @@ cudaError_t zgemv_dense(cudaStream_t s, const cplx* A, long long n, const cplx* 
 long long lanczos_work_elems(long long n, int max_iter);
 // Leading k eigenvalues of M = A B (A, B Hermitian, B positive definite) by
 // Lanczos in the B inner product with full reorthogonalisation; on return
-// s_sel[0..k) holds the Ritz values, descending (device), perm their indices.
+// s_sel[0..k) holds the Ritz values, descending (device).
 cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long long n, int k, int max_iter,
-                            double tol, uint64_t seed, cplx* work, long long work_elems, double* sigma, int* perm,
-                            double* s_sel, double* dwork, int* counters, DevStatus* st, int jac_sweeps,
+                            double tol, uint64_t seed, cplx* work, long long work_elems, double* s_sel,
                             LanczosResult* res);
 // lam = theta / Re tr(A B) (k values) and out = {-sum lam ln lam, 1 - sum lam}
 cudaError_t topk_finish(cudaStream_t s, const cplx* A, const cplx* B, long long n, const double* theta, int k,

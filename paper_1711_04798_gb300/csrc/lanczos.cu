@@ -14,8 +14,9 @@
 //     r -= V (U^H r)  (twice: full reorthogonalisation in the B product),
 //     s = B r,  beta_{j+1} = sqrt(r^H s),  v_{j+1} = r / beta,  u_{j+1} = s / beta.
 // The Ritz values are the eigenvalues of the tridiagonal T(alpha, beta),
-// found by the FP64 one-sided Jacobi kernel; the residual of Ritz pair i is
-// beta_m |y_i[m-1]| (Parlett, "The Symmetric Eigenvalue Problem", ch. 13).
+// found by bisection on Sturm counts; the residual of Ritz pair i is
+// beta_m |y_i[m-1]| (Parlett, "The Symmetric Eigenvalue Problem", ch. 13),
+// the last component from inverse iteration.
 // Everything is FP64; A and B are dense row-major complex matrices.
 #include "ctm_internal.h"
 
@@ -172,29 +173,84 @@ __global__ void scale_pair_kernel(const cplx* __restrict__ r, const cplx* __rest
   }
 }
 
-// T = tridiag(alpha_0..m-1; beta_1..m-1) as an m x m complex matrix
-__global__ void tridiag_kernel(const double2* __restrict__ adot, const double2* __restrict__ bdot, int m,
-                               cplx* __restrict__ T) {
-  const long long total = (long long)m * m;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / m), j = (int)(e % m);
-    double v = 0.0;
-    if (i == j) v = adot[i].x;
-    else if (j == i + 1) v = beta_of(bdot[j]);
-    else if (i == j + 1) v = beta_of(bdot[i]);
-    T[e] = make_double2(v, 0.0);
+// Leading k eigenvalues of the symmetric tridiagonal T (diagonal alpha_i =
+// adot[i].x, off-diagonal beta_i = sqrt(bdot[i].x), i = 1..m-1) and the
+// residual estimates beta_m |y_i[m-1]| of their Ritz pairs.  Block a finds the
+// a-th largest eigenvalue by bisection on Sturm counts (the number of negative
+// pivots of T - x I is the number of eigenvalues below x; Wilkinson, "The
+// Algebraic Eigenvalue Problem", ch. 5), then the eigenvector's last
+// component by inverse iteration with (T - theta I) factored without pivoting
+// (a tiny shift guards exact singularity).  One lane per block computes.
+__device__ int sturm_below(const double2* __restrict__ adot, const double2* __restrict__ bdot, int m, double x,
+                           double pivmin) {
+  int cnt = 0;
+  double q = adot[0].x - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < m; ++i) {
+    const double b2 = bdot[i].x > 0.0 ? bdot[i].x : 0.0;
+    q = (adot[i].x - x) - b2 / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
   }
+  return cnt;
 }
 
-// residual of Ritz pair i: beta_m |last component of eigenvector i|; the
-// eigenvectors of T are the conjugated rows of the accumulated rotations Tv
-__global__ void ritz_resid_kernel(const cplx* __restrict__ Tv, int m, const double2* __restrict__ bdot,
-                                  const int* __restrict__ perm, int k, double* __restrict__ resid) {
-  const double bm = beta_of(bdot[m]);
-  for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    const int i = perm[a];
-    resid[a] = i < 0 ? 0.0 : bm * hypot(Tv[(long long)i * m + m - 1].x, Tv[(long long)i * m + m - 1].y);
+__global__ void tridiag_topk_kernel(const double2* __restrict__ adot, const double2* __restrict__ bdot, int m, int k,
+                                    double* __restrict__ theta, double* __restrict__ resid, double* __restrict__ work) {
+  const int a = blockIdx.x;
+  if (threadIdx.x != 0 || a >= k) return;
+  // Gershgorin interval
+  double lo = 1e300, hi = -1e300, bmax = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double bl = i > 0 ? beta_of(bdot[i]) : 0.0, br = i + 1 < m ? beta_of(bdot[i + 1]) : 0.0;
+    lo = fmin(lo, adot[i].x - bl - br);
+    hi = fmax(hi, adot[i].x + bl + br);
+    bmax = fmax(bmax, bl);
   }
+  const double scale = fmax(fabs(lo), fabs(hi));
+  const double pivmin = fmax(1e-300, 1e-30 * scale * scale) / fmax(scale, 1e-300);
+  // the (m - 1 - a)-th smallest = the a-th largest
+  const int target = m - a;  // eigenvalue with exactly target - 1 below it
+  double l = lo, h = hi;
+  for (int it = 0; it < 200 && h - l > 2.2e-16 * fmax(fabs(l), fabs(h)) + 1e-300; ++it) {
+    const double mid = 0.5 * (l + h);
+    if (sturm_below(adot, bdot, m, mid, pivmin) >= target) h = mid; else l = mid;
+  }
+  const double th = 0.5 * (l + h);
+  theta[a] = th;
+  // inverse iteration on (T - s I), s = th + tiny: y <- solve, normalise
+  double* dd = work + (long long)a * 3 * m;  // pivots
+  double* y = dd + m;
+  double* lw = y + m;  // multipliers
+  const double shift = th + 1e-14 * fmax(scale, 1e-300);
+  for (int i = 0; i < m; ++i) y[i] = 1.0;
+  double last = 0.0;
+  for (int pass = 0; pass < 3; ++pass) {
+    // LU of T - shift I without pivoting: d_0 = a_0 - s, l_i = b_i / d_{i-1}, d_i = a_i - s - l_i b_i
+    double d = adot[0].x - shift;
+    if (fabs(d) < pivmin) d = pivmin;
+    dd[0] = d;
+    for (int i = 1; i < m; ++i) {
+      const double b = beta_of(bdot[i]);
+      const double li = b / dd[i - 1];
+      lw[i] = li;
+      double di = (adot[i].x - shift) - li * b;
+      if (fabs(di) < pivmin) di = pivmin;
+      dd[i] = di;
+    }
+    // forward (L z = y), backward (U x = z), U = diag(d) + superdiag(b)
+    for (int i = 1; i < m; ++i) y[i] -= lw[i] * y[i - 1];
+    y[m - 1] /= dd[m - 1];
+    for (int i = m - 2; i >= 0; --i) y[i] = (y[i] - beta_of(bdot[i + 1]) * y[i + 1]) / dd[i];
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
+    nrm = sqrt(nrm);
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = 0; i < m; ++i) y[i] *= inv;
+    last = y[m - 1];
+  }
+  resid[a] = beta_of(bdot[m]) * fabs(last);
 }
 
 // lam = theta / tr M (k values, descending); out = {S = -sum lam ln lam, 1 - sum lam}
@@ -241,8 +297,7 @@ long long lanczos_work_elems(long long n, int max_iter) {
 }
 
 cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long long n, int k, int max_iter,
-                            double tol, uint64_t seed, cplx* work, long long work_elems, double* sigma, int* perm,
-                            double* s_sel, double* dwork, int* counters, DevStatus* st, int jac_sweeps,
+                            double tol, uint64_t seed, cplx* work, long long work_elems, double* s_sel,
                             LanczosResult* res) {
   res->iters = 0;
   res->converged = 0;
@@ -256,9 +311,8 @@ cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long l
   cplx* w = U + (M + 1) * n;
   cplx* r = w + n;
   cplx* sv = r + n;
-  cplx* T = sv + n;
-  cplx* Tv = T + M * M;
-  cplx* c = Tv + M * M;
+  cplx* T = sv + n;  // 2 M^2 complex slots: work of the tridiagonal eigensolver
+  cplx* c = T + 2 * M * M;
   double2* adot = (double2*)(c + M);
   double2* bdot = adot + M;
   double* resid = (double*)(bdot + M + 1);  // M doubles
@@ -315,12 +369,7 @@ cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long l
     }
     // Ritz check every 10 steps once k + 10 values exist (the end is handled below)
     if (m >= k + 10 && m % 10 == 0 && m < max_iter) {
-      tridiag_kernel<<<blocks_for((long long)m * m), 256, 0, s>>>(adot, bdot, m, T);
-      count_launch();
-      if ((e = check()) != cudaSuccess) return e;
-      if ((e = jacobi_rows(s, T, m, m, m, Tv, sigma, jac_sweeps, dwork, counters, st)) != cudaSuccess) return e;
-      if ((e = select_top(s, sigma, m, k, 0.0, perm, s_sel)) != cudaSuccess) return e;
-      ritz_resid_kernel<<<1, 256, 0, s>>>(Tv, m, bdot, perm, k, resid);
+      tridiag_topk_kernel<<<k, 32, 0, s>>>(adot, bdot, m, k, s_sel, resid, (double*)T);
       count_launch();
       if ((e = check()) != cudaSuccess) return e;
       double th0 = 0.0;
@@ -341,16 +390,16 @@ cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long l
     // fewer steps than requested values (breakdown): all m Ritz values are exact
     res->converged = m;
   }
-  tridiag_kernel<<<blocks_for((long long)m * m), 256, 0, s>>>(adot, bdot, m, T);
+  const int kk = m < k ? m : k;  // after an early breakdown only m Ritz values exist
+  if (kk < k) {
+    if ((e = cudaMemsetAsync(s_sel, 0, k * sizeof(double), s)) != cudaSuccess) return e;
+  }
+  tridiag_topk_kernel<<<kk, 32, 0, s>>>(adot, bdot, m, kk, s_sel, resid, (double*)T);
   count_launch();
   if ((e = check()) != cudaSuccess) return e;
-  if ((e = jacobi_rows(s, T, m, m, m, Tv, sigma, jac_sweeps, dwork, counters, st)) != cudaSuccess) return e;
-  if ((e = select_top(s, sigma, m, k, 0.0, perm, s_sel)) != cudaSuccess) return e;
   if (res->breakdown) {
-    res->converged = m < k ? m : k;
+    res->converged = kk;
   } else {
-    ritz_resid_kernel<<<1, 256, 0, s>>>(Tv, m, bdot, perm, k, resid);
-    count_launch();
     if ((e = check()) != cudaSuccess) return e;
     double th0 = 0.0;
     std::vector<double> rs(k);
