@@ -192,9 +192,13 @@ ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int
  * precision forms), phase-fixed and Hermitised.  The k largest eigenvalues of
  * M = sigma_L^T sigma_R then come from a Lanczos iteration in the sigma_R
  * inner product <x,y> = x^H sigma_R y, in which M is self-adjoint when
- * sigma_R is positive definite, with full reorthogonalisation, all in FP64;
- * it stops when each of the k Ritz values has residual <= tol times the
- * largest, or after max_iter steps.  The values are divided by tr M.
+ * sigma_R is positive definite, with full reorthogonalisation: Krylov
+ * vectors, inner products, reorthogonalisation and the tridiagonal eigenvalues
+ * in FP64; the mat-vec products in FP64 for an FP64 handle and on the FP32
+ * pipe with FP64 accumulation in the precision forms (whose ring operators
+ * carry ~1e-6 relative error).  It stops when each of the k Ritz values has
+ * residual <= tol times the largest, or after max_iter steps.  The values
+ * are divided by tr M.
  *   eig_out: k doubles, descending (caller-owned host; may be NULL);
  *   *n_conv: how many of the k met tol (k when an invariant subspace was hit);
  *   *S_vn = -sum lam ln lam over the k values; *rest = 1 - sum of the k.

@@ -1917,7 +1917,7 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
     prof_begin(h, &pl);
     if (e == cudaSuccess)
       e = lanczos_leading(h->stream, sL, sR, n, k, max_iter, tol, h->opt.omega_seed ^ 0x5bd1e995ULL, work,
-                          work_elems, h->s_sel, &res);
+                          work_elems, h->s_sel, h->opt.prec != IPEPS_PREC_FP64, &res);
     prof_end(h, pl, (double)res.iters, 4);
     double2* partial = (double2*)work;
     double2* trd = partial + 512;

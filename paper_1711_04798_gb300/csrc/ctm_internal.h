@@ -145,16 +145,18 @@ struct LanczosResult {
 };
 // *out = sum conj(x) y over n entries (fixed order); partial: 512 double2
 cudaError_t zdotc_dev(cudaStream_t s, const cplx* x, const cplx* y, long long n, double2* partial, double2* out);
-// y = A x for a dense n x n row-major A
-cudaError_t zgemv_dense(cudaStream_t s, const cplx* A, long long n, const cplx* x, cplx* y);
+// y = A x for a dense n x n row-major A; fp32_products: products on the FP32
+// pipe, FP64 accumulation of groups of four (for precision-form operators)
+cudaError_t zgemv_dense(cudaStream_t s, const cplx* A, long long n, const cplx* x, cplx* y, bool fp32_products);
 // complex elements of work lanczos_leading needs
 long long lanczos_work_elems(long long n, int max_iter);
 // Leading k eigenvalues of M = A B (A, B Hermitian, B positive definite) by
 // Lanczos in the B inner product with full reorthogonalisation; on return
-// s_sel[0..k) holds the Ritz values, descending (device).
+// s_sel[0..k) holds the Ritz values, descending (device).  fp32_products:
+// mat-vecs with FP32 products (operators built in the precision form).
 cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long long n, int k, int max_iter,
                             double tol, uint64_t seed, cplx* work, long long work_elems, double* s_sel,
-                            LanczosResult* res);
+                            bool fp32_products, LanczosResult* res);
 // lam = theta / Re tr(A B) (k values) and out = {-sum lam ln lam, 1 - sum lam}
 cudaError_t topk_finish(cudaStream_t s, const cplx* A, const cplx* B, long long n, const double* theta, int k,
                         double2* partial, double2* trd, double* lam, double* out);

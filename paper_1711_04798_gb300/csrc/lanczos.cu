@@ -77,6 +77,45 @@ __global__ void __launch_bounds__(256) zgemv_kernel(const cplx* __restrict__ A, 
   if (lane == 0) y[row] = make_double2(re, im);
 }
 
+// y = A x as zgemv_kernel, with the products on the FP32 pipe: A is read as
+// FP64 and narrowed on the integer pipe, x is narrowed once per element,
+// four products are summed in FP32 and every such group is added in FP64.
+// For operators built in the precision form (their entries carry ~1e-6
+// relative error); GB300 issues FP64 too slowly for an HBM-rate mat-vec.
+__global__ void __launch_bounds__(256) zgemv_mixed_kernel(const cplx* __restrict__ A, long long n,
+                                                          const cplx* __restrict__ x, cplx* __restrict__ y) {
+  const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const cplx* a = A + row * n;
+  double re = 0.0, im = 0.0;
+  long long t = lane;
+  for (; t + 96 < n; t += 128) {
+    const cplx a0 = __ldcs(a + t), a1 = __ldcs(a + t + 32), a2 = __ldcs(a + t + 64), a3 = __ldcs(a + t + 96);
+    const cplx x0 = x[t], x1 = x[t + 32], x2 = x[t + 64], x3 = x[t + 96];
+    float r = 0.f, i = 0.f;
+    const float ar0 = d2f_bits(a0.x), ai0 = d2f_bits(a0.y), xr0 = d2f_bits(x0.x), xi0 = d2f_bits(x0.y);
+    const float ar1 = d2f_bits(a1.x), ai1 = d2f_bits(a1.y), xr1 = d2f_bits(x1.x), xi1 = d2f_bits(x1.y);
+    const float ar2 = d2f_bits(a2.x), ai2 = d2f_bits(a2.y), xr2 = d2f_bits(x2.x), xi2 = d2f_bits(x2.y);
+    const float ar3 = d2f_bits(a3.x), ai3 = d2f_bits(a3.y), xr3 = d2f_bits(x3.x), xi3 = d2f_bits(x3.y);
+    r = fmaf(ar0, xr0, r); r = fmaf(-ai0, xi0, r); i = fmaf(ar0, xi0, i); i = fmaf(ai0, xr0, i);
+    r = fmaf(ar1, xr1, r); r = fmaf(-ai1, xi1, r); i = fmaf(ar1, xi1, i); i = fmaf(ai1, xr1, i);
+    r = fmaf(ar2, xr2, r); r = fmaf(-ai2, xi2, r); i = fmaf(ar2, xi2, i); i = fmaf(ai2, xr2, i);
+    r = fmaf(ar3, xr3, r); r = fmaf(-ai3, xi3, r); i = fmaf(ar3, xi3, i); i = fmaf(ai3, xr3, i);
+    re += f2d_bits(r);
+    im += f2d_bits(i);
+  }
+  for (; t < n; t += 32) {
+    const cplx a0 = __ldcs(a + t), x0 = x[t];
+    const float ar = d2f_bits(a0.x), ai = d2f_bits(a0.y), xr = d2f_bits(x0.x), xi = d2f_bits(x0.y);
+    re += f2d_bits(fmaf(ar, xr, -ai * xi));
+    im += f2d_bits(fmaf(ar, xi, ai * xr));
+  }
+  re = warp_sum_d(re);
+  im = warp_sum_d(im);
+  if (lane == 0) y[row] = make_double2(re, im);
+}
+
 // partial[b] = sum over block b's grid-stride slice of conj(x) y
 __global__ void __launch_bounds__(256) zdotc_partial_kernel(const cplx* __restrict__ x, const cplx* __restrict__ y,
                                                             long long n, double2* __restrict__ partial) {
@@ -285,8 +324,11 @@ cudaError_t zdotc_dev(cudaStream_t s, const cplx* x, const cplx* y, long long n,
   return cudaGetLastError();
 }
 
-cudaError_t zgemv_dense(cudaStream_t s, const cplx* A, long long n, const cplx* x, cplx* y) {
-  zgemv_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, x, y);
+cudaError_t zgemv_dense(cudaStream_t s, const cplx* A, long long n, const cplx* x, cplx* y, bool fp32_products) {
+  if (fp32_products)
+    zgemv_mixed_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, x, y);
+  else
+    zgemv_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, x, y);
   count_launch();
   return cudaGetLastError();
 }
@@ -298,7 +340,7 @@ long long lanczos_work_elems(long long n, int max_iter) {
 
 cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long long n, int k, int max_iter,
                             double tol, uint64_t seed, cplx* work, long long work_elems, double* s_sel,
-                            LanczosResult* res) {
+                            bool fp32_products, LanczosResult* res) {
   res->iters = 0;
   res->converged = 0;
   res->breakdown = 0;
@@ -323,7 +365,7 @@ cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long l
 
   // v0: uniform random entries (the range-finder generator), B-normalised
   if ((e = fill_omega_t(s, r, 1, (int)n, seed)) != cudaSuccess) return e;
-  if ((e = zgemv_dense(s, B, n, r, sv)) != cudaSuccess) return e;
+  if ((e = zgemv_dense(s, B, n, r, sv, fp32_products)) != cudaSuccess) return e;
   if ((e = zdotc_dev(s, r, sv, n, partial, &bdot[0])) != cudaSuccess) return e;
   scale_pair_kernel<<<gb, 256, 0, s>>>(r, sv, &bdot[0], n, V, U);
   count_launch();
@@ -334,7 +376,7 @@ cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long l
   for (int j = 0; j < max_iter; ++j) {
     cplx* vj = V + (long long)j * n;
     cplx* uj = U + (long long)j * n;
-    if ((e = zgemv_dense(s, A, n, uj, w)) != cudaSuccess) return e;
+    if ((e = zgemv_dense(s, A, n, uj, w, fp32_products)) != cudaSuccess) return e;
     if ((e = zdotc_dev(s, uj, w, n, partial, &adot[j])) != cudaSuccess) return e;
     lanczos_update_kernel<<<gb, 256, 0, s>>>(w, vj, j > 0 ? vj - n : vj, adot, bdot, j, n, r);
     count_launch();
@@ -344,7 +386,7 @@ cudaError_t lanczos_leading(cudaStream_t s, const cplx* A, const cplx* B, long l
       count_launch(2);
     }
     if ((e = check()) != cudaSuccess) return e;
-    if ((e = zgemv_dense(s, B, n, r, sv)) != cudaSuccess) return e;
+    if ((e = zgemv_dense(s, B, n, r, sv, fp32_products)) != cudaSuccess) return e;
     if ((e = zdotc_dev(s, r, sv, n, partial, &bdot[j + 1])) != cudaSuccess) return e;
     scale_pair_kernel<<<gb, 256, 0, s>>>(r, sv, &bdot[j + 1], n, V + (long long)(j + 1) * n,
                                          U + (long long)(j + 1) * n);
