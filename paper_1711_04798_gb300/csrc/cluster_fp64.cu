@@ -30,6 +30,24 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Sums of four values over a warp with 6 FP64 additions per lane instead of
+// 20: the first two butterfly levels halve the values each lane carries.  On
+// return lane 0 holds the total of a, lane 8 of b, lane 16 of c, lane 24 of d.
+__device__ __forceinline__ double warp_sum4(double a, double b, double c, double d) {
+  const int lane = threadIdx.x & 31;
+  const bool up = lane & 16;
+  double k1 = up ? c : a, k2 = up ? d : b;
+  k1 += __shfl_xor_sync(0xffffffffu, up ? a : c, 16);
+  k2 += __shfl_xor_sync(0xffffffffu, up ? b : d, 16);
+  const bool b3 = lane & 8;
+  double k = b3 ? k2 : k1;
+  k += __shfl_xor_sync(0xffffffffu, b3 ? k1 : k2, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
 __device__ __forceinline__ void pair_of(int r, int p, int np, int rounds, int* i, int* j) {
   int a, b;
   if (p == 0) {
@@ -112,27 +130,31 @@ __global__ void __launch_bounds__(CL_THREADS)
           gr += x.x * y.x + x.y * y.y;
           gim += x.x * y.y - x.y * y.x;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        gr = warp_sum(gr);
-        gim = warp_sum(gim);
+        {
+          const double tot = warp_sum4(al, be, gr, gim);
+          al = __shfl_sync(0xffffffffu, tot, 0);
+          be = __shfl_sync(0xffffffffu, tot, 8);
+          gr = __shfl_sync(0xffffffffu, tot, 16);
+          gim = __shfl_sync(0xffffffffu, tot, 24);
+        }
         // the rotation's scalars on one lane (FP64 divides and roots are
-        // costly here), broadcast to the warp
+        // costly here: two reciprocal roots, one root, one divide), broadcast
         double c = 1.0, s = 0.0, phr = 1.0, phi = 0.0;
         int rot = 0;
         if (lane == 0) {
-          const double g = hypot(gr, gim);
-          if (al > negligible && be > negligible && g > tol * sqrt(al * be)) {
-            const double zeta = (be - al) / (2.0 * g);
+          const double g2 = gr * gr + gim * gim;
+          if (al > negligible && be > negligible && g2 > tol * tol * al * be) {
+            const double ig = rsqrt(g2);
+            const double zeta = 0.5 * (be - al) * ig;
             const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + t * t);
+            c = rsqrt(1.0 + t * t);
             s = c * t;
-            phr = gr / g;
-            phi = -gim / g;
+            phr = gr * ig;
+            phi = -gim * ig;
             rot = 1;
             // a rotation with off-orthogonality or angle above 1e-8 keeps the
             // sweep from being the last one
-            if (g * g > 1e-16 * al * be || fabs(s) > 1e-8) s_big = 1;
+            if (g2 > 1e-16 * al * be || fabs(s) > 1e-8) s_big = 1;
           }
         }
         rot = __shfl_sync(0xffffffffu, rot, 0);
@@ -239,9 +261,9 @@ __global__ void __launch_bounds__(CL_THREADS)
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
   const int R = (n + cs - 1) / cs;
-  extern __shared__ cplx sm[];  // [R x n] rows of the working copy W
-  __shared__ double s_max;
-  double mx = 0.0;
+  extern __shared__ cplx sm[];  // [R x n] rows of the working copy W, then one row: R[j, :]
+  cplx* rj = sm + (long long)R * n;
+  __shared__ double s_max, s_rjj, s_inv;
   for (int l = 0; l < R; ++l) {
     const int i = l * cs + rank;
     if (i >= n) break;
@@ -249,6 +271,7 @@ __global__ void __launch_bounds__(CL_THREADS)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    double mx = 0.0;
     for (int l = 0; l < R; ++l) {
       const int i = l * cs + rank;
       if (i >= n) break;
@@ -262,32 +285,37 @@ __global__ void __launch_bounds__(CL_THREADS)
   const double thr = tol * dmax;
   for (int j = 0; j < n; ++j) {
     const cplx* wj = cl.map_shared_rank(sm, j % cs) + (long long)(j / cs) * n;
-    const double d = wj[j].x;
-    const bool keep = d > thr;
-    const double rjj = keep ? sqrt(d) : 0.0, inv = keep ? 1.0 / rjj : 0.0;
-    if (j % cs == rank) {
-      // row j of R (zero row for a dropped direction)
-      for (int l = threadIdx.x; l < n; l += CL_THREADS) {
-        cplx v = make_double2(0.0, 0.0);
-        if (keep && l >= j) {
-          const cplx g = wj[l];
-          v = make_double2(l == j ? rjj : g.x * inv, l == j ? 0.0 : g.y * inv);
-        }
-        Rout[(long long)j * n + l] = v;
-      }
+    // the pivot's root and reciprocal once per CTA (FP64 roots and divides
+    // are slow on this part), then row j of R once into local shared memory
+    if (threadIdx.x == 0) {
+      const double d = wj[j].x;
+      const bool keep = d > thr;
+      s_rjj = keep ? sqrt(d) : 0.0;
+      s_inv = keep ? 1.0 / s_rjj : 0.0;
     }
+    __syncthreads();
+    const double rjj = s_rjj, inv = s_inv;
+    const bool keep = rjj > 0.0;
+    for (int l = threadIdx.x; l < n; l += CL_THREADS) {
+      cplx v = make_double2(0.0, 0.0);
+      if (keep && l >= j) {
+        const cplx g = wj[l];
+        v = l == j ? make_double2(rjj, 0.0) : make_double2(g.x * inv, g.y * inv);
+      }
+      rj[l] = v;
+      if (j % cs == rank) Rout[(long long)j * n + l] = v;  // zero row for a dropped direction
+    }
+    __syncthreads();
     if (keep) {
       // own rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i
       for (int l0 = 0; l0 < R; ++l0) {
         const int i = l0 * cs + rank;
         if (i >= n) break;
         if (i <= j) continue;
-        const cplx gi = wj[i];
-        const cplx a = make_double2(gi.x * inv, gi.y * inv);
+        const cplx a = rj[i];
         cplx* wi = sm + (long long)l0 * n;
         for (int l = i + threadIdx.x; l < n; l += CL_THREADS) {
-          const cplx gl = wj[l];
-          const cplx b = make_double2(l == j ? rjj : gl.x * inv, l == j ? 0.0 : gl.y * inv);
+          const cplx b = rj[l];
           wi[l].x -= a.x * b.x + a.y * b.y;
           wi[l].y -= a.x * b.y - a.y * b.x;
         }
@@ -385,14 +413,14 @@ bool chol_cluster_fits(int n) {
   if (n < 32) return false;
   if (cluster_init() != cudaSuccess) return false;
   const long long R = (n + g_csize - 1) / g_csize;
-  return R * n * (long long)sizeof(cplx) <= CL_SMEM;
+  return (R + 1) * n * (long long)sizeof(cplx) <= CL_SMEM;
 }
 
 cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol) {
   cudaError_t e;
   if ((e = cluster_init()) != cudaSuccess) return e;
   const long long rows = (n + g_csize - 1) / g_csize;
-  const size_t smem = (size_t)(rows * n * sizeof(cplx));
+  const size_t smem = (size_t)((rows + 1) * n * sizeof(cplx));
   void* args[] = {&G, &R, &n, &tol};
   e = launch_cluster((const void*)chol_cluster_kernel, args, smem, s);
   count_launch();
