@@ -133,3 +133,25 @@ def test_errors_are_reported_not_fatal():
     with pytest.raises(CTMError):
         g.boundary_rho(0, 3)  # not a multiple of Ly
     g.sweep(1)  # the handle is still usable
+
+
+@pytest.mark.parametrize("chi", [33, 40])
+def test_cluster_sized_cores_match_oracle(chi):
+    """chi >= 32: the projector core (k = chi + 16 rows), the CholeskyQR
+    factorisations and the corner spectra (chi x chi) run on the 16-CTA cluster
+    kernels; odd chi leaves a dummy player in the Jacobi pair schedule."""
+    w = synth.workload("cfg2", seed=6, D=2, chi=chi)
+    g = gpu_ctm(w["tensors"], w["pattern"], chi)
+    g.sweep(2)
+    st = _oracle_run(w, chi, ["sweep"] * 2)
+    e_ref = O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2)
+    assert abs(g.energy(w["J"]) - e_ref) < TOL * abs(e_ref)
+    _compare_rdms(g, st, w)
+    _compare_spectra(g, st)
+    g.close()
+    gp = gpu_ctm(w["tensors"], w["pattern"], chi, prec="bf16x3", cutoff=1e-6)
+    gp.sweep(2)
+    st6 = _oracle_run(w, chi, ["sweep"] * 2, cutoff=1e-6)
+    e6 = O.energy_per_spin(O.bond_rdms(st6, w["tensors"], w["pattern"]), w["J"], 2, 2)
+    assert abs(gp.energy(w["J"]) - e6) < 1e-5
+    gp.close()
