@@ -363,6 +363,41 @@ static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cp
   return IPEPS_OK;
 }
 
+// View of tensor X (labels lx) with rows over labels `rows` and columns over
+// labels `cols` (each in the given order); adjacent axes contiguous in X are
+// merged.  False when either side needs more than four axes.
+static bool make_view(const TV& X, const std::string& lx, const std::string& rows, const std::string& cols,
+                      bool cj, TcView* v) {
+  long long str[8];
+  long long acc = 1;
+  for (int a = X.nd - 1; a >= 0; --a) {
+    str[a] = acc;
+    acc *= X.dims[a];
+  }
+  auto side = [&](const std::string& labs, int* n, int* dim, long long* st) {
+    *n = 0;
+    for (char c : labs) {
+      const int a = (int)lx.find(c);
+      if (*n > 0 && st[*n - 1] == str[a] * X.dims[a]) {  // contiguous with the previous axis: merge
+        dim[*n - 1] *= X.dims[a];
+        st[*n - 1] = str[a];
+        continue;
+      }
+      if (*n == 4) return false;
+      dim[*n] = X.dims[a];
+      st[*n] = str[a];
+      ++*n;
+    }
+    return true;
+  };
+  v->p = X.p;
+  v->conj = cj ? 1 : 0;
+  if (!side(rows, &v->nr, v->rdim, v->rstr) || !side(cols, &v->nc, v->cdim, v->cstr)) return false;
+  if (v->nr == 0) { v->nr = 1; v->rdim[0] = 1; v->rstr[0] = 0; }
+  if (v->nc == 0) { v->nc = 1; v->cdim[0] = 1; v->cstr[0] = 0; }
+  return true;
+}
+
 static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV B, bool conjB,
                              TV C, cplx alpha = ONE) {
   std::string s(spec);
@@ -419,6 +454,12 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
   for (char c : kc) Kd *= dimA(c);
 
   const long long mark = h->scratch_top;
+  // Tensor-core products: an operand that is not already in GEMM form is
+  // gathered by the operand packing through a view (fused permute-and-pack)
+  // instead of being permuted into a copy first.
+  const bool tc = h->opt.prec != IPEPS_PREC_FP64 &&
+                  ((direct && swap) ? (N >= 64 && M >= 32 && Kd >= 16) : (M >= 64 && N >= 32 && Kd >= 16)) &&
+                  (2 * std::max(M, N) + 512) * (2 * Kd + 128) < (1LL << 31);  // gathers index in 32 bits
   // arrange one operand as [free..., k...] (op N) or [k..., free...] (op T)
   auto arrange = [&](TV X, const std::string& lx, bool cj, const std::string& fo,
                      const std::string& ko, const cplx** out, long long* ld, int* op) -> ipeps_status {
@@ -457,10 +498,13 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
     }
     if (!is_form(la, Mo, ko) && is_form(lb, No, kb)) ko = kb;
   }
-  const cplx *pa, *pb;
-  long long lda, ldb;
-  int opa, opb;
-  CKS(arrange(A, la, conjA, Mo, ko, &pa, &lda, &opa));
+  const cplx *pa = nullptr, *pb = nullptr;
+  long long lda = 0, ldb = 0;
+  int opa = OP_N, opb = OP_N;
+  TcView va, vb;
+  bool use_va = false, use_vb = false;
+  if (tc && !is_form(la, Mo, ko)) use_va = make_view(A, la, Mo, ko, conjA, &va);
+  if (!use_va) CKS(arrange(A, la, conjA, Mo, ko, &pa, &lda, &opa));
   // B must be [ko, No] (op N) or [No, ko] (op T); arrange() returns [No, ko] forms
   {
     long long fdim = 1, kdim = 1;
@@ -470,6 +514,8 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
       pb = B.p; ldb = fdim; opb = OP_N | (conjB ? OP_CONJ : 0);
     } else if (lb == No + ko) {
       pb = B.p; ldb = kdim; opb = OP_T | (conjB ? OP_CONJ : 0);
+    } else if (tc && make_view(B, lb, No, ko, conjB, &vb)) {
+      use_vb = true;
     } else {
       std::string want = ko + No;
       int perm[8];
@@ -479,6 +525,61 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
       CK(permute(h->stream, B.p, t, B.nd, B.dims, perm, conjB, ONE));
       pb = t; ldb = fdim; opb = OP_N;
     }
+  }
+  // a plain operand as a view, for the products that take one view
+  auto plain_view = [&](const cplx* p, long long ld, int op, int rows, int cols, bool as_b, TcView* v) {
+    // A role: element (m, k) of op(A); B role: element (n, k) of op(B)^T
+    const bool t = (op & OP_T) != 0;
+    v->p = p;
+    v->conj = (op & OP_CONJ) ? 1 : 0;
+    v->nr = v->nc = 1;
+    v->rdim[0] = rows;
+    v->cdim[0] = cols;
+    const bool row_major_rows = as_b ? t : !t;  // rows stride ld, columns stride 1
+    v->rstr[0] = row_major_rows ? ld : 1;
+    v->cstr[0] = row_major_rows ? 1 : ld;
+  };
+  if (use_va || use_vb) {
+    // at least one gathered operand: one tensor-core product with views
+    const TcView* VA = use_va ? &va : nullptr;
+    const TcView* VB = use_vb ? &vb : nullptr;
+    cudaEvent_t ev = nullptr;
+    if (direct && swap) {
+      // C[No, Mo] = B' A'^T: the B operand takes the A role, A the B role
+      TcView xa, xb;
+      if (VB) xa = *VB; else plain_view(pb, ldb, opb ^ OP_T, (int)N, (int)Kd, false, &xa);
+      if (VA) xb = *VA; else plain_view(pa, lda, opa ^ OP_T, (int)M, (int)Kd, true, &xb);
+      prof_begin(h, &ev);
+      cudaError_t e = tc_zgemm_views(h->stream, (int)h->opt.prec, (int)N, (int)M, (int)Kd, alpha, &xa, nullptr, 0, 0,
+                                     &xb, nullptr, 0, 0, C.p, M, h->scratch, h->scratch_elems, h->scratch_top,
+                                     h->tuner);
+      prof_end(h, ev, 8.0 * (double)M * (double)N * (double)Kd, 0);
+      CK(e);
+    } else {
+      cplx* out = C.p;
+      cplx* t = nullptr;
+      if (!direct) {
+        t = scratch_alloc(h, M * N);
+        if (!t) return fail(IPEPS_ENOMEM, "scratch exhausted in %s", spec);
+        out = t;
+      }
+      prof_begin(h, &ev);
+      cudaError_t e = tc_zgemm_views(h->stream, (int)h->opt.prec, (int)M, (int)N, (int)Kd, direct ? alpha : ONE, VA,
+                                     pa, lda, opa, VB, pb, ldb, opb, out, N, h->scratch, h->scratch_elems,
+                                     h->scratch_top, h->tuner);
+      prof_end(h, ev, 8.0 * (double)M * (double)N * (double)Kd, 0);
+      CK(e);
+      if (!direct) {
+        std::string have = Mo + No;
+        int dims[8], perm[8];
+        for (size_t i = 0; i < have.size(); ++i)
+          dims[i] = la.find(have[i]) != std::string::npos ? dimA(have[i]) : dimB(have[i]);
+        for (size_t i = 0; i < lc.size(); ++i) perm[i] = (int)have.find(lc[i]);
+        CK(permute(h->stream, t, C.p, (int)have.size(), dims, perm, false, alpha));
+      }
+    }
+    h->scratch_top = mark;
+    return IPEPS_OK;
   }
   if (direct && !swap) {
     CKS(gemm_dispatch(h, (int)M, (int)N, (int)Kd, pa, lda, opa, pb, ldb, opb, C.p, N, alpha));

@@ -401,6 +401,68 @@ __global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int 
   }
 }
 
+__device__ __forceinline__ long long view_off(unsigned idx, int n, const int* dim, const long long* str) {
+  long long off = 0;
+  for (int a = n - 1; a >= 0; --a) {
+    const unsigned d = (unsigned)dim[a];
+    const unsigned q = idx / d;
+    off += (long long)(idx - q * d) * str[a];
+    idx = q;
+  }
+  return off;
+}
+
+__device__ __forceinline__ cplx view_at(const TcView& V, int r, int c) {
+  cplx v = V.p[view_off((unsigned)r, V.nr, V.rdim, V.rstr) + view_off((unsigned)c, V.nc, V.cdim, V.cstr)];
+  if (V.conj) v.y = neg_bits(v.y);
+  return v;
+}
+
+__device__ __forceinline__ void store_pair(int prec, long long e, double x0, double x1, void* o0, void* o1) {
+  // two consecutive packed reals at element e (e even)
+  if (prec == PREC_TF32) {
+    ((uint2*)o0)[e >> 1] = make_uint2(to_tf32(d2f_bits(x0)), to_tf32(d2f_bits(x1)));
+  } else {
+    const float f0 = d2f_bits(x0), f1 = d2f_bits(x1);
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
+    ((__nv_bfloat162*)o0)[e >> 1] = __halves2bfloat162(h0, h1);
+    ((__nv_bfloat162*)o1)[e >> 1] = __halves2bfloat162(l0, l1);
+  }
+}
+
+// Ar[m, kr] gathered through a view (rows m, columns k): a fused
+// permute-and-pack of the A operand, padded to Mp x Krp; one thread per
+// complex element (its two reals written as a pair)
+template <int PREC>
+__global__ void pack_a_view_kernel(TcView V, int M, int K, int Mp, int Krp, void* __restrict__ o0,
+                                   void* __restrict__ o1) {
+  const unsigned kc = (unsigned)(Krp >> 1), total = (unsigned)Mp * kc;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const unsigned m = e / kc, k = e - m * kc;
+    cplx v = make_double2(0.0, 0.0);
+    if ((int)m < M && (int)k < K) v = view_at(V, (int)m, (int)k);
+    store_pair(PREC, (long long)m * Krp + 2 * k, v.x, v.y, o0, o1);
+  }
+}
+
+// Br^T[nr, kr] gathered through a view (rows n, columns k), padded to Nrp x Krp:
+// complex (n, k) gives rows 2n: (Re, -Im) and 2n+1: (Im, Re) at columns 2k, 2k+1
+template <int PREC>
+__global__ void pack_b_view_kernel(TcView V, int N, int K, int Nrp, int Krp, void* __restrict__ o0,
+                                   void* __restrict__ o1) {
+  const unsigned kc = (unsigned)(Krp >> 1), total = (unsigned)(Nrp >> 1) * kc;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const unsigned n = e / kc, k = e - n * kc;
+    cplx v = make_double2(0.0, 0.0);
+    if ((int)n < N && (int)k < K) v = view_at(V, (int)n, (int)k);
+    const long long r0 = (long long)(2 * n) * Krp + 2 * k;
+    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1);
+    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 cudaError_t get_encoder() {
@@ -606,7 +668,8 @@ namespace {
 template <int PREC>
 cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
                 const cplx* B, long long ldb, int opB, const TcPacked* pre, cplx* C, long long ldc, bool conj_out,
-                char* scratch, size_t scratch_bytes, TcTuner* tuner, const TcChoice* force) {
+                char* scratch, size_t scratch_bytes, TcTuner* tuner, const TcChoice* force,
+                const TcView* va = nullptr, const TcView* vb = nullptr) {
   using K_ = Cfg<PREC, 256>;
   Operands o;
   o.Mp = (M + BM - 1) / BM * BM;
@@ -643,7 +706,12 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   }
   if (part_bytes(eff_splits(o.kb_total, choice.splits)) > part_room) return cudaErrorMemoryAllocation;
 
-  if (o.Mp * o.Krp < (1LL << 31))
+  if (va && o.Mp * o.Krp < (1LL << 31))
+    pack_a_view_kernel<PREC><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(*va, M, K, (int)o.Mp, (int)o.Krp, o.a0,
+                                                                         o.a1);
+  else if (va)
+    return cudaErrorNotSupported;
+  else if (o.Mp * o.Krp < (1LL << 31))
     pack_a_kernel<PREC, unsigned><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp,
                                                                          o.a0, o.a1);
   else
@@ -655,6 +723,12 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     if (pre->prec != PREC || pre->N != N || pre->K != K) return cudaErrorInvalidValue;
     o.b0 = pre->b0;
     o.b1 = pre->b1;
+  } else if (vb) {
+    if (o.Nrp * o.Krp >= (1LL << 31)) return cudaErrorNotSupported;
+    pack_b_view_kernel<PREC><<<grid_for(o.Nrp * o.Krp / 4), 256, 0, s>>>(*vb, N, K, (int)o.Nrp, (int)o.Krp, o.b0,
+                                                                          o.b1);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, o.Nrp, o.Krp, o.b0, o.b1)) != cudaSuccess) {
     return e;
   }
@@ -718,6 +792,22 @@ cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, 
   if (prec == PREC_BF16X3)
     return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
                             tuner, force);
+  return cudaErrorNotSupported;
+}
+
+cudaError_t tc_zgemm_views(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const TcView* va,
+                           const cplx* A, long long lda, int opA, const TcView* vb, const cplx* B, long long ldb,
+                           int opB, cplx* C, long long ldc, cplx* scratch, long long scratch_elems,
+                           long long scratch_top, TcTuner* tuner) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
+  char* base = (char*)(scratch + scratch_top);
+  const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
+  if (prec == PREC_TF32)
+    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes, tuner,
+                          nullptr, va, vb);
+  if (prec == PREC_BF16X3)
+    return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
+                            tuner, nullptr, va, vb);
   return cudaErrorNotSupported;
 }
 

@@ -9,6 +9,19 @@
 // shape has no tensor-core kernel.
 struct TcTuner;
 struct TcChoice;
+
+// An operand read through a strided view instead of a permuted copy: element
+// (r, c) is p[roff(r) + coff(c)], roff / coff sums of per-axis strides over
+// up to four axes each (the last axis fastest), conjugated when conj.  For
+// the A role rows are m and columns k; for the B role rows are n and columns
+// k (the transpose of op(B)).
+struct TcView {
+  const cplx* p;
+  int nr, nc;
+  int rdim[4], cdim[4];
+  long long rstr[4], cstr[4];
+  int conj;
+};
 // force: a fixed tile choice instead of the tuner's or the default one
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A,
                      long long lda, int opA, const cplx* B, long long ldb, int opB, cplx* C,
@@ -53,6 +66,14 @@ bool tc_tuner_entry(const TcTuner* t, int i, int fields[6], double us[2]);
 // one-time setup (kernel attributes, driver entry point); called before any
 // stream capture so that captured products make no such calls.
 cudaError_t tc_init();
+
+// C[M,N] = alpha A B with either operand given as a view (the other, when the
+// view pointer is null, as (ptr, ld, op) like tc_zgemm): the operand packing
+// gathers straight from the source tensor (a fused permute-and-pack).
+cudaError_t tc_zgemm_views(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const TcView* va,
+                           const cplx* A, long long lda, int opA, const TcView* vb, const cplx* B, long long ldb,
+                           int opB, cplx* C, long long ldc, cplx* scratch, long long scratch_elems,
+                           long long scratch_top, TcTuner* tuner = nullptr);
 
 // number of bounded-wait timeouts inside tensor-core kernels since the last
 // call (resets the counter); synchronous.
