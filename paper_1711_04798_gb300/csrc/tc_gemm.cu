@@ -310,27 +310,31 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return u;
 }
 
+__device__ __forceinline__ void store_pair(int prec, long long e, double x0, double x1, void* o0, void* o1) {
+  // two consecutive packed reals at element e (e even)
+  if (prec == PREC_TF32) {
+    ((uint2*)o0)[e >> 1] = make_uint2(to_tf32(d2f_bits(x0)), to_tf32(d2f_bits(x1)));
+  } else {
+    const float f0 = d2f_bits(x0), f1 = d2f_bits(x1);
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
+    ((__nv_bfloat162*)o0)[e >> 1] = __halves2bfloat162(h0, h1);
+    ((__nv_bfloat162*)o1)[e >> 1] = __halves2bfloat162(l0, l1);
+  }
+}
+
 // Ar[m, kr], padded to Mp x Krp (K-major)
 template <int PREC, typename Idx>
 __global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int Krp,
                               void* __restrict__ o0, void* __restrict__ o1) {
-  const Idx total = (Idx)Mp * (Idx)Krp;
+  // one thread per complex element: its (Re, Im) pair stored together
+  const Idx kc = (Idx)(Krp >> 1), total = (Idx)Mp * kc;
   for (Idx e = (Idx)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (Idx)gridDim.x * blockDim.x) {
-    const int m = (int)(e / (Idx)Krp), kr = (int)(e - (Idx)m * (Idx)Krp);
-    double x = 0.0;
-    if (m < M && kr < 2 * K) {
-      const cplx v = load_op(A, lda, opA, m, kr >> 1);
-      x = (kr & 1) ? v.y : v.x;
-    }
-    if (PREC == PREC_TF32) {
-      ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
-    } else {
-      const float xf = d2f_bits(x);  // 23 mantissa bits: more than hi + lo keep
-      const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
-      ((__nv_bfloat16*)o0)[e] = hi;
-      ((__nv_bfloat16*)o1)[e] = lo;
-    }
+    const Idx m = e / kc, k = e - m * kc;
+    cplx v = make_double2(0.0, 0.0);
+    if ((int)m < M && (int)k < K) v = load_op(A, lda, opA, (int)m, (int)k);
+    store_pair(PREC, (long long)m * Krp + 2 * (long long)k, v.x, v.y, o0, o1);
   }
 }
 
@@ -338,24 +342,15 @@ __global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA
 template <int PREC, typename Idx>
 __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp, int Krp,
                               void* __restrict__ o0, void* __restrict__ o1) {
-  const Idx total = (Idx)Nrp * (Idx)Krp;
+  // one thread per complex element B[k, n]: rows 2n (Re, -Im) and 2n+1 (Im, Re)
+  const Idx kc = (Idx)(Krp >> 1), total = (Idx)(Nrp >> 1) * kc;
   for (Idx e = (Idx)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (Idx)gridDim.x * blockDim.x) {
-    const int nr = (int)(e / (Idx)Krp), kr = (int)(e - (Idx)nr * (Idx)Krp);
-    double x = 0.0;
-    if (nr < 2 * N && kr < 2 * K) {
-      const cplx v = load_op(B, ldb, opB, kr >> 1, nr >> 1);
-      const int a = kr & 1, b = nr & 1;
-      x = (a == b) ? v.x : (a == 0 ? v.y : neg_bits(v.y));
-    }
-    if (PREC == PREC_TF32) {
-      ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
-    } else {
-      const float xf = d2f_bits(x);  // 23 mantissa bits: more than hi + lo keep
-      const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
-      ((__nv_bfloat16*)o0)[e] = hi;
-      ((__nv_bfloat16*)o1)[e] = lo;
-    }
+    const Idx n = e / kc, k = e - n * kc;
+    cplx v = make_double2(0.0, 0.0);
+    if ((int)n < N && (int)k < K) v = load_op(B, ldb, opB, (int)k, (int)n);
+    const long long r0 = (long long)(2 * n) * Krp + 2 * (long long)k;
+    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1);
+    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1);
   }
 }
 
@@ -416,20 +411,6 @@ __device__ __forceinline__ cplx view_at(const TcView& V, int r, int c) {
   cplx v = V.p[view_off((unsigned)r, V.nr, V.rdim, V.rstr) + view_off((unsigned)c, V.nc, V.cdim, V.cstr)];
   if (V.conj) v.y = neg_bits(v.y);
   return v;
-}
-
-__device__ __forceinline__ void store_pair(int prec, long long e, double x0, double x1, void* o0, void* o1) {
-  // two consecutive packed reals at element e (e even)
-  if (prec == PREC_TF32) {
-    ((uint2*)o0)[e >> 1] = make_uint2(to_tf32(d2f_bits(x0)), to_tf32(d2f_bits(x1)));
-  } else {
-    const float f0 = d2f_bits(x0), f1 = d2f_bits(x1);
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(f0 - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(f1 - __bfloat162float(h1));
-    ((__nv_bfloat162*)o0)[e >> 1] = __halves2bfloat162(h0, h1);
-    ((__nv_bfloat162*)o1)[e >> 1] = __halves2bfloat162(l0, l1);
-  }
 }
 
 // Ar[m, kr] gathered through a view (rows m, columns k): a fused
@@ -501,9 +482,9 @@ cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, in
                        long long Krp, void* b0, void* b1) {
   if (opB & OP_T) {
     if (Nrp * Krp < (1LL << 31))
-      pack_b_kernel<PREC, unsigned><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
+      pack_b_kernel<PREC, unsigned><<<grid_for(Nrp * Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
     else
-      pack_b_kernel<PREC, unsigned long long><<<grid_for(Nrp * Krp), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp,
+      pack_b_kernel<PREC, unsigned long long><<<grid_for(Nrp * Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp,
                                                                                    (int)Krp, b0, b1);
   } else {
     dim3 grid((unsigned)((Nrp / 2 + 31) / 32), (unsigned)((Krp / 2 + 31) / 32));
@@ -712,10 +693,10 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   else if (va)
     return cudaErrorNotSupported;
   else if (o.Mp * o.Krp < (1LL << 31))
-    pack_a_kernel<PREC, unsigned><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp,
+    pack_a_kernel<PREC, unsigned><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp,
                                                                          o.a0, o.a1);
   else
-    pack_a_kernel<PREC, unsigned long long><<<grid_for(o.Mp * o.Krp), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp,
+    pack_a_kernel<PREC, unsigned long long><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp,
                                                                                    (int)o.Krp, o.a0, o.a1);
   count_launch();
   cudaError_t e;
