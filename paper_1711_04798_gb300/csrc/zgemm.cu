@@ -2,7 +2,9 @@
 // contractions) and the generic index permutation that feeds it.
 #include "ctm_internal.h"
 
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches += (uint64_t)n; }
@@ -10,7 +12,7 @@ uint64_t launch_counter() { return g_launches.load(); }
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16;
 constexpr cplx ONE_C = {1.0, 0.0};
 constexpr cplx ZERO_C = {0.0, 0.0};
 
@@ -20,21 +22,24 @@ __device__ __forceinline__ cplx ld_op(const cplx* p, bool cj) {
   return v;
 }
 
-// 64x64 output tile per CTA, 256 threads, each thread a 4x4 block of outputs
-// strided by 16 so that shared-memory reads are broadcast / conflict-free.
-__global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alpha,
+// TM x TN output tile per CTA (64 x 64 with 256 threads, or 32 x 32 with 64
+// threads for small outputs), each thread a 4x4 block of outputs strided by
+// TM/4 (TN/4) so that shared-memory reads are broadcast / conflict-free.
+template <int TM, int TN>
+__global__ void __launch_bounds__((TM / 4) * (TN / 4)) zgemm_kernel(int M, int N, int K, cplx alpha,
                                                    const cplx* __restrict__ A, long long lda,
                                                    int opA, const cplx* __restrict__ B,
                                                    long long ldb, int opB, cplx beta,
                                                    cplx* __restrict__ C, long long ldc,
                                                    long long sA, long long sB, long long sC,
                                                    int ksplit, int flags) {
+  constexpr int BM = TM, BN = TN, NT = (TM / 4) * (TN / 4), SX = TN / 4, SY = TM / 4;
   __shared__ cplx As[BK][BM + 1];
   __shared__ cplx Bs[BK][BN + 1];
   const long long bz = blockIdx.z;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if ((flags & ZG_UPPER_TILES) && blockIdx.y > blockIdx.x) return;  // tile below the diagonal: not needed
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % SX, ty = threadIdx.x / SX;
   const bool tA = opA & OP_T, cA = opA & OP_CONJ;
   const bool tB = opB & OP_T, cB = opB & OP_CONJ;
   if (ksplit > 0) {
@@ -79,9 +84,9 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
     for (int kk = 0; kk < BK; ++kk) {
       cplx a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + SY * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + SX * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -97,11 +102,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
   const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty + 16 * i;
+    const int m = m0 + ty + SY * i;
     if (m >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx + 16 * j;
+      const int n = n0 + tx + SX * j;
       if (n >= N) continue;
       cplx* cp = C + (long long)m * ldc + n;
       double r = alpha.x * cr[i][j] - alpha.y * ci[i][j];
@@ -118,11 +123,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, cplx alp
 
 // C = alpha * sum_z W[z] (+ beta C), fixed summation order
 __global__ void splitk_sum_kernel(const cplx* __restrict__ W, int S, int M, int N, cplx alpha, cplx beta,
-                                  cplx* __restrict__ C, long long ldc, int flags) {
+                                  cplx* __restrict__ C, long long ldc, int flags, int tm, int tn) {
   const long long total = (long long)M * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    if ((flags & ZG_UPPER_TILES) && ((int)(e / N)) / BM > ((int)(e % N)) / BN) {
+    if ((flags & ZG_UPPER_TILES) && ((int)(e / N)) / tm > ((int)(e % N)) / tn) {
       C[(long long)(e / N) * ldc + (e % N)] = make_double2(0.0, 0.0);  // tile not computed
       continue;
     }
@@ -177,47 +182,60 @@ cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A
                   long long ldc, GemmBatch batch, cplx* work, long long work_elems, int flags) {
   if (M <= 0 || N <= 0 || batch.count <= 0) return cudaSuccess;
   if ((flags & ZG_UPPER_TILES) && M != N) return cudaErrorInvalidValue;
-  const long long tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  const long long tiles = (flags & ZG_UPPER_TILES) ? tm * (tm + 1) / 2 : tm * tn;
-  // Few output tiles: split K over the grid, whole k-tiles per split.  Every
-  // SM's FP64 units carry the product, and one 8-warp CTA per SM leaves them
-  // idle part of the time: measured on GB300, a lone CTA takes ~1.64x the time
-  // per k-tile of two co-resident ones.  Cost = k-tiles per CTA x (1.64 for a
-  // single wave of at most one CTA per SM, else the CTAs on the busiest SM).
-  if (batch.count == 1 && work && tiles < 152 && K >= 2 * BK) {
-    const long long kb = (K + BK - 1) / BK;
-    long long best_S = 1;
-    double best_cost = -1.0;
-    for (long long S = 1; S <= 160 && S <= kb; ++S) {
+  // Tile size and K split from a cost model of the FP64 pipe: every SM's FP64
+  // units carry the product; an SM runs at full rate with >= 16 resident warps
+  // and, measured on GB300, at 0.61x with one 8-warp CTA (rate ~ (warps/16)^0.72
+  // below 16).  Cost = k-tiles per CTA x CTAs on the busiest SM x tile work /
+  // rate; splits keep whole k-tiles.
+  const long long kb = (K + BK - 1) / BK;
+  int best_T = 64;
+  long long best_S = 1;
+  double best_cost = -1.0;
+  for (int T : {64, 32}) {
+    if (batch.count != 1 && T != 64) continue;
+    const long long tm = (M + T - 1) / T, tn = (N + T - 1) / T;
+    const long long tiles = (flags & ZG_UPPER_TILES) ? tm * (tm + 1) / 2 : tm * tn;
+    const double unit = T == 64 ? 1.0 : 0.25;
+    const int warps = T == 64 ? 8 : 2;
+    const bool can_split = batch.count == 1 && work && K >= 2 * BK;
+    for (long long S = 1; S <= (can_split ? 160 : 1) && S <= kb; ++S) {
       const long long kps = (kb + S - 1) / S, Se = (kb + kps - 1) / kps;
       if (Se > 1 && Se * M * N > work_elems) break;
-      const long long ctas = tiles * Se;
-      const double per_sm = ctas <= 152 ? 1.64 : (double)((ctas + 151) / 152);
-      const double cost = (double)kps * per_sm + 1e-4 * (double)Se;  // tie-break: fewer partials
+      const long long busy = (tiles * Se * batch.count + 151) / 152;
+      const double rate = std::min(1.0, std::pow((double)(busy * warps) / 16.0, 0.72));
+      const double cost = (double)kps * (double)busy * unit / rate + 1e-4 * (double)Se;
       if (best_cost < 0.0 || cost < best_cost) {
         best_cost = cost;
         best_S = Se;
+        best_T = T;
       }
     }
-    if (best_S >= 2) {
-      const long long kps = (kb + best_S - 1) / best_S;
-      const int ksplit = (int)(kps * BK);
-      const long long S = (K + ksplit - 1) / ksplit;
-      dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)S);
-      zgemm_kernel<<<grid, NT, 0, s>>>(M, N, K, ONE_C, A, lda, opA, B, ldb, opB, ZERO_C, work, N, 0, 0,
-                                       (long long)M * N, ksplit, flags);
-      long long blocks = ((long long)M * N + 255) / 256;
-      if (blocks > 152 * 16) blocks = 152 * 16;
-      splitk_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(work, (int)S, M, N, alpha, beta, C, ldc, flags);
-      count_launch(2);
-      return cudaGetLastError();
-    }
+  }
+  const int T = best_T;
+  const long long tm = (M + T - 1) / T, tn = (N + T - 1) / T;
+  auto launch = [&](dim3 grid, cplx al, cplx be, cplx* out, long long ldo, long long sC, int ksplit, int fl) {
+    if (T == 64)
+      zgemm_kernel<64, 64><<<grid, 256, 0, s>>>(M, N, K, al, A, lda, opA, B, ldb, opB, be, out, ldo, batch.sA,
+                                                batch.sB, sC, ksplit, fl);
+    else
+      zgemm_kernel<32, 32><<<grid, 64, 0, s>>>(M, N, K, al, A, lda, opA, B, ldb, opB, be, out, ldo, batch.sA,
+                                               batch.sB, sC, ksplit, fl);
+  };
+  if (best_S >= 2) {
+    const long long kps = (kb + best_S - 1) / best_S;
+    const int ksplit = (int)(kps * BK);
+    const long long S = (K + ksplit - 1) / ksplit;
+    launch(dim3((unsigned)tn, (unsigned)tm, (unsigned)S), ONE_C, ZERO_C, work, N, (long long)M * N, ksplit, flags);
+    long long blocks = ((long long)M * N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    splitk_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(work, (int)S, M, N, alpha, beta, C, ldc, flags, T, T);
+    count_launch(2);
+    return cudaGetLastError();
   }
   if (flags & ZG_UPPER_TILES) flags &= ~ZG_UPPER_TILES;  // unsplit: full tiles (lower ones are cheap here)
   dim3 grid((unsigned)tn, (unsigned)tm, batch.count);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-  zgemm_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,
-                                   batch.sA, batch.sB, batch.sC, 0, flags);
+  launch(grid, alpha, beta, C, ldc, batch.sC, 0, flags);
   count_launch();
   return cudaGetLastError();
 }
