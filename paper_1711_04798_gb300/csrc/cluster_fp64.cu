@@ -16,7 +16,8 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int CL_THREADS = 128;         // 4 warps per CTA
+constexpr int CL_THREADS = 128;         // 4 warps per CTA (Cholesky)
+constexpr int JC_THREADS = 256;         // Jacobi: 8 warps per CTA, two per row pair
 constexpr int CL_SMEM = 200 * 1024;     // dynamic shared memory bound per CTA
 int g_csize = 0;                        // CTAs per cluster (16 if schedulable, else 8)
 
@@ -65,32 +66,33 @@ __device__ __forceinline__ void pair_of(int r, int p, int np, int rounds, int* i
 // One-sided Jacobi on the n rows of G (length m): rows and, with Vt, the rows
 // of the accumulated rotation (length n, from the identity) in the cluster's
 // shared memory.
-__global__ void __launch_bounds__(CL_THREADS)
+__global__ void __launch_bounds__(JC_THREADS)
     jacobi_cluster_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt, int max_sweeps,
                           double tol, double4* __restrict__ log, int* sweeps_used, DevStatus* st) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = CL_THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = JC_THREADS / 32;
   const int R = (n + cs - 1) / cs;  // row slots per CTA
   extern __shared__ cplx sm[];      // [R x m] rows of G, then [R x n] rows of Vt
   __shared__ double s_fro;
   __shared__ int s_rot, s_big;
+  __shared__ double s_part[JC_THREADS / 64][2][4];  // [pair slot][half][al, be, Re g, Im g]
   cplx* gl = sm;
   cplx* vl = sm + (long long)R * m;
   double f = 0.0;
   for (int l = 0; l < R; ++l) {
     const int i = l * cs + rank;
     if (i >= n) break;
-    for (int t = threadIdx.x; t < m; t += CL_THREADS) {
+    for (int t = threadIdx.x; t < m; t += JC_THREADS) {
       const cplx x = G[(long long)i * ldg + t];
       gl[(long long)l * m + t] = x;
       f += x.x * x.x + x.y * x.y;
     }
     if (Vt)
-      for (int t = threadIdx.x; t < n; t += CL_THREADS) vl[(long long)l * n + t] = make_double2(t == i ? 1.0 : 0.0, 0.0);
+      for (int t = threadIdx.x; t < n; t += JC_THREADS) vl[(long long)l * n + t] = make_double2(t == i ? 1.0 : 0.0, 0.0);
   }
   f = warp_sum(f);
-  __shared__ double s_w[CL_THREADS / 32];
+  __shared__ double s_w[JC_THREADS / 32];
   if (lane == 0) s_w[warp] = f;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -108,78 +110,81 @@ __global__ void __launch_bounds__(CL_THREADS)
   auto vrow = [&](int i) { return cl.map_shared_rank(vl, i % cs) + (long long)(i / cs) * n; };
   const int np = (n + 1) & ~1;
   const int rounds = np - 1, npairs = np / 2;
-  const int gw = rank * nwarps + warp, nw = cs * nwarps;
   bool converged = false;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < rounds; ++r) {
-      for (int p = gw; p < npairs; p += nw) {
-        int i, j;
-        pair_of(r, p, np, rounds, &i, &j);
-        if (j >= n) {
-          if (log && lane == 0) log[((long long)sweep * rounds + r) * npairs + p] = make_double4(2.0, 0.0, 0.0, 0.0);
-          continue;
-        }
-        cplx* gi = grow(i);
-        cplx* gj = grow(j);
-        double al = 0.0, be = 0.0, gr = 0.0, gim = 0.0;
-        for (int t = lane; t < m; t += 32) {
-          const cplx x = gi[t], y = gj[t];
-          al += x.x * x.x + x.y * x.y;
-          be += y.x * y.x + y.y * y.y;
-          gr += x.x * y.x + x.y * y.y;
-          gim += x.x * y.y - x.y * y.x;
-        }
-        {
+      // two warps per pair: warp (slot, half) takes the columns of 32-wide
+      // chunks 2j + half; the halves' sums meet in shared memory (fixed order)
+      for (int p0 = rank * (nwarps / 2); p0 < npairs; p0 += cs * (nwarps / 2)) {
+        const int slot = warp % (nwarps / 2), half = warp / (nwarps / 2);
+        const int p = p0 + slot;
+        int i = 0, j = n;
+        if (p < npairs) pair_of(r, p, np, rounds, &i, &j);
+        const bool active = p < npairs && j < n;
+        cplx* gi = active ? grow(i) : nullptr;
+        cplx* gj = active ? grow(j) : nullptr;
+        if (active) {
+          double al = 0.0, be = 0.0, gr = 0.0, gim = 0.0;
+          for (int t = lane + 32 * half; t < m; t += 64) {
+            const cplx x = gi[t], y = gj[t];
+            al += x.x * x.x + x.y * x.y;
+            be += y.x * y.x + y.y * y.y;
+            gr += x.x * y.x + x.y * y.y;
+            gim += x.x * y.y - x.y * y.x;
+          }
           const double tot = warp_sum4(al, be, gr, gim);
-          al = __shfl_sync(0xffffffffu, tot, 0);
-          be = __shfl_sync(0xffffffffu, tot, 8);
-          gr = __shfl_sync(0xffffffffu, tot, 16);
-          gim = __shfl_sync(0xffffffffu, tot, 24);
+          if ((lane & 7) == 0) s_part[slot][half][lane >> 3] = tot;
         }
-        // the rotation's scalars on one lane (FP64 divides and roots are
-        // costly here: two reciprocal roots, one root, one divide), broadcast
-        double c = 1.0, s = 0.0, phr = 1.0, phi = 0.0;
+        __syncthreads();
+        double c = 1.0, sn = 0.0, phr = 1.0, phi = 0.0;
         int rot = 0;
-        if (lane == 0) {
+        if (active && lane == 0) {
+          const double al = s_part[slot][0][0] + s_part[slot][1][0], be = s_part[slot][0][1] + s_part[slot][1][1];
+          const double gr = s_part[slot][0][2] + s_part[slot][1][2], gim = s_part[slot][0][3] + s_part[slot][1][3];
           const double g2 = gr * gr + gim * gim;
           if (al > negligible && be > negligible && g2 > tol * tol * al * be) {
             const double ig = rsqrt(g2);
             const double zeta = 0.5 * (be - al) * ig;
             const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             c = rsqrt(1.0 + t * t);
-            s = c * t;
+            sn = c * t;
             phr = gr * ig;
             phi = -gim * ig;
             rot = 1;
-            // a rotation with off-orthogonality or angle above 1e-8 keeps the
-            // sweep from being the last one
-            if (g2 > 1e-16 * al * be || fabs(s) > 1e-8) s_big = 1;
+            if (half == 0) {
+              atomicAdd(&s_rot, 1);
+              // a rotation with off-orthogonality or angle above 1e-8 keeps
+              // the sweep from being the last one
+              if (g2 > 1e-16 * al * be || fabs(sn) > 1e-8) s_big = 1;
+            }
           }
+          if (log && half == 0)
+            log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4(c, sn, phr, phi)
+                                                                   : make_double4(2.0, 0.0, 0.0, 0.0);
+        } else if (!active && lane == 0 && half == 0 && log && p < npairs) {
+          log[((long long)sweep * rounds + r) * npairs + p] = make_double4(2.0, 0.0, 0.0, 0.0);
         }
+        __syncthreads();  // partial sums read before the next pair overwrites them
         rot = __shfl_sync(0xffffffffu, rot, 0);
-        if (log && lane == 0)
-          log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4(c, s, phr, phi)
-                                                                  : make_double4(2.0, 0.0, 0.0, 0.0);
         if (rot) {
           c = __shfl_sync(0xffffffffu, c, 0);
-          s = __shfl_sync(0xffffffffu, s, 0);
+          sn = __shfl_sync(0xffffffffu, sn, 0);
           const cplx ph = make_double2(__shfl_sync(0xffffffffu, phr, 0), __shfl_sync(0xffffffffu, phi, 0));
-          for (int q = lane; q < m; q += 32) {
+          for (int q = lane + 32 * half; q < m; q += 64) {
             const cplx x = gi[q], y = cmul(gj[q], ph);
-            gi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-            gj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+            gi[q] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
+            gj[q] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
           }
           if (Vt) {
             cplx* vi = vrow(i);
             cplx* vj = vrow(j);
-            for (int q = lane; q < n; q += 32) {
+            for (int q = lane + 32 * half; q < n; q += 64) {
               const cplx x = vi[q], y = cmul(vj[q], ph);
-              vi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-              vj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+              vi[q] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
+              vj[q] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
             }
           }
-          if (lane == 0) atomicAdd(&s_rot, 1);
         }
       }
       cl.sync();
@@ -207,9 +212,9 @@ __global__ void __launch_bounds__(CL_THREADS)
   for (int l = 0; l < R; ++l) {
     const int i = l * cs + rank;
     if (i >= n) break;
-    for (int t = threadIdx.x; t < m; t += CL_THREADS) G[(long long)i * ldg + t] = gl[(long long)l * m + t];
+    for (int t = threadIdx.x; t < m; t += JC_THREADS) G[(long long)i * ldg + t] = gl[(long long)l * m + t];
     if (Vt)
-      for (int t = threadIdx.x; t < n; t += CL_THREADS) Vt[(long long)i * n + t] = vl[(long long)l * n + t];
+      for (int t = threadIdx.x; t < n; t += JC_THREADS) Vt[(long long)i * n + t] = vl[(long long)l * n + t];
   }
   if (rank == 0 && threadIdx.x == 0) {
     if (sweeps_used) *sweeps_used = converged ? sweep + 1 : max_sweeps;
@@ -359,7 +364,8 @@ static cudaError_t cluster_init() {
 
 cudaError_t fp64_cluster_init() { return cluster_init(); }
 
-static cudaError_t launch_cluster(const void* fn, void** args, size_t smem, cudaStream_t s) {
+static cudaError_t launch_cluster(const void* fn, void** args, size_t smem, cudaStream_t s,
+                                  int threads = CL_THREADS) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
@@ -367,7 +373,7 @@ static cudaError_t launch_cluster(const void* fn, void** args, size_t smem, cuda
   attr.val.clusterDim.y = 1;
   attr.val.clusterDim.z = 1;
   cfg.gridDim = dim3(g_csize);
-  cfg.blockDim = dim3(CL_THREADS);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = &attr;
@@ -399,7 +405,7 @@ cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg,
   const size_t smem = (size_t)(R * ((long long)m + (Vin ? n : 0)) * sizeof(cplx));
   double tol = (double)m * 2.220446049250313e-16;
   void* args[] = {&G, &n, &m, &ldg, &Vin, &max_sweeps, &tol, &logp, &su, &st};
-  e = launch_cluster((const void*)jacobi_cluster_kernel, args, smem, s);
+  e = launch_cluster((const void*)jacobi_cluster_kernel, args, smem, s, JC_THREADS);
   count_launch();
   if (e != cudaSuccess || !replay) return e;
   const int npairs = ((n + 1) & ~1) / 2;
