@@ -16,7 +16,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int CL_THREADS = 128;         // 4 warps per CTA (Cholesky)
+constexpr int CL_THREADS = 256;         // 8 warps per CTA (Cholesky): FP64 pipe occupancy
 constexpr int JC_THREADS = 256;         // Jacobi: 8 warps per CTA, two per row pair
 constexpr int CL_SMEM = 200 * 1024;     // dynamic shared memory bound per CTA
 int g_csize = 0;                        // CTAs per cluster (16 if schedulable, else 8)
