@@ -161,6 +161,41 @@ def oracle_move_seconds(D, chi, n_moves=1):
     return (time.perf_counter() - t0) / n_moves
 
 
+# ---------------------------------------------------------------------------
+# multi-rank bookkeeping (replicas: one independent instance per rank, no
+# collective on the data path; only the timing is reduced)
+# ---------------------------------------------------------------------------
+def init_dist(world):
+    """torch.distributed for world > 1: NCCL with GPUs, else gloo (CPU tests)."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return dist
+
+
+def max_over_ranks(x, dist):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, seconds_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
+def rank_seed(rank):
+    """Workload seed of a replica: each rank contracts its own synthetic state."""
+    return rank
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -194,12 +229,9 @@ def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1711_04798_gb300 import CTM
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = init_dist(world)
     stream = torch.cuda.current_stream()
-    w = workload(args.D, args.chi, seed=rank)
+    w = workload(args.D, args.chi, seed=rank_seed(rank))
     J = w["J"]
     g = CTM(w["tensors"], w["pattern"], args.chi, prec=args.prec, stream=stream.cuda_stream)
     tuned = 0 if args.no_tune else g.autotune()
@@ -229,11 +261,8 @@ def run_ours(args, rank, world, local_rank):
     jac = g.profile_read(1)
     f64g = g.profile_read(2)
     g.profile(False)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps * MOVES_PER_STEP / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist)
+    value = job_value(args.steps * MOVES_PER_STEP, world, ms_max * 1e-3)
 
     # end to end through the public API: host tensors in, energy out, every step
     host_tensors = w["tensors"]
@@ -248,10 +277,7 @@ def run_ours(args, rank, world, local_rank):
         g.energy(J)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * MOVES_PER_STEP / float(te.item())
+    e2e_value = job_value(args.steps * MOVES_PER_STEP, world, max_over_ranks(e2e_s, dist))
 
     if rank != 0:
         g.close()
@@ -345,11 +371,8 @@ def run_scan(args, rank, world, local_rank):
     import synth
     from paper_1711_04798_gb300 import Batch, CTM
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    insts = synth.scan(seed=rank, n=args.instances)
+    dist = init_dist(world)
+    insts = synth.scan(seed=rank_seed(rank), n=args.instances)
     t0 = time.perf_counter()
     b = Batch(insts, tune=not args.no_tune, prec=args.prec)
     create_s = time.perf_counter() - t0
@@ -372,12 +395,9 @@ def run_scan(args, rank, world, local_rank):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = b.launch_count() - l0
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     n = len(insts)
-    value = world * n * MOVES_PER_STEP * args.steps / (ms_max * 1e-3)
+    value = job_value(n * MOVES_PER_STEP * args.steps, world, ms_max * 1e-3)
     energies = b.energies([i["J"] for i in insts])
     tuning = b.tuning()
     b.close()
@@ -451,7 +471,7 @@ def run_cylinder(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     D = args.D if args.D != 5 else 6
     chi = args.chi if args.chi != 100 else 144
-    w = synth.workload("cfg5", seed=rank, D=D, chi=chi)
+    w = synth.workload("cfg5", seed=rank_seed(rank), D=D, chi=chi)
     stream = torch.cuda.current_stream()
     g = CTM(w["tensors"], w["pattern"], chi, prec=args.prec, stream=stream.cuda_stream)
 

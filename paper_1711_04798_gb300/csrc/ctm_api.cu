@@ -1415,8 +1415,6 @@ ipeps_status ctm_check_status(ipeps_ctm h) { return check_status(h); }
 ipeps_status ctm_reinit_env(ipeps_ctm h) { return trace_init_env(h); }
 void ctm_set_tuner(ipeps_ctm h, TcTuner* t) { h->tuner = t; }
 void ctm_set_sequential_cuts(ipeps_ctm h, bool on) { h->no_alt = on; }
-int ctm_chi(ipeps_ctm h) { return h->chi; }
-int ctm_bond_dim(ipeps_ctm h) { return h->D; }
 
 // ---------------------------------------------------------------------------
 // spectra / convergence

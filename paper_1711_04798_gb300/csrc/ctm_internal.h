@@ -78,8 +78,6 @@ cudaError_t zgemm(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A
                   long long work_elems = 0, int flags = 0);
 // sigma[i] = ||row i|| of G (n rows of length m, stride ldg)
 cudaError_t row_norms(cudaStream_t s, const cplx* G, int n, int m, long long ldg, double* sigma);
-// x <- conj(x)
-cudaError_t conj_inplace(cudaStream_t s, cplx* x, long long n);
 
 // out = alpha * (conj?) permute(in): out axis i is in axis perm[i].
 cudaError_t permute(cudaStream_t s, const cplx* in, cplx* out, int nd, const int* in_dims,
@@ -126,7 +124,6 @@ cudaError_t scale_rows_isqrt(cudaStream_t s, cplx* X, int rows, int m, long long
 cudaError_t trace_product(cudaStream_t s, const cplx* rho, const cplx* H, int n, double* acc,
                           int idx, double w);
 cudaError_t trace_normalize(cudaStream_t s, cplx* rho, int n, double* work);
-cudaError_t copy_to_complex(cudaStream_t s, const double* in, cplx* out, long long n);
 
 // Cholesky with dropped pivots (d <= tol * max diagonal) of the Hermitian n x n G:
 // R upper triangular (dropped rows zero); work: n*n scratch.  One CTA.

@@ -550,18 +550,6 @@ __global__ void trace_normalize_kernel(cplx* rho, int n) {
   for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) rho[e] = cmul(rho[e], inv);
 }
 
-__global__ void conj_kernel(cplx* x, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    x[i].y = -x[i].y;
-}
-
-__global__ void to_complex_kernel(const double* in, cplx* out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = make_double2(in[i], 0.0);
-}
-
 unsigned grid_for(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -727,20 +715,9 @@ cudaError_t trace_normalize(cudaStream_t s, cplx* rho, int n, double* work) {
   return cudaGetLastError();
 }
 
-cudaError_t copy_to_complex(cudaStream_t s, const double* in, cplx* out, long long n) {
-  to_complex_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
-  count_launch();
-  return cudaGetLastError();
-}
-
 cudaError_t row_norms(cudaStream_t s, const cplx* G, int n, int m, long long ldg, double* sigma) {
   row_norms_kernel<<<n < 1024 ? n : 1024, 256, 0, s>>>(G, n, m, ldg, sigma);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t conj_inplace(cudaStream_t s, cplx* x, long long n) {
-  conj_kernel<<<grid_for(n), 256, 0, s>>>(x, n);
-  count_launch();
-  return cudaGetLastError();
-}
