@@ -50,13 +50,13 @@ def parse():
 
 def workload(D, chi, seed):
     import synth
-    return synth.workload("cfg3", seed=seed, D=D, chi=chi)
+    return synth.workload("product_noise", seed=seed, D=D, chi=chi)
 
 
 def config_desc(args, prec):
     return {
         "workload": f"2x2 ruby block-site cell, d=8, D={args.D}, chi={args.chi}, complex product state "
-                    f"+ 0.1 complex-normal noise (config 3 recipe), rSVD projectors k=chi+16, q=2",
+                    f"+ 0.1 complex-normal noise, rSVD projectors k=chi+16, q=2",
         "step": "double-layer rebuild + 1 sweep (L,R,U,D) + 8 bond RDMs + energy",
         "prec": prec,
         "cell": "2x2",
@@ -471,7 +471,7 @@ def run_cylinder(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     D = args.D if args.D != 5 else 6
     chi = args.chi if args.chi != 100 else 144
-    w = synth.workload("cfg5", seed=rank_seed(rank), D=D, chi=chi)
+    w = synth.workload("product_noise", seed=rank_seed(rank), D=D, chi=chi)
     stream = torch.cuda.current_stream()
     g = CTM(w["tensors"], w["pattern"], chi, prec=args.prec, stream=stream.cuda_stream)
 
@@ -516,7 +516,7 @@ def run_cylinder(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec], "data": "synthetic",
         "config": {"workload": f"cylinder readout: 2x2 cell, d=8, D={D}, chi={chi}, complex product state + 0.1 "
-                               f"noise (config 5 recipe); {args.sweeps} sweeps then boundary rho at Nv=2,4,6",
+                               f"noise; {args.sweeps} sweeps then boundary rho at Nv=2,4,6",
                    "prec": args.prec},
         "readouts": readouts, "energy_per_spin": e,
         "corner_spectrum_tail": float(np.min(spectra[spectra > 0])), "clocks": clk.summary(),

@@ -4,8 +4,8 @@ The paper (Sec. II.C, Fig. 3) fixes WHAT is computed: an environment of four
 chi x chi corner matrices C1..C4 and eight chi x chi x D^2 half-row/column
 tensors T around a 2x2 unit cell of double-layer tensors a = sum_s A_s A_s^*
 (Fig. 3a), obtained with the directional CTM of its refs. Orus2009 and
-Corboz2010a.  It prints no move details, so the steps below are the reading
-recorded in the design notes, written out plainly:
+Corboz2010a.  It prints no move details, so the steps below are this oracle's reading of
+those references, written out plainly:
 
 * one environment set {C1..C4, T1..T4} per cell position (x, y) (x to the
   right, y downwards): C1 upper-left, C2 upper-right, C3 lower-right, C4

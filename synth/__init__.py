@@ -96,21 +96,21 @@ def omega(seed: int, rows: int, cols: int) -> np.ndarray:
 def workload(name: str, seed: int = 0, D: int | None = None, chi: int | None = None):
     """Return a dict describing one of the paper-shaped synthetic workloads.
 
-    ``cfg1_real_d8_D2_chi16``      4 real tensors, d=8, D=2, chi=16, J=(1,1,1)
-    ``cfg2_c128_d8_D4_chi64``      4 complex product+noise tensors, D=4, chi=64, J=(1,1,0.5)
-    ``cfg3_c128_d8_D5_chi100``     as cfg2 with D=5, chi=100
-    ``cfg5_c128_d8_D6_chi144``     as cfg2 with D=6, chi=144
-    D / chi may be overridden to build scaled-down variants of the same recipe.
+    ``real``           4 real iid-normal tensors, d=8, J=(1,1,1); D=2, chi=16
+                       unless given
+    ``product_noise``  4 complex all-up product + 0.1 noise tensors, d=8,
+                       J=(1,1,0.5); D and chi must be given (the paper's runs
+                       use D = 4, 5, 6 with chi = 64, 100, 144)
     """
     d = 8
-    if name.startswith("cfg1"):
+    if name == "real":
         D = D or 2
         chi = chi or 16
         tensors = [random_real(seed, t, d, D) for t in range(4)]
         J = (1.0, 1.0, 1.0)
-    elif name.startswith(("cfg2", "cfg3", "cfg5")):
-        D = D or {"cfg2": 4, "cfg3": 5, "cfg5": 6}[name[:4]]
-        chi = chi or {"cfg2": 64, "cfg3": 100, "cfg5": 144}[name[:4]]
+    elif name == "product_noise":
+        if D is None or chi is None:
+            raise ValueError("product_noise needs D and chi")
         tensors = [product_plus_noise(seed, t, d, D) for t in range(4)]
         J = (1.0, 1.0, 0.5)
     else:

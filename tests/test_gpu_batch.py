@@ -127,7 +127,7 @@ def test_batch_create_error_names_instance():
 def test_single_handle_autotune_keeps_environment():
     """ipeps_ctm_autotune restores the environment; tuned tiles change results only by rounding."""
     from paper_1711_04798_gb300 import CTM
-    w = synth.workload("cfg2", seed=4, D=3, chi=16)
+    w = synth.workload("product_noise", seed=4, D=3, chi=16)
     kw = dict(DEFAULTS, cutoff=1e-6, prec="bf16x3")
     a = CTM(w["tensors"], w["pattern"], 16, **kw)
     b = CTM(w["tensors"], w["pattern"], 16, **kw)

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _pair(D, chi, sweeps, seed=2, prec="fp64"):
-    w = synth.workload("cfg2", seed=seed, D=D, chi=chi)
+    w = synth.workload("product_noise", seed=seed, D=D, chi=chi)
     g = gpu_ctm(w["tensors"], w["pattern"], chi, prec=prec)
     g.sweep(sweeps)
     st = O.make_state(w["tensors"], w["pattern"], D, chi)

@@ -23,7 +23,7 @@ def _sweeps(ts, pat, D, chi, n, **kw):
 
 
 def test_checkerboard_two_tensor_cell():
-    w = synth.workload("cfg2", seed=8, D=2, chi=10)
+    w = synth.workload("product_noise", seed=8, D=2, chi=10)
     ts, pat = w["tensors"][:2], [[0, 1], [1, 0]]
     g = gpu_ctm(ts, pat, 10)
     g.sweep(3)
@@ -38,7 +38,7 @@ def test_checkerboard_two_tensor_cell():
 
 @pytest.mark.parametrize("pat", [[[0, 1]], [[0], [1]]])
 def test_rectangular_cells(pat):
-    w = synth.workload("cfg2", seed=9, D=2, chi=8)
+    w = synth.workload("product_noise", seed=9, D=2, chi=8)
     ts = w["tensors"][:2]
     g = gpu_ctm(ts, pat, 8)
     g.sweep(2)
@@ -82,7 +82,7 @@ def test_full_size_config3_one_sweep():
     """D = 5, chi = 100 (the bench's workload): one sweep from the trace
     initialisation, FP64 GPU path vs the oracle at 1e-10, and the BF16x3
     precision form within the 1e-6 energy target."""
-    w = synth.workload("cfg3", seed=0)
+    w = synth.workload("product_noise", seed=0, D=5, chi=100)
     st = _sweeps(w["tensors"], w["pattern"], 5, 100, 1)
     rd = O.bond_rdms(st, w["tensors"], w["pattern"])
     e_ref = O.energy_per_spin(rd, w["J"], 2, 2)

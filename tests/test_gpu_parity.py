@@ -36,7 +36,7 @@ def _compare_spectra(g, st, floor=1e-8, tol=1e-8):
 
 
 def test_trace_init_environment_matches():
-    w = synth.workload("cfg1", seed=3)
+    w = synth.workload("real", seed=3)
     g = gpu_ctm(w["tensors"], w["pattern"], 8)
     st = O.make_state(w["tensors"], w["pattern"], w["D"], 8)
     for role in range(8):
@@ -48,7 +48,7 @@ def test_trace_init_environment_matches():
 
 @pytest.mark.parametrize("direction", ["L", "R", "U", "D"])
 def test_single_move_each_direction(direction):
-    w = synth.workload("cfg1", seed=1, chi=12)
+    w = synth.workload("real", seed=1, chi=12)
     g = gpu_ctm(w["tensors"], w["pattern"], 12)
     g.move(direction, 1)
     st = _oracle_run(w, 12, [direction])
@@ -56,9 +56,9 @@ def test_single_move_each_direction(direction):
     _compare_spectra(g, st)
 
 
-def test_cfg1_twenty_sweeps_energy_rdms_spectra():
-    """Config 1: real d=8, D=2, chi=16, 20 sweeps, J=(1,1,1)."""
-    w = synth.workload("cfg1", seed=0)
+def test_real_D2_chi16_twenty_sweeps_energy_rdms_spectra():
+    """Real iid tensors, d=8, D=2, chi=16, 20 sweeps, J=(1,1,1)."""
+    w = synth.workload("real", seed=0)
     g = gpu_ctm(w["tensors"], w["pattern"], 16)
     g.sweep(20)
     st = _oracle_run(w, 16, ["sweep"] * 20)
@@ -69,9 +69,9 @@ def test_cfg1_twenty_sweeps_energy_rdms_spectra():
     _compare_spectra(g, st)
 
 
-def test_cfg2_recipe_scaled_complex():
+def test_product_noise_D3_chi18_complex():
     """Config-2 recipe (complex product state + 0.1 noise) at D=3, chi=18."""
-    w = synth.workload("cfg2", seed=2, D=3, chi=18)
+    w = synth.workload("product_noise", seed=2, D=3, chi=18)
     g = gpu_ctm(w["tensors"], w["pattern"], 18)
     g.sweep(3)
     st = _oracle_run(w, 18, ["sweep"] * 3)
@@ -91,8 +91,8 @@ def test_ising_onsager_on_gpu():
 
 
 def test_kappa_and_fidelity_match_oracle():
-    w1 = synth.workload("cfg2", seed=4, D=2, chi=8)
-    w2 = synth.workload("cfg2", seed=5, D=2, chi=8)
+    w1 = synth.workload("product_noise", seed=4, D=2, chi=8)
+    w2 = synth.workload("product_noise", seed=5, D=2, chi=8)
     t1, t2, pat = w1["tensors"], w2["tensors"], w1["pattern"]
     hs = [gpu_ctm(t1, pat, 8, bra=t2), gpu_ctm(t1, pat, 8), gpu_ctm(t2, pat, 8)]
     ks_ref = []
@@ -114,7 +114,7 @@ def test_kappa_and_fidelity_match_oracle():
 
 @pytest.mark.parametrize("Nv", [2, 4])
 def test_boundary_rho_matches_oracle(Nv):
-    w = synth.workload("cfg2", seed=6, D=2, chi=8)
+    w = synth.workload("product_noise", seed=6, D=2, chi=8)
     g = gpu_ctm(w["tensors"], w["pattern"], 8)
     g.sweep(3)
     st = _oracle_run(w, 8, ["sweep"] * 3)
@@ -126,7 +126,7 @@ def test_boundary_rho_matches_oracle(Nv):
 
 def test_errors_are_reported_not_fatal():
     from paper_1711_04798_gb300 import CTMError
-    w = synth.workload("cfg1", seed=0)
+    w = synth.workload("real", seed=0)
     with pytest.raises(CTMError):
         gpu_ctm(w["tensors"], w["pattern"], 3)  # chi < D^2
     g = gpu_ctm(w["tensors"], w["pattern"], 8)
@@ -140,7 +140,7 @@ def test_cluster_sized_cores_match_oracle(chi):
     """chi >= 32: the projector core (k = chi + 16 rows), the CholeskyQR
     factorisations and the corner spectra (chi x chi) run on the 16-CTA cluster
     kernels; odd chi leaves a dummy player in the Jacobi pair schedule."""
-    w = synth.workload("cfg2", seed=6, D=2, chi=chi)
+    w = synth.workload("product_noise", seed=6, D=2, chi=chi)
     g = gpu_ctm(w["tensors"], w["pattern"], chi)
     g.sweep(2)
     st = _oracle_run(w, chi, ["sweep"] * 2)

@@ -17,7 +17,7 @@ BOUND = {"bf16x3": 3e-6, "tf32": 1e-3}
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_precision_form_energy_error(prec):
-    w = synth.workload("cfg2", seed=2, D=3, chi=18)
+    w = synth.workload("product_noise", seed=2, D=3, chi=18)
     g = gpu_ctm(w["tensors"], w["pattern"], 18, prec=prec)
     g.sweep(6)
     st = O.make_state(w["tensors"], w["pattern"], w["D"], 18)

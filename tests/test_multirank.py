@@ -31,7 +31,7 @@ def _rank_main(rank, world, port, q):
     t_max = bench.max_over_ranks(local_seconds, dist)
     value = bench.job_value(8, world, t_max)
     seed = bench.rank_seed(rank)
-    w = synth.workload("cfg2", seed=seed, D=2, chi=8)
+    w = synth.workload("product_noise", seed=seed, D=2, chi=8)
     scan = synth.scan(seed=seed, n=4, Ds=(2, 3), chis=(9, 12))
     q.put((rank, dist.get_backend(), t_max, value, seed, float(np.abs(w["tensors"][0]).sum()),
            [(i["D"], i["chi"]) for i in scan]))

@@ -490,7 +490,7 @@ def test_product_state_boundary_entropy_is_zero():
 
 
 def _converged_state(seed, D, chi, sweeps):
-    w = synth.workload("cfg2", seed=seed, D=D, chi=chi)
+    w = synth.workload("product_noise", seed=seed, D=D, chi=chi)
     st = O.make_state(w["tensors"], w["pattern"], D, chi)
     opt = O.CTMOptions(chi=chi, proj="rsvd", omega=synth.omega(7, chi * D * D, chi + 16))
     for _ in range(sweeps):

@@ -33,7 +33,7 @@ def _lib():
 def test_noalloc_corner_spectrum_matches_spectra_twice():
     import torch
     lib, f = _lib()
-    w = synth.workload("cfg1", seed=11, chi=16)
+    w = synth.workload("real", seed=11, chi=16)
     g = gpu_ctm(w["tensors"], w["pattern"], 16)
     g.sweep(2)
     s_ref = g.spectra()  # existing entry point, [4][Ly][Lx][chi]
