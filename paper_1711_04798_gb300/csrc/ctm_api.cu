@@ -785,7 +785,6 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   CKS(validate(c, o));
   if (!out) return fail(IPEPS_EINVAL, "null out");
   ipeps_ctm h = new ipeps_ctm_s();
-  memset(h, 0, sizeof *h);
   h->Lx = c->Lx; h->Ly = c->Ly; h->d = c->d; h->D = c->D; h->D2 = c->D * c->D;
   h->chi = o->chi; h->K = o->chi * h->D2; h->k = o->chi + o->rsvd_oversample;
   h->ntens = c->n_tensors;

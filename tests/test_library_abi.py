@@ -55,3 +55,139 @@ def test_argument_validation_without_gpu(lib):
     cell.pattern[3] = 7
     h = ctypes.c_void_p()
     assert lib.ipeps_ctm_create(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(h)) == 1
+
+
+def _good(lib):
+    """A valid 2x2, d=8, D=4, chi=64 cell (fake non-null tensor pointers)."""
+    from paper_1711_04798_gb300.binding import Cell, Options
+    cell = Cell()
+    cell.Lx = cell.Ly = 2
+    for i in range(4):
+        cell.pattern[i] = i
+    cell.n_tensors, cell.d, cell.D, cell.dtype = 4, 8, 4, 1
+    ptrs = (ctypes.c_void_p * 4)(1, 1, 1, 1)
+    cell.tensors = ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p))
+    opt = Options()
+    lib.ipeps_default_options(ctypes.byref(opt))
+    opt.chi = 64
+    return cell, opt, ptrs
+
+
+def _set(obj, field, value):
+    if field == "pattern":
+        obj.pattern[2] = value
+    elif field == "tensors":
+        obj.tensors = None
+    else:
+        setattr(obj, field, value)
+
+
+# (target, field, value, fragment of the error message)
+_RULES = [
+    ("cell", "Lx", 0, b"Lx"), ("cell", "Lx", 3, b"Lx"), ("cell", "Ly", 0, b"Ly"),
+    ("cell", "n_tensors", 0, b"n_tensors"), ("cell", "n_tensors", 5, b"n_tensors"),
+    ("cell", "pattern", 4, b"pattern"), ("cell", "pattern", -1, b"pattern"),
+    ("cell", "d", 0, b"d in"), ("cell", "d", 65, b"d in"), ("cell", "D", 13, b"D in"),
+    ("cell", "dtype", 9, b"dtype"), ("cell", "tensors", None, b"null tensors"),
+    ("opt", "chi", 15, b"chi"), ("opt", "chi", 1025, b"chi > 1024"),
+    ("opt", "rsvd_oversample", -1, b"rsvd"), ("opt", "rsvd_power", -1, b"rsvd"),
+    ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 3, b"prec"),
+    ("opt", "prec", -1, b"prec"), ("opt", "jacobi_max_sweeps", 0, b"jacobi"),
+]
+
+
+@pytest.mark.parametrize("target,field,value,frag", _RULES)
+def test_each_create_rule_rejects_before_cuda(lib, target, field, value, frag):
+    cell, opt, _keep = _good(lib)
+    n = ctypes.c_size_t()
+    assert lib.ipeps_ctm_workspace_size(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(n)) == 0
+    _set(cell if target == "cell" else opt, field, value)
+    assert lib.ipeps_ctm_workspace_size(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(n)) == 1
+    assert frag in lib.ipeps_last_error(), lib.ipeps_last_error()
+    h = ctypes.c_void_p()
+    assert lib.ipeps_ctm_create(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(h)) == 1
+    assert h.value is None
+
+
+def test_workspace_grows_with_chi_and_D(lib):
+    cell, opt, _keep = _good(lib)
+    sizes = {}
+    for D, chi in [(2, 16), (4, 64), (4, 100), (5, 100)]:
+        cell.D, opt.chi = D, chi
+        n = ctypes.c_size_t()
+        assert lib.ipeps_ctm_workspace_size(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(n)) == 0
+        sizes[(D, chi)] = n.value
+        # at least the environment: 4 corners chi^2 and 4 edges chi^2 D^2 per site, complex
+        assert n.value >= 4 * 16 * chi * chi * (1 + D * D)
+    assert sizes[(2, 16)] < sizes[(4, 64)] < sizes[(4, 100)] < sizes[(5, 100)]
+
+
+def test_null_handles_are_rejected(lib):
+    D = ctypes.c_double
+    buf = (D * 64)()
+    i = ctypes.c_int()
+    J = (D * 3)(1, 1, 1)
+    calls = [
+        lambda: lib.ipeps_ctm_move(None, 0, 1),
+        lambda: lib.ipeps_ctm_spectra(None, buf),
+        lambda: lib.ipeps_ctm_converge(None, 1e-10, 5, ctypes.byref(i), buf),
+        lambda: lib.ipeps_rdm(None, buf, buf),
+        lambda: lib.ipeps_energy(None, J, buf),
+        lambda: lib.ipeps_kappa(None, buf),
+        lambda: lib.ipeps_fidelity(None, None, None, buf, buf),
+        lambda: lib.ipeps_boundary_rho(None, 0, 2, buf, ctypes.byref(i), buf),
+        lambda: lib.ipeps_boundary_rho_topk(None, 0, 2, 4, 50, 1e-10, buf, ctypes.byref(i), buf, buf),
+        lambda: lib.ipeps_ctm_autotune(None),
+        lambda: lib.ipeps_ctm_set_tensors(None, None, None),
+        lambda: lib.ipeps_ctm_reset_env(None),
+        lambda: lib.ipeps_ctm_sync(None),
+        lambda: lib.ipeps_ctm_profile(None, 1),
+        lambda: lib.ipeps_batch_move(None, 0, 1),
+        lambda: lib.ipeps_batch_energy(None, J, buf),
+        lambda: lib.ipeps_batch_sync(None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 1, (k, lib.ipeps_last_error())
+        assert b"null" in lib.ipeps_last_error(), (k, lib.ipeps_last_error())
+    # queries on null handles answer with neutral values, destroy is a no-op
+    assert lib.ipeps_ctm_launch_count(None) == 0
+    assert lib.ipeps_ctm_tuning_size(None) == 0
+    assert lib.ipeps_batch_instance(None, 0) is None
+    assert lib.ipeps_batch_launch_count(None) == 0
+    assert lib.ipeps_batch_tuning_size(None) == 0
+    assert lib.ipeps_batch_stream(None) is None
+    lib.ipeps_ctm_destroy(None)
+    lib.ipeps_batch_destroy(None)
+
+
+def test_batch_create_rejects_empty(lib):
+    cell, opt, _keep = _good(lib)
+    b = ctypes.c_void_p()
+    assert lib.ipeps_batch_create(0, ctypes.byref(cell), ctypes.byref(opt), 0, ctypes.byref(b)) == 1
+    assert lib.ipeps_batch_create(1, None, ctypes.byref(opt), 0, ctypes.byref(b)) == 1
+    assert b.value is None
+
+
+def test_gemm_entry_points_reject_bad_shapes(lib):
+    I, P = ctypes.c_int, ctypes.c_void_p
+    one = P(16)
+    # ipeps_zgemm(prec, M, N, K, A, opA, B, opB, C)
+    assert lib.ipeps_zgemm(I(0), I(0), I(4), I(4), one, I(0), one, I(0), one) == 1
+    assert lib.ipeps_zgemm(I(0), I(4), I(4), I(4), None, I(0), one, I(0), one) == 1
+    assert lib.ipeps_zgemm(I(3), I(4), I(4), I(4), one, I(0), one, I(0), one) == 1
+    assert lib.ipeps_zgemm(I(0), I(4), I(4), I(4), one, I(4), one, I(0), one) == 1
+    # ipeps_zgemm_tile(prec, bn, splits, ...): tensor-core precisions and BN in {128, 256} only
+    args = (I(4), I(4), I(4), one, I(0), one, I(0), one)
+    assert lib.ipeps_zgemm_tile(I(0), I(128), I(1), *args) == 1
+    assert lib.ipeps_zgemm_tile(I(2), I(64), I(1), *args) == 1
+    assert lib.ipeps_zgemm_tile(I(2), I(128), I(0), *args) == 1
+    assert b"tile" in lib.ipeps_last_error()
+
+
+def test_noalloc_rejects_before_touching_scratch(lib):
+    I, P = ctypes.c_int, ctypes.c_void_p
+    assert lib.ipeps_corner_spectrum_noalloc(None, I(8), P(16), None) == 1
+    assert b"null" in lib.ipeps_last_error()
+    for chi in (0, -3, 257):
+        assert lib.ipeps_corner_spectrum_noalloc(P(16), I(chi), P(16), None) == 1
+        assert b"outside 1..256" in lib.ipeps_last_error()
