@@ -53,7 +53,8 @@ typedef enum {
   IPEPS_ENOCONV = 4,     /* converge: max_sweeps reached above tolerance      */
   IPEPS_ETIMEOUT = 5,    /* an iteration budget inside a kernel ran out       */
   IPEPS_ENUMERIC = 6,    /* NaN/Inf or a zero norm met                        */
-  IPEPS_EUNSUPPORTED = 7 /* option combination not built                      */
+  IPEPS_EUNSUPPORTED = 7, /* option combination not built                     */
+  IPEPS_EIO = 8           /* checkpoint file missing, unwritable, short, corrupt */
 } ipeps_status;
 
 typedef enum { IPEPS_REAL64 = 0, IPEPS_COMPLEX128 = 1 } ipeps_dtype;
@@ -214,6 +215,46 @@ ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int k, int max_
 /* Copy one environment tensor to the host: role 0..3 = C1..C4 (chi*chi
  * complex), 4..7 = T1..T4 (chi*D*D*chi complex), at cell position (x,y). */
 ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* host_out);
+
+/* Overwrite one environment tensor from the host, same role / position /
+ * layout as ipeps_ctm_env_get (complex128, interleaved re, im; C[a,b] chi*chi
+ * and T[a,k,b] chi*D*D*chi row-major, the D*D leg fused ket*D + bra).  This is
+ * the user-supplied initial environment (instead of the trace initialisation
+ * of create / reset_env): the next move starts from what was set.  The
+ * library copies the data; nothing is normalised.  Errors: EINVAL (null
+ * pointer, role outside 0..7, position outside the cell), ECUDA. */
+ipeps_status ipeps_ctm_env_set(ipeps_ctm h, int role, int x, int y, const double* host_in);
+
+/* Checkpoint and resume of the environment (the CTM state that moves
+ * update; the site tensors and options are the caller's and are not stored).
+ *
+ * File format (little-endian):
+ *   bytes 0..7    "IPEPSENV"
+ *   12 x int32    version (1), Lx, Ly, d, D, chi, n_tensors, pattern[4], 0
+ *   payload       for site y*Lx + x in order, for role 0..7 (C1..C4, T1..T4):
+ *                 the tensor as ipeps_ctm_env_get returns it (complex128)
+ *   uint64        checksum of the payload: h = 0xcbf29ce484222325, then for
+ *                 each 8-byte little-endian word w: h = (h ^ w) * 0x100000001b3
+ *                 (mod 2^64; FNV-1a applied to 64-bit words)
+ *
+ * ipeps_ctm_save writes `path` through a temporary "<path>.part" renamed on
+ * success, so an interrupted save leaves any earlier file intact.  Errors:
+ * EINVAL (null argument), ECUDA, EIO (cannot write). */
+ipeps_status ipeps_ctm_save(ipeps_ctm h, const char* path);
+
+/* Load a checkpoint written by ipeps_ctm_save into a handle with the same Lx,
+ * Ly, D and chi (d, the tensors and the pattern may differ: a converged
+ * environment of one coupling point is a warm start for a nearby one).  The
+ * file is read and its checksum verified before the handle is touched, so
+ * after EINVAL or EIO the environment is unchanged (after ECUDA it may be
+ * partly loaded).  Errors: EINVAL (null argument, geometry differs), EIO
+ * (missing, short, not a checkpoint, bad checksum), ECUDA. */
+ipeps_status ipeps_ctm_load(ipeps_ctm h, const char* path);
+
+/* Read and verify a checkpoint's header and checksum without a handle or a
+ * GPU.  info (caller-owned, 11 ints): version, Lx, Ly, d, D, chi, n_tensors,
+ * pattern[4].  Errors: EINVAL (null argument), EIO as ipeps_ctm_load. */
+ipeps_status ipeps_env_file_info(const char* path, int* info);
 
 /* Block until all work of the handle is done. */
 ipeps_status ipeps_ctm_sync(ipeps_ctm h);

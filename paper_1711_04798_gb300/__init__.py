@@ -5,4 +5,4 @@ by ``build.build()``); ``binding`` is a thin ctypes layer over its C ABI
 (``include/ipeps_ctm.h``).  There is no CPU fallback: loading fails loudly
 when the library is missing.
 """
-from .binding import CTM, Batch, CTMError, load_library  # noqa: F401
+from .binding import CTM, Batch, CTMError, env_file_info, load_library  # noqa: F401

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libipeps_ctm.so")
 PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2}
 DIRS = {"L": 0, "U": 1, "R": 2, "D": 3, "sweep": 4}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT",
-          6: "ENUMERIC", 7: "EUNSUPPORTED"}
+          6: "ENUMERIC", 7: "EUNSUPPORTED", 8: "EIO"}
 
 EXPORTS = [
     "ipeps_default_options", "ipeps_ctm_workspace_size", "ipeps_ctm_create",
@@ -24,7 +24,8 @@ EXPORTS = [
     "ipeps_batch_create", "ipeps_batch_move", "ipeps_batch_energy", "ipeps_batch_instance",
     "ipeps_batch_tuning_size", "ipeps_batch_tuning_entry", "ipeps_batch_launch_count",
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
-    "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile",
+    "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile", "ipeps_ctm_env_set",
+    "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info",
 ]
 
 
@@ -74,6 +75,10 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_fidelity.argtypes = [P, P, P, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_boundary_rho.argtypes = [P, I, I, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
     lib.ipeps_ctm_env_get.argtypes = [P, I, I, I, C.POINTER(D)]
+    lib.ipeps_ctm_env_set.argtypes = [P, I, I, I, C.POINTER(D)]
+    lib.ipeps_ctm_save.argtypes = [P, C.c_char_p]
+    lib.ipeps_ctm_load.argtypes = [P, C.c_char_p]
+    lib.ipeps_env_file_info.argtypes = [C.c_char_p, C.POINTER(I)]
     lib.ipeps_ctm_autotune.argtypes = [P]
     lib.ipeps_ctm_tuning_size.argtypes = [P]
     lib.ipeps_boundary_rho_topk.argtypes = [P, I, I, I, I, D, C.POINTER(D), C.POINTER(I), C.POINTER(D),
@@ -107,6 +112,17 @@ def load_library(path: str = LIB_PATH):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
+
+
+def env_file_info(path) -> dict:
+    """Header of a verified environment checkpoint (no GPU needed)."""
+    lib = load_library()
+    info = (C.c_int * 11)()
+    _check(lib.ipeps_env_file_info(os.fsencode(path), info))
+    keys = ("version", "Lx", "Ly", "d", "D", "chi", "n_tensors")
+    out = dict(zip(keys, info[:7]))
+    out["pattern"] = list(info[7:11])
+    return out
 
 
 def _check(st: int):
@@ -319,6 +335,22 @@ class CTM:
         if role < 4:
             return out.reshape(self.chi, self.chi)
         return out.reshape(self.chi, self.D * self.D, self.chi)
+
+    def set_env(self, role, x, y, t: np.ndarray):
+        """Overwrite one environment tensor (layout of ``env``): a user-supplied start."""
+        n = self.chi * self.chi if role < 4 else self.chi * self.D * self.D * self.chi
+        buf = np.ascontiguousarray(t, dtype=np.complex128).reshape(-1)
+        if buf.size != n:
+            raise ValueError(f"role {role} needs {n} complex elements, got {buf.size}")
+        _check(self.lib.ipeps_ctm_env_set(self.h, role, x, y, _dptr(buf.view(np.float64))))
+
+    def save(self, path):
+        """Write the environment to a checkpoint file."""
+        _check(self.lib.ipeps_ctm_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        """Replace the environment by a checkpoint of the same Lx, Ly, D and chi."""
+        _check(self.lib.ipeps_ctm_load(self.h, os.fsencode(path)))
 
     def sync(self):
         _check(self.lib.ipeps_ctm_sync(self.h))

@@ -2049,6 +2049,23 @@ extern "C" ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, d
   return IPEPS_OK;
 }
 
+extern "C" ipeps_status ipeps_ctm_env_set(ipeps_ctm h, int role, int x, int y, const double* in) {
+  if (!h || !in) return fail(IPEPS_EINVAL, "null argument");
+  if (role < 0 || role > 7 || x < 0 || x >= h->Lx || y < 0 || y >= h->Ly)
+    return fail(IPEPS_EINVAL, "bad role/position");
+  const long long n = role < 4 ? (long long)h->chi * h->chi : (long long)h->chi * h->D2 * h->chi;
+  cplx* dst = role < 4 ? h->C[role][y * h->Lx + x] : h->T[role - 4][y * h->Lx + x];
+  CK(cudaMemcpyAsync(dst, in, n * sizeof(cplx), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return IPEPS_OK;
+}
+
+// geometry for the checkpoint module: Lx, Ly, d, D, chi, n_tensors, pattern[4]
+void ctm_geometry(ipeps_ctm h, int g[10]) {
+  g[0] = h->Lx; g[1] = h->Ly; g[2] = h->d; g[3] = h->D; g[4] = h->chi; g[5] = h->ntens;
+  for (int i = 0; i < 4; ++i) g[6 + i] = h->pattern[i];
+}
+
 // ---------------------------------------------------------------------------
 // stand-alone complex GEMM (building block, host buffers) for unit tests
 // ---------------------------------------------------------------------------

@@ -191,3 +191,58 @@ def test_noalloc_rejects_before_touching_scratch(lib):
     for chi in (0, -3, 257):
         assert lib.ipeps_corner_spectrum_noalloc(P(16), I(chi), P(16), None) == 1
         assert b"outside 1..256" in lib.ipeps_last_error()
+
+
+def _fnv64_words(payload: np.ndarray) -> int:
+    """The checkpoint checksum as the header states it (FNV-1a over 64-bit words)."""
+    h = 0xCBF29CE484222325
+    for w in payload.view(np.uint64).tolist():
+        h = ((h ^ w) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _write_checkpoint(path, Lx, Ly, d, D, chi, pattern, seed=0, version=1):
+    import struct
+    rng = np.random.default_rng(seed)
+    n = Lx * Ly * (4 * chi * chi + 4 * chi * D * D * chi)
+    payload = rng.standard_normal(2 * n)
+    with open(path, "wb") as f:
+        f.write(b"IPEPSENV")
+        f.write(struct.pack("<12i", version, Lx, Ly, d, D, chi, 4, *pattern, 0))
+        f.write(payload.astype("<f8").tobytes())
+        f.write(struct.pack("<Q", _fnv64_words(payload)))
+    return payload
+
+
+def test_checkpoint_header_and_checksum_verified_without_gpu(lib, tmp_path):
+    from paper_1711_04798_gb300 import CTMError, env_file_info
+    p = tmp_path / "env.ipeps"
+    _write_checkpoint(p, 2, 2, 8, 2, 6, [0, 1, 1, 0])
+    info = env_file_info(p)
+    assert info == {"version": 1, "Lx": 2, "Ly": 2, "d": 8, "D": 2, "chi": 6, "n_tensors": 4,
+                    "pattern": [0, 1, 1, 0]}
+    raw = bytearray(p.read_bytes())
+    # one flipped payload bit, a truncated file, a foreign file, a newer version
+    bad = tmp_path / "bad.ipeps"
+    flipped = bytearray(raw)
+    flipped[56 + 100] ^= 0x10
+    cases = {"checksum": bytes(flipped), "bytes, expected": bytes(raw[:-9]),
+             "not an environment": b"NOTENV!!" + bytes(raw[8:]),
+             "version": bytes(raw[:8]) + (2).to_bytes(4, "little") + bytes(raw[12:])}
+    for frag, blob in cases.items():
+        bad.write_bytes(blob)
+        with pytest.raises(CTMError) as e:
+            env_file_info(bad)
+        assert e.value.status == 8 and frag in str(e.value), (frag, str(e.value))
+    with pytest.raises(CTMError) as e:
+        env_file_info(tmp_path / "missing.ipeps")
+    assert e.value.status == 8
+
+
+def test_checkpoint_calls_reject_null_handles(lib, tmp_path):
+    buf = (ctypes.c_double * 8)()
+    assert lib.ipeps_ctm_env_set(None, 0, 0, 0, buf) == 1
+    assert lib.ipeps_ctm_save(None, str(tmp_path / "x").encode()) == 1
+    assert lib.ipeps_ctm_load(None, str(tmp_path / "x").encode()) == 1
+    assert lib.ipeps_env_file_info(None, (ctypes.c_int * 11)()) == 1
+    assert not (tmp_path / "x").exists() and not (tmp_path / "x.part").exists()
