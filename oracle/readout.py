@@ -15,6 +15,8 @@ from .ctm import CTMState, rotate_k
 __all__ = [
     "rdm_horizontal",
     "bond_rdms",
+    "rdm_site",
+    "site_rdms",
     "pauli_block_ops",
     "ruby_bond_hamiltonians",
     "energy_per_spin",
@@ -72,6 +74,53 @@ def rdm_horizontal(st: CTMState, A_cell, x: int, y: int) -> np.ndarray:
     d = A.shape[0]
     rho = rho.reshape(d * d, d * d)
     return rho / np.trace(rho)
+
+
+def rdm_site(st: CTMState, A_cell, x: int, y: int) -> np.ndarray:
+    """One-site RDM at (x,y), normalised to trace 1, as a (d, d) matrix
+    rho[p, p'] (row ket, column bra).
+
+    Sec. II.C: a local expectation value is the network with the site's
+    physical legs left open, the rest of the plane replaced by its environment
+    (Fig. 3b).  Written as its definition: the eight environment tensors of
+    the site are contracted into one ring E over the site's four double
+    legs, then closed with A and conj(A):
+
+        C1 T1 C2
+        T4  .  T2        E[(u u'), (l l'), (d d'), (r r')]
+        C4 T3 C3
+    """
+    Lx, Ly, D = st.Lx, st.Ly, st.D
+    x0, y0 = x % Lx, y % Ly
+    C = [st.C[j][y0][x0] for j in range(4)]
+    T = [st.T[j][y0][x0] for j in range(4)]
+    # C1[d,r] T1[l,u,r] C2[l,d]: a = C1 down, U = site up leg, e = C2 down
+    top = np.einsum("ab,bUc->aUc", C[0], T[0])
+    top = np.einsum("aUc,ce->aUe", top, C[1])
+    # C4[r,u] T3[r,u,l] C3[u,l]: f = C4 up, V = site down leg, g = C3 up
+    bottom = np.einsum("hf,iVh->fVi", C[3], T[2])
+    bottom = np.einsum("fVi,gi->fVg", bottom, C[2])
+    # T4[d,r,u] = [f, L, a], T2[u,l,d] = [e, R, g]
+    E = np.einsum("aUe,fLa->UefL", top, T[3])
+    E = np.einsum("UefL,eRg->UfLRg", E, T[1])
+    E = np.einsum("UfLRg,fVg->ULVR", E, bottom)
+    E = E.reshape(D, D, D, D, D, D, D, D)  # u u' l l' d d' r r'
+    A = A_cell[y0][x0].astype(np.complex128)
+    half = np.einsum("uUlLsSrR,pulsr->pULSR", E, A)
+    rho = np.einsum("pULSR,qULSR->pq", half, np.conj(A))
+    return rho / np.trace(rho)
+
+
+def site_rdms(st: CTMState, tensors, pattern) -> np.ndarray:
+    """One-site RDMs of every cell position: array [Ly, Lx, d, d]."""
+    Lx, Ly = st.Lx, st.Ly
+    A_cell = [[tensors[pattern[y][x]] for x in range(Lx)] for y in range(Ly)]
+    d = A_cell[0][0].shape[0]
+    out = np.zeros((Ly, Lx, d, d), dtype=np.complex128)
+    for y in range(Ly):
+        for x in range(Lx):
+            out[y, x] = rdm_site(st, A_cell, x, y)
+    return out
 
 
 def _rotate_tensor(A: np.ndarray) -> np.ndarray:

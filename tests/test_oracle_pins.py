@@ -325,6 +325,66 @@ def test_trace_init_rdm_equals_bruteforce_patch():
     assert np.allclose(rho, ref, atol=1e-13)
 
 
+def test_trace_init_site_rdm_equals_bruteforce_patch():
+    """At the trace initialisation the one-site window is the 3x3 open patch."""
+    ts = random_tensors(17, 4, 2, 2)
+    pat = [[0, 1], [2, 3]]
+    st = O.make_state(ts, pat, 2, 4)
+    A_cell = [[ts[pat[y][x]] for x in range(2)] for y in range(2)]
+    for (x, y) in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        rho = O.rdm_site(st, A_cell, x, y)
+        ref = brute_force_rdm(ts, pat, range(x - 1, x + 2), range(y - 1, y + 2), [(x, y)])
+        assert np.allclose(rho, ref, atol=1e-13), (x, y)
+
+
+@pytest.mark.parametrize("direction", ["L", "R", "U", "D"])
+def test_untruncated_move_site_rdm_equals_bruteforce_patch(direction):
+    ts = random_tensors(19, 1, 3, 2)
+    st = O.make_state(ts, [[0]], 2, 64)
+    st = O.move(st, direction, O.CTMOptions(chi=64, proj="svd", cutoff=1e-14))
+    rho = O.rdm_site(st, [[ts[0]]], 0, 0)
+    xs = {"L": range(-2, 2), "R": range(-1, 3)}.get(direction, range(-1, 2))
+    ys = {"U": range(-2, 2), "D": range(-1, 3)}.get(direction, range(-1, 2))
+    ref = brute_force_rdm(ts, [[0]], xs, ys, [(0, 0)])
+    assert np.allclose(rho, ref, atol=1e-9)
+
+
+def test_product_state_site_rdm():
+    phis, ts = product_tensors(21)
+    pat = [[0, 1], [2, 3]]
+    st = O.sweep(O.make_state(ts, pat, 1, 2), O.CTMOptions(chi=2, proj="svd"))
+    r = O.site_rdms(st, ts, pat)
+    for y in range(2):
+        for x in range(2):
+            phi = phis[pat[y][x]]
+            assert np.allclose(r[y, x], np.outer(phi, phi.conj()) / np.vdot(phi, phi), atol=1e-14)
+
+
+def test_site_rdm_is_partial_trace_of_bond_rdms_when_converged():
+    """At a converged environment the one-site window and the two-site windows
+    describe the same state: tracing either site out of a bond RDM gives the
+    site RDM (up to the truncation error)."""
+    w = synth.workload("product_noise", seed=23, D=2, chi=16)
+    st = O.make_state(w["tensors"], w["pattern"], 2, 16)
+    opt = O.CTMOptions(chi=16, proj="svd", cutoff=1e-12)
+    for _ in range(12):
+        st = O.sweep(st, opt)
+    rs = O.site_rdms(st, w["tensors"], w["pattern"])
+    rb = O.bond_rdms(st, w["tensors"], w["pattern"])
+    d = 8
+    for y in range(2):
+        for x in range(2):
+            h = rb["h"][y, x].reshape(d, d, d, d)  # [p q, p' q']
+            v = rb["v"][y, x].reshape(d, d, d, d)
+            assert np.allclose(np.einsum("pqrq->pr", h), rs[y, x], atol=1e-9)
+            assert np.allclose(np.einsum("pqpr->qr", h), rs[y, (x + 1) % 2], atol=1e-9)
+            assert np.allclose(np.einsum("pqrq->pr", v), rs[y, x], atol=1e-9)
+            assert np.allclose(np.einsum("pqpr->qr", v), rs[(y + 1) % 2, x], atol=1e-9)
+            herm = rs[y, x]
+            assert np.allclose(herm, herm.conj().T, atol=1e-13)
+            assert np.min(np.linalg.eigvalsh(herm)) > -1e-12
+
+
 def test_untruncated_column_absorption_equals_bruteforce_patch():
     """2x2 cell, four tensors: absorbing column 0 without truncation gives the
     environment of the patch one column wider (bond (1,0)-(2,0))."""
