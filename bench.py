@@ -463,7 +463,7 @@ def run_scan(args, rank, world, local_rank):
 
 
 def run_cylinder(args, rank, world, local_rank):
-    """Config-5 readout: environment at D=6 chi=144, boundary spectrum and
+    """Long-cylinder readout: environment at D=6 chi=144, boundary spectrum and
     entanglement entropy on cylinders of Nv = 2, 4 (dense) and 6 (Lanczos)."""
     import torch
     import synth

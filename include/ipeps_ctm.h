@@ -159,6 +159,14 @@ ipeps_status ipeps_ctm_converge(ipeps_ctm h, double tol, int max_sweeps, int* sw
  * rows (p_first, p_second) ket, columns the bra pair.  Either may be NULL. */
 ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v);
 
+/* One-site RDMs normalised to trace one (Sec. II.C: the site's physical legs
+ * left open inside its 3x3 window C1 T1 C2 / T4 . T2 / C4 T3 C3 of Fig. 3b).
+ * rho_s: [Ly][Lx][d][d] complex (interleaved doubles), rows ket, columns bra,
+ * caller-owned.  At a converged environment these equal the partial traces
+ * of the bond RDMs up to the truncation error.  Errors: EINVAL (null
+ * argument), ENOMEM (scratch), ECUDA, ENUMERIC. */
+ipeps_status ipeps_rdm_site(ipeps_ctm h, double* rho_s);
+
 /* Energy per spin of the ruby model H_R = -sum_a J_a sum s^a s^a (Eq. H-KR)
  * in the block-site form of App. A (2x2 cell, d = 8): J = {Jx, Jy, Jz}. */
 ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e_per_spin);

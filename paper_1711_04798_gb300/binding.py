@@ -25,7 +25,7 @@ EXPORTS = [
     "ipeps_batch_tuning_size", "ipeps_batch_tuning_entry", "ipeps_batch_launch_count",
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
     "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile", "ipeps_ctm_env_set",
-    "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info",
+    "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info", "ipeps_rdm_site",
 ]
 
 
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_ctm_spectra.argtypes = [P, C.POINTER(D)]
     lib.ipeps_ctm_converge.argtypes = [P, D, I, C.POINTER(I), C.POINTER(D)]
     lib.ipeps_rdm.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_rdm_site.argtypes = [P, C.POINTER(D)]
     lib.ipeps_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_kappa.argtypes = [P, C.POINTER(D)]
     lib.ipeps_fidelity.argtypes = [P, P, P, C.POINTER(D), C.POINTER(D)]
@@ -294,6 +295,12 @@ class CTM:
         rv = np.zeros_like(rh)
         _check(self.lib.ipeps_rdm(self.h, _dptr(rh.view(np.float64)), _dptr(rv.view(np.float64))))
         return {"h": rh, "v": rv}
+
+    def site_rdms(self) -> np.ndarray:
+        """One-site RDMs [Ly, Lx, d, d] (rows ket), trace one."""
+        out = np.zeros((self.Ly, self.Lx, self.d, self.d), dtype=np.complex128)
+        _check(self.lib.ipeps_rdm_site(self.h, _dptr(out.view(np.float64))))
+        return out
 
     def energy(self, J) -> float:
         Jv = np.asarray(J, dtype=np.float64)

@@ -1483,19 +1483,14 @@ extern "C" ipeps_status ipeps_ctm_converge(ipeps_ctm h, double tol, int max_swee
 // ---------------------------------------------------------------------------
 // RDMs and energy (frame f horizontal bond (x,y)-(x+1,y))
 // ---------------------------------------------------------------------------
-static ipeps_status rdm_horizontal(ipeps_ctm h, int f, int x, int y, cplx* rho) {
+// Left half of the window of site (x,y) in frame f, its physical legs open:
+// C1 T1 / T4 [A, A*] / C4 T3 contracted into left[h, r, s, k, p, q] with h
+// T1's right leg, (r, s) the site's right double leg (ket, bra), k T3's right
+// leg and (p, q) the physical (ket, bra) pair.  L2, L3, L4, small are work.
+static ipeps_status rdm_left_half(ipeps_ctm h, int f, int x, int y, cplx* L2, cplx* L3, cplx* L4, cplx* small,
+                                  cplx* left) {
   const int c = h->chi, D = h->D, d = h->d;
   const cplx* Aa = h->A[f][tensor_id(h, f, x, y)];
-  const cplx* Ab = h->A[f][tensor_id(h, f, x + 1, y)];
-  const long long big = (long long)c * c * D * D * D * D * d;
-  cplx* L2 = scratch_alloc(h, (long long)c * c * D * D * D * D);
-  cplx* L3 = scratch_alloc(h, big);
-  cplx* L4 = scratch_alloc(h, big);
-  cplx* left = scratch_alloc(h, (long long)c * c * D * D * d * d);
-  cplx* right = scratch_alloc(h, (long long)c * c * D * D * d * d);
-  cplx* small = scratch_alloc(h, (long long)c * c * D * D);
-  if (!L2 || !L3 || !L4 || !left || !right || !small) return fail(IPEPS_ENOMEM, "scratch exhausted (rdm)");
-  // left half
   CKS(contract(h, "ab,bUVh->aUVh", tv(envC(h, f, 0, x, y), {c, c}), false,
                tv(envT(h, f, 0, x, y), {c, D, D, c}), false, tv(small, {c, D, D, c})));
   CKS(contract(h, "eLMa,aUVh->eLMUVh", tv(envT(h, f, 3, x, y), {c, D, D, c}), false,
@@ -1508,6 +1503,21 @@ static ipeps_status rdm_horizontal(ipeps_ctm h, int f, int x, int y, cplx* rho) 
                tv(small, {c, c, D, D}), false, tv(L4, {D, D, c, d, D, c, D})));
   CKS(contract(h, "MVhprkT,qVMTs->hrskpq", tv(L4, {D, D, c, d, D, c, D}), false,
                tv((cplx*)Aa, {d, D, D, D, D}), true, tv(left, {c, D, D, c, d, d})));
+  return IPEPS_OK;
+}
+
+static ipeps_status rdm_horizontal(ipeps_ctm h, int f, int x, int y, cplx* rho) {
+  const int c = h->chi, D = h->D, d = h->d;
+  const cplx* Ab = h->A[f][tensor_id(h, f, x + 1, y)];
+  const long long big = (long long)c * c * D * D * D * D * d;
+  cplx* L2 = scratch_alloc(h, (long long)c * c * D * D * D * D);
+  cplx* L3 = scratch_alloc(h, big);
+  cplx* L4 = scratch_alloc(h, big);
+  cplx* left = scratch_alloc(h, (long long)c * c * D * D * d * d);
+  cplx* right = scratch_alloc(h, (long long)c * c * D * D * d * d);
+  cplx* small = scratch_alloc(h, (long long)c * c * D * D);
+  if (!L2 || !L3 || !L4 || !left || !right || !small) return fail(IPEPS_ENOMEM, "scratch exhausted (rdm)");
+  CKS(rdm_left_half(h, f, x, y, L2, L3, L4, small, left));
   // right half
   CKS(contract(h, "hUVc,cf->hUVf", tv(envT(h, f, 0, x + 1, y), {c, D, D, c}), false,
                tv(envC(h, f, 1, x + 1, y), {c, c}), false, tv(small, {c, D, D, c})));
@@ -1526,6 +1536,49 @@ static ipeps_status rdm_horizontal(ipeps_ctm h, int f, int x, int y, cplx* rho) 
   CK(trace_normalize(h->stream, rho, d * d, h->dwork));
   h->scratch_top = 0;
   return IPEPS_OK;
+}
+
+// One-site RDM at (x,y) (frame 0): the left half closed by the site's own
+// right column C2 T2 C3 (col[h, r, s, k]).
+static ipeps_status rdm_site(ipeps_ctm h, int x, int y, cplx* rho) {
+  const int c = h->chi, D = h->D, d = h->d;
+  const long long big = (long long)c * c * D * D * D * D * d;
+  cplx* L2 = scratch_alloc(h, (long long)c * c * D * D * D * D);
+  cplx* L3 = scratch_alloc(h, big);
+  cplx* L4 = scratch_alloc(h, big);
+  cplx* left = scratch_alloc(h, (long long)c * c * D * D * d * d);
+  cplx* small = scratch_alloc(h, (long long)c * c * D * D);
+  cplx* col = scratch_alloc(h, (long long)c * c * D * D);
+  if (!L2 || !L3 || !L4 || !left || !small || !col) return fail(IPEPS_ENOMEM, "scratch exhausted (site rdm)");
+  CKS(rdm_left_half(h, 0, x, y, L2, L3, L4, small, left));
+  CKS(contract(h, "hf,fRSg->hRSg", tv(envC(h, 0, 1, x, y), {c, c}), false,
+               tv(envT(h, 0, 1, x, y), {c, D, D, c}), false, tv(small, {c, D, D, c})));
+  CKS(contract(h, "hRSg,gk->hRSk", tv(small, {c, D, D, c}), false, tv(envC(h, 0, 2, x, y), {c, c}), false,
+               tv(col, {c, D, D, c})));
+  CKS(contract(h, "hrskpq,hrsk->pq", tv(left, {c, D, D, c, d, d}), false, tv(col, {c, D, D, c}), false,
+               tv(rho, {d, d})));
+  CK(trace_normalize(h->stream, rho, d, h->dwork));
+  h->scratch_top = 0;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_rdm_site(ipeps_ctm h, double* rho_s) {
+  if (!h || !rho_s) return fail(IPEPS_EINVAL, "null argument");
+  CKS(reset_status(h));
+  const long long n1 = (long long)h->d * h->d;
+  const long long n = n1 * h->Lx * h->Ly;
+  // results at the top of the scratch arena, below them the per-site work
+  cplx* rs = h->scratch + h->scratch_elems - n;
+  const long long save = h->scratch_elems;
+  h->scratch_elems -= n;
+  ipeps_status st = IPEPS_OK;
+  for (int y = 0; y < h->Ly && st == IPEPS_OK; ++y)
+    for (int x = 0; x < h->Lx && st == IPEPS_OK; ++x) st = rdm_site(h, x, y, rs + (y * h->Lx + x) * n1);
+  h->scratch_elems = save;
+  CKS(st);
+  CK(cudaMemcpyAsync(rho_s, rs, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_status(h);
 }
 
 // all bond RDMs into device buffers rh, rv ([Ly][Lx][d^2][d^2] each)

@@ -1,7 +1,7 @@
 """Unit cells and sizes beyond the 2x2 four-tensor workloads: the paper's own
 A/B checkerboard of two tensors (Sec. II.B), rectangular 2x1 / 1x2 cells (the
 frame rotations with Lx != Ly), D = 1 product states against their closed
-forms, and the full config-3 size (D = 5, chi = 100) against the oracle."""
+forms, and the full D = 5, chi = 100 size against the oracle."""
 import numpy as np
 import pytest
 
@@ -78,7 +78,7 @@ def test_product_states_D1_closed_forms():
     g.close()
 
 
-def test_full_size_config3_one_sweep():
+def test_full_size_D5_chi100_one_sweep():
     """D = 5, chi = 100 (the bench's workload): one sweep from the trace
     initialisation, FP64 GPU path vs the oracle at 1e-10, and the BF16x3
     precision form within the 1e-6 energy target."""

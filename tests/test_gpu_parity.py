@@ -28,6 +28,11 @@ def _compare_rdms(g, st, w, tol=TOL):
         assert rel_err(r_gpu[key], r_ref[key]) < tol, key
 
 
+def _compare_site_rdms(g, st, w, tol=TOL):
+    r_ref = O.site_rdms(st, w["tensors"], w["pattern"])
+    assert rel_err(g.site_rdms(), r_ref) < tol
+
+
 def _compare_spectra(g, st, floor=1e-8, tol=1e-8):
     s_gpu = g.spectra()
     s_ref = O.corner_spectra(st)
@@ -66,11 +71,12 @@ def test_real_D2_chi16_twenty_sweeps_energy_rdms_spectra():
     e_gpu = g.energy(w["J"])
     assert abs(e_gpu - e_ref) < TOL * abs(e_ref)
     _compare_rdms(g, st, w)
+    _compare_site_rdms(g, st, w)
     _compare_spectra(g, st)
 
 
 def test_product_noise_D3_chi18_complex():
-    """Config-2 recipe (complex product state + 0.1 noise) at D=3, chi=18."""
+    """Complex product state + 0.1 noise, D=3, chi=18, 3 sweeps."""
     w = synth.workload("product_noise", seed=2, D=3, chi=18)
     g = gpu_ctm(w["tensors"], w["pattern"], 18)
     g.sweep(3)
@@ -78,7 +84,20 @@ def test_product_noise_D3_chi18_complex():
     e_ref = O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2)
     assert abs(g.energy(w["J"]) - e_ref) < TOL * abs(e_ref)
     _compare_rdms(g, st, w)
+    _compare_site_rdms(g, st, w)
     _compare_spectra(g, st)
+
+
+def test_site_rdms_at_trace_init_and_on_a_1x1_cell():
+    w = synth.workload("product_noise", seed=7, D=3, chi=9)
+    g = gpu_ctm(w["tensors"], w["pattern"], 9)
+    _compare_site_rdms(g, O.make_state(w["tensors"], w["pattern"], 3, 9), w)
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((2, 2, 2, 2, 2)) + 1j * rng.standard_normal((2, 2, 2, 2, 2))
+    w1 = {"tensors": [A / np.abs(A).max()], "pattern": [[0]], "D": 2}
+    g1 = gpu_ctm(w1["tensors"], w1["pattern"], 8)
+    g1.sweep(2)
+    _compare_site_rdms(g1, _oracle_run(w1, 8, ["sweep"] * 2), w1)
 
 
 def test_ising_onsager_on_gpu():

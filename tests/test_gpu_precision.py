@@ -28,3 +28,7 @@ def test_precision_form_energy_error(prec):
     e = g.energy(w["J"])
     print(f"{prec}: E = {e:.12f}, oracle {e_ref:.12f}, |dE| = {abs(e - e_ref):.3e}")
     assert abs(e - e_ref) < BOUND[prec]
+    # one-site RDMs: entries of size <= 1, errors of the energy's order
+    err = np.max(np.abs(g.site_rdms() - O.site_rdms(st, w["tensors"], w["pattern"])))
+    print(f"{prec}: site RDM max |d rho| = {err:.3e}")
+    assert err < 10 * BOUND[prec]

@@ -132,6 +132,7 @@ def test_null_handles_are_rejected(lib):
         lambda: lib.ipeps_ctm_spectra(None, buf),
         lambda: lib.ipeps_ctm_converge(None, 1e-10, 5, ctypes.byref(i), buf),
         lambda: lib.ipeps_rdm(None, buf, buf),
+        lambda: lib.ipeps_rdm_site(None, buf),
         lambda: lib.ipeps_energy(None, J, buf),
         lambda: lib.ipeps_kappa(None, buf),
         lambda: lib.ipeps_fidelity(None, None, None, buf, buf),
