@@ -776,7 +776,12 @@ static ipeps_status check_status(ipeps_ctm h) {
   return IPEPS_OK;
 }
 
+// Called where every operation starts.  The scratch arenas are bump-allocated
+// per operation: an operation that failed part way may have left its
+// allocations in place, so they are released here as well.
 static ipeps_status reset_status(ipeps_ctm h) {
+  h->scratch_top = 0;
+  h->alt.scratch_top = 0;
   CK(cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream));
   return IPEPS_OK;
 }
