@@ -62,6 +62,12 @@ class CTMOptions:
     ``proj``: ``"svd"`` = exact truncated SVD of X (LAPACK), ``"rsvd"`` = the
     randomized range finder with subspace iteration (Halko, Martinsson & Tropp
     2011, Alg. 4.4 + 5.1) using the fixed test matrix ``omega``.
+
+    ``ties`` collects every cut where the chi-th and (chi+1)-th singular values
+    agree to a relative ``tie_tol``: the truncation then splits a multiplet,
+    the kept subspace is not unique, and the environment (and every readout
+    after it) depends on rounding, so a run that records a tie is not a parity
+    reference at that chi.  Recording changes nothing in the arithmetic.
     """
 
     chi: int
@@ -71,6 +77,8 @@ class CTMOptions:
     cutoff: float = 1e-8
     orth_tol: float = 1e-14
     omega: np.ndarray | None = None
+    tie_tol: float = 1e-10
+    ties: list = field(default_factory=list)  # (chi, s_chi, s_chi+1) per tied cut
 
 
 @dataclass
@@ -289,6 +297,8 @@ def projectors(Q1, Q2, Q3, Q4, opt: CTMOptions):
     keep = 0
     if s.size and s[0] > 0:
         keep = int(min(chi, np.count_nonzero(s > opt.cutoff * s[0])))
+    if keep == chi and s.size > chi and s[chi] > opt.cutoff * s[0] and s[chi - 1] - s[chi] <= opt.tie_tol * s[chi]:
+        opt.ties.append((chi, float(s[chi - 1]), float(s[chi])))
     P = np.zeros((N, chi), dtype=np.complex128)
     Pt = np.zeros((chi, N), dtype=np.complex128)
     if keep:

@@ -476,6 +476,46 @@ def test_c4v_symmetric_tensor_gives_symmetric_environment():
 # Projectors: the randomized range finder is exact once it spans everything,
 # and converges to the exact truncated SVD with more subspace iterations.
 # ---------------------------------------------------------------------------
+def _ring_with_spectrum(s, seed=0):
+    """Corners with Q2 = Q3 = Q4 = 1, so the ring X = Q1^T has singular values s."""
+    rng = np.random.default_rng(seed)
+    n = len(s)
+    U, V = random_unitary(rng, n), random_unitary(rng, n)
+    X = (U * np.asarray(s)[None, :]) @ V.conj().T
+    eye = np.eye(n, dtype=np.complex128)
+    return X.T, eye, eye, eye
+
+
+@pytest.mark.parametrize("proj", ["svd", "rsvd"])
+def test_split_multiplet_at_the_cut_is_recorded(proj):
+    s = [1.0, 0.5, 0.3, 0.3, 0.1, 0.05]
+    Q = _ring_with_spectrum(s)
+
+    def run(chi, cutoff):
+        opt = O.CTMOptions(chi=chi, proj=proj, oversample=4, cutoff=cutoff,
+                           omega=synth.omega(3, 6, chi + 4))
+        P, Pt, sv = O.projectors(*Q, opt)
+        assert np.allclose(sv[:len(s)], s, atol=1e-12)
+        return opt.ties
+
+    ties = run(3, 1e-8)  # k = chi + 4 >= 6: full span, exact values  # cut between the two 0.3's
+    assert len(ties) == 1 and ties[0][0] == 3 and abs(ties[0][1] - 0.3) < 1e-12
+    assert run(2, 1e-8) == []  # 0.5 | 0.3: distinct
+    assert run(4, 1e-8) == []  # 0.3 | 0.1: distinct
+    assert run(3, 0.35) == []  # truncated by the cutoff (keep 2), not by chi
+
+
+def test_random_parity_recipes_record_no_ties():
+    for w, chi in ((synth.workload("real", seed=0), 16),
+                   (synth.workload("product_noise", seed=2, D=2, chi=12), 12)):
+        D = w["D"]
+        opt = O.CTMOptions(chi=chi, omega=synth.omega(7, chi * D * D, chi + 16))
+        st = O.make_state(w["tensors"], w["pattern"], D, chi)
+        for _ in range(3):
+            st = O.sweep(st, opt)
+        assert opt.ties == []
+
+
 def test_rsvd_full_span_equals_svd():
     ts = random_tensors(13, 4, 8, 2)
     pat = [[0, 1], [2, 3]]
