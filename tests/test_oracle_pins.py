@@ -188,6 +188,29 @@ def test_ising_free_energy_and_bond_correlation(beta):
         assert abs(corr - onsager_nn_corr(beta)) < 1e-9
 
 
+@pytest.mark.parametrize("beta", [0.5, 0.6])
+def test_ising_spontaneous_magnetisation_from_spin_up_boundary(beta):
+    """Ordered phase (beta > beta_c = ln(1 + sqrt 2) / 2): an environment
+    started from spin-up boundary sites (the user-supplied initial environment)
+    converges to the + phase, whose one-site RDM gives Yang's (1952)
+    M = (1 - sinh(2 beta)^-4)^(1/8); the symmetric trace initialisation keeps
+    the Z2 symmetry and gives M = 0."""
+    A = ising_tensor(beta)
+    A_up = A.copy()
+    A_up[1] = 0.0  # boundary sites fixed to s = +1
+    opt = O.CTMOptions(chi=16, proj="svd", cutoff=1e-12)
+    st = O.make_state([A], [[0]], 2, 16)
+    st.C, st.T = O.trace_init([[O.double_layer(A_up)]], 2, 16)
+    st, _, _ = O.ctm_converge(st, opt, 1e-10, 200)
+    rho = O.site_rdms(st, [A], [[0]])[0, 0]
+    M = np.real(rho[0, 0] - rho[1, 1])
+    assert abs(M - (1.0 - np.sinh(2 * beta) ** -4) ** 0.125) < 1e-9
+    st0, _, _ = O.ctm_converge(O.make_state([A], [[0]], 2, 16), opt, 1e-10, 200)
+    rho0 = O.site_rdms(st0, [A], [[0]])[0, 0]
+    assert abs(np.real(rho0[0, 0] - rho0[1, 1])) < 1e-6
+    assert opt.ties == []
+
+
 def test_ising_fidelity_closed_form():
     """Overlap of Ising PEPS at b1 and b2 is the Ising model at (b1+b2)/2, so
     d = Z((b1+b2)/2) / sqrt(Z(b1) Z(b2)) per site (Sec. III with Onsager)."""
