@@ -19,6 +19,7 @@ __all__ = [
     "site_rdms",
     "pauli_block_ops",
     "ruby_bond_hamiltonians",
+    "xyz_all_edges_bond_hamiltonians",
     "energy_per_spin",
     "site_type",
     "partition_ratios",
@@ -199,9 +200,40 @@ def ruby_bond_hamiltonians(J):
     return {"H_r": H_r, "H_l": H_l, "H_u": H_v, "H_d": H_v.copy(), "h_site": h_site}
 
 
-def energy_per_spin(rdms, J, Lx: int, Ly: int) -> float:
-    """(1/(3 Lx Ly)) * sum over the cell's 2 Lx Ly bonds of Re tr(rho_b H_b)."""
-    H = ruby_bond_hamiltonians(J)
+def xyz_all_edges_bond_hamiltonians(J):
+    """Bond operators of the literal reading -sum_edges (Jx xx + Jy yy + Jz zz):
+    the links of ``ruby_bond_hamiltonians`` (triangle edges inside a block
+    site, spin 1-1 and 3-3 across a horizontal A-B bond, upper 3 - lower 2 and
+    upper 2 - lower 1 across a vertical bond), each carrying all three terms
+    instead of its own colour's."""
+    Jx, Jy, Jz = J
+    o = pauli_block_ops()
+    I8 = np.eye(8, dtype=np.complex128)
+
+    def link_in(a, b):
+        return -sum(Jc * o[f"{al}{a}"] @ o[f"{al}{b}"] for al, Jc in (("x", Jx), ("y", Jy), ("z", Jz)))
+
+    def link_across(a, b):
+        return -sum(Jc * np.kron(o[f"{al}{a}"], o[f"{al}{b}"]) for al, Jc in (("x", Jx), ("y", Jy), ("z", Jz)))
+
+    h_site = link_in(1, 2) + link_in(1, 3) + link_in(2, 3)
+    H_r = link_across(1, 1) + link_across(3, 3)
+    H_l = np.zeros((64, 64), dtype=np.complex128)
+    H_v = 0.5 * (np.kron(h_site, I8) + np.kron(I8, h_site)) + link_across(3, 2) + link_across(2, 1)
+    return {"H_r": H_r, "H_l": H_l, "H_u": H_v, "H_d": H_v.copy(), "h_site": h_site}
+
+
+def energy_per_spin(rdms, J, Lx: int, Ly: int, model: str = "ruby") -> float:
+    """(1/(3 Lx Ly)) * sum over the cell's 2 Lx Ly bonds of Re tr(rho_b H_b).
+
+    model: "ruby" (each link its own colour's term, Eq. H-KR) or
+    "xyz_all_edges" (every link all three terms, for comparison)."""
+    if model == "ruby":
+        H = ruby_bond_hamiltonians(J)
+    elif model == "xyz_all_edges":
+        H = xyz_all_edges_bond_hamiltonians(J)
+    else:
+        raise ValueError(model)
     e = 0.0
     for y in range(Ly):
         for x in range(Lx):

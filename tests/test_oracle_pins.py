@@ -304,6 +304,33 @@ def test_product_state_rdm_and_energy_closed_form():
     assert abs(e - e_exact) < 1e-13
 
 
+def test_xyz_all_edges_reading_product_states():
+    """The literal all-edges reading: every ruby link carries all three terms;
+    checked on D=1 product states against the independent link list."""
+    phis, ts = product_tensors(4)
+    pat = [[0, 1], [2, 3]]
+    J = (0.7, 1.3, 0.9)
+    st = O.sweep(O.make_state(ts, pat, 1, 2), O.CTMOptions(chi=2, proj="svd"))
+    r = O.bond_rdms(st, ts, pat)
+    site_phi = {(x, y): phis[pat[y][x]] for x in range(2) for y in range(2)}
+
+    def term(s1, k1, s2, k2, al):
+        if s1 == s2:
+            return pair_expect(site_phi[s1], k1, k2, al)
+        return spin_expect(site_phi[s1], k1, al) * spin_expect(site_phi[s2], k2, al)
+
+    Jd = {"x": J[0], "y": J[1], "z": J[2]}
+    e_exact = sum(-Jd[al] * term(l[0], l[1], l[2], l[3], al) for l in ruby_links() for al in "xyz") / 12
+    assert abs(O.energy_per_spin(r, J, 2, 2, model="xyz_all_edges") - e_exact) < 1e-13
+    # all spins up: every one of the 24 links gives <zz> = 1
+    A = np.zeros((8, 1, 1, 1, 1))
+    A[0] = 1.0
+    st = O.sweep(O.make_state([A] * 4, pat, 1, 1), O.CTMOptions(chi=1, proj="svd"))
+    r = O.bond_rdms(st, [A] * 4, pat)
+    assert abs(O.energy_per_spin(r, (0.3, 0.4, 0.37), 2, 2, model="xyz_all_edges") + 2 * 0.37) < 1e-14
+    assert abs(O.energy_per_spin(r, (0.3, 0.4, 0.37), 2, 2) + 0.37) < 1e-14
+
+
 def test_all_up_energy_is_minus_Jz():
     d = 8
     A = np.zeros((d, 1, 1, 1, 1))
@@ -650,8 +677,9 @@ def test_topk_product_state_single_eigenvalue():
     assert np.allclose(lam, [1.0]) and abs(S) < 1e-15 and abs(rest) < 1e-14
 
 
-def test_hamiltonian_terms_hermitian_and_trivial_bond():
-    H = O.ruby_bond_hamiltonians((0.3, 0.5, 0.7))
+@pytest.mark.parametrize("build", ["ruby_bond_hamiltonians", "xyz_all_edges_bond_hamiltonians"])
+def test_hamiltonian_terms_hermitian_and_trivial_bond(build):
+    H = getattr(O, build)((0.3, 0.5, 0.7))
     for k in ("H_r", "H_u", "H_d"):
         assert np.allclose(H[k], H[k].conj().T)
     assert not np.any(H["H_l"])
