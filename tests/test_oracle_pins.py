@@ -566,6 +566,23 @@ def test_random_parity_recipes_record_no_ties():
         assert opt.ties == []
 
 
+def test_energy_converges_with_chi():
+    """chi-convergence (reported): on the real iid workload the energy's
+    distance to its chi = 24 value shrinks monotonically with chi."""
+    w = synth.workload("real", seed=0)
+    es = {}
+    for chi in (4, 8, 16, 24):
+        opt = O.CTMOptions(chi=chi, proj="svd", cutoff=1e-12)
+        st = O.make_state(w["tensors"], w["pattern"], 2, chi)
+        for _ in range(20):
+            st = O.sweep(st, opt)
+        es[chi] = O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2)
+    gaps = [abs(es[c] - es[24]) for c in (4, 8, 16)]
+    print("E(chi):", es, "gaps to chi=24:", gaps)
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 1e-9
+
+
 def test_rsvd_full_span_equals_svd():
     ts = random_tensors(13, 4, 8, 2)
     pat = [[0, 1], [2, 3]]
