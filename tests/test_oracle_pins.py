@@ -498,6 +498,39 @@ def test_unitary_gauge_invariance():
     assert abs(res[0][2] - res[1][2]) < 1e-12
 
 
+def test_invertible_gauge_energy_gap_shrinks_with_chi():
+    """Random invertible (non-unitary) gauges on every bond leave the state
+    unchanged but not the truncation: the energies of the two networks agree
+    only up to a truncation error that shrinks as chi grows (reported)."""
+    w = synth.workload("real", seed=0)
+    ts, pat = w["tensors"], w["pattern"]
+    rng = np.random.default_rng(5)
+    g = [t.copy() for t in ts]
+    for y in range(2):
+        for x in range(2):
+            G = np.eye(2) + 0.3 * rng.standard_normal((2, 2))
+            L, R = pat[y][x], pat[y][(x + 1) % 2]
+            g[L] = np.einsum("puldr,rs->pulds", g[L], G)
+            g[R] = np.einsum("sl,puldr->pusdr", np.linalg.inv(G), g[R])
+            G = np.eye(2) + 0.3 * rng.standard_normal((2, 2))
+            T_, B_ = pat[y][x], pat[(y + 1) % 2][x]
+            g[T_] = np.einsum("puldr,ds->pulsr", g[T_], G)
+            g[B_] = np.einsum("su,puldr->psldr", np.linalg.inv(G), g[B_])
+    gaps = []
+    for chi in (4, 8, 16):
+        es = []
+        for tens in (ts, g):
+            opt = O.CTMOptions(chi=chi, proj="svd", cutoff=1e-12)
+            st = O.make_state(tens, pat, 2, chi)
+            for _ in range(20):
+                st = O.sweep(st, opt)
+            es.append(O.energy_per_spin(O.bond_rdms(st, tens, pat), w["J"], 2, 2))
+        gaps.append(abs(es[0] - es[1]))
+    print("invertible-gauge energy gaps at chi = 4, 8, 16:", gaps)
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 1e-9
+
+
 def c4v_symmetrize(A):
     rot = lambda t: np.transpose(t, (0, 4, 1, 2, 3))       # (u,l,d,r) -> (r,u,l,d)
     ref = lambda t: np.transpose(t, (0, 1, 4, 3, 2))       # swap l <-> r
