@@ -680,6 +680,46 @@ def test_ring_sigma_at_trace_init_is_column_of_sites():
     assert np.allclose(sR / np.linalg.norm(sR), ref / np.linalg.norm(ref), atol=1e-13)
 
 
+def _exact_cylinder_spectrum(A):
+    """Boundary spectrum of the exact infinite cylinder of circumference 2:
+    sigma_L, sigma_R = left / right fixed points of the column transfer matrix
+    E[(l0 l1), (r0 r1)] = sum_{u, c} a[u,l0,c,r0] a[c,l1,u,r1] (periodic
+    vertical bonds), each reshaped to a (ket..., bra...) operator, phase-fixed
+    to a positive trace and Hermitised; eigenvalues of sigma_L^T sigma_R / tr."""
+    D = A.shape[1]
+    a = O.double_layer(A)
+    E = np.einsum("alcr,cmas->lmrs", a, a).reshape(D ** 4, D ** 4)
+    ops = []
+    for M in (E.T, E):  # left fixed point: eigenvector of E^T
+        w, V = np.linalg.eig(M)
+        v = V[:, np.argmax(np.abs(w))].reshape(D, D, D, D)  # k0 b0 k1 b1
+        m = np.transpose(v, (0, 2, 1, 3)).reshape(D * D, D * D)
+        m = m * np.exp(-1j * np.angle(np.trace(m)))
+        ops.append(0.5 * (m + m.conj().T))
+    sL, sR = ops
+    M = sL.T @ sR
+    return np.sort(np.real(np.linalg.eigvals(M)))[::-1] / np.real(np.trace(M))
+
+
+@pytest.mark.parametrize("case", ["ising_0.3", "random_complex"])
+def test_ctm_ring_approximates_the_exact_cylinder(case):
+    """Sec. IV approximates the cylinder's boundary operators by rings of the
+    converged half-plane edge tensors; on a circumference-2 cylinder the
+    exact ones come from the column transfer matrix.  Sanity tolerances: the
+    approximation is close where the correlation length is short."""
+    A = ising_tensor(0.3) if case == "ising_0.3" else random_tensors(4, 1, 2, 2)[0]
+    lam_x = _exact_cylinder_spectrum(A)
+    st = O.make_state([A], [[0]], 2, 16)
+    st, _, _ = O.ctm_converge(st, O.CTMOptions(chi=16, proj="svd", cutoff=1e-12), 1e-10, 200)
+    lam_c = O.boundary_spectrum(st, 0, 2)
+    S_x, S_c = O.entropy(lam_x[lam_x > 0]), O.entropy(lam_c)
+    print(case, "exact", lam_x, "ring", lam_c, "S", S_x, S_c)
+    if case == "ising_0.3":
+        assert np.max(np.abs(lam_c - lam_x)) < 1e-5 and abs(S_c - S_x) < 1e-4
+    else:
+        assert abs(S_c - S_x) < 0.02 * S_x
+
+
 def test_product_state_boundary_entropy_is_zero():
     _, ts = product_tensors(15)
     pat = [[0, 1], [2, 3]]
