@@ -103,37 +103,59 @@ typedef struct {
   size_t workspace_bytes;           /* its size; see ipeps_ctm_workspace_size      */
 } ipeps_options;
 
-/* Fill *opt with the defaults: prec FP64, oversample 16, power 2, cutoff 0 (automatic),
- * orth_tol 1e-14, omega_seed 7, jacobi_max_sweeps 40, NULL stream/workspace.
- * chi is set to 0 and must be chosen by the caller. */
+/* Fill *opt (caller-owned) with the defaults: prec FP64, oversample 16,
+ * power 2, cutoff 0 (automatic), orth_tol 1e-14, omega_seed 7,
+ * jacobi_max_sweeps 40, NULL stream/workspace.  chi is set to 0 and must be
+ * chosen by the caller.  The projector choices are the readings of the CTM
+ * the paper cites in Sec. II.C (it prints none).  No effect if opt is NULL. */
 void ipeps_default_options(ipeps_options* opt);
 
-/* Device bytes a handle with this cell/options needs (workspace sizing). */
+/* Device bytes a handle with this cell/options needs, for sizing a
+ * caller-owned workspace (ipeps_options.workspace).  Host only: no CUDA call.
+ * *bytes is written (caller-owned).  Errors: EINVAL (the checks of
+ * ipeps_ctm_create on cell and options, or bytes NULL). */
 ipeps_status ipeps_ctm_workspace_size(const ipeps_cell* cell, const ipeps_options* opt,
                                       size_t* bytes);
 
 /* Copy the tensors to the device, build every double-layer tensor (Fig. 3a;
  * the mixed e of Sec. III when tensors_bra is given), and initialise the
  * environment by tracing the outer legs of the neighbouring sites ket against
- * bra.  EINVAL if chi < D*D, Lx/Ly not in {1,2}, ids out of range. */
+ * bra (Sec. II.C, environment of Fig. 3b).  The host tensors are copied and
+ * may be freed on return; *out is a new handle owned by the caller (release
+ * it with ipeps_ctm_destroy).  Errors: EINVAL (cell or options out of range:
+ * Lx/Ly not in {1,2}, n_tensors not 1..4, pattern ids out of range, d not
+ * 1..64, D not 1..12, chi < D*D or chi + oversample > 1024, bad dtype or
+ * prec, NULL pointers), ENOMEM (device allocation failed or the caller's
+ * workspace is smaller than ipeps_ctm_workspace_size), ECUDA, ENUMERIC (a
+ * zero-norm initial environment tensor); *out is left unset on error. */
 ipeps_status ipeps_ctm_create(const ipeps_cell* cell, const ipeps_options* opt, ipeps_ctm* out);
 
 /* Replace the site tensors (same shapes) and rebuild the double layers; the
  * environment is kept, as when an update step reuses it (Sec. II.C).  With
  * tensors == NULL the double layers are rebuilt from the tensors already on
- * the device (no copy; the call does not wait for the device). */
+ * the device (no copy; the call does not wait for the device).  Host tensors
+ * are copied (caller-owned).  Errors: EINVAL (NULL handle; tensors_bra given
+ * or omitted unlike at create), ECUDA. */
 ipeps_status ipeps_ctm_set_tensors(ipeps_ctm h, const void* const* tensors,
                                    const void* const* tensors_bra);
 
-/* Re-run the trace initialisation of the environment. */
+/* Re-run the trace initialisation of the environment (as at create).
+ * Errors: EINVAL (NULL handle), ECUDA, ENUMERIC (a zero-norm tensor). */
 ipeps_status ipeps_ctm_reset_env(ipeps_ctm h);
 
 /* Apply `count` moves in direction dir (ipeps_dir).  Each move computes the
  * enlarged corners, the projectors of every cut and renormalises the
- * corners/edges of each column (row) of the cell in turn (Sec. II.C). */
+ * corners/edges of each column (row) of the cell in turn (Sec. II.C, Fig. 3b:
+ * the environment is grown and truncated back to chi).  Returns when the
+ * moves are done.  Errors: EINVAL (NULL handle, dir outside 0..4, count < 0),
+ * ENOMEM (scratch), ECUDA, ETIMEOUT (a Jacobi SVD or a tensor-core wait ran
+ * out of its budget), ENUMERIC (NaN/Inf or a zero norm); after an error the
+ * environment is unspecified (ipeps_ctm_reset_env or ipeps_ctm_load restores
+ * a defined one). */
 ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count);
 
-/* Autotune the tensor-core products of this handle: one sweep is run with
+/* Implementation support (no paper counterpart).
+ * Autotune the tensor-core products of this handle: one sweep is run with
  * every product shape timed under each candidate tile choice (128 x 128 or
  * 128 x 256 output tiles, K splits) and the fastest recorded; later moves use
  * the recorded choices (results change only by rounding).  The environment is
@@ -144,19 +166,28 @@ ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count);
 ipeps_status ipeps_ctm_autotune(ipeps_ctm h);
 int ipeps_ctm_tuning_size(ipeps_ctm h);
 
-/* Singular values of every corner, divided by the largest: s_out is
- * [4][Ly][Lx][chi] doubles (C1..C4), caller-owned. */
+/* Singular values of every corner, divided by the largest (the corner
+ * spectra whose change measures the convergence of the environment, Sec.
+ * II.C): s_out is [4][Ly][Lx][chi] doubles (C1..C4), descending, zeros past
+ * the rank, caller-owned host memory.  Errors: EINVAL (NULL argument), ECUDA,
+ * ETIMEOUT (Jacobi budget). */
 ipeps_status ipeps_ctm_spectra(ipeps_ctm h, double* s_out);
 
 /* Sweep until max over corners of ||s/s_0 - s_old/s_old_0||_2 < tol or
- * max_sweeps is reached (ENOCONV).  sweeps/delta may be NULL. */
+ * max_sweeps is reached (Sec. II.C: moves repeated until the environment
+ * converges).  *sweeps = sweeps done, *delta = the last change (caller-owned,
+ * either may be NULL; both are written on ENOCONV too).  Errors: EINVAL (NULL
+ * handle), ENOCONV (max_sweeps reached, or max_sweeps <= 0), and any error of
+ * ipeps_ctm_move / ipeps_ctm_spectra. */
 ipeps_status ipeps_ctm_converge(ipeps_ctm h, double tol, int max_sweeps, int* sweeps,
                                 double* delta);
 
 /* Nearest-neighbour two-site RDMs normalised to trace one (paper Sec. II.C,
  * used for the correlators of Sec. VI).  rho_h: bonds (x,y)-(x+1,y), rho_v:
  * bonds (x,y)-(x,y+1), each [Ly][Lx][d*d][d*d] complex (interleaved doubles),
- * rows (p_first, p_second) ket, columns the bra pair.  Either may be NULL. */
+ * rows (p_first, p_second) ket, columns the bra pair; caller-owned host
+ * memory, either may be NULL.  Errors: EINVAL (NULL handle), ENOMEM
+ * (scratch), ECUDA, ENUMERIC (zero trace). */
 ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v);
 
 /* One-site RDMs normalised to trace one (Sec. II.C: the site's physical legs
@@ -168,18 +199,26 @@ ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v);
 ipeps_status ipeps_rdm_site(ipeps_ctm h, double* rho_s);
 
 /* Energy per spin of the ruby model H_R = -sum_a J_a sum s^a s^a (Eq. H-KR)
- * in the block-site form of App. A (2x2 cell, d = 8): J = {Jx, Jy, Jz}. */
+ * in the block-site form of App. A (2x2 cell, d = 8): J = {Jx, Jy, Jz}
+ * (host, read only), *e_per_spin written (caller-owned): the trace of every
+ * bond RDM with its bond operator, summed over the 8 bonds of the cell, / 12.
+ * Errors: EINVAL (NULL argument; not a 2x2 cell of d = 8 sites), ENOMEM,
+ * ECUDA, ENUMERIC. */
 ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e_per_spin);
 
 /* Partition-function ratio kappa = Z(window) Z(corners) / (Z(columns)
  * Z(rows)) of the 2x2 window of sites at (0,0), cell indices taken mod
  * (Lx, Ly) (Eq. "fidelity", Fig. 4): the weight of those four sites per unit
- * of infinite lattice.  kappa_out = {re, im}. */
+ * of infinite lattice.  kappa_out = {re, im} (2 caller-owned doubles).
+ * Errors: EINVAL (NULL argument), ENOMEM, ECUDA, ENUMERIC. */
 ipeps_status ipeps_kappa(ipeps_ctm h, double* kappa_out);
 
 /* Fidelity per block site d = |k12|^(1/4) / (|k11| |k22|)^(1/8) (the 2x2 window),
  * from a converged mixed-network handle h12 (tensors_bra set) and the two
- * converged plain handles (Sec. III); d_spin = d_block^(1/3). */
+ * converged plain handles (Sec. III, Eq. "fidelity"); d_spin = d_block^(1/3).
+ * Outputs are caller-owned doubles, either may be NULL.  Errors: EINVAL
+ * (NULL handle; the three cells differ in Lx, Ly), and any error of
+ * ipeps_kappa on the three handles. */
 ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double* d_block,
                             double* d_spin);
 
@@ -220,11 +259,16 @@ ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int
 ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int k, int max_iter, double tol,
                                      double* eig_out, int* n_conv, double* S_vn, double* rest);
 
-/* Copy one environment tensor to the host: role 0..3 = C1..C4 (chi*chi
- * complex), 4..7 = T1..T4 (chi*D*D*chi complex), at cell position (x,y). */
+/* Copy one environment tensor (Fig. 3b: the C and T of Sec. II.C) to the
+ * host: role 0..3 = C1..C4 (chi*chi complex), 4..7 = T1..T4 (chi*D*D*chi
+ * complex), at cell position (x,y); host_out is caller-owned, interleaved
+ * doubles, row-major in the leg order of the conventions above.  Errors:
+ * EINVAL (NULL argument, role outside 0..7, position outside the cell),
+ * ECUDA. */
 ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* host_out);
 
-/* Overwrite one environment tensor from the host, same role / position /
+/* Overwrite one environment tensor (Sec. II.C, Fig. 3b) from the host, same
+ * role / position /
  * layout as ipeps_ctm_env_get (complex128, interleaved re, im; C[a,b] chi*chi
  * and T[a,k,b] chi*D*D*chi row-major, the D*D leg fused ket*D + bra).  This is
  * the user-supplied initial environment (instead of the trace initialisation
@@ -235,6 +279,7 @@ ipeps_status ipeps_ctm_env_set(ipeps_ctm h, int role, int x, int y, const double
 
 /* Checkpoint and resume of the environment (the CTM state that moves
  * update; the site tensors and options are the caller's and are not stored).
+ * No paper counterpart: persistence of the state of Sec. II.C.
  *
  * File format (little-endian):
  *   bytes 0..7    "IPEPSENV"
@@ -260,15 +305,16 @@ ipeps_status ipeps_ctm_save(ipeps_ctm h, const char* path);
 ipeps_status ipeps_ctm_load(ipeps_ctm h, const char* path);
 
 /* Read and verify a checkpoint's header and checksum without a handle or a
- * GPU.  info (caller-owned, 11 ints): version, Lx, Ly, d, D, chi, n_tensors,
+ * GPU (no paper counterpart; see ipeps_ctm_save).  info (caller-owned, 11 ints): version, Lx, Ly, d, D, chi, n_tensors,
  * pattern[4].  Errors: EINVAL (null argument), EIO as ipeps_ctm_load. */
 ipeps_status ipeps_env_file_info(const char* path, int* info);
 
-/* Block until all work of the handle is done. */
+/* Block until all work of the handle is done (no paper counterpart).
+ * Errors: EINVAL (NULL handle), ECUDA (an earlier asynchronous failure). */
 ipeps_status ipeps_ctm_sync(ipeps_ctm h);
 
 /* Number of kernels this handle launched since create (a counter kept on
- * the host, for launch accounting). */
+ * the host, for launch accounting; no paper counterpart).  0 for NULL. */
 uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
 
 /* Kernel-class timing for roofline reports: with enable != 0 every
@@ -283,28 +329,36 @@ uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
  * operators; flops: the two ring products, 16 n^2 chi^2) and kind 4 (the
  * Lanczos iteration; "flops" holds its step count).  With two projector lanes the brackets of concurrent work
  * overlap, so class times can sum to more than the step.  Not a paper
- * operation: measurement support only. */
+ * operation: measurement support only.  The outputs of profile_read are
+ * caller-owned and may each be NULL.  Errors: EINVAL (NULL handle), ECUDA. */
 ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable);
 ipeps_status ipeps_ctm_profile_read(ipeps_ctm h, int kind, double* total_ms, uint64_t* launches,
                                     double* flops);
 
+/* Wait for the handle's work, then release everything it allocated (a
+ * caller's workspace stays the caller's).  NULL is a no-op. */
 void ipeps_ctm_destroy(ipeps_ctm h);
 
-/* Complex GEMM building block of every contraction, for unit tests: C = opA(A)
+/* Building block, no paper counterpart.
+ * Complex GEMM building block of every contraction, for unit tests: C = opA(A)
  * opB(B) with M x N output, complex interleaved doubles in host memory
  * (row-major; op 0 = N, 1 = T, 2 = conj, 3 = conj-transpose, so that opA(A)
  * is M x K and A is stored M x K for op 0/2 and K x M for op 1/3).  prec as
  * ipeps_prec: FP64 CUDA-core kernel or the tcgen05 TF32 / split-BF16 kernel
  * (with its operand packing and split-K reduction).  Allocates and frees its
- * own device buffers; synchronises the device. */
+ * own device buffers; synchronises the device.  A, B, C are caller-owned host
+ * arrays.  Errors: EINVAL (M, N or K <= 0, NULL pointer, prec or op out of
+ * range), ECUDA (including a failed device allocation), ETIMEOUT (a
+ * tensor-core wait ran out). */
 ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
                          double* C);
 
 /* As ipeps_zgemm for the tensor-core precisions, with the tile choice fixed
  * instead of the default: output tiles of 128 x bn real columns (bn = 128 or
  * 256) and `splits` K splits (reduced to the number of 128-byte k-blocks if
- * larger).  For unit tests of every choice the batch autotuner can make.
- * EINVAL for prec FP64 or a bad choice. */
+ * larger).  For unit tests of every choice the batch autotuner can make (no
+ * paper counterpart).  Host buffers as ipeps_zgemm.  Errors: EINVAL (prec
+ * FP64, bn not 128 or 256, splits < 1, or as ipeps_zgemm), ECUDA, ETIMEOUT. */
 ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K, const double* A, int opA,
                               const double* B, int opB, double* C);
 
@@ -360,8 +414,10 @@ ipeps_status ipeps_batch_create(int n, const ipeps_cell* cells, const ipeps_opti
  * instance's status (ETIMEOUT, ENUMERIC, ...), named in ipeps_last_error(). */
 ipeps_status ipeps_batch_move(ipeps_batch b, int dir, int count);
 
-/* Energy per spin of every instance (as ipeps_energy), J = n x {Jx, Jy, Jz},
- * e_out = n doubles; both caller-owned host arrays. */
+/* Energy per spin of every instance (as ipeps_energy, Eq. H-KR), J = n x
+ * {Jx, Jy, Jz}, e_out = n doubles; both caller-owned host arrays.  Errors:
+ * EINVAL (NULL argument), or the first failing instance's ipeps_energy
+ * status. */
 ipeps_status ipeps_batch_energy(ipeps_batch b, const double* J, double* e_out);
 
 /* Instance i as a handle for every single-instance readout (spectra, RDMs,
@@ -370,27 +426,34 @@ ipeps_status ipeps_batch_energy(ipeps_batch b, const double* J, double* e_out);
  * out of range. */
 ipeps_ctm ipeps_batch_instance(ipeps_batch b, int i);
 
-/* Autotuner table: number of product shapes tuned, and entry i as fields =
- * {prec, M, N, K, n-tile width, K splits} (M x N x K the complex product) and
- * us = {time of the chosen tile, time of the default choice} in microseconds. */
+/* Autotuner table (implementation support, no paper counterpart): number of
+ * product shapes tuned (0 for NULL), and entry i as fields = {prec, M, N, K,
+ * n-tile width, K splits} (M x N x K the complex product) and us = {time of
+ * the chosen tile, time of the default choice} in microseconds, both
+ * caller-owned.  Errors: EINVAL (NULL argument, i out of range). */
 int ipeps_batch_tuning_size(ipeps_batch b);
 ipeps_status ipeps_batch_tuning_entry(ipeps_batch b, int i, int fields[6], double us[2]);
 
 /* Kernels the batch launched since create (graph replays count every kernel
- * inside the graph). */
+ * inside the graph; launch accounting, no paper counterpart).  0 for NULL. */
 uint64_t ipeps_batch_launch_count(ipeps_batch b);
 
-/* Block until all work of the batch is done. */
+/* Block until all work of the batch is done.  Errors: EINVAL (NULL batch),
+ * ECUDA. */
 ipeps_status ipeps_batch_sync(ipeps_batch b);
 
 /* The batch's own stream (cudaStream_t, owned by the batch): the graph of
  * every batch move is launched on it, so events recorded on it before and
- * after ipeps_batch_move bracket the whole move on the device. */
+ * after ipeps_batch_move bracket the whole move on the device.  NULL for a
+ * NULL batch. */
 void* ipeps_batch_stream(ipeps_batch b);
 
+/* Wait for the batch's work, then release its graphs, streams, tuner and
+ * every instance handle.  NULL is a no-op. */
 void ipeps_batch_destroy(ipeps_batch b);
 
-/* Thread-local message of the last failed call ("" if none). */
+/* Thread-local message of the last failed call on this thread ("" if none);
+ * owned by the library, valid until the next failing call on this thread. */
 const char* ipeps_last_error(void);
 
 #ifdef __cplusplus

@@ -686,6 +686,7 @@ static void ruby_bonds(const double J[3], CM* Hr, CM* Hv) {
 // create / destroy
 // ---------------------------------------------------------------------------
 extern "C" void ipeps_default_options(ipeps_options* o) {
+  if (!o) return;
   memset(o, 0, sizeof *o);
   o->chi = 0;
   o->prec = IPEPS_PREC_FP64;
@@ -784,6 +785,20 @@ static ipeps_status reset_status(ipeps_ctm h) {
   h->alt.scratch_top = 0;
   CK(cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream));
   return IPEPS_OK;
+}
+
+// The second lane's stream and its fork/join events: each released if it was
+// created (creation can stop part way, leaving has_alt false).
+static void release_lane(ipeps_ctm h) {
+  if (h->alt.stream) {
+    cudaStreamSynchronize(h->alt.stream);
+    cudaStreamDestroy(h->alt.stream);
+    h->alt.stream = nullptr;
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->ev_fork = h->ev_join = nullptr;
+  h->has_alt = false;
 }
 
 extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_options* o, ipeps_ctm* out) {
@@ -903,6 +918,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   if (st == IPEPS_OK) st = trace_init_env(h);
   if (st == IPEPS_OK) st = check_status(h);
   if (st != IPEPS_OK) {
+    release_lane(h);
     if (h->own_mem) cudaFree(h->base);
     delete h;
     return st;
@@ -953,12 +969,7 @@ extern "C" void ipeps_ctm_destroy(ipeps_ctm h) {
     cudaEventDestroy(r.b);
   }
   for (auto e : h->pool) cudaEventDestroy(e);
-  if (h->has_alt) {
-    cudaStreamSynchronize(h->alt.stream);
-    cudaStreamDestroy(h->alt.stream);
-    cudaEventDestroy(h->ev_fork);
-    cudaEventDestroy(h->ev_join);
-  }
+  release_lane(h);
   if (h->own_tuner) tc_tuner_destroy(h->tuner);
   if (h->own_mem) cudaFree(h->base);
   delete h;
