@@ -63,6 +63,11 @@ class CTMOptions:
     randomized range finder with subspace iteration (Halko, Martinsson & Tropp
     2011, Alg. 4.4 + 5.1) using the fixed test matrix ``omega``.
 
+    ``corners``: 4 (default) builds the projectors from the full ring of the
+    four enlarged corners; 2 from the left half only, R_up = Q1 and R_dn = Q4
+    (the two-corner variant, about a third of the cost): untruncated both are
+    exact, truncated they differ by the truncation error.
+
     ``ties`` collects every cut where the chi-th and (chi+1)-th singular values
     agree to a relative ``tie_tol``: the truncation then splits a multiplet,
     the kept subspace is not unique, and the environment (and every readout
@@ -79,6 +84,7 @@ class CTMOptions:
     omega: np.ndarray | None = None
     tie_tol: float = 1e-10
     ties: list = field(default_factory=list)  # (chi, s_chi, s_chi+1) per tied cut
+    corners: int = 4  # 4: four-corner ring; 2: two-corner (left half) projectors
 
 
 @dataclass
@@ -290,7 +296,13 @@ def projectors(Q1, Q2, Q3, Q4, opt: CTMOptions):
         Pt = S^{-1/2} U^H R_up^T  (chi x N)   -> tensors below the cut
     so that R_up^T (P Pt) R_dn = U_chi S_chi V_chi^H.
     """
-    R_up, R_dn, X = ring_matrix_factors(Q1, Q2, Q3, Q4)
+    if opt.corners == 4:
+        R_up, R_dn, X = ring_matrix_factors(Q1, Q2, Q3, Q4)
+    elif opt.corners == 2:
+        R_up, R_dn = Q1, Q4
+        X = R_up.T @ R_dn
+    else:
+        raise ValueError(f"corners must be 4 or 2, not {opt.corners}")
     U, s, V = truncated_svd(X, opt)
     chi = opt.chi
     N = X.shape[0]

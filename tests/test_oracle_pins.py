@@ -448,12 +448,14 @@ def test_untruncated_column_absorption_equals_bruteforce_patch():
     assert np.allclose(rho, ref, atol=1e-9)
 
 
+@pytest.mark.parametrize("corners", [4, 2])
 @pytest.mark.parametrize("direction", ["L", "R", "U", "D"])
-def test_untruncated_move_equals_bruteforce_patch(direction):
-    """1x1 cell: one move in each direction widens the patch on that side."""
+def test_untruncated_move_equals_bruteforce_patch(direction, corners):
+    """1x1 cell: one move in each direction widens the patch on that side
+    (four-corner and two-corner projectors alike: untruncated, both exact)."""
     ts = random_tensors(9, 1, 4, 2)
     st = O.make_state(ts, [[0]], 2, 64)
-    st = O.move(st, direction, O.CTMOptions(chi=64, proj="svd", cutoff=1e-14))
+    st = O.move(st, direction, O.CTMOptions(chi=64, proj="svd", cutoff=1e-14, corners=corners))
     rho = O.rdm_horizontal(st, [[ts[0]]], 0, 0)
     xs = {"L": range(-2, 3), "R": range(-1, 4)}.get(direction, range(-1, 3))
     ys = {"U": range(-2, 2), "D": range(-1, 3)}.get(direction, range(-1, 2))
@@ -597,6 +599,27 @@ def test_random_parity_recipes_record_no_ties():
         for _ in range(3):
             st = O.sweep(st, opt)
         assert opt.ties == []
+
+
+def test_two_corner_projectors_approach_the_four_corner_energy():
+    """Truncated, the two-corner projectors see less of the environment; the
+    energy gap to the four-corner result shrinks as chi grows."""
+    w = synth.workload("real", seed=0)
+    gaps = []
+    for chi in (8, 16, 24):
+        es = []
+        for corners in (4, 2):
+            opt = O.CTMOptions(chi=chi, proj="svd", cutoff=1e-12, corners=corners)
+            st = O.make_state(w["tensors"], w["pattern"], 2, chi)
+            for _ in range(20):
+                st = O.sweep(st, opt)
+            es.append(O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2))
+        gaps.append(abs(es[0] - es[1]))
+    print("two- vs four-corner energy gaps at chi = 8, 16, 24:", gaps)
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 1e-9
+    with pytest.raises(ValueError):
+        O.projectors(*(np.eye(2),) * 4, O.CTMOptions(chi=1, proj="svd", corners=3))
 
 
 def test_energy_converges_with_chi():
