@@ -1,0 +1,108 @@
+"""A CPU model of the precision form's rounding error.
+
+The BF16x3 path splits every operand x into bf16 parts hi = bf16(x) and
+lo = bf16(x - hi), forms hi*hi + hi*lo + lo*hi and accumulates in FP32.  Here
+that arithmetic is emulated in numpy (bf16 by round-to-nearest-even on the top
+16 bits of an FP32 word, products summed in complex64 so the accumulation is
+FP32) and substituted into the oracle's pairwise contractions: the moves
+(enlarged corners, absorption, the ring matrix) and/or the readouts (RDM
+contractions), while orthonormalisation, SVDs and normalisation stay FP64 as
+on the GPU.  At the GPU precision test's workload (D = 3, chi = 18, six sweeps,
+cutoff 1e-8) the GPU measured |dE| = 1.1e-6 and a site-RDM error of 6.8e-6;
+the model gives errors of the same size, so those are the arithmetic's, and
+splits them: the environment carries most of the energy error, and the
+readout contractions alone already put ~2e-6 into RDM elements.  The oracle
+itself is unchanged (the substitution is undone after each run)."""
+import types
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.ctm as OC
+import oracle.readout as OR
+import synth
+from gpu_common import oracle_options
+
+
+def bf16(x):
+    """Round FP32 values to bfloat16 (nearest, ties to even), returned as FP32."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32)
+    u = (u + (((u >> 16) & 1) + 0x7FFF)) & np.uint32(0xFFFF0000)
+    return u.view(np.float32)
+
+
+def _split(a):
+    re, im = np.real(a).astype(np.float64), np.imag(a).astype(np.float64)
+    hr, hi = bf16(re.astype(np.float32)), bf16(im.astype(np.float32))
+    lr, li = bf16((re - hr).astype(np.float32)), bf16((im - hi).astype(np.float32))
+    return (hr + 1j * hi).astype(np.complex64), (lr + 1j * li).astype(np.complex64)
+
+
+def _bf16x3_einsum(spec, *ops, **kw):
+    if len(ops) != 2:
+        return np.einsum(spec, *ops, **kw)
+    (ah, al), (bh, bl) = _split(np.asarray(ops[0])), _split(np.asarray(ops[1]))
+    r = (np.einsum(spec, ah, bh, optimize=True) + np.einsum(spec, ah, bl, optimize=True)
+         + np.einsum(spec, al, bh, optimize=True))
+    return r.astype(np.complex128)
+
+
+class _Numpy(types.ModuleType):
+    """numpy with einsum replaced by the BF16x3 emulation."""
+
+    def __getattr__(self, name):
+        return getattr(np, name)
+
+
+_NP_BF16X3 = _Numpy("numpy_bf16x3")
+_NP_BF16X3.einsum = _bf16x3_einsum
+
+
+def _ring_bf16x3(Q1, Q2, Q3, Q4):
+    R_up = _bf16x3_einsum("ij,jk->ik", Q1, Q2)
+    R_dn = _bf16x3_einsum("ij,kj->ik", Q4, Q3)
+    return R_up, R_dn, _bf16x3_einsum("ji,jk->ik", R_up, R_dn)
+
+
+def _run(monkeypatch, moves, readouts):
+    with monkeypatch.context() as m:
+        if moves:
+            m.setattr(OC, "np", _NP_BF16X3)
+            m.setattr(OC, "ring_matrix_factors", _ring_bf16x3)
+        if readouts:
+            m.setattr(OR, "np", _NP_BF16X3)
+        w = synth.workload("product_noise", seed=2, D=3, chi=18)
+        opt = oracle_options(18, 3, cutoff=1e-8)
+        st = O.make_state(w["tensors"], w["pattern"], 3, 18)
+        for _ in range(6):
+            st = O.sweep(st, opt)
+        rs = O.site_rdms(st, w["tensors"], w["pattern"])
+        rb = O.bond_rdms(st, w["tensors"], w["pattern"])
+    return rs, O.energy_per_spin(rb, w["J"], 2, 2)
+
+
+def test_bf16_rounding():
+    one = np.float32(1.0)
+    assert bf16(one) == one
+    assert bf16(np.float32(1 + 2 ** -8)) == one                       # tie -> even
+    assert bf16(np.float32(1 + 3 * 2 ** -9)) == np.float32(1 + 2 ** -7)
+    assert bf16(np.float32(-2.5)) == np.float32(-2.5)
+    x = np.float32(0.1234567)
+    assert abs(float(bf16(x)) - float(x)) <= 2 ** -9 * abs(float(x))
+
+
+def test_bf16x3_rounding_explains_the_precision_form_error(monkeypatch):
+    rs0, e0 = _run(monkeypatch, False, False)
+    rs_all, e_all = _run(monkeypatch, True, True)
+    rs_ro, e_ro = _run(monkeypatch, False, True)
+    err_all, err_ro = np.max(np.abs(rs_all - rs0)), np.max(np.abs(rs_ro - rs0))
+    print(f"emulated BF16x3 everywhere: |dE| {abs(e_all - e0):.2e}, site RDM {err_all:.2e}; "
+          f"readouts only: |dE| {abs(e_ro - e0):.2e}, site RDM {err_ro:.2e}")
+    # same order as the GPU's measured 1.1e-6 / 6.8e-6
+    assert 3e-7 < abs(e_all - e0) < 3e-6
+    assert 1e-6 < err_all < 2e-5
+    # the readout contractions alone exceed 1e-6 in RDM elements but not in energy
+    assert 5e-7 < err_ro < 1e-5 and abs(e_ro - e0) < abs(e_all - e0)
+    # the oracle is back to plain FP64
+    assert OC.np is np and OR.np is np and OC.ring_matrix_factors is O.ring_matrix_factors
