@@ -13,10 +13,10 @@ the model gives errors of the same size, so those are the arithmetic's, and
 splits them: the environment carries most of the energy error, and the
 readout contractions alone already put ~2e-6 into RDM elements.  The oracle
 itself is unchanged (the substitution is undone after each run)."""
+import functools
 import types
 
 import numpy as np
-import pytest
 
 import oracle as O
 import oracle.ctm as OC
@@ -48,38 +48,82 @@ def _bf16x3_einsum(spec, *ops, **kw):
     return r.astype(np.complex128)
 
 
+def _bf16x3_fp64_accumulate_einsum(spec, *ops, **kw):
+    """The same three bf16 products, summed exactly (FP64) instead of in FP32."""
+    if len(ops) != 2:
+        return np.einsum(spec, *ops, **kw)
+    (ah, al), (bh, bl) = _split(np.asarray(ops[0])), _split(np.asarray(ops[1]))
+    c = lambda t: t.astype(np.complex128)
+    return sum(np.einsum(spec, c(x), c(y), optimize=True) for x, y in ((ah, bh), (ah, bl), (al, bh)))
+
+
+def _split3(a):
+    """Three bf16 parts x = p0 + p1 + p2 + O(2^-24 |x|) (24 significand bits)."""
+    re, im = np.real(a).astype(np.float64), np.imag(a).astype(np.float64)
+    parts = []
+    for _ in range(3):
+        pr, pi = bf16(re.astype(np.float32)), bf16(im.astype(np.float32))
+        parts.append((pr + 1j * pi).astype(np.complex64))
+        re, im = re - pr, im - pi
+    return parts
+
+
+def _bf16x6_einsum(spec, *ops, **kw):
+    """Three-way split, the six products p_i q_j with i + j <= 2, FP32 accumulation."""
+    if len(ops) != 2:
+        return np.einsum(spec, *ops, **kw)
+    A, B = _split3(np.asarray(ops[0])), _split3(np.asarray(ops[1]))
+    r = sum(np.einsum(spec, A[i], B[j], optimize=True) for i in range(3) for j in range(3) if i + j <= 2)
+    return r.astype(np.complex128)
+
+
 class _Numpy(types.ModuleType):
-    """numpy with einsum replaced by the BF16x3 emulation."""
+    """numpy with einsum replaced by an emulated product."""
 
     def __getattr__(self, name):
         return getattr(np, name)
 
 
-_NP_BF16X3 = _Numpy("numpy_bf16x3")
-_NP_BF16X3.einsum = _bf16x3_einsum
+def _numpy_with(einsum):
+    m = _Numpy("numpy_emulated")
+    m.einsum = einsum
+    return m
 
 
-def _ring_bf16x3(Q1, Q2, Q3, Q4):
-    R_up = _bf16x3_einsum("ij,jk->ik", Q1, Q2)
-    R_dn = _bf16x3_einsum("ij,kj->ik", Q4, Q3)
-    return R_up, R_dn, _bf16x3_einsum("ji,jk->ik", R_up, R_dn)
+def _ring_with(einsum):
+    def ring(Q1, Q2, Q3, Q4):
+        R_up = einsum("ij,jk->ik", Q1, Q2)
+        R_dn = einsum("ij,kj->ik", Q4, Q3)
+        return R_up, R_dn, einsum("ji,jk->ik", R_up, R_dn)
+    return ring
 
 
-def _run(monkeypatch, moves, readouts):
+def _sweeps_and_readouts():
+    """Six sweeps at D = 3, chi = 18, then site RDMs and the energy."""
+    w = synth.workload("product_noise", seed=2, D=3, chi=18)
+    opt = oracle_options(18, 3, cutoff=1e-8)
+    st = O.make_state(w["tensors"], w["pattern"], 3, 18)
+    for _ in range(6):
+        st = O.sweep(st, opt)
+    rs = O.site_rdms(st, w["tensors"], w["pattern"])
+    return rs, O.energy_per_spin(O.bond_rdms(st, w["tensors"], w["pattern"]), w["J"], 2, 2)
+
+
+@functools.lru_cache(maxsize=1)
+def _exact():
+    """The plain FP64 oracle (computed once)."""
+    return _sweeps_and_readouts()
+
+
+def _run(monkeypatch, moves, readouts, einsum=_bf16x3_einsum):
+    """The same run with `einsum` in the moves and/or the readout contractions."""
     with monkeypatch.context() as m:
         if moves:
-            m.setattr(OC, "np", _NP_BF16X3)
-            m.setattr(OC, "ring_matrix_factors", _ring_bf16x3)
+            m.setattr(OC, "np", _numpy_with(einsum))
+            m.setattr(OC, "ring_matrix_factors", _ring_with(einsum))
         if readouts:
-            m.setattr(OR, "np", _NP_BF16X3)
-        w = synth.workload("product_noise", seed=2, D=3, chi=18)
-        opt = oracle_options(18, 3, cutoff=1e-8)
-        st = O.make_state(w["tensors"], w["pattern"], 3, 18)
-        for _ in range(6):
-            st = O.sweep(st, opt)
-        rs = O.site_rdms(st, w["tensors"], w["pattern"])
-        rb = O.bond_rdms(st, w["tensors"], w["pattern"])
-    return rs, O.energy_per_spin(rb, w["J"], 2, 2)
+            m.setattr(OR, "np", _numpy_with(einsum))
+        return _sweeps_and_readouts()
 
 
 def test_bf16_rounding():
@@ -93,7 +137,7 @@ def test_bf16_rounding():
 
 
 def test_bf16x3_rounding_explains_the_precision_form_error(monkeypatch):
-    rs0, e0 = _run(monkeypatch, False, False)
+    rs0, e0 = _exact()
     rs_all, e_all = _run(monkeypatch, True, True)
     rs_ro, e_ro = _run(monkeypatch, False, True)
     err_all, err_ro = np.max(np.abs(rs_all - rs0)), np.max(np.abs(rs_ro - rs0))
@@ -106,3 +150,18 @@ def test_bf16x3_rounding_explains_the_precision_form_error(monkeypatch):
     assert 5e-7 < err_ro < 1e-5 and abs(e_ro - e0) < abs(e_all - e0)
     # the oracle is back to plain FP64
     assert OC.np is np and OR.np is np and OC.ring_matrix_factors is O.ring_matrix_factors
+
+
+def test_bf16x3_is_limited_by_its_split_not_by_accumulation(monkeypatch):
+    """hi + lo keeps 16 significand bits, so summing the three products exactly
+    does not help; a three-way split (24 bits) with six products reaches the
+    1e-6 RDM target at twice the tensor-core work of BF16x3."""
+    rs0, e0 = _exact()
+    rs3, e3 = _run(monkeypatch, True, True)
+    rs_acc, e_acc = _run(monkeypatch, True, True, _bf16x3_fp64_accumulate_einsum)
+    rs6, e6 = _run(monkeypatch, True, True, _bf16x6_einsum)
+    d3, d_acc, d6 = (np.max(np.abs(r - rs0)) for r in (rs3, rs_acc, rs6))
+    print(f"site RDM error: BF16x3 {d3:.2e}, exact accumulation {d_acc:.2e}, three-way split {d6:.2e}; "
+          f"|dE| {abs(e3 - e0):.2e}, {abs(e_acc - e0):.2e}, {abs(e6 - e0):.2e}")
+    assert d_acc > 0.5 * d3
+    assert d6 < 1e-6 and d6 < 0.2 * d3 and abs(e6 - e0) < 0.2 * abs(e3 - e0)
