@@ -175,6 +175,18 @@ static void prof_end(ipeps_ctm h, cudaEvent_t a, double flops, int kind) {
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// cudaMalloc that leaves no error behind when it fails: a failed allocation is
+// also recorded as the runtime's last error, which the launch checks of every
+// later call would otherwise report as their own failure.
+static cudaError_t dev_alloc(void** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+  }
+  return e;
+}
+
 // swap the handle's active projector resources with the second lane
 static void swap_lane(ipeps_ctm h) {
   std::swap(h->stream, h->alt.stream);
@@ -825,7 +837,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
     h->bytes = o->workspace_bytes;
     h->own_mem = false;
   } else {
-    cudaError_t e = cudaMalloc((void**)&h->base, sz.total);
+    cudaError_t e = dev_alloc((void**)&h->base, sz.total);
     if (e != cudaSuccess) {
       delete h;
       return fail(IPEPS_ENOMEM, "cudaMalloc(%zu) failed: %s", sz.total, cudaGetErrorString(e));
@@ -1395,7 +1407,7 @@ extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
   const int ncell = h->Lx * h->Ly;
   const size_t cb = (size_t)h->chi * h->chi * sizeof(cplx), tb = (size_t)h->chi * h->D2 * h->chi * sizeof(cplx);
   char* snap = nullptr;
-  CK(cudaMalloc((void**)&snap, 4 * ncell * (cb + tb)));
+  CK(dev_alloc((void**)&snap, 4 * ncell * (cb + tb)));
   for (int j = 0; j < 4; ++j)
     for (int i = 0; i < ncell; ++i) {
       CK(cudaMemcpyAsync(snap + (j * ncell + i) * (cb + tb), h->C[j][i], cb, cudaMemcpyDeviceToDevice, h->stream));
@@ -2049,7 +2061,7 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
   const long long krylov_phase = 2 * n2 + lanczos_work_elems(n, max_iter) + 1024;
   const long long region_elems = std::max(ring_phase, krylov_phase);
   cplx* mem = nullptr;
-  cudaError_t e = cudaMalloc((void**)&mem, (size_t)(n2 + region_elems) * sizeof(cplx));
+  cudaError_t e = dev_alloc((void**)&mem, (size_t)(n2 + region_elems) * sizeof(cplx));
   if (e != cudaSuccess)
     return fail(IPEPS_ENOMEM, "boundary rho: cudaMalloc of %.1f GB failed: %s",
                 (double)(n2 + region_elems) * 16e-9, cudaGetErrorString(e));
@@ -2164,10 +2176,10 @@ static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, i
   cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dS = nullptr;
   ipeps_status st = IPEPS_OK;
   auto cleanup = [&]() { cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dS); };
-  cudaError_t e = cudaMalloc(&dA, na * sizeof(cplx));
-  if (e == cudaSuccess) e = cudaMalloc(&dB, nb * sizeof(cplx));
-  if (e == cudaSuccess) e = cudaMalloc(&dC, nc * sizeof(cplx));
-  if (e == cudaSuccess && prec) e = cudaMalloc(&dS, scratch_elems * sizeof(cplx));
+  cudaError_t e = dev_alloc((void**)&dA, na * sizeof(cplx));
+  if (e == cudaSuccess) e = dev_alloc((void**)&dB, nb * sizeof(cplx));
+  if (e == cudaSuccess) e = dev_alloc((void**)&dC, nc * sizeof(cplx));
+  if (e == cudaSuccess && prec) e = dev_alloc((void**)&dS, scratch_elems * sizeof(cplx));
   if (e == cudaSuccess) e = cudaMemcpy(dA, A, na * sizeof(cplx), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dB, B, nb * sizeof(cplx), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cleanup(); return fail(IPEPS_ECUDA, "zgemm setup: %s", cudaGetErrorString(e)); }

@@ -247,3 +247,14 @@ def test_checkpoint_calls_reject_null_handles(lib, tmp_path):
     assert lib.ipeps_ctm_load(None, str(tmp_path / "x").encode()) == 1
     assert lib.ipeps_env_file_info(None, (ctypes.c_int * 11)()) == 1
     assert not (tmp_path / "x").exists() and not (tmp_path / "x.part").exists()
+
+
+def test_too_small_workspace_is_refused_before_cuda(lib):
+    cell, opt, _keep = _good(lib)
+    n = ctypes.c_size_t()
+    assert lib.ipeps_ctm_workspace_size(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(n)) == 0
+    opt.workspace = ctypes.c_void_p(4096)  # never touched: the size check comes first
+    opt.workspace_bytes = n.value - 1
+    h = ctypes.c_void_p()
+    assert lib.ipeps_ctm_create(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(h)) == 2
+    assert b"workspace too small" in lib.ipeps_last_error() and h.value is None
