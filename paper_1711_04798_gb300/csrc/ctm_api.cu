@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ipeps_ctm.h"
 #include "ctm_internal.h"
 #include "tc_gemm.h"
@@ -174,6 +176,15 @@ static void prof_end(ipeps_ctm h, cudaEvent_t a, double flops, int kind) {
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// NVTX range over a host scope (a move direction, a readout), so profilers can
+// select or group the kernels it enqueues; a no-op when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // cudaMalloc that leaves no error behind when it fails: a failed allocation is
 // also recorded as the runtime's last error, which the launch checks of every
@@ -1378,10 +1389,15 @@ static ipeps_status left_move(ipeps_ctm h, int f) {
 // the device or reading its status: the work a batch captures in a graph.
 ipeps_status ctm_enqueue_move(ipeps_ctm h, int dir) {
   static const int sweep[4] = {IPEPS_MOVE_LEFT, IPEPS_MOVE_RIGHT, IPEPS_MOVE_UP, IPEPS_MOVE_DOWN};
+  static const char* names[4] = {"ctm move L", "ctm move U", "ctm move R", "ctm move D"};
   if (dir == IPEPS_SWEEP) {
-    for (int i = 0; i < 4; ++i) CKS(left_move(h, sweep[i]));
+    for (int i = 0; i < 4; ++i) {
+      NvtxRange r(names[sweep[i]]);
+      CKS(left_move(h, sweep[i]));
+    }
     return IPEPS_OK;
   }
+  NvtxRange r(names[dir]);
   return left_move(h, dir);
 }
 
@@ -1473,6 +1489,7 @@ static ipeps_status spectra_device(ipeps_ctm h, double* host) {
 
 extern "C" ipeps_status ipeps_ctm_spectra(ipeps_ctm h, double* s_out) {
   if (!h || !s_out) return fail(IPEPS_EINVAL, "null argument");
+  NvtxRange range("corner spectra");
   CKS(reset_status(h));
   CKS(spectra_device(h, s_out));
   return check_status(h);
@@ -1592,6 +1609,7 @@ static ipeps_status rdm_site(ipeps_ctm h, int x, int y, cplx* rho) {
 
 extern "C" ipeps_status ipeps_rdm_site(ipeps_ctm h, double* rho_s) {
   if (!h || !rho_s) return fail(IPEPS_EINVAL, "null argument");
+  NvtxRange range("rdm sites");
   CKS(reset_status(h));
   const long long n1 = (long long)h->d * h->d;
   const long long n = n1 * h->Lx * h->Ly;
@@ -1632,6 +1650,7 @@ static ipeps_status rdm_buffers(ipeps_ctm h, cplx** rh, cplx** rv) {
 
 extern "C" ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
+  NvtxRange range("rdm bonds");
   CKS(reset_status(h));
   cplx *rh, *rv;
   CKS(rdm_buffers(h, &rh, &rv));
@@ -1667,6 +1686,7 @@ extern "C" ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e) 
   if (!h || !J || !e) return fail(IPEPS_EINVAL, "null argument");
   if (h->d != 8 || h->Lx != 2 || h->Ly != 2)
     return fail(IPEPS_EINVAL, "the ruby energy needs a 2x2 cell of d = 8 block sites");
+  NvtxRange range("energy");
   CKS(reset_status(h));
   CKS(upload_bonds(h, J));
   cplx *rh, *rv;
@@ -1813,6 +1833,7 @@ static ipeps_status kappa_host(ipeps_ctm h, double* kre, double* kim) {
 
 extern "C" ipeps_status ipeps_kappa(ipeps_ctm h, double* k) {
   if (!h || !k) return fail(IPEPS_EINVAL, "null argument");
+  NvtxRange range("kappa");
   CKS(reset_status(h));
   CKS(kappa_host(h, k, k + 1));
   return check_status(h);
@@ -1903,6 +1924,7 @@ extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* e
   long long n = 1;
   for (int i = 0; i < Nv; ++i) n *= h->D;
   if (n > 4096) return fail(IPEPS_EINVAL, "D^Nv = %lld > 4096", n);
+  NvtxRange range("boundary rho");
   CKS(reset_status(h));
   const int nn = (int)n;
   const long long mark = h->scratch_top;
@@ -2045,6 +2067,7 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
   if (k < 1 || max_iter < k || max_iter > 1024 || max_iter > n)
     return fail(IPEPS_EINVAL, "need 1 <= k <= max_iter <= min(1024, D^Nv)");
   if (!(tol > 0.0)) return fail(IPEPS_EINVAL, "tol must be positive");
+  NvtxRange range("boundary rho leading");
   CKS(reset_status(h));
   const long long c2 = (long long)h->chi * h->chi;
   long long K1 = 1, K2 = 1;
