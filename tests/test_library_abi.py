@@ -4,6 +4,7 @@ CUDA call."""
 import ctypes
 import os
 import re
+import sys
 
 import numpy as np
 import pytest
@@ -258,3 +259,29 @@ def test_too_small_workspace_is_refused_before_cuda(lib):
     h = ctypes.c_void_p()
     assert lib.ipeps_ctm_create(ctypes.byref(cell), ctypes.byref(opt), ctypes.byref(h)) == 2
     assert b"workspace too small" in lib.ipeps_last_error() and h.value is None
+
+
+def test_product_path_never_loads_the_oracle():
+    """The package (binding and build) neither imports the oracle nor has a CPU
+    path: importing it leaves `oracle` unloaded, and no source mentions it."""
+    import subprocess
+    code = ("import sys; sys.path.insert(0, %r); import paper_1711_04798_gb300 as p; "
+            "print('oracle' in sys.modules, 'synth' in sys.modules)" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True)
+    assert out.stdout.split() == ["False", "False"], out.stdout
+    pkg = os.path.join(ROOT, "paper_1711_04798_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert not re.search(r"^\s*(import|from)\s+(oracle|synth)\b", src, re.M), name
+
+
+def test_missing_library_fails_loudly():
+    from paper_1711_04798_gb300 import binding
+    saved = binding._lib
+    binding._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            binding.load_library(os.path.join(ROOT, "no_such_dir", "libnothing.so"))
+    finally:
+        binding._lib = saved
