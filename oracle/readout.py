@@ -27,6 +27,7 @@ __all__ = [
     "fidelity",
     "ring_sigma",
     "boundary_spectrum",
+    "spectrum_of_rings",
     "boundary_spectrum_topk",
     "fixed_rings",
     "entropy",
@@ -363,6 +364,20 @@ def boundary_spectrum(st: CTMState, x: int, Nv: int):
     when it is positive, as for an exact environment).
     """
     sL, sR = fixed_rings(st, x, Nv)
+    return spectrum_of_rings(sL, sR)
+
+
+def spectrum_of_rings(sL: np.ndarray, sR: np.ndarray) -> np.ndarray:
+    """The boundary spectrum of ``boundary_spectrum`` for given Hermitian rings.
+
+    Eq. "rho" needs sqrt(sigma_L^T), defined for a positive sigma_L.  A ring
+    built from truncated edge tensors can carry small negative eigenvalues;
+    the square root used here is that of |sigma_L^T| = (S^H S)^(1/2), which is
+    sqrt(sigma_L^T) itself whenever sigma_L^T is positive (so on positive rings
+    every route -- eigenvalues of sigma_L^T sigma_R, of the similar operator,
+    or these singular values -- gives the same numbers), and which keeps the
+    weights non-negative otherwise.
+    """
     _, s, Vh = np.linalg.svd(sL.T)
     W = (Vh.conj().T * np.sqrt(s)[None, :]) @ Vh
     H = W @ sR @ W

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import synth
-from gpu_common import DEFAULTS, oracle_options
+from gpu_common import DEFAULTS, oracle_options, spectra_err
 
 pytestmark = pytest.mark.gpu
 
@@ -37,9 +37,7 @@ def test_batch_fp64_matches_oracle():
     for i, inst in enumerate(insts):
         e_ref, s_ref = _oracle_energy(inst, 2)
         assert abs(e[i] - e_ref) < TOL * abs(e_ref), (i, e[i], e_ref)
-        s = b.instance(i).spectra()
-        mask = s_ref > 1e-8
-        assert np.max(np.abs(s - s_ref)[mask]) < 1e-8, i
+        assert spectra_err(b.instance(i).spectra(), s_ref) < TOL, i
     assert b.launch_count() > 0
     b.close()
 

@@ -799,3 +799,64 @@ def test_hamiltonian_terms_hermitian_and_trivial_bond(build):
     # each Pauli-product term is traceless: trace of every bond operator vanishes
     for k in ("H_r", "H_u", "H_d"):
         assert abs(np.trace(H[k])) < 1e-12
+
+
+def _exact_cylinder_rings(A):
+    """sigma_L, sigma_R of the exact circumference-2 cylinder (fixed points of
+    the column transfer matrix, as in _exact_cylinder_spectrum)."""
+    D = A.shape[1]
+    a = O.double_layer(A)
+    E = np.einsum("alcr,cmas->lmrs", a, a).reshape(D ** 4, D ** 4)
+    ops = []
+    for M in (E.T, E):
+        w, V = np.linalg.eig(M)
+        v = V[:, np.argmax(np.abs(w))].reshape(D, D, D, D)
+        m = np.transpose(v, (0, 2, 1, 3)).reshape(D * D, D * D)
+        m = m * np.exp(-1j * np.angle(np.trace(m)))
+        ops.append(0.5 * (m + m.conj().T))
+    return ops
+
+
+def test_boundary_spectrum_route_on_positive_rings():
+    """Eq. "rho": on positive rings (the exact cylinder's fixed points are
+    positive: they are reduced density operators of the virtual space) the
+    oracle's route -- singular values of |sigma_L^T|^(1/2) sigma_R
+    |sigma_L^T|^(1/2) -- gives the eigenvalues of sigma_L^T sigma_R, the
+    quantity Sec. IV diagonalises, and the eigenvalues of the similar operator
+    built from the positive square root."""
+    for A in (ising_tensor(0.3), ising_tensor(0.5)):
+        sL, sR = _exact_cylinder_rings(A)
+        assert np.linalg.eigvalsh(sL).min() > -1e-14 and np.linalg.eigvalsh(sR).min() > -1e-14
+        lam = O.spectrum_of_rings(sL, sR)
+        M = sL.T @ sR
+        ev = np.sort(np.real(np.linalg.eigvals(M)))[::-1] / np.real(np.trace(M))
+        w, V = np.linalg.eigh(sL.T)
+        Wh = (V * np.sqrt(np.clip(w, 0, None))) @ V.conj().T
+        ev2 = np.sort(np.linalg.eigvalsh(Wh @ sR @ Wh))[::-1]
+        ev2 = ev2 / ev2.sum()
+        assert np.allclose(lam, ev, atol=1e-12) and np.allclose(lam, ev2, atol=1e-12)
+        assert np.allclose(lam, _exact_cylinder_spectrum(A), atol=1e-12)
+
+
+def test_boundary_spectrum_route_on_an_indefinite_ring():
+    """Where a ring has a negative eigenvalue (possible for rings of truncated
+    edge tensors) sqrt(sigma_L^T) is undefined; the oracle's |sigma_L^T|^(1/2)
+    keeps every weight non-negative and summing to one, and it differs from
+    dropping the negative part (clamping), which changes the operator: the
+    two routes are told apart here."""
+    rng = np.random.default_rng(8)
+    n = 6
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    sL = (U * np.array([1.0, 0.5, 0.3, 0.2, 0.1, -0.05])) @ U.conj().T
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    sR = G @ G.conj().T
+    lam = O.spectrum_of_rings(sL, sR)
+    assert lam.min() >= 0 and abs(lam.sum() - 1) < 1e-14
+    w, V = np.linalg.eig(sL.T)
+    absL = (V * np.sqrt(np.abs(w))) @ np.linalg.inv(V)  # |sigma_L^T|^(1/2) by eigenvectors
+    ref = np.linalg.svd(absL @ sR @ absL, compute_uv=False)
+    assert np.allclose(lam, ref / ref.sum(), atol=1e-12)
+    wh, Vh = np.linalg.eigh(sL.T)
+    clamp = (Vh * np.sqrt(np.clip(wh, 0, None))) @ Vh.conj().T
+    ev_c = np.sort(np.linalg.eigvalsh(clamp @ sR @ clamp))[::-1]
+    assert np.max(np.abs(lam - ev_c / ev_c.sum())) > 1e-3
