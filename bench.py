@@ -32,7 +32,7 @@ def parse():
     p.add_argument("--steps", type=int, default=4)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3"])
+    p.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3", "bf16x6"])
     p.add_argument("--no-fp64-check", action="store_true",
                    help="skip the FP64 comparison run (moves/s and |dE| of the plain FP64 GPU path)")
     p.add_argument("--D", type=int, default=5)
@@ -225,6 +225,68 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+PASSES = {"fp64": 1, "tf32": 1, "bf16x3": 3, "bf16x6": 6}  # tensor-core products per complex product
+DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}
+
+
+def stored_oracle(D, chi, seed, cutoff):
+    """The FP64 oracle's converged state of this workload, when tests/golden
+    holds it (written by tests/golden/make_golden.py from oracle/ alone)."""
+    name = {(5, 100, 0, 1e-6): "product_noise_D5_chi100_cut6"}.get((D, chi, seed, cutoff))
+    path = os.path.join(GOLDEN, f"{name}.npz") if name else None
+    if not path or not os.path.exists(path):
+        return None
+    with np.load(path) as z:
+        return {k: z[k] for k in z.files} if "E_conv" in z.files else None
+
+
+def kernel_classes(g, prec, ms_step, steps, peaks, peak_src, zpk):
+    """Per-class roofline records from one profiled pass (library CUDA events
+    on the stream each kernel runs on)."""
+    classes = []
+    rd = {k: g.profile_read(k) for k in (1, 2, 5, 6, 7, 8)}
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    zsrc = "cuBLAS complex128 GEMM measured in this run (no FP64 entry in the peaks file)"
+    if prec == "fp64":
+        c0 = g.profile_read(0)
+        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM, CUDA cores): contractions", "bound": "alu",
+                        "ms": c0["ms"], "work": c0["flops"] / 1e12, "launches": c0["launches"], "peak": zpk,
+                        "unit": "TFLOP/s", "peak_source": zsrc})
+    else:
+        npass = PASSES[prec]
+        # a contraction takes the peak of its own dtype: BF16 dense (measured); TF32 at half of it
+        pk = bf16 if prec != "tf32" else bf16 / 2.0
+        classes.append({"kernel": f"tc_gemm_kernel (tcgen05 {prec}), wide products: enlarged corners, absorption, "
+                                  "readouts", "bound": "tensor", "ms": rd[5]["ms"],
+                        "work": rd[5]["flops"] * npass / 1e12, "launches": rd[5]["launches"], "peak": pk,
+                        "unit": "TFLOP/s",
+                        "peak_source": f"bf16 dense sustained ({peak_src}){' x 1/2 for TF32' if prec == 'tf32' else ''};"
+                                       f" executed flops = 8MNK algorithmic x {npass} products"})
+        classes.append({"kernel": f"tc_gemm_kernel (tcgen05 {prec}), thin products: range finder and projector "
+                                  "assembly", "bound": "hbm", "ms": rd[7]["ms"], "work": rd[7]["flops"] / 1e9,
+                        "launches": rd[7]["launches"], "peak": hbm, "unit": "GB/s",
+                        "peak_source": f"HBM copy ({peak_src}); bytes = packed operands read once + output written",
+                        "algorithmic_tflops": rd[6]["flops"] / (rd[6]["ms"] * 1e-3) / 1e12 if rd[6]["ms"] else None})
+        classes.append({"kernel": "splitk_reduce_kernel (FP32 partial sums)", "bound": "hbm", "ms": rd[8]["ms"],
+                        "work": rd[8]["flops"] / 1e9, "launches": rd[8]["launches"], "peak": hbm, "unit": "GB/s",
+                        "peak_source": f"HBM copy ({peak_src})"})
+        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM): CholeskyQR Grams/applies of the projectors",
+                        "bound": "alu", "ms": rd[2]["ms"], "work": rd[2]["flops"] / 1e12,
+                        "launches": rd[2]["launches"], "peak": zpk, "unit": "TFLOP/s", "peak_source": zsrc})
+    classes.append({"kernel": "Jacobi SVD kernels (FP64, projector cores and orthonormalisation)", "bound": "alu",
+                    "ms": rd[1]["ms"], "work": None, "launches": rd[1]["launches"], "peak": None, "unit": None,
+                    "peak_source": "latency-bound FP64 rotations; mean sweeps per call "
+                                   f"{rd[1]['flops']:.2f}"})
+    for c in classes:
+        c["achieved"] = c["work"] / (c["ms"] * 1e-3) if c["ms"] and c["work"] else None
+        c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
+        c["share_of_step"] = c["ms"] / (ms_step * steps) if ms_step else None
+        c["ms_per_launch"] = c["ms"] / c["launches"] if c["launches"] else None
+    return classes
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1711_04798_gb300 import CTM
@@ -246,7 +308,6 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    g.profile(True)
     l0 = g.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
@@ -257,10 +318,6 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = g.launch_count() - l0
-    gemm = g.profile_read(0)
-    jac = g.profile_read(1)
-    f64g = g.profile_read(2)
-    g.profile(False)
     ms_max = max_over_ranks(ms, dist)
     value = job_value(args.steps * MOVES_PER_STEP, world, ms_max * 1e-3)
 
@@ -285,56 +342,34 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
             dist.destroy_process_group()
         return
+    # profiled pass (the same steps, kernels launched one by one and bracketed
+    # by the library's CUDA events): per-class times for the roofline
+    g.profile(True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1) / args.steps
     peaks, peak_src = measured_peaks()
     zpk = zgemm_peak_tflops(torch)
-    zsrc = "cuBLAS complex128 GEMM measured in this run (no FP64 entry in the peaks file)"
-    classes = []
-    if args.prec == "fp64":
-        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM, CUDA cores): contractions", "bound": "alu",
-                        "ms": gemm["ms"], "flops": gemm["flops"], "launches": gemm["launches"], "peak": zpk,
-                        "peak_source": zsrc})
-    else:
-        classes.append({"kernel": "tc_gemm_kernel (tcgen05 " + args.prec + ") with operand packing: contractions",
-                        "bound": "tensor", "ms": gemm["ms"], "flops": gemm["flops"], "launches": gemm["launches"],
-                        "peak": peaks.get("bf16_tflops_sustained", 1700.0),
-                        "peak_source": f"bf16 sustained ({peak_src}); algorithmic flops (x3 executed for bf16x3)"})
-        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM): CholeskyQR Grams/applies of the projectors",
-                        "bound": "alu", "ms": f64g["ms"], "flops": f64g["flops"], "launches": f64g["launches"],
-                        "peak": zpk, "peak_source": zsrc})
-    for c in classes:
-        c["achieved"] = c["flops"] / (c["ms"] * 1e-3) / 1e12 if c["ms"] else None
-        c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
-        c["share_of_step"] = c["ms"] / ms if ms else None  # lanes overlap: shares can sum above 1
-        c["unit"] = "TFLOP/s"
-    dom = max(classes, key=lambda c: c["ms"])
-    roof = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"], "unit": "TFLOP/s",
-            "frac": dom["frac"], "traffic": None, "kernel": dom["kernel"], "peak_source": dom["peak_source"],
-            "dominant_by": "CUDA-event time of the kernel class inside the timed steps",
-            "by_class": [{k: c[k] for k in ("kernel", "bound", "achieved", "peak", "frac", "share_of_step",
-                                             "launches")} for c in classes],
-            "jacobi_ms_share": jac["ms"] / ms if ms else None, "jacobi_calls": jac["launches"],
-            "jacobi_mean_sweeps": jac["flops"]}
+    classes = kernel_classes(g, args.prec, ms_prof, args.steps, peaks, peak_src, zpk)
+    g.profile(False)
+    timed = [c for c in classes if c["achieved"]]
+    dom = max(timed, key=lambda c: c["ms"])
+    roof = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
+            "frac": dom["frac"], "traffic": TRAFFIC.get((args.prec, dom["bound"])), "kernel": dom["kernel"],
+            "peak_source": dom["peak_source"],
+            "dominant_by": "CUDA-event time per kernel class in a profiled pass of the same steps "
+                           f"({ms_prof:.1f} ms per step with per-launch events, vs {ms_max / args.steps:.1f} ms "
+                           "as CUDA graphs)",
+            "by_class": [{k: c.get(k) for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                                "share_of_step", "launches", "ms_per_launch")} for c in classes]}
     fp64_cmp = None
     if args.prec != "fp64" and not args.no_fp64_check:
-        # the same number of sweeps from the trace initialisation, plain FP64 GPU path
-        n_sw = 2
-        gm = CTM(w["tensors"], w["pattern"], args.chi, prec=args.prec, stream=stream.cuda_stream)
-        gf = CTM(w["tensors"], w["pattern"], args.chi, prec="fp64", stream=stream.cuda_stream)
-        gm.sweep(n_sw)
-        em = gm.energy(J)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        gf.sweep(n_sw)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ef = gf.energy(J)
-        fp64_cmp = {"sweeps": n_sw, "fp64_moves_per_s": 4 * n_sw / (f0.elapsed_time(f1) * 1e-3),
-                    "energy_mixed": em, "energy_fp64": ef, "abs_dE": abs(em - ef),
-                    "speedup_vs_fp64": None}
-        fp64_cmp["speedup_vs_fp64"] = value / fp64_cmp["fp64_moves_per_s"]
-        gm.close()
-        gf.close()
+        fp64_cmp = fp64_comparison(args, w, J, stream, torch, value)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         secs = oracle_move_seconds(args.D, args.chi)
@@ -344,20 +379,80 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec],
+        "dtype": DTYPE[args.prec],
         "data": "synthetic", "config": config_desc(args, args.prec),
-        "tflops": gemm["flops"] / (ms * 1e-3) / 1e12 if ms else None,
+        "tflops": MOVES_PER_STEP * flops_per_move(args.D, args.chi) / (ms_max / args.steps * 1e-3) / 1e12,
         "autotuned_shapes": tuned,
         "energy_per_spin": energies[-1],
         "roofline": roof, "cpu_baseline": cpu, "fp64_comparison": fp64_cmp,
         "e2e": {"value": e2e_value, "unit": "moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-        "gpu_launches": launches, "clocks": clk.summary(),
+        "gpu_launches": launches, "host_graph_launches_per_step": MOVES_PER_STEP // 4,
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     g.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# DRAM bytes per launch of the dominant class from one ncu capture (profiles/),
+# keyed by (precision, bound); absent until captured for the current kernel
+TRAFFIC = {}
+
+
+def flops_per_move(D, chi, q=2, over=16):
+    """Algorithmic real flops of one move (the survey's count: 16 enlarged
+    corners, the range finder and projector assembly of four cuts, and the
+    absorption of two columns; complex = 8 real flops per multiply-add)."""
+    D2, N, k = D * D, chi * D * D, chi + over
+    Q = chi ** 3 * D2 + chi ** 3 * D2 ** 2 + chi ** 2 * D2 ** 4
+    return 8.0 * (16 * Q + 4 * ((2 * q + 2) * 4 * N * N * k + 2 * N * N * chi) + 8 * 2 * chi ** 3 * D2
+                  + 4 * (2 * chi ** 3 * D2 ** 2 + chi ** 2 * D2 ** 4))
+
+
+def fp64_comparison(args, w, J, stream, torch, value):
+    """The precision form against FP64: the plain FP64 GPU path's speed over one
+    sweep, and -- where the stored oracle record of this workload exists --
+    the converged precision-form energy, RDMs and corner spectra against the
+    FP64 oracle's converged values at the same truncation cutoff."""
+    from paper_1711_04798_gb300 import CTM
+    gf = CTM(w["tensors"], w["pattern"], args.chi, prec="fp64", stream=stream.cuda_stream)
+    gf.sweep(1)  # capture
+    gf.reset_env()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    gf.sweep(1)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    out = {"fp64_moves_per_s": 4 / (f0.elapsed_time(f1) * 1e-3)}
+    out["speedup_vs_fp64"] = value / out["fp64_moves_per_s"]
+    gf.close()
+    cut = 1e-6
+    ref = stored_oracle(args.D, args.chi, 0, cut) if rank_seed(0) == 0 else None
+    if ref is None:
+        out["converged"] = None
+        return out
+    gm = CTM(w["tensors"], w["pattern"], args.chi, prec=args.prec, cutoff=cut, stream=stream.cuda_stream)
+    n, delta, ok = gm.converge(1e-8, 40)
+    r = gm.rdms()
+    e = gm.energy(J)
+    s = gm.spectra()
+    sref = ref["spectra_conv"]
+    mask = sref > 1e-5
+    out["converged"] = {
+        "reference": "FP64 oracle (exact truncated SVD), converged to 1e-10 in the corner spectra, cutoff 1e-6, "
+                     f"{int(ref['sweeps'])} sweeps; stored by tests/golden/make_golden.py",
+        "sweeps": n, "delta": delta, "converged_to_1e-8": ok, "cutoff": cut,
+        "energy": e, "energy_oracle": float(ref["E_conv"]), "abs_dE": abs(e - float(ref["E_conv"])),
+        "max_abs_drho": float(max(np.max(np.abs(r["h"] - ref["rho_h_conv"])),
+                                  np.max(np.abs(r["v"] - ref["rho_v_conv"])))),
+        "max_spectrum_err": float(np.max(np.abs(s - sref)[mask])),
+        "targets": {"abs_dE": 1e-6, "max_abs_drho": 1e-6, "max_spectrum_err": 1e-5},
+    }
+    gm.close()
+    return out
 
 
 SCAN_DESC = ("batched scan: {n} independent instances on the line Jx=Jy=(2-Jz)/2, Jz_k=2k/{n1}; "
@@ -439,7 +534,7 @@ def run_scan(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "instance-moves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec],
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
         "data": "synthetic",
         "config": {"workload": SCAN_DESC.format(n=n, n1=n - 1), "step": "one sweep (L,R,U,D) of every instance",
                    "prec": args.prec, "autotune": not args.no_tune,
@@ -514,7 +609,7 @@ def run_cylinder(args, rank, world, local_rank):
         "metric": METRIC, "value": 4 * args.sweeps / ctm_s, "unit": "moves/s", "n_gpus": world,
         "steps": args.sweeps, "warmup": 1, "ms_per_step": 1e3 * ctm_s / args.sweeps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec], "data": "synthetic",
+        "dtype": DTYPE[args.prec], "data": "synthetic",
         "config": {"workload": f"cylinder readout: 2x2 cell, d=8, D={D}, chi={chi}, complex product state + 0.1 "
                                f"noise; {args.sweeps} sweeps then boundary rho at Nv=2,4,6",
                    "prec": args.prec},

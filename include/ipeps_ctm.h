@@ -64,7 +64,10 @@ typedef enum { IPEPS_REAL64 = 0, IPEPS_COMPLEX128 = 1 } ipeps_dtype;
 typedef enum {
   IPEPS_PREC_FP64 = 0,   /* complex FP64 on the CUDA cores                    */
   IPEPS_PREC_TF32 = 1,   /* tcgen05 TF32 tensor cores, FP32 accumulate        */
-  IPEPS_PREC_BF16X3 = 2  /* tcgen05 split-BF16 (hi*hi + hi*lo + lo*hi), FP32  */
+  IPEPS_PREC_BF16X3 = 2, /* tcgen05 split-BF16 (hi*hi + hi*lo + lo*hi), FP32  */
+  IPEPS_PREC_BF16X6 = 3  /* tcgen05 split-BF16 in three parts p0+p1+p2 (24    *
+                          * significand bits), the six products p_i q_j with  *
+                          * i + j <= 2, FP32 accumulate: FP32-class products  */
 } ipeps_prec;
 
 typedef enum {
@@ -94,18 +97,24 @@ typedef struct {
   int rsvd_oversample;              /* projector range finder width k = chi + p    */
   int rsvd_power;                   /* subspace iterations q                       */
   double svd_cutoff;                /* keep singular values > cutoff * largest;
-                                       <= 0: 1e-8 (FP64), 1e-6 (BF16X3), 1e-5 (TF32) */
+                                       <= 0: 1e-8 (FP64), 1e-6 (BF16X3, BF16X6),
+                                       1e-5 (TF32) */
   double orth_tol;                  /* range-finder basis: drop s < tol * largest  */
   uint64_t omega_seed;              /* SplitMix64 stream of the test matrix        */
   int jacobi_max_sweeps;            /* iteration budget of every Jacobi SVD        */
   void* stream;                     /* cudaStream_t; NULL = legacy default stream  */
   void* workspace;                  /* optional caller-owned device memory         */
   size_t workspace_bytes;           /* its size; see ipeps_ctm_workspace_size      */
+  long long wait_cycles;            /* limit of each device-side wait on other
+                                       CTAs (the grid barrier of the small-row
+                                       Jacobi), in SM clock cycles; after it the
+                                       wait gives up and the call reports
+                                       ETIMEOUT.  <= 0: 4e9 (about 2 s)        */
 } ipeps_options;
 
 /* Fill *opt (caller-owned) with the defaults: prec FP64, oversample 16,
  * power 2, cutoff 0 (automatic), orth_tol 1e-14, omega_seed 7,
- * jacobi_max_sweeps 40, NULL stream/workspace.  chi is set to 0 and must be
+ * jacobi_max_sweeps 40, NULL stream/workspace, wait_cycles 0 (automatic).  chi is set to 0 and must be
  * chosen by the caller.  The projector choices are the readings of the CTM
  * the paper cites in Sec. II.C (it prints none).  No effect if opt is NULL. */
 void ipeps_default_options(ipeps_options* opt);
@@ -146,8 +155,14 @@ ipeps_status ipeps_ctm_reset_env(ipeps_ctm h);
 /* Apply `count` moves in direction dir (ipeps_dir).  Each move computes the
  * enlarged corners, the projectors of every cut and renormalises the
  * corners/edges of each column (row) of the cell in turn (Sec. II.C, Fig. 3b:
- * the environment is grown and truncated back to chi).  Returns when the
- * moves are done.  Errors: EINVAL (NULL handle, dir outside 0..4, count < 0),
+ * the environment is grown and truncated back to chi).  The work of one
+ * move (or sweep) in a direction is captured once as a CUDA graph, on a
+ * stream of the handle's own, and launched on the handle's stream for every
+ * later call (one launch per move; the handle's buffers never move, so the
+ * graph stays valid until ipeps_ctm_autotune changes the tile choices);
+ * while kernel-class profiling is enabled the kernels are launched one by
+ * one instead.  Returns when the moves are done.  Errors: EINVAL (NULL
+ * handle, dir outside 0..4, count < 0),
  * ENOMEM (scratch), ECUDA, ETIMEOUT (a Jacobi SVD or a tensor-core wait ran
  * out of its budget), ENUMERIC (NaN/Inf or a zero norm); after an error the
  * environment is unspecified (ipeps_ctm_reset_env or ipeps_ctm_load restores
@@ -327,8 +342,17 @@ uint64_t ipeps_ctm_launch_count(ipeps_ctm h);
  * results count their nonzero part), or (kind 1) the mean number of sweeps per
  * Jacobi call.  ipeps_boundary_rho_topk adds kind 3 (building both dense ring
  * operators; flops: the two ring products, 16 n^2 chi^2) and kind 4 (the
- * Lanczos iteration; "flops" holds its step count).  With two projector lanes the brackets of concurrent work
- * overlap, so class times can sum to more than the step.  Not a paper
+ * Lanczos iteration; "flops" holds its step count).  Tensor-core products
+ * are also timed without their operand packing: kind 5 the main tcgen05
+ * kernel of products with more than 256 output rows (enlarged corners,
+ * absorption, readouts) and kind 6 of thin products (at most 256 rows: the
+ * range finder and the projector assembly), each with algorithmic flops;
+ * kind 7 the kind-6 launches again with the bytes the kernel must move
+ * (packed operands read once, output or FP32 partials written once) in the
+ * third output; kind 8 the split-K reductions with their bytes.  With two
+ * projector lanes the brackets of concurrent work overlap, so class times can
+ * sum to more than the step.  While enabled, moves run without CUDA graphs
+ * (the events are per launch).  Not a paper
  * operation: measurement support only.  The outputs of profile_read are
  * caller-owned and may each be NULL.  Errors: EINVAL (NULL handle), ECUDA. */
 ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable);
@@ -344,7 +368,8 @@ void ipeps_ctm_destroy(ipeps_ctm h);
  * opB(B) with M x N output, complex interleaved doubles in host memory
  * (row-major; op 0 = N, 1 = T, 2 = conj, 3 = conj-transpose, so that opA(A)
  * is M x K and A is stored M x K for op 0/2 and K x M for op 1/3).  prec as
- * ipeps_prec: FP64 CUDA-core kernel or the tcgen05 TF32 / split-BF16 kernel
+ * ipeps_prec: FP64 CUDA-core kernel or the tcgen05 TF32 / split-BF16x3 /
+ * split-BF16x6 kernel
  * (with its operand packing and split-K reduction).  Allocates and frees its
  * own device buffers; synchronises the device.  A, B, C are caller-owned host
  * arrays.  Errors: EINVAL (M, N or K <= 0, NULL pointer, prec or op out of
@@ -355,10 +380,11 @@ ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA
 
 /* As ipeps_zgemm for the tensor-core precisions, with the tile choice fixed
  * instead of the default: output tiles of 128 x bn real columns (bn = 128 or
- * 256) and `splits` K splits (reduced to the number of 128-byte k-blocks if
- * larger).  For unit tests of every choice the batch autotuner can make (no
- * paper counterpart).  Host buffers as ipeps_zgemm.  Errors: EINVAL (prec
- * FP64, bn not 128 or 256, splits < 1, or as ipeps_zgemm), ECUDA, ETIMEOUT. */
+ * 256; BF16X6 tiles are 128 wide) and `splits` K splits (reduced to the
+ * number of 128-byte k-blocks if larger).  For unit tests of every choice the
+ * batch autotuner can make (no paper counterpart).  Host buffers as
+ * ipeps_zgemm.  Errors: EINVAL (prec FP64, bn not 128 or 256, bn 256 with
+ * BF16X6, splits < 1, or as ipeps_zgemm), ECUDA, ETIMEOUT. */
 ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K, const double* A, int opA,
                               const double* B, int opB, double* C);
 
@@ -371,12 +397,14 @@ ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K,
  * doubles receiving its singular values in descending order divided by the
  * largest (zeros where the matrix has none) -- the same values
  * ipeps_ctm_spectra returns for a corner.  stream: cudaStream_t (NULL =
- * default stream); the call returns when s_dev is written.
+ * default stream); the call synchronises that stream (it reads the SVD's
+ * status back) and returns when s_dev is written.
  * All intermediates live in one fixed device array of about 1 MiB inside
  * the library (every GPU that loads the library holds it until exit), so
- * chi is limited to 1..256; larger chi returns EINVAL.  The first call on
- * each device looks up that array's address with that device current; make
- * the first call before any stream capture.  All calls share the array: two
+ * chi is limited to 1..256; larger chi returns EINVAL.  Every call looks up
+ * that array's device address with the caller's device current; the first
+ * call on a device also loads the library's device code there, so make the
+ * first call before any stream capture.  All calls share the array: two
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and give wrong results.  Errors: EINVAL (null pointer, chi out of range),
  * ECUDA, ETIMEOUT (Jacobi sweep budget), with ipeps_last_error(). */

@@ -10,7 +10,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libipeps_ctm.so")
 
-PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3}
 DIRS = {"L": 0, "U": 1, "R": 2, "D": 3, "sweep": 4}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT",
           6: "ENUMERIC", 7: "EUNSUPPORTED", 8: "EIO"}
@@ -39,7 +39,8 @@ class Options(C.Structure):
     _fields_ = [("chi", C.c_int), ("prec", C.c_int), ("rsvd_oversample", C.c_int),
                 ("rsvd_power", C.c_int), ("svd_cutoff", C.c_double), ("orth_tol", C.c_double),
                 ("omega_seed", C.c_uint64), ("jacobi_max_sweeps", C.c_int),
-                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+                ("wait_cycles", C.c_longlong)]
 
 
 class CTMError(RuntimeError):
@@ -161,7 +162,7 @@ def _make_cell(tensors, pattern, bra=None):
 
 
 def _make_options(lib, chi, prec="fp64", oversample=16, power=2, cutoff=0.0, orth_tol=1e-14,
-                  omega_seed=7, jacobi_max_sweeps=40, stream=None, workspace=None):
+                  omega_seed=7, jacobi_max_sweeps=40, stream=None, workspace=None, wait_cycles=0):
     opt = Options()
     lib.ipeps_default_options(C.byref(opt))
     opt.chi = chi
@@ -170,6 +171,7 @@ def _make_options(lib, chi, prec="fp64", oversample=16, power=2, cutoff=0.0, ort
     opt.svd_cutoff, opt.orth_tol = cutoff, orth_tol
     opt.omega_seed = omega_seed
     opt.jacobi_max_sweeps = jacobi_max_sweeps
+    opt.wait_cycles = wait_cycles
     opt.stream = stream
     if workspace is not None:
         opt.workspace = C.c_void_p(workspace[0])
@@ -187,7 +189,7 @@ class CTM:
 
     def __init__(self, tensors, pattern, chi, prec="fp64", bra=None, oversample=16, power=2,
                  cutoff=0.0, orth_tol=1e-14, omega_seed=7, jacobi_max_sweeps=40, stream=None,
-                 workspace=None):
+                 workspace=None, wait_cycles=0):
         lib = load_library()
         self.lib = lib
         self._borrowed = False
@@ -195,7 +197,7 @@ class CTM:
         self._keep, self._keep_bra, self._ptrs, self._bptrs, self._dtype = keep
         self._set_meta(tensors, pattern, chi)
         opt = _make_options(lib, chi, prec, oversample, power, cutoff, orth_tol, omega_seed,
-                            jacobi_max_sweeps, stream, workspace)
+                            jacobi_max_sweeps, stream, workspace, wait_cycles)
         self._cell, self._opt = cell, opt
         h = C.c_void_p()
         _check(lib.ipeps_ctm_create(C.byref(cell), C.byref(opt), C.byref(h)))

@@ -68,7 +68,7 @@ __device__ __forceinline__ void pair_of(int r, int p, int np, int rounds, int* i
 // shared memory.
 __global__ void __launch_bounds__(JC_THREADS)
     jacobi_cluster_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt, int max_sweeps,
-                          double tol, double4* __restrict__ log, int* sweeps_used, DevStatus* st) {
+                          double tol, double4_16a* __restrict__ log, int* sweeps_used, DevStatus* st) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = JC_THREADS / 32;
@@ -160,10 +160,10 @@ __global__ void __launch_bounds__(JC_THREADS)
             }
           }
           if (log && half == 0)
-            log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4(c, sn, phr, phi)
-                                                                   : make_double4(2.0, 0.0, 0.0, 0.0);
+            log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4_16a(c, sn, phr, phi)
+                                                                   : make_double4_16a(2.0, 0.0, 0.0, 0.0);
         } else if (!active && lane == 0 && half == 0 && log && p < npairs) {
-          log[((long long)sweep * rounds + r) * npairs + p] = make_double4(2.0, 0.0, 0.0, 0.0);
+          log[((long long)sweep * rounds + r) * npairs + p] = make_double4_16a(2.0, 0.0, 0.0, 0.0);
         }
         __syncthreads();  // partial sums read before the next pair overwrites them
         rot = __shfl_sync(0xffffffffu, rot, 0);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(JC_THREADS)
 // column q (columns are independent): thread p applies pair p of every round,
 // rounds in order, the column held in shared memory.  Rotation c = 2 marks a
 // pair that was not rotated.
-__global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4* __restrict__ log,
+__global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4_16a* __restrict__ log,
                                      const int* __restrict__ sweeps_used) {
   extern __shared__ cplx col[];
   const int q = blockIdx.x;
@@ -242,7 +242,7 @@ __global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4
     for (int r = 0; r < rounds; ++r) {
       const int p = threadIdx.x;
       if (p < npairs) {
-        const double4 rec = log[((long long)sw * rounds + r) * npairs + p];
+        const double4_16a rec = log[((long long)sw * rounds + r) * npairs + p];
         if (rec.x < 1.5) {
           int i, j;
           pair_of(r, p, np, rounds, &i, &j);
@@ -390,7 +390,7 @@ bool jacobi_cluster_fits(int n, int m, bool vt_in_smem) {
 
 long long jacobi_log_elems(int n, int max_sweeps) {
   const long long np = (n + 1) & ~1;
-  return (long long)max_sweeps * (np - 1) * (np / 2) * 2;  // one double4 = two complex slots per pair
+  return (long long)max_sweeps * (np - 1) * (np / 2) * 2;  // one double4_16a = two complex slots per pair
 }
 
 cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
@@ -399,7 +399,7 @@ cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg,
   if ((e = cluster_init()) != cudaSuccess) return e;
   const bool replay = Vt && rotlog && sweeps_used && n <= 2048;
   cplx* Vin = replay ? nullptr : Vt;  // with a log, Vt is rebuilt afterwards across the GPU
-  double4* logp = replay ? (double4*)rotlog : nullptr;
+  double4_16a* logp = replay ? (double4_16a*)rotlog : nullptr;
   int* su = replay ? sweeps_used : nullptr;
   const long long R = (n + g_csize - 1) / g_csize;
   const size_t smem = (size_t)(R * ((long long)m + (Vin ? n : 0)) * sizeof(cplx));
@@ -410,7 +410,7 @@ cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg,
   if (e != cudaSuccess || !replay) return e;
   const int npairs = ((n + 1) & ~1) / 2;
   const int threads = (npairs + 31) / 32 * 32;
-  jacobi_replay_kernel<<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4*)rotlog, sweeps_used);
+  jacobi_replay_kernel<<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4_16a*)rotlog, sweeps_used);
   count_launch();
   return cudaGetLastError();
 }

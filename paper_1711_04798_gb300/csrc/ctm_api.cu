@@ -143,10 +143,20 @@ struct ipeps_ctm_s {
   TcTuner* tuner;     // tile choices of the tensor-core products, or null
   bool own_tuner;     // created by ipeps_ctm_autotune (else owned by a batch)
   cudaEvent_t ev_fork, ev_join;
+  // CUDA graphs of the moves: one per direction (and one per sweep), captured
+  // on the private stream cap_stream at first use, launched on `stream`
+  cudaStream_t cap_stream;
+  cudaGraphExec_t exec[5];
+  int exec_kernels[5];  // kernels inside each graph (launch accounting)
   // optional per-kernel-class timing (CUDA events on the handle's stream)
   bool profiling;
   long long jac_sweeps, jac_calls;  // accumulated while profiling
-  struct Rec { cudaEvent_t a, b; double flops; int kind; };
+  struct Rec {
+    cudaEvent_t a, b;
+    double flops;
+    int kind;
+    bool own_a = true, own_b = true;  // events shared between records belong to one of them
+  };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
 };
@@ -173,6 +183,36 @@ static void prof_end(ipeps_ctm h, cudaEvent_t a, double flops, int kind) {
   cudaEvent_t b = pool_event(h);
   cudaEventRecord(b, h->stream);
   h->recs.push_back({a, b, flops, kind});
+}
+
+// Tensor-core products, timed apart from their operand packing: kind 5 the
+// main kernel of wide products (more than 256 output rows: enlarged corners,
+// absorption, readouts; algorithmic flops), kind 6 the main kernel of thin
+// products (at most 256 rows: the range finder and projector assembly;
+// algorithmic flops) and kind 7 the same launches as kind 6 with the bytes the
+// kernel must move (packed operands read once, output written once), kind 8
+// the split-K reductions (bytes of partials read and output written).
+static TcProbe* tc_probe_begin(ipeps_ctm h, TcProbe* p) {
+  if (!h->profiling) return nullptr;
+  for (int i = 0; i < 3; ++i) p->ev[i] = pool_event(h);
+  return p;
+}
+static void tc_probe_end(ipeps_ctm h, TcProbe* p, int M, int N, int K) {
+  if (!p) return;
+  const double flops = 8.0 * (double)M * (double)N * (double)K;
+  const bool thin = M <= 256;
+  h->recs.push_back({p->ev[0], p->ev[1], flops, thin ? 6 : 5, true, true});
+  if (thin) {
+    const double ab = (double)p->Mp * p->Krp * p->elem_bytes * p->parts;
+    const double bb = (double)p->Nrp * p->Krp * p->elem_bytes * p->parts;
+    const double out = p->splits > 1 ? (double)p->splits * p->Mp * p->Nrp * 4.0 : (double)M * N * 16.0;
+    h->recs.push_back({p->ev[0], p->ev[1], ab + bb + out, 7, false, false});
+  }
+  if (p->splits > 1)
+    h->recs.push_back({p->ev[1], p->ev[2], (double)p->splits * p->Mp * p->Nrp * 4.0 + (double)M * N * 16.0, 8,
+                       false, true});
+  else
+    h->pool.push_back(p->ev[2]);
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -260,7 +300,7 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   const long long rdm = 6 * (long long)chi * chi * D2 * D2 * d + 3 * (long long)chi * chi * D2 * d * d;
   s.scratch = std::max(6 * s.Q, rdm) + (1 << 16);
   // packed tensor-core operands (padded to 128 x 256 tiles) and split-K partials
-  if (prec != IPEPS_PREC_FP64) s.scratch = s.scratch * 3 / 2 + (1 << 22);
+  if (prec != IPEPS_PREC_FP64) s.scratch = s.scratch * (prec == IPEPS_PREC_BF16X6 ? 2 : 3) / 2 + (1 << 22);
   size_t tot = 0;
   auto add = [&](long long n, size_t el) { tot += align_up((size_t)n * el); };
   for (int i = 0; i < 2 * 4 * ntens; ++i) add(s.tens, 16);
@@ -375,8 +415,12 @@ static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cp
                                       long long ldc, cplx alpha) {
   // small products (a few tiles of zero padding would dominate) stay FP64
   if (h->opt.prec != IPEPS_PREC_FP64 && M >= 64 && N >= 32 && K >= 16) {
+    TcProbe pr;
+    TcProbe* p = tc_probe_begin(h, &pr);
     cudaError_t e = tc_zgemm(h->stream, (int)h->opt.prec, M, N, K, alpha, A, lda, opA, B, ldb,
-                             opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top, h->tuner);
+                             opB, C, ldc, h->scratch, h->scratch_elems, h->scratch_top, &h->st->tc_timeouts,
+                             h->tuner, nullptr, p);
+    if (e == cudaSuccess) tc_probe_end(h, p, M, N, K);
     if (e == cudaErrorNotSupported) return fail(IPEPS_EUNSUPPORTED, "tensor-core GEMM unavailable for this shape");
     CK(e);
     return IPEPS_OK;
@@ -573,10 +617,13 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
       if (VB) xa = *VB; else plain_view(pb, ldb, opb ^ OP_T, (int)N, (int)Kd, false, &xa);
       if (VA) xb = *VA; else plain_view(pa, lda, opa ^ OP_T, (int)M, (int)Kd, true, &xb);
       prof_begin(h, &ev);
+      TcProbe pr;
+      TcProbe* p = tc_probe_begin(h, &pr);
       cudaError_t e = tc_zgemm_views(h->stream, (int)h->opt.prec, (int)N, (int)M, (int)Kd, alpha, &xa, nullptr, 0, 0,
                                      &xb, nullptr, 0, 0, C.p, M, h->scratch, h->scratch_elems, h->scratch_top,
-                                     h->tuner);
+                                     &h->st->tc_timeouts, h->tuner, p);
       prof_end(h, ev, 8.0 * (double)M * (double)N * (double)Kd, 0);
+      if (e == cudaSuccess) tc_probe_end(h, p, (int)N, (int)M, (int)Kd);
       CK(e);
     } else {
       cplx* out = C.p;
@@ -587,10 +634,13 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
         out = t;
       }
       prof_begin(h, &ev);
+      TcProbe pr;
+      TcProbe* p = tc_probe_begin(h, &pr);
       cudaError_t e = tc_zgemm_views(h->stream, (int)h->opt.prec, (int)M, (int)N, (int)Kd, direct ? alpha : ONE, VA,
                                      pa, lda, opa, VB, pb, ldb, opb, out, N, h->scratch, h->scratch_elems,
-                                     h->scratch_top, h->tuner);
+                                     h->scratch_top, &h->st->tc_timeouts, h->tuner, p);
       prof_end(h, ev, 8.0 * (double)M * (double)N * (double)Kd, 0);
+      if (e == cudaSuccess) tc_probe_end(h, p, (int)M, (int)N, (int)Kd);
       CK(e);
       if (!direct) {
         std::string have = Mo + No;
@@ -734,7 +784,7 @@ static ipeps_status validate(const ipeps_cell* c, const ipeps_options* o) {
   if (o->chi > 1024) return fail(IPEPS_EINVAL, "chi > 1024");
   if (o->rsvd_oversample < 0 || o->rsvd_power < 0) return fail(IPEPS_EINVAL, "bad rsvd options");
   if (o->chi + o->rsvd_oversample > 1024) return fail(IPEPS_EINVAL, "chi + oversample > 1024");
-  if (o->prec < IPEPS_PREC_FP64 || o->prec > IPEPS_PREC_BF16X3) return fail(IPEPS_EINVAL, "bad prec");
+  if (o->prec < IPEPS_PREC_FP64 || o->prec > IPEPS_PREC_BF16X6) return fail(IPEPS_EINVAL, "bad prec");
   if (o->jacobi_max_sweeps < 1) return fail(IPEPS_EINVAL, "jacobi_max_sweeps >= 1");
   return IPEPS_OK;
 }
@@ -791,12 +841,11 @@ static ipeps_status check_status(ipeps_ctm h) {
     h->jac_calls += st.jacobi_calls;
   }
   if (st.nonfinite) return fail(IPEPS_ENUMERIC, "non-finite or zero norm met (%d times)", st.nonfinite);
+  if (st.barrier_timeouts)  // before the sweep budget: a CTA that gave up leaves its SVD unconverged too
+    return fail(IPEPS_ETIMEOUT, "%d grid-barrier waits of the Jacobi SVD ran out", st.barrier_timeouts);
   if (st.jacobi_unconverged)
     return fail(IPEPS_ETIMEOUT, "%d Jacobi SVDs hit the sweep budget", st.jacobi_unconverged);
-  if (h->opt.prec != IPEPS_PREC_FP64) {
-    const int n = tc_take_errors();
-    if (n) return fail(IPEPS_ETIMEOUT, "%d tensor-core GEMM waits timed out", n);
-  }
+  if (st.tc_timeouts) return fail(IPEPS_ETIMEOUT, "%d tensor-core GEMM waits timed out", st.tc_timeouts);
   return IPEPS_OK;
 }
 
@@ -812,7 +861,20 @@ static ipeps_status reset_status(ipeps_ctm h) {
 
 // The second lane's stream and its fork/join events: each released if it was
 // created (creation can stop part way, leaving has_alt false).
+static void drop_graphs(ipeps_ctm h) {
+  for (int d = 0; d < 5; ++d)
+    if (h->exec[d]) {
+      cudaGraphExecDestroy(h->exec[d]);
+      h->exec[d] = nullptr;
+    }
+}
+
 static void release_lane(ipeps_ctm h) {
+  drop_graphs(h);
+  if (h->cap_stream) {
+    cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+  }
   if (h->alt.stream) {
     cudaStreamSynchronize(h->alt.stream);
     cudaStreamDestroy(h->alt.stream);
@@ -836,7 +898,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   h->dtype = c->dtype;
   h->opt = *o;
   if (!(h->opt.svd_cutoff > 0.0))  // automatic: above the noise floor of the contraction arithmetic
-    h->opt.svd_cutoff = o->prec == IPEPS_PREC_FP64 ? 1e-8 : (o->prec == IPEPS_PREC_BF16X3 ? 1e-6 : 1e-5);
+    h->opt.svd_cutoff = o->prec == IPEPS_PREC_FP64 ? 1e-8 : (o->prec == IPEPS_PREC_TF32 ? 1e-5 : 1e-6);
   h->stream = (cudaStream_t)o->stream;
   Sizes sz = plan_sizes(h->Lx, h->Ly, h->d, h->D, h->chi, h->k, h->ntens, o->prec);
   if (o->workspace) {
@@ -923,6 +985,10 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess)
     h->has_alt = true;
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->cap_stream = nullptr;  // moves then run without graphs
+  }
   // host -> device copies of the tensors (real inputs promoted to complex)
   std::vector<double> buf;
   for (int t = 0; t < h->ntens && st == IPEPS_OK; ++t) {
@@ -954,8 +1020,8 @@ extern "C" ipeps_status ipeps_ctm_profile(ipeps_ctm h, int enable) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
   CK(cudaStreamSynchronize(h->stream));
   for (auto& r : h->recs) {
-    h->pool.push_back(r.a);
-    h->pool.push_back(r.b);
+    if (r.own_a) h->pool.push_back(r.a);
+    if (r.own_b) h->pool.push_back(r.b);
   }
   h->recs.clear();
   h->profiling = enable != 0;
@@ -988,8 +1054,8 @@ extern "C" void ipeps_ctm_destroy(ipeps_ctm h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (auto& r : h->recs) {
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+    if (r.own_a) cudaEventDestroy(r.a);
+    if (r.own_b) cudaEventDestroy(r.b);
   }
   for (auto e : h->pool) cudaEventDestroy(e);
   release_lane(h);
@@ -1107,9 +1173,13 @@ static ipeps_status thin_mul_packed(ipeps_ctm h, const cplx* in, int opin, cplx*
                                     bool conj_out) {
   cudaEvent_t a = nullptr;
   prof_begin(h, &a);
+  TcProbe pr;
+  TcProbe* p = tc_probe_begin(h, &pr);
   cudaError_t e = tc_zgemm_packed(h->stream, (int)h->opt.prec, rows, ONE, in, h->K, opin, h->Qp[q][v], out, h->K,
-                                  conj_out, h->scratch, h->scratch_elems, h->scratch_top, h->tuner);
+                                  conj_out, h->scratch, h->scratch_elems, h->scratch_top, &h->st->tc_timeouts,
+                                  h->tuner, p);
   prof_end(h, a, 8.0 * (double)rows * (double)h->K * (double)h->K, 0);
+  if (e == cudaSuccess) tc_probe_end(h, p, rows, h->K, h->K);
   CK(e);
   return IPEPS_OK;
 }
@@ -1160,7 +1230,7 @@ static ipeps_status orth(ipeps_ctm h, cplx* G) {
   cudaEvent_t a = nullptr;
   prof_begin(h, &a);
   CK(jacobi_rows(h->stream, G, h->k, h->K, h->K, nullptr, h->sigma, h->opt.jacobi_max_sweeps,
-                 h->dwork, h->counters, h->st));
+                 h->dwork, h->counters, h->st, nullptr, 0, h->opt.wait_cycles));
   prof_end(h, a, 0.0, 1);
   CK(orth_rows_finish(h->stream, G, h->k, h->K, h->K, h->sigma, h->opt.orth_tol));
   return IPEPS_OK;
@@ -1241,7 +1311,7 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
     cplx* rotlog = scratch_alloc(h, nlog);
     if (!rotlog) return fail(IPEPS_ENOMEM, "scratch exhausted (rotation log)");
     CK(jacobi_rows(h->stream, Rt, k, k, k, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                   h->counters, h->st, rotlog, nlog));
+                   h->counters, h->st, rotlog, nlog, h->opt.wait_cycles));
     prof_end(h, a, 0.0, 1);
   }
   // out = V^T Wt  (rows (W v_i)^T)
@@ -1278,7 +1348,7 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
     cudaEvent_t a = nullptr;
     prof_begin(h, &a);
     CK(jacobi_rows(h->stream, Zt, k, K, K, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                   h->counters, h->st));
+                   h->counters, h->st, nullptr, 0, h->opt.wait_cycles));
     prof_end(h, a, 0.0, 1);
     Wrot = Zt;
   } else {
@@ -1401,10 +1471,56 @@ ipeps_status ctm_enqueue_move(ipeps_ctm h, int dir) {
   return left_move(h, dir);
 }
 
+// Capture the move (or sweep) `dir` as a CUDA graph: the work is enqueued on
+// the private capture stream (the second projector lane joins the capture
+// through the fork/join events), so the graph can be launched on any stream,
+// the legacy default stream included.  Every buffer a move touches keeps its
+// address for the life of the handle, so the graph stays valid until the
+// tile choices change (autotuning), which drops it.
+static ipeps_status capture_move(ipeps_ctm h, int dir) {
+  CK(kernels_init());
+  CK(fp64_cluster_init());
+  if (h->opt.prec != IPEPS_PREC_FP64) CK(tc_init());
+  cudaStream_t user = h->stream;
+  const uint64_t l0 = launch_counter();
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+  h->stream = h->cap_stream;
+  ipeps_status st = ctm_enqueue_move(h, dir);
+  h->stream = user;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  h->scratch_top = 0;
+  h->alt.scratch_top = 0;
+  h->exec_kernels[dir] = (int)(launch_counter() - l0);
+  count_launch(-h->exec_kernels[dir]);  // counted at each launch instead
+  if (st != IPEPS_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st != IPEPS_OK) return st;
+    return fail(IPEPS_ECUDA, "move capture: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&h->exec[dir], g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    h->exec[dir] = nullptr;
+    return fail(IPEPS_ECUDA, "move graph: %s", cudaGetErrorString(e2));
+  }
+  return IPEPS_OK;
+}
+
 extern "C" ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
   if (dir < 0 || dir > 4 || count < 0) return fail(IPEPS_EINVAL, "bad dir/count");
   CKS(reset_status(h));
+  // graphs unless per-kernel timing is on (its events are per launch)
+  if (count > 0 && h->cap_stream && !h->profiling) {
+    if (!h->exec[dir]) CKS(capture_move(h, dir));
+    for (int n = 0; n < count; ++n) {
+      CK(cudaGraphLaunch(h->exec[dir], h->stream));
+      count_launch(h->exec_kernels[dir]);
+    }
+    return check_status(h);
+  }
   for (int n = 0; n < count; ++n) CKS(ctm_enqueue_move(h, dir));
   return check_status(h);
 }
@@ -1419,6 +1535,7 @@ extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
     if (!h->tuner) return fail(IPEPS_ECUDA, "tuner events");
     h->own_tuner = true;
   }
+  drop_graphs(h);  // captured with the previous tile choices
   // snapshot of the environment, restored after the tuning sweep
   const int ncell = h->Lx * h->Ly;
   const size_t cb = (size_t)h->chi * h->chi * sizeof(cplx), tb = (size_t)h->chi * h->D2 * h->chi * sizeof(cplx);
@@ -1456,8 +1573,14 @@ cudaStream_t ctm_stream(ipeps_ctm h) { return h->stream; }
 ipeps_status ctm_reset_status(ipeps_ctm h) { return reset_status(h); }
 ipeps_status ctm_check_status(ipeps_ctm h) { return check_status(h); }
 ipeps_status ctm_reinit_env(ipeps_ctm h) { return trace_init_env(h); }
-void ctm_set_tuner(ipeps_ctm h, TcTuner* t) { h->tuner = t; }
-void ctm_set_sequential_cuts(ipeps_ctm h, bool on) { h->no_alt = on; }
+void ctm_set_tuner(ipeps_ctm h, TcTuner* t) {
+  drop_graphs(h);
+  h->tuner = t;
+}
+void ctm_set_sequential_cuts(ipeps_ctm h, bool on) {
+  if (h->no_alt != on) drop_graphs(h);
+  h->no_alt = on;
+}
 
 // ---------------------------------------------------------------------------
 // spectra / convergence
@@ -1471,7 +1594,7 @@ static ipeps_status spectra_device(ipeps_ctm h, double* host) {
     for (int i = 0; i < ncell; ++i) {
       CK(cudaMemcpyAsync(w, h->C[j][i], (size_t)c * c * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
       CK(jacobi_rows(h->stream, w, c, c, c, nullptr, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                     h->counters, h->st));
+                     h->counters, h->st, nullptr, 0, h->opt.wait_cycles));
       CK(select_top(h->stream, h->sigma, c, c, 0.0, h->perm, h->s_sel));
       CK(cudaMemcpyAsync(host + (size_t)(j * ncell + i) * c, h->s_sel, c * sizeof(double),
                          cudaMemcpyDeviceToHost, h->stream));
@@ -1949,7 +2072,7 @@ extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* e
   // lambda_i w_i^H; G = (rows)^H scaled by sigma_i^(-1/2) column-wise.
   CK(cudaMemcpyAsync(G, sL, n * n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
   CK(jacobi_rows(h->stream, G, nn, nn, nn, nullptr, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                 h->counters, h->st));
+                 h->counters, h->st, nullptr, 0, h->opt.wait_cycles));
   // Gm = G^H (n x n), columns scaled
   {
     const int dims[2] = {nn, nn}, perm[2] = {1, 0};
@@ -1962,7 +2085,7 @@ extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* e
   CK(zgemm(h->stream, nn, nn, nn, ONE, sR, nn, OP_N, Hm, nn, OP_N, ZERO, G, nn));
   CK(zgemm(h->stream, nn, nn, nn, ONE, Hm, nn, OP_H, G, nn, OP_N, ZERO, Vt, nn));
   CK(jacobi_rows(h->stream, Vt, nn, nn, nn, nullptr, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                 h->counters, h->st));
+                 h->counters, h->st, nullptr, 0, h->opt.wait_cycles));
   bnd::launch_spectrum_finish(h->stream, h->sigma, nn, h->s_sel, h->dacc);
   count_launch();
   CK(cudaGetLastError());
@@ -2183,8 +2306,10 @@ extern "C" ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double*
 
 extern "C" ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K, const double* A, int opA,
                                          const double* B, int opB, double* C) {
-  if (prec != IPEPS_PREC_TF32 && prec != IPEPS_PREC_BF16X3) return fail(IPEPS_EINVAL, "tile choice needs TF32/BF16X3");
-  if ((bn != 128 && bn != 256) || splits < 1) return fail(IPEPS_EINVAL, "bad tile choice");
+  if (prec != IPEPS_PREC_TF32 && prec != IPEPS_PREC_BF16X3 && prec != IPEPS_PREC_BF16X6)
+    return fail(IPEPS_EINVAL, "tile choice needs TF32/BF16X3/BF16X6");
+  if ((bn != 128 && bn != 256) || splits < 1 || (prec == IPEPS_PREC_BF16X6 && bn != 128))
+    return fail(IPEPS_EINVAL, "bad tile choice");
   const TcChoice c{bn, splits};
   return zgemm_host(prec, M, N, K, A, opA, B, opB, C, &c);
 }
@@ -2192,14 +2317,17 @@ extern "C" ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, in
 static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
                                double* C, const TcChoice* force) {
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return fail(IPEPS_EINVAL, "bad GEMM arguments");
-  if (prec < 0 || prec > 2 || opA < 0 || opA > 3 || opB < 0 || opB > 3) return fail(IPEPS_EINVAL, "bad prec/op");
+  if (prec < 0 || prec > 3 || opA < 0 || opA > 3 || opB < 0 || opB > 3) return fail(IPEPS_EINVAL, "bad prec/op");
   const size_t na = (size_t)M * K, nb = (size_t)K * N, nc = (size_t)M * N;
   const size_t scratch_elems = 4 * (na + nb) + 8 * nc + (force ? 4 * (size_t)force->splits * (nc + 256 * (size_t)M) : 0) +
                                (1 << 20);
   cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dS = nullptr;
+  int* dT = nullptr;  // tensor-core wait timeouts of this call
   ipeps_status st = IPEPS_OK;
-  auto cleanup = [&]() { cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dS); };
-  cudaError_t e = dev_alloc((void**)&dA, na * sizeof(cplx));
+  auto cleanup = [&]() { cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dS); cudaFree(dT); };
+  cudaError_t e = dev_alloc((void**)&dT, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(dT, 0, sizeof(int));
+  if (e == cudaSuccess) e = dev_alloc((void**)&dA, na * sizeof(cplx));
   if (e == cudaSuccess) e = dev_alloc((void**)&dB, nb * sizeof(cplx));
   if (e == cudaSuccess) e = dev_alloc((void**)&dC, nc * sizeof(cplx));
   if (e == cudaSuccess && prec) e = dev_alloc((void**)&dS, scratch_elems * sizeof(cplx));
@@ -2208,14 +2336,16 @@ static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, i
   if (e != cudaSuccess) { cleanup(); return fail(IPEPS_ECUDA, "zgemm setup: %s", cudaGetErrorString(e)); }
   const long long lda = (opA & OP_T) ? M : K, ldb = (opB & OP_T) ? K : N;
   if (prec == 0) e = zgemm(0, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, ZERO, dC, N);
-  else e = tc_zgemm(0, prec, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, dC, N, dS, (long long)scratch_elems, 0,
+  else e = tc_zgemm(0, prec, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, dC, N, dS, (long long)scratch_elems, 0, dT,
                     nullptr, force);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(C, dC, nc * sizeof(cplx), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "zgemm: %s", cudaGetErrorString(e));
   if (st == IPEPS_OK && prec) {
-    const int n = tc_take_errors();
-    if (n) st = fail(IPEPS_ETIMEOUT, "%d tensor-core GEMM waits timed out", n);
+    int n = 0;
+    e = cudaMemcpy(&n, dT, sizeof n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "zgemm: %s", cudaGetErrorString(e));
+    else if (n) st = fail(IPEPS_ETIMEOUT, "%d tensor-core GEMM waits timed out", n);
   }
   cleanup();
   return st;

@@ -50,6 +50,8 @@ struct DevStatus {
   int nonfinite;           // a NaN/Inf met in a norm
   int jacobi_sweeps;       // sweeps used by all Jacobi calls (accounting)
   int jacobi_calls;
+  int tc_timeouts;         // bounded waits inside tensor-core GEMMs that ran out
+  int barrier_timeouts;    // grid-barrier waits (small-row Jacobi) that ran out
 };
 
 // ---------------------------------------------------------------------------
@@ -102,9 +104,13 @@ cudaError_t set_zero(cudaStream_t s, cplx* x, long long n);
 // work: 1 double of scratch.
 // rotlog (optional, jacobi_log_elems(n, max_sweeps) complex slots): lets the
 // cluster path rebuild Vt from logged rotations instead of holding it.
+// wait_cycles: limit of each grid-barrier wait of the small-row kernel (<= 0:
+// about 2 s of clock); a wait that runs out is counted in st->barrier_timeouts
+// and its CTA stops.
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
-                        DevStatus* st, cplx* rotlog = nullptr, long long rotlog_elems = 0);
+                        DevStatus* st, cplx* rotlog = nullptr, long long rotlog_elems = 0,
+                        long long wait_cycles = 0);
 // rows of G scaled to unit norm where sigma > tol*max(sigma), zero otherwise
 cudaError_t orth_rows_finish(cudaStream_t s, cplx* G, int n, int m, long long ldg,
                              const double* sigma, double tol);

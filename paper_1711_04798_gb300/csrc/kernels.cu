@@ -288,10 +288,10 @@ __global__ void __launch_bounds__(JAC_THREADS)
 // per CTA, warp-shuffle reductions only, and a light generation barrier
 // between rounds (bounded spin; all CTAs are co-resident by cooperative launch).
 // ---------------------------------------------------------------------------
-constexpr long long BARRIER_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long BARRIER_WAIT_CYCLES = 4000000000LL;  // default limit: ~2 s at 2 GHz
 
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
-                                             unsigned& my_gen) {
+                                             unsigned& my_gen, long long limit) {
   __syncwarp();
   bool ok = true;
   if ((threadIdx.x & 31) == 0) {
@@ -304,7 +304,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
     } else {
       const long long t0 = clock64();
       while (*gen == g0) {
-        if (clock64() - t0 > BARRIER_WAIT_CYCLES) { ok = false; break; }
+        if (clock64() - t0 > limit) { ok = false; break; }
       }
     }
     __threadfence();
@@ -324,7 +324,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(32)
     jacobi_small_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt,
                         int max_sweeps, double tol, int* counters, double* fro2, unsigned* bar,
-                        DevStatus* st) {
+                        DevStatus* st, long long wait_limit) {
   const int lane = threadIdx.x;
   unsigned my_gen = 0;
   const unsigned nb = gridDim.x;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(32)
     v = warp_sum(v);
     if (lane == 0) atomicAdd(fro2, v);
   }
-  alive = grid_barrier(bar, bar + 1, nb, my_gen);
+  alive = grid_barrier(bar, bar + 1, nb, my_gen, wait_limit);
   const double negligible = *((volatile double*)fro2) * 1e-30;
   const int np = (n + 1) & ~1;
   const int rounds = np - 1, npairs = np / 2;
@@ -395,21 +395,22 @@ __global__ void __launch_bounds__(32)
           if (lane == 0) atomicAdd(&counters[sweep & 1], 1);
         }
       }
-      alive = grid_barrier(bar, bar + 1, nb, my_gen);
+      alive = grid_barrier(bar, bar + 1, nb, my_gen, wait_limit);
     }
     if (!alive) break;
     const int cnt = *((volatile int*)&counters[sweep & 1]);
     if (blockIdx.x == 0 && lane == 0) counters[(sweep + 1) & 1] = 0;
-    alive = grid_barrier(bar, bar + 1, nb, my_gen);
+    alive = grid_barrier(bar, bar + 1, nb, my_gen, wait_limit);
     if (cnt == 0) {
       converged = true;
       break;
     }
   }
+  if (!alive && lane == 0) atomicAdd(&st->barrier_timeouts, 1);  // this CTA gave up waiting
   if (blockIdx.x == 0 && lane == 0) {
     atomicAdd(&st->jacobi_calls, 1);
     atomicAdd(&st->jacobi_sweeps, converged ? sweep + 1 : max_sweeps);
-    if (!converged) atomicAdd(&st->jacobi_unconverged, 1);
+    if (!converged && alive) atomicAdd(&st->jacobi_unconverged, 1);
   }
 }
 
@@ -619,7 +620,7 @@ cudaError_t kernels_init() {
 
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
-                        DevStatus* st, cplx* rotlog, long long rotlog_elems) {
+                        DevStatus* st, cplx* rotlog, long long rotlog_elems, long long wait_cycles) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
   if ((e = kernels_init()) != cudaSuccess) return e;
@@ -650,7 +651,8 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
     int grid = npairs < max_small ? npairs : max_small;
     double tol = (double)m * 2.220446049250313e-16;
     unsigned* bar = (unsigned*)(counters + 2);
-    void* args[] = {&G, &n, &m, &ldg, &Vt, &max_sweeps, &tol, &counters, &work, &bar, &st};
+    long long limit = wait_cycles > 0 ? wait_cycles : BARRIER_WAIT_CYCLES;
+    void* args[] = {&G, &n, &m, &ldg, &Vt, &max_sweeps, &tol, &counters, &work, &bar, &st, &limit};
     e = cudaLaunchCooperativeKernel((const void*)jacobi_small_kernel, dim3(grid), dim3(32), args, 0, s);
     count_launch();
     if (e != cudaSuccess) return e;

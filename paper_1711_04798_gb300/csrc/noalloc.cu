@@ -7,7 +7,7 @@
 // ipeps_corner_spectrum_noalloc computes the singular values of one chi x chi
 // corner matrix with the same Jacobi SVD kernel as ipeps_ctm_spectra, keeping
 // every intermediate in the fixed file-scope device array below.
-#include <mutex>
+#include <cstdio>
 
 #include "../../include/ipeps_ctm.h"
 #include "ctm_internal.h"
@@ -31,10 +31,6 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_STATUS + 256;  // about 1.01 MiB
 // holds its own copy until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-unsigned char* g_scratch_addr[MAX_DEVICES] = {nullptr};
-std::mutex g_setup_mutex;
-
 thread_local char g_msg_buf[256];  // formatted here, then handed to ipeps_last_error()
 
 // s_out[a] = s_sel[a] / s_sel[0] (zero when s_sel[0] == 0)
@@ -43,34 +39,20 @@ __global__ void normalise_by_first_kernel(const double* s_sel, int n, double* s_
   for (int a = threadIdx.x; a < n; a += blockDim.x) s_out[a] = s0 > 0.0 ? s_sel[a] / s0 : 0.0;
 }
 
-// device address of the scratch array for the current device (set-up on the
-// first call on each device, with that device current)
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in; its device address is looked
+// up on every call, with the caller's device current, so that it stays right
+// after a device reset or on a context created later (the first lookup on a
+// device also loads this library's device code there).
 ipeps_status scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    snprintf(g_msg_buf, sizeof g_msg_buf, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    snprintf(g_msg_buf, sizeof g_msg_buf, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
     set_last_error_message(g_msg_buf);
     return IPEPS_ECUDA;
   }
-  if (dev < 0 || dev >= MAX_DEVICES) {
-    snprintf(g_msg_buf, sizeof g_msg_buf, "device ordinal %d beyond %d", dev, MAX_DEVICES);
-    set_last_error_message(g_msg_buf);
-    return IPEPS_EUNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      snprintf(g_msg_buf, sizeof g_msg_buf, "cudaGetSymbolAddress(scratch) failed: %s",
-               cudaGetErrorString(e));
-      set_last_error_message(g_msg_buf);
-      return IPEPS_ECUDA;
-    }
-    g_scratch_addr[dev] = (unsigned char*)p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = (unsigned char*)p;
   return IPEPS_OK;
 }
 

@@ -5,9 +5,11 @@
 //     Ar[m, 2k+c]      = (Re, Im)[c] of A[m,k]                       (M x 2K)
 //     Br^T[2n+b, 2k+a] = [[Re, Im], [-Im, Re]][a][b] of B[k,n]        (2N x 2K)
 //     Cr[m, 2n+b]      = (Re, Im)[b] of C[m,n]
-// Both packed operands are K-major, in TF32 (one array) or in BF16 hi/lo
-// pairs (x = hi + lo, three products hi*hi + hi*lo + lo*hi accumulated in
-// FP32 in tensor memory).  One CTA computes a 128 x 256 tile of Cr: warp 0
+// Both packed operands are K-major, in TF32 (one array), in BF16 hi/lo pairs
+// (x = hi + lo, three products hi*hi + hi*lo + lo*hi accumulated in FP32 in
+// tensor memory: 16 significand bits per operand) or in BF16 hi/mid/lo
+// triples (x = p0 + p1 + p2, the six products p_i q_j with i + j <= 2: 24
+// significand bits, the FP32 class).  One CTA computes a 128 x BN tile of Cr: warp 0
 // issues the TMA loads (128-byte swizzle), warp 1 issues tcgen05.mma, all four
 // warps drain the accumulator with tcgen05.ld.  Thin products (few output
 // tiles) split K over the grid's z dimension into FP32 partials, summed in a
@@ -21,28 +23,31 @@
 #include <algorithm>
 #include <map>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 namespace {
 
 constexpr int BM = 128, NPAD = 256, NTHREADS = 128;  // N of every packed B operand padded to NPAD
-constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2;
+constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2, PREC_BF16X6 = 3;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
 
-__device__ int g_tc_errors;  // timeouts of bounded waits (read by tc_take_errors)
 
 // Tile configuration: 128 x BN output tile (BN = 128 or 256), 128-byte k-blocks,
-// as many pipeline stages as fit in ~192 KB of shared memory.
+// as many pipeline stages as fit in ~192 KB of shared memory.  NOPS parts per
+// operand (1 TF32, 2 BF16 hi/lo, 3 BF16 hi/mid/lo); BF16x6 runs BN = 128 only
+// (two stages of three A and three B parts).
 template <int PREC, int BN_>
 struct Cfg {
   static constexpr int BN = BN_;
   static constexpr int ELEM = PREC == PREC_TF32 ? 4 : 2;
   static constexpr int BK = 128 / ELEM;                 // elements per k-block (128 bytes)
-  static constexpr int NOPS = PREC == PREC_TF32 ? 1 : 2;
+  static constexpr int NOPS = PREC == PREC_TF32 ? 1 : (PREC == PREC_BF16X3 ? 2 : 3);
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+  static_assert(PREC != PREC_BF16X6 || BN == 128, "BF16x6 tiles are 128 wide");
   static constexpr int UMMA_K = PREC == PREC_TF32 ? 8 : 16;  // K of one MMA
   static constexpr int KSTEPS = BK / UMMA_K;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
@@ -139,10 +144,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 template <int PREC, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                   const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+                   const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+                   const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
                    int kb_total, int kb_per_split, int M, int Nr, cplx alpha, cplx* __restrict__ C,
                    long long ldc, float* __restrict__ partial, int Nrp, long long pstride, int conj_out,
-                   int unit_alpha) {
+                   int unit_alpha, int* __restrict__ timeouts) {
   using K_ = Cfg<PREC, BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -176,41 +182,63 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // producer: one k-block per stage
+    int issued = 0;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % K_::STAGES, r = i / K_::STAGES;
       if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
-        atomicAdd(&g_tc_errors, 1);
+        atomicAdd(timeouts, 1);
         break;
       }
       unsigned char* st = smem + s * K_::STAGE_BYTES;
       mbar_expect_tx(&full[s], K_::STAGE_BYTES);
       const int kx = (kb0 + i) * K_::BK;
+      unsigned char* sb = st + K_::NOPS * K_::A_BYTES;
       tma_load_2d(st, &mA0, &full[s], kx, m_tile * BM);
-      if (K_::NOPS == 2) tma_load_2d(st + K_::A_BYTES, &mA1, &full[s], kx, m_tile * BM);
-      tma_load_2d(st + K_::NOPS * K_::A_BYTES, &mB0, &full[s], kx, n_tile * BN);
-      if (K_::NOPS == 2)
-        tma_load_2d(st + K_::NOPS * K_::A_BYTES + K_::B_BYTES, &mB1, &full[s], kx, n_tile * BN);
+      tma_load_2d(sb, &mB0, &full[s], kx, n_tile * BN);
+      if (K_::NOPS >= 2) {
+        tma_load_2d(st + K_::A_BYTES, &mA1, &full[s], kx, m_tile * BM);
+        tma_load_2d(sb + K_::B_BYTES, &mB1, &full[s], kx, n_tile * BN);
+      }
+      if (K_::NOPS == 3) {
+        tma_load_2d(st + 2 * K_::A_BYTES, &mA2, &full[s], kx, m_tile * BM);
+        tma_load_2d(sb + 2 * K_::B_BYTES, &mB2, &full[s], kx, n_tile * BN);
+      }
+      issued = i + 1;
     }
+    // the last loads of every stage have landed before the CTA can leave
+    // (they are what an MMA issuer that gave up may not have waited for)
+    for (int i = max(0, issued - K_::STAGES); i < issued; ++i)
+      if (!mbar_wait(&full[i % K_::STAGES], (i / K_::STAGES) & 1)) atomicAdd(timeouts, 1);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     for (int i = 0; i < nkb; ++i) {
       const int s = i % K_::STAGES, r = i / K_::STAGES;
       if (!mbar_wait(&full[s], r & 1)) {
-        atomicAdd(&g_tc_errors, 1);
+        atomicAdd(timeouts, 1);
         break;
       }
       fence_after();
       const uint32_t base = smem_u32(smem + s * K_::STAGE_BYTES);
-      const uint32_t a0 = base, a1 = base + K_::A_BYTES;
-      const uint32_t b0 = base + K_::NOPS * K_::A_BYTES, b1 = b0 + K_::B_BYTES;
+      const uint32_t a0 = base, a1 = base + K_::A_BYTES, a2 = base + 2 * K_::A_BYTES;
+      const uint32_t b0 = base + K_::NOPS * K_::A_BYTES, b1 = b0 + K_::B_BYTES, b2 = b0 + 2 * K_::B_BYTES;
 #pragma unroll
       for (int j = 0; j < K_::KSTEPS; ++j) {
         const uint32_t ko = j * 32;  // bytes of one MMA's K inside the 128-byte row
         const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
-        umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), acc);
-        if (K_::NOPS == 2) {
+        if (K_::NOPS == 3) {
+          // smallest parts first: p_i q_j with i + j = 2, then 1, then 0
+          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b2 + ko), acc);
+          umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b1 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc(a2 + ko), sdesc(b0 + ko), 1u);
           umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
           umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), 1u);
+        } else {
+          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), acc);
+          if (K_::NOPS == 2) {
+            umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
+            umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+          }
         }
       }
       umma_commit(&empty[s]);  // frees the stage when these MMAs are done
@@ -221,7 +249,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
   const bool ready = mbar_wait(accb, 0);
-  if (!ready && lane == 0) atomicAdd(&g_tc_errors, 1);
+  if (!ready && lane == 0) atomicAdd(timeouts, 1);
   __syncwarp();
   fence_after();
   if (ready) {
@@ -310,10 +338,37 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return u;
 }
 
-__device__ __forceinline__ void store_pair(int prec, long long e, double x0, double x1, void* o0, void* o1) {
+// binary64 -> binary32 rounded to nearest (ties away from zero) on the
+// integer pipe: half an FP32 ulp is added to the magnitude bits before the
+// truncation of d2f_bits (a carry into the exponent is the correct rounding).
+__device__ __forceinline__ float d2f_rn_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  if (mag >= 0x7FF0000000000000ull) return d2f_bits(x);  // Inf / NaN
+  return d2f_bits(__longlong_as_double((long long)((b & 0x8000000000000000ull) | (mag + (1ull << 28)))));
+}
+
+// x = p0 + p1 + p2 exactly for the FP32 value f (24 significand bits): each
+// part is the BF16 rounding of the remainder the previous parts leave
+__device__ __forceinline__ void split3(float f, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+  p0 = __float2bfloat16_rn(f);
+  const float r1 = f - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r1);
+  p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+}
+
+__device__ __forceinline__ void store_pair(int prec, long long e, double x0, double x1, void* o0, void* o1,
+                                           void* o2) {
   // two consecutive packed reals at element e (e even)
   if (prec == PREC_TF32) {
     ((uint2*)o0)[e >> 1] = make_uint2(to_tf32(d2f_bits(x0)), to_tf32(d2f_bits(x1)));
+  } else if (prec == PREC_BF16X6) {
+    __nv_bfloat16 a0, a1, a2, c0, c1, c2;
+    split3(d2f_rn_bits(x0), a0, a1, a2);
+    split3(d2f_rn_bits(x1), c0, c1, c2);
+    ((__nv_bfloat162*)o0)[e >> 1] = __halves2bfloat162(a0, c0);
+    ((__nv_bfloat162*)o1)[e >> 1] = __halves2bfloat162(a1, c1);
+    ((__nv_bfloat162*)o2)[e >> 1] = __halves2bfloat162(a2, c2);
   } else {
     const float f0 = d2f_bits(x0), f1 = d2f_bits(x1);
     const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
@@ -327,21 +382,21 @@ __device__ __forceinline__ void store_pair(int prec, long long e, double x0, dou
 // Ar[m, kr], padded to Mp x Krp (K-major)
 template <int PREC, typename Idx>
 __global__ void pack_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int Krp,
-                              void* __restrict__ o0, void* __restrict__ o1) {
+                              void* __restrict__ o0, void* __restrict__ o1, void* __restrict__ o2) {
   // one thread per complex element: its (Re, Im) pair stored together
   const Idx kc = (Idx)(Krp >> 1), total = (Idx)Mp * kc;
   for (Idx e = (Idx)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (Idx)gridDim.x * blockDim.x) {
     const Idx m = e / kc, k = e - m * kc;
     cplx v = make_double2(0.0, 0.0);
     if ((int)m < M && (int)k < K) v = load_op(A, lda, opA, (int)m, (int)k);
-    store_pair(PREC, (long long)m * Krp + 2 * (long long)k, v.x, v.y, o0, o1);
+    store_pair(PREC, (long long)m * Krp + 2 * (long long)k, v.x, v.y, o0, o1, o2);
   }
 }
 
 // Br^T[nr, kr] = [[Re, Im], [-Im, Re]][kr%2][nr%2] of B[kr/2, nr/2], padded to Nrp x Krp
 template <int PREC, typename Idx>
 __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp, int Krp,
-                              void* __restrict__ o0, void* __restrict__ o1) {
+                              void* __restrict__ o0, void* __restrict__ o1, void* __restrict__ o2) {
   // one thread per complex element B[k, n]: rows 2n (Re, -Im) and 2n+1 (Im, Re)
   const Idx kc = (Idx)(Krp >> 1), total = (Idx)(Nrp >> 1) * kc;
   for (Idx e = (Idx)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (Idx)gridDim.x * blockDim.x) {
@@ -349,8 +404,8 @@ __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB
     cplx v = make_double2(0.0, 0.0);
     if ((int)n < N && (int)k < K) v = load_op(B, ldb, opB, (int)k, (int)n);
     const long long r0 = (long long)(2 * n) * Krp + 2 * (long long)k;
-    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1);
-    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1);
+    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1, o2);
+    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1, o2);
   }
 }
 
@@ -359,7 +414,7 @@ __global__ void pack_b_kernel(const cplx* __restrict__ B, long long ldb, int opB
 // writes along kr (the plain kernel would read with stride ldb).
 template <int PREC>
 __global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int conj, int N, int K, int Nrp,
-                                 int Krp, void* __restrict__ o0, void* __restrict__ o1) {
+                                 int Krp, void* __restrict__ o0, void* __restrict__ o1, void* __restrict__ o2) {
   __shared__ cplx tile[32][33];
   const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -385,6 +440,12 @@ __global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int 
       const long long e = (long long)nr * Krp + kr;
       if (PREC == PREC_TF32) {
         ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
+      } else if (PREC == PREC_BF16X6) {
+        __nv_bfloat16 p0, p1, p2;
+        split3(d2f_rn_bits(x), p0, p1, p2);
+        ((__nv_bfloat16*)o0)[e] = p0;
+        ((__nv_bfloat16*)o1)[e] = p1;
+        ((__nv_bfloat16*)o2)[e] = p2;
       } else {
         const float xf = d2f_bits(x);
         const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
@@ -418,13 +479,13 @@ __device__ __forceinline__ cplx view_at(const TcView& V, int r, int c) {
 // complex element (its two reals written as a pair)
 template <int PREC>
 __global__ void pack_a_view_kernel(TcView V, int M, int K, int Mp, int Krp, void* __restrict__ o0,
-                                   void* __restrict__ o1) {
+                                   void* __restrict__ o1, void* __restrict__ o2) {
   const unsigned kc = (unsigned)(Krp >> 1), total = (unsigned)Mp * kc;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const unsigned m = e / kc, k = e - m * kc;
     cplx v = make_double2(0.0, 0.0);
     if ((int)m < M && (int)k < K) v = view_at(V, (int)m, (int)k);
-    store_pair(PREC, (long long)m * Krp + 2 * k, v.x, v.y, o0, o1);
+    store_pair(PREC, (long long)m * Krp + 2 * k, v.x, v.y, o0, o1, o2);
   }
 }
 
@@ -432,15 +493,15 @@ __global__ void pack_a_view_kernel(TcView V, int M, int K, int Mp, int Krp, void
 // complex (n, k) gives rows 2n: (Re, -Im) and 2n+1: (Im, Re) at columns 2k, 2k+1
 template <int PREC>
 __global__ void pack_b_view_kernel(TcView V, int N, int K, int Nrp, int Krp, void* __restrict__ o0,
-                                   void* __restrict__ o1) {
+                                   void* __restrict__ o1, void* __restrict__ o2) {
   const unsigned kc = (unsigned)(Krp >> 1), total = (unsigned)(Nrp >> 1) * kc;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const unsigned n = e / kc, k = e - n * kc;
     cplx v = make_double2(0.0, 0.0);
     if ((int)n < N && (int)k < K) v = view_at(V, (int)n, (int)k);
     const long long r0 = (long long)(2 * n) * Krp + 2 * k;
-    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1);
-    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1);
+    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1, o2);
+    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1, o2);
   }
 }
 
@@ -479,17 +540,18 @@ unsigned grid_for(long long n) {
 
 template <int PREC>
 cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, int N, int K, long long Nrp,
-                       long long Krp, void* b0, void* b1) {
+                       long long Krp, void* b0, void* b1, void* b2) {
   if (opB & OP_T) {
     if (Nrp * Krp < (1LL << 31))
-      pack_b_kernel<PREC, unsigned><<<grid_for(Nrp * Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1);
+      pack_b_kernel<PREC, unsigned><<<grid_for(Nrp * Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp, (int)Krp, b0, b1,
+                                                                          b2);
     else
       pack_b_kernel<PREC, unsigned long long><<<grid_for(Nrp * Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, (int)Nrp,
-                                                                                   (int)Krp, b0, b1);
+                                                                                   (int)Krp, b0, b1, b2);
   } else {
     dim3 grid((unsigned)((Nrp / 2 + 31) / 32), (unsigned)((Krp / 2 + 31) / 32));
     pack_b_tr_kernel<PREC><<<grid, dim3(32, 8), 0, s>>>(B, ldb, (opB & OP_CONJ) ? 1 : 0, N, K, (int)Nrp, (int)Krp,
-                                                        b0, b1);
+                                                        b0, b1, b2);
   }
   count_launch();
   return cudaGetLastError();
@@ -497,22 +559,22 @@ cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, in
 
 template <int PREC>
 void padded(int N, int K, long long* Nrp, long long* Krp) {
-  constexpr int BK = Cfg<PREC, 256>::BK;
+  constexpr int BK = Cfg<PREC, 128>::BK;
   *Krp = (2LL * K + BK - 1) / BK * BK;
   *Nrp = (2LL * N + NPAD - 1) / NPAD * NPAD;
 }
 
-// Default tile choice: 256-wide tiles; a product with fewer output tiles than
-// SMs splits K until about two waves of CTAs exist.
-TcChoice heuristic(long long Mp, long long Nrp, int kb_total) {
-  const long long tiles = (Mp / BM) * (Nrp / 256);
+// Default tile choice: 256-wide tiles (128 for BF16x6); a product with fewer
+// output tiles than SMs splits K until about two waves of CTAs exist.
+TcChoice heuristic(long long Mp, long long Nrp, int kb_total, int bn = 256) {
+  const long long tiles = (Mp / BM) * (Nrp / bn);
   int S = 1;
   if (tiles < 152) {
     S = (int)((2 * 152 + tiles - 1) / tiles);
     if (S > kb_total / 2) S = kb_total / 2;
     if (S < 1) S = 1;
   }
-  return TcChoice{256, S};
+  return TcChoice{bn, S};
 }
 
 // effective number of splits (every split gets at least one k-block)
@@ -525,7 +587,7 @@ int eff_splits(int kb_total, int S) {
 
 // The packed operands of one product, ready for the main kernel.
 struct Operands {
-  void *a0, *a1, *b0, *b1;
+  void *a0, *a1, *a2, *b0, *b1, *b2;
   long long Mp, Nrp, Krp;
   int kb_total;
 };
@@ -545,43 +607,64 @@ cudaError_t ensure_attr() {
 
 template <int PREC, int BN>
 cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, cplx alpha, cplx* C, long long ldc,
-                        float* part, bool conj_out) {
+                        float* part, bool conj_out, int* timeouts, TcProbe* probe) {
   using K_ = Cfg<PREC, BN>;
   cudaError_t e;
   if ((e = ensure_attr<PREC, BN>()) != cudaSuccess) return e;
   if ((e = get_encoder()) != cudaSuccess) return e;
-  CUtensorMap mA0, mA1, mB0, mB1;
+  CUtensorMap mA0, mA1, mA2, mB0, mB1, mB2;
   if ((e = make_map(&mA0, o.a0, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
   if ((e = make_map(&mB0, o.b0, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
-  mA1 = mA0;
-  mB1 = mB0;
-  if (K_::NOPS == 2) {
+  mA1 = mA2 = mA0;
+  mB1 = mB2 = mB0;
+  if (K_::NOPS >= 2) {
     if ((e = make_map(&mA1, o.a1, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
     if ((e = make_map(&mB1, o.b1, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
+  }
+  if (K_::NOPS == 3) {
+    if ((e = make_map(&mA2, o.a2, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
+    if ((e = make_map(&mB2, o.b2, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
   }
   S = eff_splits(o.kb_total, S);
   const int kps = (o.kb_total + S - 1) / S;
   dim3 grid((unsigned)(o.Nrp / BN), (unsigned)(o.Mp / BM), (unsigned)S);
   const int unit = alpha.x == 1.0 && alpha.y == 0.0;
-  tc_gemm_kernel<PREC, BN><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mB0, mB1, o.kb_total, kps, M, 2 * N, alpha,
+  if (probe) {
+    probe->Mp = o.Mp;
+    probe->Nrp = o.Nrp;
+    probe->Krp = o.Krp;
+    probe->splits = S;
+    probe->bn = BN;
+    probe->parts = K_::NOPS;
+    probe->elem_bytes = K_::ELEM;
+    if ((e = cudaEventRecord(probe->ev[0], s)) != cudaSuccess) return e;
+  }
+  tc_gemm_kernel<PREC, BN><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mA2, mB0, mB1, mB2, o.kb_total, kps, M, 2 * N, alpha,
                                                              C, ldc, S > 1 ? part : nullptr, (int)o.Nrp,
-                                                             o.Mp * o.Nrp, conj_out ? 1 : 0, unit);
+                                                             o.Mp * o.Nrp, conj_out ? 1 : 0, unit, timeouts);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (probe && (e = cudaEventRecord(probe->ev[1], s)) != cudaSuccess) return e;
   if (S > 1) {
     splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, o.Mp * o.Nrp, (int)o.Nrp, M, N, alpha,
                                                                     C, ldc, conj_out ? 1 : 0, unit);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (probe && (e = cudaEventRecord(probe->ev[2], s)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 template <int PREC>
 cudaError_t launch_choice(cudaStream_t s, const Operands& o, TcChoice c, int M, int N, cplx alpha, cplx* C,
-                          long long ldc, float* part, bool conj_out) {
-  if (c.bn == 128) return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out);
-  return launch_main<PREC, 256>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out);
+                          long long ldc, float* part, bool conj_out, int* timeouts, TcProbe* probe = nullptr) {
+  if constexpr (PREC == PREC_BF16X6) {
+    return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
+  } else {
+    if (c.bn == 128)
+      return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
+    return launch_main<PREC, 256>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
+  }
 }
 
 }  // namespace
@@ -649,9 +732,10 @@ namespace {
 template <int PREC>
 cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, long long lda, int opA,
                 const cplx* B, long long ldb, int opB, const TcPacked* pre, cplx* C, long long ldc, bool conj_out,
-                char* scratch, size_t scratch_bytes, TcTuner* tuner, const TcChoice* force,
-                const TcView* va = nullptr, const TcView* vb = nullptr) {
-  using K_ = Cfg<PREC, 256>;
+                char* scratch, size_t scratch_bytes, TcTuner* tuner, const TcChoice* force, int* timeouts,
+                TcProbe* probe, const TcView* va = nullptr, const TcView* vb = nullptr) {
+  if (!timeouts) return cudaErrorInvalidValue;
+  using K_ = Cfg<PREC, 128>;  // element size, k-block and parts do not depend on the tile width
   Operands o;
   o.Mp = (M + BM - 1) / BM * BM;
   padded<PREC>(N, K, &o.Nrp, &o.Krp);
@@ -666,11 +750,13 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   char* p = (char*)(((uintptr_t)scratch + 1023) & ~(uintptr_t)1023);
   o.a0 = p;
   o.a1 = p + abytes;
+  o.a2 = p + 2 * abytes;
   o.b0 = p + K_::NOPS * abytes;
   o.b1 = (char*)o.b0 + bbytes;
+  o.b2 = (char*)o.b0 + 2 * bbytes;
   float* part = (float*)((char*)o.b0 + K_::NOPS * bbytes);
 
-  TcChoice choice = heuristic(o.Mp, o.Nrp, o.kb_total);
+  TcChoice choice = heuristic(o.Mp, o.Nrp, o.kb_total, PREC == PREC_BF16X6 ? 128 : 256);
   const TcTuner::Key key{PREC, M, N, K};
   bool tune_now = false;
   if (tuner) {
@@ -681,7 +767,7 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
       tune_now = tuner->measuring;
   }
   if (force) {
-    if (force->bn != 128 && force->bn != 256) return cudaErrorInvalidValue;
+    if (force->bn != 128 && (force->bn != 256 || PREC == PREC_BF16X6)) return cudaErrorInvalidValue;
     choice = TcChoice{force->bn, eff_splits(o.kb_total, force->splits)};
     tune_now = false;
   }
@@ -689,28 +775,29 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
 
   if (va && o.Mp * o.Krp < (1LL << 31))
     pack_a_view_kernel<PREC><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(*va, M, K, (int)o.Mp, (int)o.Krp, o.a0,
-                                                                         o.a1);
+                                                                         o.a1, o.a2);
   else if (va)
     return cudaErrorNotSupported;
   else if (o.Mp * o.Krp < (1LL << 31))
     pack_a_kernel<PREC, unsigned><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp,
-                                                                         o.a0, o.a1);
+                                                                         o.a0, o.a1, o.a2);
   else
     pack_a_kernel<PREC, unsigned long long><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp,
-                                                                                   (int)o.Krp, o.a0, o.a1);
+                                                                                   (int)o.Krp, o.a0, o.a1, o.a2);
   count_launch();
   cudaError_t e;
   if (pre) {
     if (pre->prec != PREC || pre->N != N || pre->K != K) return cudaErrorInvalidValue;
     o.b0 = pre->b0;
     o.b1 = pre->b1;
+    o.b2 = pre->b2;
   } else if (vb) {
     if (o.Nrp * o.Krp >= (1LL << 31)) return cudaErrorNotSupported;
     pack_b_view_kernel<PREC><<<grid_for(o.Nrp * o.Krp / 4), 256, 0, s>>>(*vb, N, K, (int)o.Nrp, (int)o.Krp, o.b0,
-                                                                          o.b1);
+                                                                          o.b1, o.b2);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, o.Nrp, o.Krp, o.b0, o.b1)) != cudaSuccess) {
+  } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, o.Nrp, o.Krp, o.b0, o.b1, o.b2)) != cudaSuccess) {
     return e;
   }
   if (tune_now) {
@@ -720,7 +807,8 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
       for (int rep = 0; rep < 2; ++rep) {
         cudaError_t r;
         if ((r = cudaEventRecord(tuner->e0, s)) != cudaSuccess) return r;
-        if ((r = launch_choice<PREC>(s, o, c, M, N, alpha, C, ldc, part, conj_out)) != cudaSuccess) return r;
+        if ((r = launch_choice<PREC>(s, o, c, M, N, alpha, C, ldc, part, conj_out, timeouts)) != cudaSuccess)
+          return r;
         if ((r = cudaEventRecord(tuner->e1, s)) != cudaSuccess) return r;
         if ((r = cudaEventSynchronize(tuner->e1)) != cudaSuccess) return r;
         float ms = 0;
@@ -738,6 +826,7 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     static const int splits[7] = {1, 2, 4, 8, 12, 16, 32};
     for (int bn : bns)
       for (int S0 : splits) {
+        if (PREC == PREC_BF16X6 && bn != 128) continue;
         const int S = eff_splits(o.kb_total, S0);
         if (S != S0 && S0 != 1) continue;        // duplicate of a smaller split count
         if (S > 1 && o.kb_total / S < 2) continue;  // splits of a single k-block
@@ -756,41 +845,55 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     tuner->order.push_back(key);
     choice = ent.choice;
   }
-  return launch_choice<PREC>(s, o, choice, M, N, alpha, C, ldc, part, conj_out);
+  if (probe) probe->packed_b = pre != nullptr;
+  return launch_choice<PREC>(s, o, choice, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
+}
+
+
+// dispatch on the precision mode (a run<> instantiation per mode)
+template <typename F>
+cudaError_t by_prec(int prec, F&& f) {
+  switch (prec) {
+    case PREC_TF32:
+      return f(std::integral_constant<int, PREC_TF32>());
+    case PREC_BF16X3:
+      return f(std::integral_constant<int, PREC_BF16X3>());
+    case PREC_BF16X6:
+      return f(std::integral_constant<int, PREC_BF16X6>());
+    default:
+      return cudaErrorNotSupported;
+  }
 }
 
 }  // namespace
 
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A, long long lda,
                      int opA, const cplx* B, long long ldb, int opB, cplx* C, long long ldc, cplx* scratch,
-                     long long scratch_elems, long long scratch_top, TcTuner* tuner, const TcChoice* force) {
+                     long long scratch_elems, long long scratch_top, int* timeouts, TcTuner* tuner,
+                     const TcChoice* force, TcProbe* probe) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
-  if (prec == PREC_TF32)
-    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes, tuner,
-                          force);
-  if (prec == PREC_BF16X3)
-    return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
-                            tuner, force);
-  return cudaErrorNotSupported;
+  return by_prec(prec, [&](auto P) {
+    return run<decltype(P)::value>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
+                                   tuner, force, timeouts, probe);
+  });
 }
 
 cudaError_t tc_zgemm_views(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const TcView* va,
                            const cplx* A, long long lda, int opA, const TcView* vb, const cplx* B, long long ldb,
                            int opB, cplx* C, long long ldc, cplx* scratch, long long scratch_elems,
-                           long long scratch_top, TcTuner* tuner) {
+                           long long scratch_top, int* timeouts, TcTuner* tuner, TcProbe* probe) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorNotSupported;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
-  if (prec == PREC_TF32)
-    return run<PREC_TF32>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes, tuner,
-                          nullptr, va, vb);
-  if (prec == PREC_BF16X3)
-    return run<PREC_BF16X3>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
-                            tuner, nullptr, va, vb);
-  return cudaErrorNotSupported;
+  return by_prec(prec, [&](auto P) {
+    return run<decltype(P)::value>(s, M, N, K, alpha, A, lda, opA, B, ldb, opB, nullptr, C, ldc, false, base, bytes,
+                                   tuner, nullptr, timeouts, probe, va, vb);
+  });
 }
+
+static int n_parts(int prec) { return prec == PREC_TF32 ? 1 : (prec == PREC_BF16X3 ? 2 : 3); }
 
 size_t tc_packed_bytes(int prec, int N, int K) {
   long long Nrp, Krp;
@@ -798,8 +901,8 @@ size_t tc_packed_bytes(int prec, int N, int K) {
     padded<PREC_TF32>(N, K, &Nrp, &Krp);
     return (size_t)Nrp * Krp * 4 + 2048;
   }
-  padded<PREC_BF16X3>(N, K, &Nrp, &Krp);
-  return 2 * ((size_t)Nrp * Krp * 2 + 1024) + 2048;
+  padded<PREC_BF16X3>(N, K, &Nrp, &Krp);  // BF16 k-blocks: the same padding for x3 and x6
+  return (size_t)n_parts(prec) * ((size_t)Nrp * Krp * 2 + 1024) + 2048;
 }
 
 cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, int opB, int N, int K, void* mem,
@@ -811,33 +914,32 @@ cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, in
   out->K = K;
   if (prec == PREC_TF32) {
     padded<PREC_TF32>(N, K, &Nrp, &Krp);
-    out->b0 = p;
-    out->b1 = p;
-    return pack_b_any<PREC_TF32>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1);
+    out->b0 = out->b1 = out->b2 = p;
+    return pack_b_any<PREC_TF32>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1, out->b2);
   }
-  if (prec == PREC_BF16X3) {
+  if (prec == PREC_BF16X3 || prec == PREC_BF16X6) {
     padded<PREC_BF16X3>(N, K, &Nrp, &Krp);
-    const size_t half = ((size_t)Nrp * Krp * 2 + 1023) & ~(size_t)1023;
+    const size_t part = ((size_t)Nrp * Krp * 2 + 1023) & ~(size_t)1023;
     out->b0 = p;
-    out->b1 = p + half;
-    return pack_b_any<PREC_BF16X3>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1);
+    out->b1 = p + part;
+    out->b2 = prec == PREC_BF16X6 ? p + 2 * part : out->b1;
+    if (prec == PREC_BF16X3) return pack_b_any<PREC_BF16X3>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1, out->b2);
+    return pack_b_any<PREC_BF16X6>(s, B, ldb, opB, N, K, Nrp, Krp, out->b0, out->b1, out->b2);
   }
   return cudaErrorNotSupported;
 }
 
 cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const cplx* A, long long lda, int opA,
                             const TcPacked& B, cplx* C, long long ldc, bool conj_out, cplx* scratch,
-                            long long scratch_elems, long long scratch_top, TcTuner* tuner) {
+                            long long scratch_elems, long long scratch_top, int* timeouts, TcTuner* tuner,
+                            TcProbe* probe) {
   if (M <= 0) return cudaSuccess;
   char* base = (char*)(scratch + scratch_top);
   const size_t bytes = (size_t)(scratch_elems - scratch_top) * sizeof(cplx);
-  if (prec == PREC_TF32)
-    return run<PREC_TF32>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out, base,
-                          bytes, tuner, nullptr);
-  if (prec == PREC_BF16X3)
-    return run<PREC_BF16X3>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out,
-                            base, bytes, tuner, nullptr);
-  return cudaErrorNotSupported;
+  return by_prec(prec, [&](auto P) {
+    return run<decltype(P)::value>(s, M, (int)B.N, (int)B.K, alpha, A, lda, opA, nullptr, 0, 0, &B, C, ldc, conj_out,
+                                   base, bytes, tuner, nullptr, timeouts, probe);
+  });
 }
 
 cudaError_t tc_init() {
@@ -846,15 +948,6 @@ cudaError_t tc_init() {
   if ((e = ensure_attr<PREC_TF32, 256>()) != cudaSuccess) return e;
   if ((e = ensure_attr<PREC_BF16X3, 128>()) != cudaSuccess) return e;
   if ((e = ensure_attr<PREC_BF16X3, 256>()) != cudaSuccess) return e;
+  if ((e = ensure_attr<PREC_BF16X6, 128>()) != cudaSuccess) return e;
   return get_encoder();
-}
-
-int tc_take_errors() {
-  int n = 0;
-  cudaMemcpyFromSymbol(&n, g_tc_errors, sizeof n);
-  if (n) {
-    const int z = 0;
-    cudaMemcpyToSymbol(g_tc_errors, &z, sizeof z);
-  }
-  return n;
 }

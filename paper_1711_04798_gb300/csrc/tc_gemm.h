@@ -1,14 +1,28 @@
-// Tensor-core (tcgen05) complex GEMM of the precision form: TF32 or
-// split-BF16 (hi*hi + hi*lo + lo*hi) with FP32 accumulation in TMEM.
+// Tensor-core (tcgen05) complex GEMM of the precision form: TF32, split-BF16x3
+// (hi*hi + hi*lo + lo*hi) or split-BF16x6 (three parts, the six products of
+// combined order <= 2) with FP32 accumulation in TMEM.
 #pragma once
 #include "ctm_internal.h"
 
 // C[M,N] = alpha * opA(A) opB(B) with complex FP64 storage of A, B, C; the
 // operands are packed (permuted, converted, real-embedded) into `scratch`
 // above scratch_top.  Returns cudaErrorNotSupported when the precision or the
-// shape has no tensor-core kernel.
+// shape has no tensor-core kernel.  `timeouts` (device int, required) counts
+// the bounded waits inside the kernel that ran out; the caller owns it and
+// reads it after the stream has drained (each handle passes its own slot).
 struct TcTuner;
 struct TcChoice;
+
+// Optional timing probe of one product (measurement support): events recorded
+// on the launching stream before the main tensor-core kernel, after it, and
+// after the split-K reduction; the call fills in the padded shape and tile
+// choice it ran, so the caller can credit algorithmic flops and bytes.
+struct TcProbe {
+  cudaEvent_t ev[3];
+  long long Mp, Nrp, Krp;  // padded real-embedded shape
+  int splits, bn, parts, elem_bytes;
+  bool packed_b;           // B came pre-packed (not repacked by this call)
+};
 
 // An operand read through a strided view instead of a permuted copy: element
 // (r, c) is p[roff(r) + coff(c)], roff / coff sums of per-axis strides over
@@ -26,15 +40,17 @@ struct TcView {
 cudaError_t tc_zgemm(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const cplx* A,
                      long long lda, int opA, const cplx* B, long long ldb, int opB, cplx* C,
                      long long ldc, cplx* scratch, long long scratch_elems, long long scratch_top,
-                     TcTuner* tuner = nullptr, const TcChoice* force = nullptr);
+                     int* timeouts, TcTuner* tuner = nullptr, const TcChoice* force = nullptr,
+                     TcProbe* probe = nullptr);
 
 // A B-role operand (op(B) is K x N complex) packed once as Br^T (2N x 2K real,
 // K-major, padded), reusable across products.
 struct TcPacked {
   int prec;
   long long N, K;
-  void* b0;  // TF32 values, or BF16 hi
-  void* b1;  // BF16 lo (== b0 for TF32)
+  void* b0;  // TF32 values, or the leading BF16 part
+  void* b1;  // second BF16 part (== b0 for TF32)
+  void* b2;  // third BF16 part of BF16x6 (== b1 otherwise)
 };
 size_t tc_packed_bytes(int prec, int N, int K);
 cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, int opB, int N, int K, void* mem,
@@ -42,7 +58,8 @@ cudaError_t tc_pack_b(cudaStream_t s, int prec, const cplx* B, long long ldb, in
 // C = alpha opA(A) B  (or its complex conjugate when conj_out), B pre-packed
 cudaError_t tc_zgemm_packed(cudaStream_t s, int prec, int M, cplx alpha, const cplx* A, long long lda, int opA,
                             const TcPacked& B, cplx* C, long long ldc, bool conj_out, cplx* scratch,
-                            long long scratch_elems, long long scratch_top, TcTuner* tuner = nullptr);
+                            long long scratch_elems, long long scratch_top, int* timeouts,
+                            TcTuner* tuner = nullptr, TcProbe* probe = nullptr);
 
 // Tile choice of one product: output tile 128 x bn (bn = 128 or 256 real
 // columns) and the number of K splits (FP32 partials summed in a fixed order).
@@ -73,8 +90,5 @@ cudaError_t tc_init();
 cudaError_t tc_zgemm_views(cudaStream_t s, int prec, int M, int N, int K, cplx alpha, const TcView* va,
                            const cplx* A, long long lda, int opA, const TcView* vb, const cplx* B, long long ldb,
                            int opB, cplx* C, long long ldc, cplx* scratch, long long scratch_elems,
-                           long long scratch_top, TcTuner* tuner = nullptr);
-
-// number of bounded-wait timeouts inside tensor-core kernels since the last
-// call (resets the counter); synchronous.
-int tc_take_errors();
+                           long long scratch_top, int* timeouts, TcTuner* tuner = nullptr,
+                           TcProbe* probe = nullptr);

@@ -57,3 +57,21 @@ def test_failed_allocation_reports_enomem_and_leaves_no_error():
         gpu_ctm([A], [[0]], 1008)  # D = 12, chi = 1008: terabytes of enlarged corners
     assert e.value.status == 2 and "cudaMalloc" in str(e.value), str(e.value)
     _healthy_sweep_matches_oracle()
+
+
+def test_grid_barrier_wait_limit_reports_etimeout():
+    """The small-row Jacobi (rows of at most 256 complex numbers, fewer than 32
+    rows: the projector of D = 2, chi = 8 with k = 24 rows of length 32) runs
+    as one cooperative launch whose CTAs meet at a grid barrier between
+    rounds.  With a wait limit of one clock cycle the waiting CTAs give up at
+    the first barrier, count it and return: ETIMEOUT from the move, and the
+    library stays usable."""
+    from paper_1711_04798_gb300 import CTMError
+    w = synth.workload("product_noise", seed=3, D=2, chi=8)
+    g = gpu_ctm(w["tensors"], w["pattern"], 8, wait_cycles=1)
+    with pytest.raises(CTMError) as e:
+        g.move("L", 1)
+    assert e.value.status == 5 and "grid-barrier" in str(e.value), str(e.value)
+    g.reset_env()
+    g.close()
+    _healthy_sweep_matches_oracle()

@@ -92,7 +92,7 @@ _RULES = [
     ("cell", "dtype", 9, b"dtype"), ("cell", "tensors", None, b"null tensors"),
     ("opt", "chi", 15, b"chi"), ("opt", "chi", 1025, b"chi > 1024"),
     ("opt", "rsvd_oversample", -1, b"rsvd"), ("opt", "rsvd_power", -1, b"rsvd"),
-    ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 3, b"prec"),
+    ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 4, b"prec"),
     ("opt", "prec", -1, b"prec"), ("opt", "jacobi_max_sweeps", 0, b"jacobi"),
 ]
 
@@ -176,13 +176,15 @@ def test_gemm_entry_points_reject_bad_shapes(lib):
     # ipeps_zgemm(prec, M, N, K, A, opA, B, opB, C)
     assert lib.ipeps_zgemm(I(0), I(0), I(4), I(4), one, I(0), one, I(0), one) == 1
     assert lib.ipeps_zgemm(I(0), I(4), I(4), I(4), None, I(0), one, I(0), one) == 1
-    assert lib.ipeps_zgemm(I(3), I(4), I(4), I(4), one, I(0), one, I(0), one) == 1
+    assert lib.ipeps_zgemm(I(4), I(4), I(4), I(4), one, I(0), one, I(0), one) == 1
     assert lib.ipeps_zgemm(I(0), I(4), I(4), I(4), one, I(4), one, I(0), one) == 1
     # ipeps_zgemm_tile(prec, bn, splits, ...): tensor-core precisions and BN in {128, 256} only
     args = (I(4), I(4), I(4), one, I(0), one, I(0), one)
     assert lib.ipeps_zgemm_tile(I(0), I(128), I(1), *args) == 1
     assert lib.ipeps_zgemm_tile(I(2), I(64), I(1), *args) == 1
     assert lib.ipeps_zgemm_tile(I(2), I(128), I(0), *args) == 1
+    assert b"tile" in lib.ipeps_last_error()
+    assert lib.ipeps_zgemm_tile(I(3), I(256), I(1), *args) == 1  # BF16x6 tiles are 128 wide
     assert b"tile" in lib.ipeps_last_error()
 
 
