@@ -38,9 +38,11 @@ def parse():
     p.add_argument("--D", type=int, default=5)
     p.add_argument("--chi", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "scan", "cylinder"],
+    p.add_argument("--workload", default="single", choices=["single", "scan", "cylinder", "fidelity"],
                    help="single: one D=5 chi=100 instance; scan: 64-instance batched phase-diagram scan; "
-                        "cylinder: D=6 chi=144 environment, boundary spectrum at Nv = 2, 4, 6")
+                        "cylinder: D=6 chi=144 environment, boundary spectrum at Nv = 2, 4, 6; "
+                        "fidelity: fidelity surface of a coupling line on the batch engine")
+    p.add_argument("--points", type=int, default=8, help="fidelity: points on the coupling line")
     p.add_argument("--sweeps", type=int, default=12, help="cylinder: CTM sweeps before the readout")
     p.add_argument("--topk", type=int, default=64, help="cylinder: leading eigenvalues at Nv = 6")
     p.add_argument("--instances", type=int, default=64)
@@ -595,6 +597,9 @@ def run_cylinder(args, rank, world, local_rank):
                                                                      tol=1e-8))
         ring, lz = g.profile_read(3), g.profile_read(4)
         g.profile(False)
+        (S2, purity), t2 = timed(lambda: g.boundary_renyi2(0, Nv))
+        readouts.append({"Nv": Nv, "route": "renyi2 from traces of the dense product sigma_L^T sigma_R",
+                         "S_renyi2": S2, "purity": purity, "seconds": t2})
         readouts.append({"Nv": Nv, "route": "lanczos", "dim": int(D ** Nv), "k": k, "converged": nconv,
                          "S_vn_topk": S, "rest_weight": rest, "seconds": t,
                          "ring_build_s": ring["ms"] * 1e-3,
@@ -619,6 +624,64 @@ def run_cylinder(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+FID_DESC = ("fidelity surface: {n} points of a synthetic coupling line (all-up product + 0.1 x (cos t N1 + sin t "
+            "N2), t in [0, pi/2]), 2x2 cell, d=8, D={D}, chi={chi}; {n} plain + {m} mixed networks advanced "
+            "together on the batch engine, then the fidelity per site of every pair")
+
+
+def run_fidelity(args, rank, world, local_rank):
+    """NEXT-row fidelity surface: the plain network of every point and the mixed
+    network of every pair of points of a coupling line, swept together by the
+    batch engine's graph launches; throughput in pairs per second."""
+    import itertools
+    import torch
+    import synth
+    from paper_1711_04798_gb300 import Batch
+    torch.cuda.set_device(local_rank)
+    D = 3 if args.D == 5 else args.D
+    chi = 24 if args.chi == 100 else args.chi
+    line = synth.fidelity_line(seed=rank_seed(rank), n=args.points, D=D)
+    pat = [[0, 1], [2, 3]]
+    insts = [{"tensors": ts, "pattern": pat, "chi": chi} for ts in line]
+    pairs = []
+    for a, b in itertools.combinations(range(args.points), 2):
+        pairs.append((len(insts), a, b))
+        insts.append({"tensors": line[a], "bra": line[b], "pattern": pat, "chi": chi})
+    b = Batch(insts, tune=not args.no_tune, prec=args.prec)
+    b.sweep(1)  # capture
+    s = torch.cuda.ExternalStream(b.stream())
+    sweeps = max(args.steps, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        e0.record(s)
+        b.sweep(sweeps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        d_block, d_spin = b.fidelity(pairs)
+        wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    b.close()
+    if rank != 0:
+        return
+    surf = np.eye(args.points)
+    for (i12, a, c), d in zip(pairs, d_block):
+        surf[a, c] = surf[c, a] = d
+    line_out = {
+        "metric": METRIC, "value": len(pairs) / wall, "unit": "fidelity pairs/s", "n_gpus": world,
+        "steps": sweeps, "warmup": 1, "ms_per_step": ms / sweeps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+        "config": {"workload": FID_DESC.format(n=args.points, D=D, chi=chi, m=len(pairs)), "prec": args.prec,
+                   "sweeps": sweeps},
+        "fidelity": {"pairs": len(pairs), "instances": len(insts), "sweeps_ms": ms,
+                     "instance_moves_per_s": 4 * sweeps * len(insts) / (ms * 1e-3),
+                     "surface_d_block": [[round(float(v), 12) for v in row] for row in surf]},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line_out), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -630,6 +693,8 @@ def main():
         run_scan(args, rank, world, local_rank)
     elif args.workload == "cylinder":
         run_cylinder(args, rank, world, local_rank)
+    elif args.workload == "fidelity":
+        run_fidelity(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

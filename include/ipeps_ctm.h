@@ -247,6 +247,19 @@ ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double*
 ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
                                 double* S_vn);
 
+/* Second Renyi entropy of the boundary density operator (Sec. IV): with
+ * sigma_L, sigma_R the rings of ipeps_boundary_rho (phase-fixed, Hermitised)
+ * and M = sigma_L^T sigma_R formed densely (D^Nv x D^Nv, one GEMM in the
+ * handle's contraction arithmetic), *purity = Re tr(M^2) / (Re tr M)^2 =
+ * sum lam^2 over the normalised spectrum and *S2 = -ln(purity); both
+ * caller-owned, either may be NULL.  Needs no eigenvalues, so it is defined
+ * for cylinders whose spectrum is only known in part (the leading-k route).
+ * Allocates about 3 n^2 complex numbers plus the product's operands (n =
+ * D^Nv; about 190 GB at D = 6, Nv = 6) for its duration.  Errors: EINVAL
+ * (Nv not a multiple of Ly, D^Nv above 4096 for the FP64 path or above
+ * 200000), ENOMEM (that allocation), ECUDA, ENUMERIC (a zero trace). */
+ipeps_status ipeps_boundary_renyi2(ipeps_ctm h, int x, int Nv, double* S2, double* purity);
+
 /* Leading boundary spectrum for cylinders beyond the dense route (Sec. IV:
  * for long circumferences only the leading eigenvalues of sigma_L^T sigma_R
  * are computed, iteratively).  sigma_L and sigma_R (as in ipeps_boundary_rho,
@@ -369,7 +382,10 @@ void ipeps_ctm_destroy(ipeps_ctm h);
  * (row-major; op 0 = N, 1 = T, 2 = conj, 3 = conj-transpose, so that opA(A)
  * is M x K and A is stored M x K for op 0/2 and K x M for op 1/3).  prec as
  * ipeps_prec: FP64 CUDA-core kernel or the tcgen05 TF32 / split-BF16x3 /
- * split-BF16x6 kernel
+ * split-BF16x6 kernel, or 4: the FP64-accurate tensor-core product of the
+ * precision form's projector step (exact base-256 digit splitting of both
+ * operands, digit-plane products summed exactly; the one rounding to FP64 is
+ * the last)
  * (with its operand packing and split-K reduction).  Allocates and frees its
  * own device buffers; synchronises the device.  A, B, C are caller-owned host
  * arrays.  Errors: EINVAL (M, N or K <= 0, NULL pointer, prec or op out of
@@ -447,6 +463,20 @@ ipeps_status ipeps_batch_move(ipeps_batch b, int dir, int count);
  * EINVAL (NULL argument), or the first failing instance's ipeps_energy
  * status. */
 ipeps_status ipeps_batch_energy(ipeps_batch b, const double* J, double* e_out);
+
+/* Fidelity surface (Sec. VI: the fidelity per site of the states at two
+ * coupling points J1, J2 of a parameter line, Sec. III, Eq. "fidelity"): for
+ * each of the n_pairs pairs p, i12[p] is the batch instance holding the mixed
+ * network of the two states (created with tensors_bra), i11[p] and i22[p] the
+ * instances of the two plain networks, all with the same Lx, Ly; d_block[p]
+ * and (if d_spin is not NULL) d_spin[p] receive the fidelity per block site
+ * and per spin exactly as ipeps_fidelity computes them.  The kappa of every
+ * instance the pairs name is computed once.  Index arrays and outputs are
+ * caller-owned host arrays of n_pairs entries.  Errors: EINVAL (NULL batch or
+ * array, an index out of range, cells that differ within a pair), or the
+ * first failing instance's ipeps_kappa status, named in ipeps_last_error(). */
+ipeps_status ipeps_batch_fidelity(ipeps_batch b, int n_pairs, const int* i12, const int* i11, const int* i22,
+                                  double* d_block, double* d_spin);
 
 /* Instance i as a handle for every single-instance readout (spectra, RDMs,
  * kappa, boundary rho, env_get).  Owned by the batch: do not destroy it; do

@@ -28,6 +28,7 @@ __all__ = [
     "ring_sigma",
     "boundary_spectrum",
     "spectrum_of_rings",
+    "boundary_renyi2",
     "boundary_spectrum_topk",
     "fixed_rings",
     "entropy",
@@ -383,6 +384,20 @@ def spectrum_of_rings(sL: np.ndarray, sR: np.ndarray) -> np.ndarray:
     H = W @ sR @ W
     lam = np.linalg.svd(H, compute_uv=False)
     return lam / lam.sum()
+
+
+def boundary_renyi2(st: CTMState, x: int, Nv: int):
+    """Second Renyi entropy of the boundary density operator of Sec. IV,
+    S_2 = -ln sum_i lam_i^2 with lam the eigenvalues of M = sigma_L^T sigma_R
+    divided by tr M: written through traces as the purity
+    tr(M^2) / (tr M)^2 (real part), which needs no eigenvalues and so is
+    available for cylinders whose spectrum is only known in part.
+    Returns (S_2, purity)."""
+    sL, sR = fixed_rings(st, x, Nv)
+    M = sL.T @ sR
+    tr = np.trace(M)
+    purity = float(np.real(np.trace(M @ M)) / np.real(tr) ** 2)
+    return float(-np.log(purity)), purity
 
 
 def entropy(lam: np.ndarray) -> float:

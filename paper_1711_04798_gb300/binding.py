@@ -25,7 +25,8 @@ EXPORTS = [
     "ipeps_batch_tuning_size", "ipeps_batch_tuning_entry", "ipeps_batch_launch_count",
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
     "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile", "ipeps_ctm_env_set",
-    "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info", "ipeps_rdm_site",
+    "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info", "ipeps_rdm_site", "ipeps_batch_fidelity",
+    "ipeps_boundary_renyi2",
 ]
 
 
@@ -96,6 +97,9 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_batch_create.argtypes = [I, C.POINTER(Cell), C.POINTER(Options), I, C.POINTER(P)]
     lib.ipeps_batch_move.argtypes = [P, I, I]
     lib.ipeps_batch_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_boundary_renyi2.argtypes = [P, I, I, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_batch_fidelity.argtypes = [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(D),
+                                         C.POINTER(D)]
     lib.ipeps_batch_instance.argtypes = [P, I]
     lib.ipeps_batch_instance.restype = P
     lib.ipeps_batch_tuning_size.argtypes = [P]
@@ -329,6 +333,12 @@ class CTM:
         _check(self.lib.ipeps_boundary_rho(self.h, x, Nv, _dptr(eig), C.byref(nout), C.byref(S)))
         return eig[: nout.value], S.value
 
+    def boundary_renyi2(self, x, Nv):
+        """Second Renyi entropy of the boundary operator from traces; returns (S2, purity)."""
+        S2, p = C.c_double(), C.c_double()
+        _check(self.lib.ipeps_boundary_renyi2(self.h, x, Nv, C.byref(S2), C.byref(p)))
+        return S2.value, p.value
+
     def boundary_rho_topk(self, x, Nv, k, max_iter=300, tol=1e-10):
         """Leading k boundary-spectrum values (Lanczos); returns (lam, S, rest, n_conv)."""
         lam = np.zeros(k)
@@ -419,6 +429,16 @@ class Batch:
 
     def instance(self, i) -> CTM:
         return self._views[i]
+
+    def fidelity(self, pairs):
+        """Fidelity per site of each (i12, i11, i22) triple of instance indices:
+        returns (d_block, d_spin) arrays (ipeps_batch_fidelity)."""
+        n = len(pairs)
+        idx = [np.ascontiguousarray([p[q] for p in pairs], dtype=np.int32) for q in range(3)]
+        db, ds = np.zeros(n), np.zeros(n)
+        ptr = [a.ctypes.data_as(C.POINTER(C.c_int)) for a in idx]
+        _check(self.lib.ipeps_batch_fidelity(self.h, n, ptr[0], ptr[1], ptr[2], _dptr(db), _dptr(ds)))
+        return db, ds
 
     def tuning(self):
         out = []

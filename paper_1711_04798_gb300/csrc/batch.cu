@@ -27,6 +27,9 @@ ipeps_status ctm_reinit_env(ipeps_ctm h);
 void ctm_set_tuner(ipeps_ctm h, TcTuner* t);
 void ctm_set_sequential_cuts(ipeps_ctm h, bool on);
 void set_last_error_message(const char* msg);
+void fidelity_from_kappa(const double k12[2], const double k11[2], const double k22[2], double* d_block,
+                         double* d_spin);
+void ctm_cell(ipeps_ctm h, int* Lx, int* Ly);
 
 namespace {
 
@@ -235,6 +238,39 @@ extern "C" ipeps_status ipeps_batch_energy(ipeps_batch b, const double* J, doubl
     ipeps_status st = ipeps_energy(b->inst[i], J + 3 * i, e_out + i);
     if (st != IPEPS_OK) return st;
   }
+  return IPEPS_OK;
+}
+
+// Fidelity surface (Sec. VI): kappa of every instance the pairs name, each
+// computed once, then the fidelity per site of each pair.
+extern "C" ipeps_status ipeps_batch_fidelity(ipeps_batch b, int n_pairs, const int* i12, const int* i11,
+                                             const int* i22, double* d_block, double* d_spin) {
+  if (!b || n_pairs < 0 || (n_pairs && (!i12 || !i11 || !i22 || !d_block)))
+    return bfail(IPEPS_EINVAL, "batch fidelity: bad arguments");
+  std::vector<int> need(b->n, 0);
+  for (int p = 0; p < n_pairs; ++p) {
+    const int idx[3] = {i12[p], i11[p], i22[p]};
+    for (int q = 0; q < 3; ++q) {
+      if (idx[q] < 0 || idx[q] >= b->n) return bfail(IPEPS_EINVAL, "batch fidelity: pair %d names instance %d", p, idx[q]);
+      need[idx[q]] = 1;
+    }
+    int lx[3], ly[3];
+    for (int q = 0; q < 3; ++q) ctm_cell(b->inst[idx[q]], &lx[q], &ly[q]);
+    if (lx[0] != lx[1] || lx[0] != lx[2] || ly[0] != ly[1] || ly[0] != ly[2])
+      return bfail(IPEPS_EINVAL, "batch fidelity: pair %d: cells differ", p);
+  }
+  std::vector<double> k(2 * (size_t)b->n, 0.0);
+  for (int i = 0; i < b->n; ++i) {
+    if (!need[i]) continue;
+    const ipeps_status st = ipeps_kappa(b->inst[i], &k[2 * i]);
+    if (st != IPEPS_OK) {
+      const std::string msg = std::string("batch instance ") + std::to_string(i) + ": " + ipeps_last_error();
+      set_last_error_message(msg.c_str());
+      return st;
+    }
+  }
+  for (int p = 0; p < n_pairs; ++p)
+    fidelity_from_kappa(&k[2 * i12[p]], &k[2 * i11[p]], &k[2 * i22[p]], d_block + p, d_spin ? d_spin + p : nullptr);
   return IPEPS_OK;
 }
 

@@ -95,9 +95,74 @@ __global__ void spectrum_finish_kernel(const double* sigma, int n, double* lam, 
   if (threadIdx.x == 0) *S_vn = red[0];
 }
 
+// partial[2b], partial[2b+1] = Re, Im of the sum of M[i][j] M[j][i] over the
+// 32 x 32 tile pairs block b visits (tiles staged in shared memory so that both
+// reads run along rows); tr(M^2) is the sum over all blocks.
+__global__ void purity_partial_kernel(const cplx* __restrict__ M, int n, double* __restrict__ partial) {
+  __shared__ cplx ta[32][33], tb[32][33];
+  __shared__ double red[2][256];
+  double sr = 0.0, si = 0.0;
+  const int nt = (n + 31) / 32;
+  const long long tiles = (long long)nt * nt;
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int ti = (int)(t / nt), tj = (int)(t % nt);
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int i = ti * 32 + r, j = tj * 32 + threadIdx.x;
+      ta[r][threadIdx.x] = (i < n && j < n) ? M[(long long)i * n + j] : make_double2(0.0, 0.0);
+      const int i2 = tj * 32 + r, j2 = ti * 32 + threadIdx.x;
+      tb[r][threadIdx.x] = (i2 < n && j2 < n) ? M[(long long)i2 * n + j2] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // M[i][j] M[j][i] with i = ti*32 + r, j = tj*32 + c: ta[r][c] * tb[c][r]
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const cplx x = ta[r][threadIdx.x], y = tb[threadIdx.x][r];
+      sr += x.x * y.x - x.y * y.y;
+      si += x.x * y.y + x.y * y.x;
+    }
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  red[0][tid] = sr;
+  red[1][tid] = si;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) {
+      red[0][tid] += red[0][tid + o];
+      red[1][tid] += red[1][tid + o];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    partial[2 * blockIdx.x] = red[0][0];
+    partial[2 * blockIdx.x + 1] = red[1][0];
+  }
+}
+
+// out = {Re tr M, Im tr M, Re tr M^2, Im tr M^2}: the block partials summed in a fixed order
+__global__ void purity_finish_kernel(const double* __restrict__ partial, int nb, const double* __restrict__ tr,
+                                     double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    a += partial[2 * i];
+    b += partial[2 * i + 1];
+  }
+  out[0] = tr[0];
+  out[1] = tr[1];
+  out[2] = a;
+  out[3] = b;
+}
+
 }  // namespace
 
 namespace bnd {
+// out[0..3] = tr M and tr M^2 (re, im) of the dense n x n M; work >= 2 + 2 * 1216 doubles
+void launch_purity(cudaStream_t s, const cplx* M, int n, double* work, double* out) {
+  const int nb = 1216;  // 152 SMs x 8
+  trace_kernel<<<1, 1024, 0, s>>>(M, n, work);
+  purity_partial_kernel<<<nb, dim3(32, 8), 0, s>>>(M, n, work + 2);
+  purity_finish_kernel<<<1, 32, 0, s>>>(work + 2, nb, work, out);
+}
 void launch_phase_herm(cudaStream_t s, cplx* S, int n, bool transpose_out, double* work) {
   trace_kernel<<<1, 1024, 0, s>>>(S, n, work);
   long long total = (long long)n * n;

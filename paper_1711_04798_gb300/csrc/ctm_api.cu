@@ -1236,15 +1236,19 @@ static ipeps_status orth(ipeps_ctm h, cplx* G) {
   return IPEPS_OK;
 }
 
-// FP64 GEMM of the projector step, bracketed as profiling class 2 with its
-// algorithmic flops (structure-aware: a Hermitian Gram counts its upper
-// triangle, a triangular factor its nonzero part).
+// FP64 GEMM of the precision form's projector step (CholeskyQR Grams and
+// applies, the core products): FP64-accurate products on the tensor cores
+// (exact digit splitting, ozaki.cu), bracketed as profiling class 2 with
+// their algorithmic flops (structure-aware: a Hermitian Gram counts its upper
+// triangle, a triangular factor its nonzero part; the digit products compute
+// the full rectangle, so `flags` only states the structure).
 static cudaError_t proj_zgemm(ipeps_ctm h, double flops, int M, int N, int K, const cplx* A, long long lda,
                               int opA, const cplx* B, long long ldb, int opB, cplx* C, long long ldc, int flags) {
+  (void)flags;
   cudaEvent_t ev = nullptr;
   prof_begin(h, &ev);
-  cudaError_t e = zgemm(h->stream, M, N, K, ONE, A, lda, opA, B, ldb, opB, ZERO, C, ldc, GemmBatch{1, 0, 0, 0},
-                        h->scratch + h->scratch_top, h->scratch_elems - h->scratch_top, flags);
+  cudaError_t e = oz_zgemm(h->stream, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, h->scratch + h->scratch_top,
+                           (size_t)(h->scratch_elems - h->scratch_top) * sizeof(cplx), &h->st->tc_timeouts);
   prof_end(h, ev, flops, 2);
   return e;
 }
@@ -1962,6 +1966,19 @@ extern "C" ipeps_status ipeps_kappa(ipeps_ctm h, double* k) {
   return check_status(h);
 }
 
+// Fidelity per block site from the kappas of the mixed and the two plain
+// networks (Eq. "fidelity" with the normalisation of each state divided out):
+// d = (|k12| / sqrt(|k11| |k22|))^(1/4) on the 2x2 window, per spin d^(1/3).
+void fidelity_from_kappa(const double k12[2], const double k11[2], const double k22[2], double* d_block,
+                         double* d_spin) {
+  const int ns = 4;  // sites of the 2x2 window kappa is taken on
+  const double l12 = log(hypot(k12[0], k12[1])), l11 = log(hypot(k11[0], k11[1]));
+  const double l22 = log(hypot(k22[0], k22[1]));
+  const double db = exp((l12 - 0.5 * (l11 + l22)) / ns);
+  if (d_block) *d_block = db;
+  if (d_spin) *d_spin = pow(db, 1.0 / 3.0);
+}
+
 extern "C" ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double* d_block,
                                        double* d_spin) {
   if (!h12 || !h11 || !h22) return fail(IPEPS_EINVAL, "null handle");
@@ -1971,13 +1988,13 @@ extern "C" ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h
   CKS(ipeps_kappa(h12, k[0]));
   CKS(ipeps_kappa(h11, k[1]));
   CKS(ipeps_kappa(h22, k[2]));
-  const int ns = 4;  // sites of the 2x2 window kappa is taken on
-  const double l12 = log(hypot(k[0][0], k[0][1])), l11 = log(hypot(k[1][0], k[1][1]));
-  const double l22 = log(hypot(k[2][0], k[2][1]));
-  const double db = exp((l12 - 0.5 * (l11 + l22)) / ns);
-  if (d_block) *d_block = db;
-  if (d_spin) *d_spin = pow(db, 1.0 / 3.0);
+  fidelity_from_kappa(k[0], k[1], k[2], d_block, d_spin);
   return IPEPS_OK;
+}
+
+void ctm_cell(ipeps_ctm h, int* Lx, int* Ly) {
+  *Lx = h->Lx;
+  *Ly = h->Ly;
 }
 
 // ---------------------------------------------------------------------------
@@ -2265,6 +2282,85 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
   return check_status(h);
 }
 
+namespace bnd {
+void launch_purity(cudaStream_t s, const cplx* M, int n, double* work, double* out);
+}
+
+// Second Renyi entropy of the boundary density operator from traces of the
+// dense product M = sigma_L^T sigma_R (Sec. IV): purity tr(M^2)/(tr M)^2.
+extern "C" ipeps_status ipeps_boundary_renyi2(ipeps_ctm h, int x, int Nv, double* S2, double* purity) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
+  const long long n_max = h->opt.prec == IPEPS_PREC_FP64 ? 4096 : 200000;
+  long long n = 1;
+  for (int i = 0; i < Nv; ++i) {
+    n *= h->D;
+    if (n > n_max) return fail(IPEPS_EINVAL, "D^Nv above %lld for this precision", n_max);
+  }
+  NvtxRange range("boundary renyi2");
+  CKS(reset_status(h));
+  const long long c2 = (long long)h->chi * h->chi, n2 = n * n;
+  long long K1 = 1, K2 = 1;
+  for (int i = 0; i < Nv / 2; ++i) K1 *= h->D;
+  for (int i = 0; i < Nv - Nv / 2; ++i) K2 *= h->D;
+  const long long ring_work = std::max(c2 * std::max(K1 * K1, K2 * K2) * 5 / 4,
+                                       (long long)(1.6 * (double)n * (double)c2)) + (1LL << 24);
+  const long long ring_phase = n2 + c2 * (K1 * K1 + K2 * K2) + ring_work;
+  // product phase: sigma_R, M and the product's packed operands (BF16x6: 2.25 n^2)
+  const long long product_phase = 2 * n2 + (h->opt.prec == IPEPS_PREC_FP64 ? n2 : (9 * n2) / 4) + (1LL << 24);
+  const long long region_elems = std::max(ring_phase, product_phase);
+  cplx* mem = nullptr;
+  cudaError_t e = dev_alloc((void**)&mem, (size_t)(n2 + region_elems) * sizeof(cplx));
+  if (e != cudaSuccess)
+    return fail(IPEPS_ENOMEM, "boundary renyi2: cudaMalloc of %.1f GB failed: %s",
+                (double)(n2 + region_elems) * 16e-9, cudaGetErrorString(e));
+  cplx* sL = mem;
+  cplx* region = mem + n2;
+  cplx* sR = region + n2;
+  cplx* save_scratch = h->scratch;
+  const long long save_elems = h->scratch_elems, save_top = h->scratch_top;
+  h->scratch = region;
+  h->scratch_elems = region_elems;
+  h->scratch_top = 0;
+  const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
+  ipeps_status st = ring_sigma_dense(h, 3, xl, Nv, sL);
+  if (st == IPEPS_OK) st = ring_sigma_dense(h, 1, xr, Nv, sR);
+  double tr[4] = {0.0, 0.0, 0.0, 0.0};
+  if (st == IPEPS_OK) {
+    bnd::launch_phase_herm(h->stream, sL, (int)n, true, h->dwork);  // sL <- sigma_L^T
+    bnd::launch_phase_herm(h->stream, sR, (int)n, false, h->dwork);
+    count_launch(4);
+    cplx* M = region;  // the half rings are dead: M takes their place, sigma_R stays after it
+    h->scratch = region + 2 * n2;
+    h->scratch_elems = region_elems - 2 * n2;
+    h->scratch_top = 0;
+    cudaEvent_t pr = nullptr;
+    prof_begin(h, &pr);
+    st = gemm_dispatch(h, (int)n, (int)n, (int)n, sL, n, OP_N, sR, n, OP_N, M, n, ONE);
+    prof_end(h, pr, 8.0 * (double)n * (double)n * (double)n, 3);
+    if (st == IPEPS_OK) {
+      double* out = h->dwork + 4000;  // after the block partials (dwork[2 .. 2434))
+      bnd::launch_purity(h->stream, M, (int)n, h->dwork, out);
+      count_launch(3);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tr, out, sizeof tr, cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) st = fail(IPEPS_ECUDA, "boundary renyi2: %s", cudaGetErrorString(e));
+    }
+  }
+  h->scratch = save_scratch;
+  h->scratch_elems = save_elems;
+  h->scratch_top = save_top;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(mem);
+  CKS(st);
+  if (!(tr[0] != 0.0) || !std::isfinite(tr[2])) return fail(IPEPS_ENUMERIC, "boundary renyi2: tr M = %g", tr[0]);
+  const double p = tr[2] / (tr[0] * tr[0]);
+  if (purity) *purity = p;
+  if (S2) *S2 = -log(p);
+  return check_status(h);
+}
+
 extern "C" ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* out) {
   if (!h || !out) return fail(IPEPS_EINVAL, "null argument");
   if (role < 0 || role > 7 || x < 0 || x >= h->Lx || y < 0 || y >= h->Ly)
@@ -2296,6 +2392,9 @@ void ctm_geometry(ipeps_ctm h, int g[10]) {
 // ---------------------------------------------------------------------------
 // stand-alone complex GEMM (building block, host buffers) for unit tests
 // ---------------------------------------------------------------------------
+// prec code of ipeps_zgemm for the FP64-accurate tensor-core GEMM (ozaki.cu)
+constexpr int ZGEMM_FP64_TC = 4;
+
 static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
                                double* C, const TcChoice* force);
 
@@ -2317,10 +2416,12 @@ extern "C" ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, in
 static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
                                double* C, const TcChoice* force) {
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return fail(IPEPS_EINVAL, "bad GEMM arguments");
-  if (prec < 0 || prec > 3 || opA < 0 || opA > 3 || opB < 0 || opB > 3) return fail(IPEPS_EINVAL, "bad prec/op");
+  if (prec < 0 || prec > ZGEMM_FP64_TC || opA < 0 || opA > 3 || opB < 0 || opB > 3)
+    return fail(IPEPS_EINVAL, "bad prec/op");
   const size_t na = (size_t)M * K, nb = (size_t)K * N, nc = (size_t)M * N;
-  const size_t scratch_elems = 4 * (na + nb) + 8 * nc + (force ? 4 * (size_t)force->splits * (nc + 256 * (size_t)M) : 0) +
-                               (1 << 20);
+  size_t scratch_elems = 4 * (na + nb) + 8 * nc + (force ? 4 * (size_t)force->splits * (nc + 256 * (size_t)M) : 0) +
+                         (1 << 20);
+  if (prec == ZGEMM_FP64_TC) scratch_elems = oz_work_bytes(M, N, K) / sizeof(cplx) + 1024;
   cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dS = nullptr;
   int* dT = nullptr;  // tensor-core wait timeouts of this call
   ipeps_status st = IPEPS_OK;
@@ -2336,6 +2437,7 @@ static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, i
   if (e != cudaSuccess) { cleanup(); return fail(IPEPS_ECUDA, "zgemm setup: %s", cudaGetErrorString(e)); }
   const long long lda = (opA & OP_T) ? M : K, ldb = (opB & OP_T) ? K : N;
   if (prec == 0) e = zgemm(0, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, ZERO, dC, N);
+  else if (prec == ZGEMM_FP64_TC) e = oz_zgemm(0, M, N, K, dA, lda, opA, dB, ldb, opB, dC, N, dS, scratch_elems * sizeof(cplx), dT);
   else e = tc_zgemm(0, prec, M, N, K, ONE, dA, lda, opA, dB, ldb, opB, dC, N, dS, (long long)scratch_elems, 0, dT,
                     nullptr, force);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -1,0 +1,485 @@
+// FP64-accurate complex GEMM on the tcgen05 tensor cores.
+//
+// GB300 runs FP64 at a small fraction of its tensor-core rate, so the FP64
+// products of the projector step (CholeskyQR Grams and applies of k x K
+// matrices) are computed here by exact splitting into integer digit planes,
+// after the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012),
+// arranged for BF16 tensor cores with FP32 accumulation:
+//
+//  * the complex product is the real product of the embedding of tc_gemm.cu:
+//    Ar (M x 2K) and Br^T (2N x 2K), both K-major;
+//  * every row r of Ar and of Br^T gets a power-of-two bound 2^e_r above its
+//    largest magnitude, and each element is rounded to 55 fraction bits below
+//    it, x = 2^e_r sum_{s<7} d_s 2^(-7-8s), with balanced base-256 digits d_s
+//    in [-128, 128] (exact in BF16), taken from the FP64 bit pattern with
+//    integer operations;
+//  * the digit-plane products P_st = sum_k dA_s dB_t are sums of integers below
+//    2^14 in magnitude; those of equal weight g = s + t accumulate in one FP32
+//    accumulator, and over a chunk of 128 reals of K a group (at most 7 pairs)
+//    stays below 2^24, so the tensor cores' FP32 sums are exact.  The 28
+//    pairs with s + t <= 6 are computed; the others weigh below 2^-53 of the
+//    terms' scale;
+//  * after each chunk the seven group sums leave tensor memory: groups 0..3
+//    combine exactly in 64-bit integers, I += 2^24 P_0 + 2^16 P_1 + 2^8 P_2 +
+//    P_3 (below 2^49 per chunk), groups 4..6 (weight 2^-32 and below) in FP32,
+//    u += P_4 + 2^-8 (P_5 + 2^-8 P_6), whose rounding weighs below 2^-56;
+//  * Cr = 2^(ea + eb - 38) (I + 2^-8 u): the only rounding to FP64 is the last.
+//
+// The error is that of the 55-bit rounding of each element relative to its
+// row's bound (and the dropped digit pairs), i.e. relative to max|a| max|b|
+// of the rows involved rather than to sum |a||b|: FP64-level for rows
+// without a wide spread of magnitudes, as the projector step's are.
+//
+// One CTA computes a 128 x 32 tile of Cr over a range of K chunks: warp 0
+// issues the TMA loads (per stage one A digit plane and the B planes it
+// pairs with), warp 1 the tcgen05.mma, warps 2..5 drain the seven group
+// accumulators after each chunk.  Ranges of K are split over the grid; the
+// exact partials (I, u) are summed by a second kernel.
+#include <cuda_bf16.h>
+
+#include "tc_gemm.h"
+#include "tc_ptx.h"
+
+namespace {
+
+constexpr int OZ_DIGITS = 7;                          // base-256 digits per element
+constexpr int OZ_GROUPS = 7;                          // weights g = s + t = 0..6
+constexpr int OZ_BM = 128, OZ_BN = 32;                // output tile (rows, real columns)
+constexpr int OZ_BK = 64;                             // bf16 elements per k-block (128 bytes)
+constexpr int OZ_CHUNK = 128;                         // reals of K per exact FP32 chunk
+constexpr int OZ_KB_PER_CHUNK = OZ_CHUNK / OZ_BK;     // 2
+constexpr int OZ_A_BYTES = OZ_BM * 128;               // one A plane k-block: 16 KB
+constexpr int OZ_B_BYTES = OZ_BN * 128;               // one B plane k-block: 4 KB
+constexpr int OZ_STAGE = OZ_A_BYTES + OZ_DIGITS * OZ_B_BYTES;  // 44 KB
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_THREADS = 192;                       // producer, MMA issuer, 4 epilogue warps
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
+constexpr int OZ_TMEM_COLS = 256;                     // 7 groups x 32 columns, rounded up
+static_assert(OZ_GROUPS * OZ_BN <= OZ_TMEM_COLS, "the group accumulators fit the tensor-memory allocation");
+static_assert(OZ_GROUPS == OZ_DIGITS, "weights 0..6 of the digit pairs s + t <= 6");
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);  // FP32 += BF16 x BF16, K-major, 128 x 32
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 2^k for k in the normal range, built from its bit pattern
+__device__ __forceinline__ double pow2(int k) {
+  k = k < -1022 ? -1022 : (k > 1023 ? 1023 : k);
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// biased binary64 exponent of x (0 for zero and subnormals)
+__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// balanced base-256 digits of x / 2^e (|x| < 2^e), rounded to 55 fraction bits:
+// x = 2^e sum_s d[s] 2^(-7-8s), d[s] in [-128, 128]
+__device__ __forceinline__ void digits7(double x, int e, int (&d)[OZ_DIGITS]) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  long long v = 0;
+  if (E != 0) {
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int shift = (E - 1023) - e + 3;  // v = x 2^(55 - e) = m 2^shift, shift <= 2
+    if (shift >= 0)
+      v = m << shift;
+    else if (shift > -60)
+      v = (m + (1LL << (-shift - 1))) >> (-shift);
+    if (b < 0) v = -v;
+  }
+#pragma unroll
+  for (int s = OZ_DIGITS - 1; s >= 1; --s) {
+    const int dd = (int)(((v + 128) & 255) - 128);
+    d[s] = dd;
+    v = (v - dd) >> 8;  // exact: v - dd is a multiple of 256
+  }
+  d[0] = (int)v;
+}
+
+__device__ __forceinline__ cplx oz_load(const cplx* X, long long ld, int op, int r, int c) {
+  // element (r, c) of op(X)
+  cplx v = (op & OP_T) ? X[(long long)c * ld + r] : X[(long long)r * ld + c];
+  if (op & OP_CONJ) v.y = -v.y;
+  return v;
+}
+
+// e[r] = (largest biased exponent of row r of op(A), M x K complex) - 1022: the
+// power-of-two bound of that row of Ar; rows at or beyond M, and zero rows, 0.
+// One warp per row.
+__global__ void oz_exp_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp,
+                                int* __restrict__ ea) {
+  const int lane = threadIdx.x & 31;
+  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < Mp; r += gridDim.x * (blockDim.x >> 5)) {
+    int E = 0;
+    if (r < M)
+      for (int c = lane; c < K; c += 32) {
+        const cplx v = oz_load(A, lda, opA, r, c);
+        E = max(E, max(bexp(v.x), bexp(v.y)));
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    if (lane == 0) ea[r] = E ? E - 1022 : 0;
+  }
+}
+
+// the same for the columns n of op(B) (K x N): rows 2n and 2n+1 of Br^T
+__global__ void oz_exp_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp,
+                                int* __restrict__ eb) {
+  const int lane = threadIdx.x & 31;
+  for (int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); n < Nrp / 2;
+       n += gridDim.x * (blockDim.x >> 5)) {
+    int E = 0;
+    if (n < N)
+      for (int k = lane; k < K; k += 32) {
+        const cplx v = oz_load(B, ldb, opB, k, n);
+        E = max(E, max(bexp(v.x), bexp(v.y)));
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+    if (lane == 0) eb[2 * n] = eb[2 * n + 1] = E ? E - 1022 : 0;
+  }
+}
+
+// digit planes of Ar: plane s is [Mp x Krp] bf16 at planes + s * Mp * Krp;
+// one thread per complex element (its two reals stored as a pair)
+__global__ void oz_split_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int Krp,
+                                  const int* __restrict__ ea, __nv_bfloat16* __restrict__ planes) {
+  const long long kc = Krp / 2, total = (long long)Mp * kc, plane = (long long)Mp * Krp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / kc), c = (int)(e - (long long)r * kc);
+    cplx v = make_double2(0.0, 0.0);
+    if (r < M && c < K) v = oz_load(A, lda, opA, r, c);
+    int dr[OZ_DIGITS], di[OZ_DIGITS];
+    digits7(v.x, ea[r], dr);
+    digits7(v.y, ea[r], di);
+    __nv_bfloat162* out = (__nv_bfloat162*)(planes + (long long)r * Krp + 2LL * c);
+#pragma unroll
+    for (int s = 0; s < OZ_DIGITS; ++s)
+      out[s * plane / 2] = __halves2bfloat162(__float2bfloat16_rn((float)dr[s]), __float2bfloat16_rn((float)di[s]));
+  }
+}
+
+// digit planes of Br^T [Nrp x Krp]: complex (k, n) of op(B) gives row 2n
+// (Re, -Im) and row 2n+1 (Im, Re) at columns 2k, 2k+1
+__global__ void oz_split_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp, int Krp,
+                                  const int* __restrict__ eb, __nv_bfloat16* __restrict__ planes) {
+  const long long kc = Krp / 2, total = (long long)(Nrp / 2) * kc, plane = (long long)Nrp * Krp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(e / kc), k = (int)(e - (long long)n * kc);
+    cplx v = make_double2(0.0, 0.0);
+    if (n < N && k < K) v = oz_load(B, ldb, opB, k, n);
+    int dr[OZ_DIGITS], di[OZ_DIGITS];
+    digits7(v.x, eb[2 * n], dr);
+    digits7(v.y, eb[2 * n], di);
+    __nv_bfloat162* r0 = (__nv_bfloat162*)(planes + (long long)(2 * n) * Krp + 2LL * k);
+    __nv_bfloat162* r1 = (__nv_bfloat162*)(planes + (long long)(2 * n + 1) * Krp + 2LL * k);
+#pragma unroll
+    for (int s = 0; s < OZ_DIGITS; ++s) {
+      const __nv_bfloat16 re = __float2bfloat16_rn((float)dr[s]), im = __float2bfloat16_rn((float)di[s]);
+      r0[s * plane / 2] = __halves2bfloat162(re, __float2bfloat16_rn((float)-di[s]));
+      r1[s * plane / 2] = __halves2bfloat162(im, re);
+    }
+  }
+}
+
+// Cr element from its exact sums: 2^(ea + eb - 38) (I + 2^-8 u)
+__device__ __forceinline__ double oz_value(long long I, float u, int ea, int eb) {
+  return ((double)I + (double)u * (1.0 / 256.0)) * pow2(ea + eb - 38);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int Mp, int Nrp,
+                   int chunks_total, int chunks_per_split, int M, int N, const int* __restrict__ ea,
+                   const int* __restrict__ eb, cplx* __restrict__ C, long long ldc, long long* __restrict__ pI,
+                   float* __restrict__ pU, int* __restrict__ timeouts) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* acc_full = empty + OZ_STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* mma_done = acc_empty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y, split = blockIdx.z;
+  const int c0 = split * chunks_per_split;
+  const int nch = min(chunks_total, c0 + chunks_per_split) - c0;  // >= 1 by construction
+  const int nstage = nch * OZ_KB_PER_CHUNK * OZ_DIGITS;             // (chunk, k-block, A digit)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);  // one arrival per epilogue warp
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: stage q = (chunk, k-block, s) holds A plane s and B planes 0..6-s
+    int issued = 0;
+    for (int q = 0; q < nstage; ++q) {
+      const int slot = q % OZ_STAGES, round = q / OZ_STAGES;
+      const int s = q % OZ_DIGITS, kb = (c0 * OZ_KB_PER_CHUNK) + q / OZ_DIGITS;
+      if (!mbar_wait(&empty[slot], (round & 1) ^ 1)) {
+        atomicAdd(timeouts, 1);
+        break;
+      }
+      unsigned char* st = smem + slot * OZ_STAGE;
+      mbar_expect_tx(&full[slot], OZ_A_BYTES + (OZ_DIGITS - s) * OZ_B_BYTES);
+      tma_load_2d(st, &mA, &full[slot], kb * OZ_BK, s * Mp + m_tile * OZ_BM);
+      for (int t = 0; t < OZ_DIGITS - s; ++t)
+        tma_load_2d(st + OZ_A_BYTES + t * OZ_B_BYTES, &mB, &full[slot], kb * OZ_BK, t * Nrp + n_tile * OZ_BN);
+      issued = q + 1;
+    }
+    // the last loads of every slot have landed before the CTA can leave
+    for (int q = max(0, issued - OZ_STAGES); q < issued; ++q)
+      if (!mbar_wait(&full[q % OZ_STAGES], (q / OZ_STAGES) & 1)) atomicAdd(timeouts, 1);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: group g = s + t accumulates in tensor-memory columns 32 g ..
+    bool ok = true;
+    for (int q = 0; q < nstage && ok; ++q) {
+      const int slot = q % OZ_STAGES, round = q / OZ_STAGES;
+      const int s = q % OZ_DIGITS, kbc = (q / OZ_DIGITS) % OZ_KB_PER_CHUNK, c = q / (OZ_DIGITS * OZ_KB_PER_CHUNK);
+      const bool chunk_start = kbc == 0 && s == 0;
+      if (chunk_start && c > 0 && !mbar_wait(acc_empty, (c - 1) & 1)) {  // epilogue drained chunk c-1
+        atomicAdd(timeouts, 1);
+        ok = false;
+        break;
+      }
+      if (!mbar_wait(&full[slot], round & 1)) {
+        atomicAdd(timeouts, 1);
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t a = smem_u32(smem + slot * OZ_STAGE);
+      for (int t = 0; t < OZ_DIGITS - s; ++t) {
+        const uint32_t b = a + OZ_A_BYTES + t * OZ_B_BYTES;
+        const uint32_t d = tmem + (uint32_t)((s + t) * OZ_BN);
+#pragma unroll
+        for (int ks = 0; ks < OZ_BK / 16; ++ks)
+          umma_bf16(d, sdesc(a + ks * 32), sdesc(b + ks * 32), (chunk_start && ks == 0) ? 0u : 1u);
+      }
+      umma_commit(&empty[slot]);  // frees the slot when these MMAs are done
+      if (kbc == OZ_KB_PER_CHUNK - 1 && s == OZ_DIGITS - 1) umma_commit(acc_full);
+    }
+    // every MMA issued has completed before the accumulators are released
+    umma_commit(mma_done);
+    if (!mbar_wait(mma_done, 0)) atomicAdd(timeouts, 1);
+  } else if (warp >= 2) {
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (the rows of its quarter)
+    const int q4 = warp & 3;
+    const int row = m_tile * OZ_BM + 32 * q4 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+    long long I[OZ_BN];
+    float u[OZ_BN];
+#pragma unroll
+    for (int j = 0; j < OZ_BN; ++j) {
+      I[j] = 0;
+      u[j] = 0.0f;
+    }
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      const bool ready = mbar_wait(acc_full, c & 1);
+      if (!ready) {
+        if (lane == 0) atomicAdd(timeouts, 1);
+        ok = false;
+        break;
+      }
+      fence_after();
+      float v[OZ_BN], t[OZ_BN];
+      // groups 0..3: exact integers (below 2^24) into the 64-bit sum
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        tmem_ld32(trow + g * OZ_BN, v);
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) I[j] += (long long)__float2int_rn(v[j]) << (8 * (3 - g));
+      }
+      // groups 4..6 (weight 2^-32 and below relative to group 0): FP32
+      tmem_ld32(trow + 6 * OZ_BN, t);
+      tmem_ld32(trow + 5 * OZ_BN, v);
+#pragma unroll
+      for (int j = 0; j < OZ_BN; ++j) t[j] = fmaf(t[j], 1.0f / 256.0f, v[j]);
+      tmem_ld32(trow + 4 * OZ_BN, v);
+#pragma unroll
+      for (int j = 0; j < OZ_BN; ++j) u[j] += fmaf(t[j], 1.0f / 256.0f, v[j]);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+    if (ok) {
+      const int col0 = n_tile * OZ_BN;
+      if (pI) {
+        // exact partial sums of this K range
+        const long long base = ((long long)split * Mp + row) * Nrp + col0;
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) {
+          pI[base + j] = I[j];
+          pU[base + j] = u[j];
+        }
+      } else if (row < M) {
+        const int er = ea[row];
+#pragma unroll
+        for (int j = 0; j < OZ_BN; j += 2) {
+          const int n = (col0 + j) >> 1;
+          if (n < N)
+            C[(long long)row * ldc + n] = make_double2(oz_value(I[j], u[j], er, eb[col0 + j]),
+                                                       oz_value(I[j + 1], u[j + 1], er, eb[col0 + j + 1]));
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+// C[m, n] from the S exact partials of (I, u) (integer sums are exact; u in FP32)
+__global__ void oz_reduce_kernel(const long long* __restrict__ pI, const float* __restrict__ pU, int S, int Mp,
+                                 int Nrp, int M, int N, const int* __restrict__ ea, const int* __restrict__ eb,
+                                 cplx* __restrict__ C, long long ldc) {
+  const long long total = (long long)M * N, pstride = (long long)Mp * Nrp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / N), n = (int)(e - (long long)m * N);
+    long long I0 = 0, I1 = 0;
+    float u0 = 0.0f, u1 = 0.0f;
+    for (int z = 0; z < S; ++z) {
+      const long long o = z * pstride + (long long)m * Nrp + 2 * n;
+      I0 += pI[o];
+      I1 += pI[o + 1];
+      u0 += pU[o];
+      u1 += pU[o + 1];
+    }
+    C[(long long)m * ldc + n] = make_double2(oz_value(I0, u0, ea[m], eb[2 * n]), oz_value(I1, u1, ea[m], eb[2 * n + 1]));
+  }
+}
+
+unsigned oz_grid(long long n) {
+  long long b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)b;
+}
+
+struct OzLayout {
+  int Mp, Nrp, Krp, chunks, S, cps;
+  size_t off_ea, off_eb, off_a, off_b, off_pi, off_pu, total;
+};
+
+OzLayout oz_layout(int M, int N, int K) {
+  OzLayout L;
+  L.Mp = (M + OZ_BM - 1) / OZ_BM * OZ_BM;
+  L.Nrp = (2 * N + OZ_BN - 1) / OZ_BN * OZ_BN;
+  L.Krp = (2 * K + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
+  L.chunks = L.Krp / OZ_CHUNK;
+  const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Nrp / OZ_BN);
+  int S = (int)((2 * 152 + tiles - 1) / tiles);  // about two waves of CTAs
+  S = S < 1 ? 1 : (S > L.chunks ? L.chunks : S);
+  L.cps = (L.chunks + S - 1) / S;
+  L.S = (L.chunks + L.cps - 1) / L.cps;
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  size_t o = 0;
+  L.off_ea = o;
+  o += al(sizeof(int) * L.Mp);
+  L.off_eb = o;
+  o += al(sizeof(int) * L.Nrp);
+  L.off_a = o;
+  o += al((size_t)OZ_DIGITS * L.Mp * L.Krp * 2);
+  L.off_b = o;
+  o += al((size_t)OZ_DIGITS * L.Nrp * L.Krp * 2);
+  L.off_pi = o;
+  o += L.S > 1 ? al((size_t)L.S * L.Mp * L.Nrp * 8) : 0;
+  L.off_pu = o;
+  o += L.S > 1 ? al((size_t)L.S * L.Mp * L.Nrp * 4) : 0;
+  L.total = o + 1024;
+  return L;
+}
+
+}  // namespace
+
+size_t oz_work_bytes(int M, int N, int K) { return oz_layout(M, N, K).total; }
+
+cudaError_t oz_zgemm(cudaStream_t s, int M, int N, int K, const cplx* A, long long lda, int opA, const cplx* B,
+                     long long ldb, int opB, cplx* C, long long ldc, void* work, size_t work_bytes, int* timeouts) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if (!timeouts) return cudaErrorInvalidValue;
+  const OzLayout L = oz_layout(M, N, K);
+  if (!work || work_bytes < L.total) return cudaErrorMemoryAllocation;
+  static bool attr = false;
+  cudaError_t e;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
+        cudaSuccess)
+      return e;
+    attr = true;
+  }
+  char* base = (char*)(((uintptr_t)work + 1023) & ~(uintptr_t)1023);
+  int* ea = (int*)(base + L.off_ea);
+  int* eb = (int*)(base + L.off_eb);
+  __nv_bfloat16* pa = (__nv_bfloat16*)(base + L.off_a);
+  __nv_bfloat16* pb = (__nv_bfloat16*)(base + L.off_b);
+  long long* pI = L.S > 1 ? (long long*)(base + L.off_pi) : nullptr;
+  float* pU = L.S > 1 ? (float*)(base + L.off_pu) : nullptr;
+  oz_exp_a_kernel<<<oz_grid(32LL * L.Mp), 256, 0, s>>>(A, lda, opA, M, K, L.Mp, ea);
+  oz_exp_b_kernel<<<oz_grid(16LL * L.Nrp), 256, 0, s>>>(B, ldb, opB, N, K, L.Nrp, eb);
+  oz_split_a_kernel<<<oz_grid((long long)L.Mp * L.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, L.Mp, L.Krp, ea, pa);
+  oz_split_b_kernel<<<oz_grid((long long)L.Nrp * L.Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, L.Nrp, L.Krp, eb, pb);
+  count_launch(4);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  if ((e = tc_encode_bf16_map(&mA, pa, (long long)OZ_DIGITS * L.Mp, L.Krp, OZ_BM)) != cudaSuccess) return e;
+  if ((e = tc_encode_bf16_map(&mB, pb, (long long)OZ_DIGITS * L.Nrp, L.Krp, OZ_BN)) != cudaSuccess) return e;
+  dim3 grid((unsigned)(L.Nrp / OZ_BN), (unsigned)(L.Mp / OZ_BM), (unsigned)L.S);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, L.Mp, L.Nrp, L.chunks, L.cps, M, N, ea, eb, C, ldc, pI, pU,
+                                                   timeouts);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (L.S > 1) {
+    oz_reduce_kernel<<<oz_grid((long long)M * N), 256, 0, s>>>(pI, pU, L.S, L.Mp, L.Nrp, M, N, ea, eb, C, ldc);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}

@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 
 #include "tc_gemm.h"
+#include "tc_ptx.h"
 
 #include <algorithm>
 #include <map>
@@ -30,7 +31,7 @@ namespace {
 
 constexpr int BM = 128, NPAD = 256, NTHREADS = 128;  // N of every packed B operand padded to NPAD
 constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2, PREC_BF16X6 = 3;
-constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
+
 
 
 // Tile configuration: 128 x BN output tile (BN = 128 or 256), 128-byte k-blocks,
@@ -57,53 +58,6 @@ struct Cfg {
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// wait for phase `parity` of the barrier; false after WAIT_CYCLES
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t addr = smem_u32(bar);
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
 template <int PREC, uint32_t IDESC>
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
   if (PREC == PREC_TF32) {
@@ -119,26 +73,6 @@ __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(IDESC), "r"(accum)
         : "memory");
   }
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <int PREC, int BN>
@@ -849,6 +783,16 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   return launch_choice<PREC>(s, o, choice, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
 }
 
+
+}  // namespace
+
+cudaError_t tc_encode_bf16_map(CUtensorMap* map, void* base, long long rows, long long kcols, int box_rows) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  return make_map(map, base, PREC_BF16X3, rows, kcols, box_rows);
+}
+
+namespace {
 
 // dispatch on the precision mode (a run<> instantiation per mode)
 template <typename F>

@@ -2,6 +2,8 @@
 // (hi*hi + hi*lo + lo*hi) or split-BF16x6 (three parts, the six products of
 // combined order <= 2) with FP32 accumulation in TMEM.
 #pragma once
+#include <cuda.h>
+
 #include "ctm_internal.h"
 
 // C[M,N] = alpha * opA(A) opB(B) with complex FP64 storage of A, B, C; the
@@ -92,3 +94,14 @@ cudaError_t tc_zgemm_views(cudaStream_t s, int prec, int M, int N, int K, cplx a
                            int opB, cplx* C, long long ldc, cplx* scratch, long long scratch_elems,
                            long long scratch_top, int* timeouts, TcTuner* tuner = nullptr,
                            TcProbe* probe = nullptr);
+
+// 2D tensor map of a K-major BF16 operand [rows x kcols] with boxes of
+// box_rows x 64 elements (128 bytes, 128-byte swizzle), for the tcgen05 kernels.
+cudaError_t tc_encode_bf16_map(CUtensorMap* map, void* base, long long rows, long long kcols, int box_rows);
+
+// FP64-accurate complex GEMM on the tensor cores (ozaki.cu): C = opA(A) opB(B)
+// (complex FP64 storage, alpha 1, beta 0).  `work` (device, work_bytes) holds
+// the digit planes, row scales and split partials: oz_work_bytes(M, N, K).
+size_t oz_work_bytes(int M, int N, int K);
+cudaError_t oz_zgemm(cudaStream_t s, int M, int N, int K, const cplx* A, long long lda, int opA, const cplx* B,
+                     long long ldb, int opB, cplx* C, long long ldc, void* work, size_t work_bytes, int* timeouts);

@@ -147,3 +147,34 @@ def scan(seed: int = 0, n: int = 64, Ds=(3, 4, 5), chis=(32, 48, 64, 100)):
         out.append({"tensors": tensors, "pattern": [[0, 1], [2, 3]], "D": D, "chi": chi,
                     "J": ((2.0 - Jz) / 2.0, (2.0 - Jz) / 2.0, Jz), "k": k})
     return out
+
+
+def fidelity_line(seed: int = 0, n: int = 5, D: int = 2, d: int = 8, eps: float = 0.1):
+    """States at n points of a synthetic coupling line, for fidelity surfaces
+    (the paper scans the fidelity per site of ground states at pairs of
+    couplings J1, J2 on a line, Sec. VI; its optimised states are not
+    available, so a smooth one-parameter family stands in for them).
+
+    Point k has angle theta_k = (pi/2) k/(n-1) and four tensors
+    A_t = all-up product + eps * (cos theta_k N1_t + sin theta_k N2_t), where
+    N1_t and N2_t are fixed complex normal draws (Re, Im ~ N(0, 1/2)) from
+    streams (seed*16 + t) and ((seed+1)*16 + t).  Returns a list of n tensor
+    lists (2x2 cell, pattern [[0, 1], [2, 3]])."""
+    size = d * D ** 4
+    base = []
+    for t in range(4):
+        g1 = normal(seed * 16 + t, 2 * size)
+        g2 = normal((seed + 1) * 16 + t, 2 * size)
+        n1 = ((g1[:size] + 1j * g1[size:]) * np.sqrt(0.5)).reshape(d, D, D, D, D)
+        n2 = ((g2[:size] + 1j * g2[size:]) * np.sqrt(0.5)).reshape(d, D, D, D, D)
+        base.append((n1, n2))
+    out = []
+    for k in range(n):
+        th = 0.5 * np.pi * k / max(n - 1, 1)
+        ts = []
+        for n1, n2 in base:
+            A = eps * (np.cos(th) * n1 + np.sin(th) * n2)
+            A[0, 0, 0, 0, 0] += 1.0
+            ts.append(A)
+        out.append(ts)
+    return out

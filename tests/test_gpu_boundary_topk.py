@@ -58,3 +58,25 @@ def test_topk_argument_errors():
     lam, _, _, _ = g.boundary_rho_topk(0, 2, 2, max_iter=4)  # the handle stays usable
     assert np.all(np.isfinite(lam))
     g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x6", 1e-5)])
+@pytest.mark.parametrize("Nv", [2, 4])
+def test_boundary_renyi2_matches_oracle(prec, tol, Nv):
+    """Second Renyi entropy from the traces of M = sigma_L^T sigma_R (Sec. IV)
+    against the oracle's, and against the dense spectrum's purity on the GPU."""
+    w = synth.workload("product_noise", seed=6, D=2, chi=8)
+    g = gpu_ctm(w["tensors"], w["pattern"], 8, prec=prec, cutoff=1e-6 if prec != "fp64" else 1e-8)
+    g.sweep(3)
+    st = O.make_state(w["tensors"], w["pattern"], 2, 8)
+    opt = oracle_options(8, 2, cutoff=1e-6 if prec != "fp64" else 1e-8)
+    for _ in range(3):
+        st = O.sweep(st, opt)
+    S2, p = g.boundary_renyi2(0, Nv)
+    S2_ref, p_ref = O.boundary_renyi2(st, 0, Nv)
+    lam, _ = g.boundary_rho(0, Nv)
+    print(f"{prec} Nv={Nv}: S2 {S2:.12f} oracle {S2_ref:.12f}; purity vs dense spectrum "
+          f"{abs(p - np.sum(lam ** 2)):.1e}")
+    assert abs(S2 - S2_ref) < tol and abs(p - p_ref) < tol
+    assert abs(p - np.sum(lam ** 2)) < tol
+    g.close()

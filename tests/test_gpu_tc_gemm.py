@@ -7,7 +7,11 @@ input kept to about 16 bits) plus FP32 accumulation, 2^-17 for the three-part
 BF16 split: its inputs carry 24 bits (the dropped products lie below 2^-22 of
 each term), so the FP32 accumulation sets the error -- about sqrt(n) 2^-24
 for a sum of n = 2K real terms in one K split (measured 2.2e-6 for K = 1500
-without splits, 1e-7 to 5e-7 where K is split)."""
+without splits, 1e-7 to 5e-7 where K is split).
+
+Precision code 4 is the FP64-accurate tensor-core product of the projector
+step (exact base-256 digit splitting, digit-plane products summed exactly):
+held to 1e-15 of the scale, and to the FP64 CUDA-core kernel (code 0)."""
 import ctypes
 
 import numpy as np
@@ -15,7 +19,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 2.0 ** -10, 2: 2.0 ** -15, 3: 2.0 ** -17}
+TOL = {0: 1e-13, 1: 2.0 ** -10, 2: 2.0 ** -15, 3: 2.0 ** -17, 4: 1e-15}
 
 
 def _zgemm(prec, A, opA, B, opB, M, N, K):
@@ -41,7 +45,7 @@ def _op(X, op):
     return X
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("shape", [(130, 77, 300), (1, 1000, 700), (116, 600, 2500), (300, 129, 33)])
 @pytest.mark.parametrize("ops", [(0, 0), (1, 3), (2, 1), (3, 2)])
 def test_tc_gemm_matches_complex128(prec, shape, ops):
@@ -97,3 +101,24 @@ def test_every_tile_choice_matches_complex128(prec, bn, splits):
     ref = A @ B.T
     scale = np.abs(A) @ np.abs(B.T)
     assert np.max(np.abs(C - ref) / scale) < TOL[prec]
+
+
+@pytest.mark.parametrize("shape,ops", [((116, 116, 2500), (2, 1)), ((116, 2500, 116), (1, 0)),
+                                       ((116, 116, 116), (1, 1)), ((33, 77, 1000), (3, 2))])
+def test_fp64_tensor_core_product_matches_the_fp64_kernel(shape, ops):
+    """The projector step's shapes (a Hermitian Gram of k x K rows, a
+    triangular apply, a k x k core product): the digit-split tensor-core
+    product against the FP64 CUDA-core kernel and against numpy."""
+    M, N, K = shape
+    opA, opB = ops
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    Ast = rng.standard_normal((K, M) if opA & 1 else (M, K)) + 1j * rng.standard_normal((K, M) if opA & 1 else (M, K))
+    Bst = rng.standard_normal((N, K) if opB & 1 else (K, N)) + 1j * rng.standard_normal((N, K) if opB & 1 else (K, N))
+    C4 = _zgemm(4, Ast, opA, Bst, opB, M, N, K)
+    C0 = _zgemm(0, Ast, opA, Bst, opB, M, N, K)
+    Aop, Bop = _op(Ast, opA), _op(Bst, opB)
+    scale = np.abs(Aop) @ np.abs(Bop)
+    e_ref = np.max(np.abs(C4 - Aop @ Bop) / scale)
+    e_fp64 = np.max(np.abs(C4 - C0) / scale)
+    print(f"shape {shape} ops {ops}: digit-split vs numpy {e_ref:.2e}, vs FP64 kernel {e_fp64:.2e}")
+    assert e_ref < 1e-15 and e_fp64 < 1e-15

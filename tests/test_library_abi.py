@@ -176,7 +176,7 @@ def test_gemm_entry_points_reject_bad_shapes(lib):
     # ipeps_zgemm(prec, M, N, K, A, opA, B, opB, C)
     assert lib.ipeps_zgemm(I(0), I(0), I(4), I(4), one, I(0), one, I(0), one) == 1
     assert lib.ipeps_zgemm(I(0), I(4), I(4), I(4), None, I(0), one, I(0), one) == 1
-    assert lib.ipeps_zgemm(I(4), I(4), I(4), I(4), one, I(0), one, I(0), one) == 1
+    assert lib.ipeps_zgemm(I(5), I(4), I(4), I(4), one, I(0), one, I(0), one) == 1
     assert lib.ipeps_zgemm(I(0), I(4), I(4), I(4), one, I(4), one, I(0), one) == 1
     # ipeps_zgemm_tile(prec, bn, splits, ...): tensor-core precisions and BN in {128, 256} only
     args = (I(4), I(4), I(4), one, I(0), one, I(0), one)

@@ -860,3 +860,19 @@ def test_boundary_spectrum_route_on_an_indefinite_ring():
     clamp = (Vh * np.sqrt(np.clip(wh, 0, None))) @ Vh.conj().T
     ev_c = np.sort(np.linalg.eigvalsh(clamp @ sR @ clamp))[::-1]
     assert np.max(np.abs(lam - ev_c / ev_c.sum())) > 1e-3
+
+
+def test_boundary_renyi2_equals_the_spectrum_purity():
+    """S_2 from traces equals -ln sum lam^2 of the boundary spectrum (Sec. IV)
+    on positive rings of a converged environment, and vanishes for a product
+    state (D = 1)."""
+    st = _converged_state(2, 2, 12, 6)
+    for Nv in (2, 4):
+        lam = O.boundary_spectrum(st, 0, Nv)
+        S2, p = O.boundary_renyi2(st, 0, Nv)
+        assert abs(p - np.sum(lam ** 2)) < 1e-12 and abs(S2 + np.log(np.sum(lam ** 2))) < 1e-10
+        assert 0 < S2 <= O.entropy(lam) + 1e-12  # Renyi-2 never exceeds von Neumann
+    _, ts = product_tensors(15)
+    pst = O.sweep(O.make_state(ts, [[0, 1], [2, 3]], 1, 1), O.CTMOptions(chi=1, proj="svd"))
+    S2, p = O.boundary_renyi2(pst, 0, 2)
+    assert abs(S2) < 1e-14 and abs(p - 1) < 1e-14

@@ -50,3 +50,21 @@ def test_workload_recipes():
     scan = synth.scan(seed=2, n=5, Ds=(2, 3), chis=(9, 12))
     assert [s["J"][2] for s in scan] == [0.0, 0.5, 1.0, 1.5, 2.0]
     assert all(abs(s["J"][0] - (2.0 - s["J"][2]) / 2) < 1e-15 for s in scan)
+
+
+def test_fidelity_line_ends_are_the_product_noise_recipe():
+    """Point 0 of the coupling line is the product-plus-noise state of stream
+    seed, the last point that of stream seed + 1 (theta = 0 and pi/2), and
+    the points in between keep the all-up entry and the noise norm."""
+    seed, D = 4, 2
+    line = synth.fidelity_line(seed=seed, n=5, D=D)
+    for t in range(4):
+        assert np.array_equal(line[0][t], synth.product_plus_noise(seed, t, 8, D))
+        assert np.allclose(line[-1][t], synth.product_plus_noise(seed + 1, t, 8, D), rtol=0, atol=1e-16)
+    # in between: all-up + eps (cos theta N1 + sin theta N2), N1, N2 the two ends' noise
+    n1 = line[0][1] / 0.1
+    n2 = line[-1][1] / 0.1
+    e0 = np.zeros_like(n1)
+    e0[0, 0, 0, 0, 0] = 1.0 / 0.1
+    th = 0.5 * np.pi * 2 / 4
+    assert np.allclose(line[2][1] / 0.1 - e0, np.cos(th) * (n1 - e0) + np.sin(th) * (n2 - e0), atol=1e-12)
