@@ -32,7 +32,7 @@ def parse():
     p.add_argument("--steps", type=int, default=4)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="bf16x3", choices=["fp64", "tf32", "bf16x3", "bf16x6"])
+    p.add_argument("--prec", default="bf16x6", choices=["fp64", "tf32", "bf16x3", "bf16x6"])
     p.add_argument("--no-fp64-check", action="store_true",
                    help="skip the FP64 comparison run (moves/s and |dE| of the plain FP64 GPU path)")
     p.add_argument("--D", type=int, default=5)
