@@ -89,6 +89,12 @@ typedef struct {
   const void* const* tensors;       /* n_tensors host pointers, A[p,u,l,d,r]       */
   const void* const* tensors_bra;   /* NULL, or the second state B of the mixed
                                        network e = sum_p A_p conj(B_p) (Sec. III)  */
+  const int* leg_dims;              /* NULL (every leg D), or 4 per tensor: the
+                                       sizes (u, l, d, r), each 1 or D, of the host
+                                       tensors A[p,u,l,d,r]; a leg of size 1 is a
+                                       trivial bond (App. B: the empty edges of the
+                                       star lattice's block sites), embedded at
+                                       index 0 of a D leg                          */
 } ipeps_cell;
 
 typedef struct {
@@ -220,6 +226,18 @@ ipeps_status ipeps_rdm_site(ipeps_ctm h, double* rho_s);
  * Errors: EINVAL (NULL argument; not a 2x2 cell of d = 8 sites), ENOMEM,
  * ECUDA, ENUMERIC. */
 ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e_per_spin);
+
+/* Energy per spin of a star-lattice spin model (App. B: the star lattice
+ * mapped onto the same 2x2 cell of d = 8 triangle block sites, its empty edges
+ * trivial bonds of dimension 1, ipeps_cell.leg_dims): Heisenberg couplings
+ * J = {J_t (inside each triangle), J_e (between triangles)} on Pauli
+ * matrices, H = J_t sum s.s + J_e sum s.s.  Reading of the block structure
+ * (the figure is absent from the text): spins 1, 2, 3 of a triangle link to
+ * its left, right and vertical neighbour; A sites (x+y even) link downwards,
+ * B sites upwards, so the vertical bond with B on top is the trivial edge.
+ * Energy per spin = (1/12) sum over the cell's 8 bonds.  Errors: EINVAL (NULL
+ * argument, cell not 2x2 with d = 8), and those of ipeps_rdm. */
+ipeps_status ipeps_energy_star(ipeps_ctm h, const double J[2], double* e_per_spin);
 
 /* Partition-function ratio kappa = Z(window) Z(corners) / (Z(columns)
  * Z(rows)) of the 2x2 window of sites at (0,0), cell indices taken mod

@@ -19,6 +19,7 @@ __all__ = [
     "site_rdms",
     "pauli_block_ops",
     "ruby_bond_hamiltonians",
+    "star_bond_hamiltonians",
     "xyz_all_edges_bond_hamiltonians",
     "energy_per_spin",
     "site_type",
@@ -225,15 +226,47 @@ def xyz_all_edges_bond_hamiltonians(J):
     return {"H_r": H_r, "H_l": H_l, "H_u": H_v, "H_d": H_v.copy(), "h_site": h_site}
 
 
+def star_bond_hamiltonians(J):
+    """Bond operators of a Heisenberg model on the star lattice (App. B), on
+    the same 2x2 cell of triangle block sites: J = (J_t, J_e) couple Pauli
+    vectors s.s inside each triangle and between triangles.  Reading of the
+    block structure (the figure is absent from the text): spins 1, 2, 3 of a
+    triangle link to the left, right and vertical neighbour of the brick wall;
+    A sites link down, B sites up, so the vertical bond with B on top is the
+    trivial (D = 1) edge and carries no term.  Horizontal bonds (either type on
+    the left) hold half of each site's triangle term plus the link of the left
+    site's spin 2 to the right site's spin 1; the vertical bond with A on top
+    links spin 3 to spin 3."""
+    Jt, Je = J
+    o = pauli_block_ops()
+    I8 = np.eye(8, dtype=np.complex128)
+
+    def dot_in(a, b):
+        return sum(o[f"{al}{a}"] @ o[f"{al}{b}"] for al in "xyz")
+
+    def dot_across(a, b):
+        return sum(np.kron(o[f"{al}{a}"], o[f"{al}{b}"]) for al in "xyz")
+
+    h_site = Jt * (dot_in(1, 2) + dot_in(1, 3) + dot_in(2, 3))
+    H_h = 0.5 * (np.kron(h_site, I8) + np.kron(I8, h_site)) + Je * dot_across(2, 1)
+    H_v = Je * dot_across(3, 3)
+    return {"H_r": H_h, "H_l": H_h.copy(), "H_u": H_v, "H_d": np.zeros((64, 64), dtype=np.complex128),
+            "h_site": h_site}
+
+
 def energy_per_spin(rdms, J, Lx: int, Ly: int, model: str = "ruby") -> float:
     """(1/(3 Lx Ly)) * sum over the cell's 2 Lx Ly bonds of Re tr(rho_b H_b).
 
-    model: "ruby" (each link its own colour's term, Eq. H-KR) or
-    "xyz_all_edges" (every link all three terms, for comparison)."""
+    model: "ruby" (each link its own colour's term, Eq. H-KR),
+    "xyz_all_edges" (every link all three terms, for comparison) or "star"
+    (the Heisenberg star-lattice model of ``star_bond_hamiltonians``, App. B;
+    J = (J_t, J_e))."""
     if model == "ruby":
         H = ruby_bond_hamiltonians(J)
     elif model == "xyz_all_edges":
         H = xyz_all_edges_bond_hamiltonians(J)
+    elif model == "star":
+        H = star_bond_hamiltonians(J)
     else:
         raise ValueError(model)
     e = 0.0

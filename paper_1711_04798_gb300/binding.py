@@ -26,14 +26,15 @@ EXPORTS = [
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
     "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile", "ipeps_ctm_env_set",
     "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info", "ipeps_rdm_site", "ipeps_batch_fidelity",
-    "ipeps_boundary_renyi2",
+    "ipeps_boundary_renyi2", "ipeps_energy_star",
 ]
 
 
 class Cell(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("pattern", C.c_int * 4), ("n_tensors", C.c_int),
                 ("d", C.c_int), ("D", C.c_int), ("dtype", C.c_int),
-                ("tensors", C.POINTER(C.c_void_p)), ("tensors_bra", C.POINTER(C.c_void_p))]
+                ("tensors", C.POINTER(C.c_void_p)), ("tensors_bra", C.POINTER(C.c_void_p)),
+                ("leg_dims", C.POINTER(C.c_int))]
 
 
 class Options(C.Structure):
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_batch_create.argtypes = [I, C.POINTER(Cell), C.POINTER(Options), I, C.POINTER(P)]
     lib.ipeps_batch_move.argtypes = [P, I, I]
     lib.ipeps_batch_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_energy_star.argtypes = [P, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_boundary_renyi2.argtypes = [P, I, I, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_batch_fidelity.argtypes = [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(D),
                                          C.POINTER(D)]
@@ -140,10 +142,15 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _bond_dim(tensors):
+    """D of a cell: the largest virtual leg (legs of size 1 are trivial bonds)."""
+    return max(max(t.shape[1:]) for t in tensors)
+
+
 def _make_cell(tensors, pattern, bra=None):
     """ipeps_cell for the host tensors (kept alive by the returned tuple)."""
     Ly, Lx = len(pattern), len(pattern[0])
-    d, D = tensors[0].shape[0], tensors[0].shape[1]
+    d, D = tensors[0].shape[0], _bond_dim(tensors)
     cplx = any(np.iscomplexobj(t) for t in tensors) or (bra is not None)
     dt = np.complex128 if cplx else np.float64
     keep = [np.ascontiguousarray(t, dtype=dt) for t in tensors]
@@ -162,7 +169,11 @@ def _make_cell(tensors, pattern, bra=None):
     if keep_bra is not None:
         bptrs = (C.c_void_p * len(tensors))(*[t.ctypes.data for t in keep_bra])
         cell.tensors_bra = C.cast(bptrs, C.POINTER(C.c_void_p))
-    return cell, (keep, keep_bra, ptrs, bptrs, dt)
+    legs = None
+    if any(t.shape[1:] != (D, D, D, D) for t in tensors):
+        legs = (C.c_int * (4 * len(tensors)))(*[s for t in tensors for s in t.shape[1:]])
+        cell.leg_dims = C.cast(legs, C.POINTER(C.c_int))
+    return cell, (keep, keep_bra, ptrs, bptrs, dt, legs)
 
 
 def _make_options(lib, chi, prec="fp64", oversample=16, power=2, cutoff=0.0, orth_tol=1e-14,
@@ -198,7 +209,7 @@ class CTM:
         self.lib = lib
         self._borrowed = False
         cell, keep = _make_cell(tensors, pattern, bra)
-        self._keep, self._keep_bra, self._ptrs, self._bptrs, self._dtype = keep
+        self._keep, self._keep_bra, self._ptrs, self._bptrs, self._dtype, self._legs = keep
         self._set_meta(tensors, pattern, chi)
         opt = _make_options(lib, chi, prec, oversample, power, cutoff, orth_tol, omega_seed,
                             jacobi_max_sweeps, stream, workspace, wait_cycles)
@@ -209,7 +220,7 @@ class CTM:
 
     def _set_meta(self, tensors, pattern, chi):
         self.Ly, self.Lx = len(pattern), len(pattern[0])
-        self.d, self.D, self.chi = tensors[0].shape[0], tensors[0].shape[1], chi
+        self.d, self.D, self.chi = tensors[0].shape[0], _bond_dim(tensors), chi
         self.n_tensors = len(tensors)
 
     @classmethod
@@ -231,7 +242,7 @@ class CTM:
             for x in range(Lx):
                 cell.pattern[y * Lx + x] = pattern[y][x]
         cell.n_tensors = len(tensors)
-        cell.d, cell.D = tensors[0].shape[0], tensors[0].shape[1]
+        cell.d, cell.D = tensors[0].shape[0], _bond_dim(tensors)
         cell.dtype = 1
         dummy = (C.c_void_p * len(tensors))(*([1] * len(tensors)))
         cell.tensors = C.cast(dummy, C.POINTER(C.c_void_p))
@@ -312,6 +323,13 @@ class CTM:
         Jv = np.asarray(J, dtype=np.float64)
         e = C.c_double()
         _check(self.lib.ipeps_energy(self.h, _dptr(Jv), C.byref(e)))
+        return e.value
+
+    def energy_star(self, J) -> float:
+        """Star-lattice Heisenberg energy per spin, J = (J_t, J_e) (ipeps_energy_star)."""
+        Jv = np.asarray(J, dtype=np.float64)
+        e = C.c_double()
+        _check(self.lib.ipeps_energy_star(self.h, _dptr(Jv), C.byref(e)))
         return e.value
 
     def kappa(self) -> complex:

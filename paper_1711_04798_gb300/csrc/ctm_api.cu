@@ -101,6 +101,7 @@ struct Lane {
 struct ipeps_ctm_s {
   int Lx, Ly, d, D, D2, chi, K, k, ntens;
   int pattern[4];
+  int leg[4][4];      // host tensor leg sizes (u, l, d, r) per tensor: D, or 1 for a trivial bond
   bool mixed;
   int dtype;
   ipeps_options opt;
@@ -780,6 +781,10 @@ static ipeps_status validate(const ipeps_cell* c, const ipeps_options* o) {
   if (c->d < 1 || c->d > 64 || c->D < 1 || c->D > 12) return fail(IPEPS_EINVAL, "d in 1..64, D in 1..12");
   if (c->dtype != IPEPS_REAL64 && c->dtype != IPEPS_COMPLEX128) return fail(IPEPS_EINVAL, "bad dtype");
   if (!c->tensors) return fail(IPEPS_EINVAL, "null tensors");
+  if (c->leg_dims)
+    for (int i = 0; i < 4 * c->n_tensors; ++i)
+      if (c->leg_dims[i] != 1 && c->leg_dims[i] != c->D)
+        return fail(IPEPS_EINVAL, "leg_dims[%d] = %d: legs are 1 (trivial) or D", i, c->leg_dims[i]);
   if (o->chi < c->D * c->D) return fail(IPEPS_EINVAL, "chi (%d) must be >= D*D (%d)", o->chi, c->D * c->D);
   if (o->chi > 1024) return fail(IPEPS_EINVAL, "chi > 1024");
   if (o->rsvd_oversample < 0 || o->rsvd_power < 0) return fail(IPEPS_EINVAL, "bad rsvd options");
@@ -830,7 +835,7 @@ static ipeps_status trace_init_env(ipeps_ctm h) {
   return IPEPS_OK;
 }
 
-static ipeps_status upload_one(ipeps_ctm h, const void* src, cplx* dst, std::vector<double>& buf);
+static ipeps_status upload_one(ipeps_ctm h, const void* src, cplx* dst, std::vector<double>& buf, int t);
 
 static ipeps_status check_status(ipeps_ctm h) {
   DevStatus st;
@@ -895,6 +900,8 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   h->ntens = c->n_tensors;
   for (int i = 0; i < 4; ++i) h->pattern[i] = i < c->Lx * c->Ly ? c->pattern[i] : 0;
   h->mixed = c->tensors_bra != nullptr;
+  for (int t = 0; t < 4; ++t)
+    for (int q = 0; q < 4; ++q) h->leg[t][q] = (c->leg_dims && t < c->n_tensors) ? c->leg_dims[4 * t + q] : c->D;
   h->dtype = c->dtype;
   h->opt = *o;
   if (!(h->opt.svd_cutoff > 0.0))  // automatic: above the noise floor of the contraction arithmetic
@@ -995,8 +1002,8 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
     const void* ket = c->tensors[t];
     const void* bra = h->mixed ? c->tensors_bra[t] : c->tensors[t];
     if (!ket || !bra) { st = fail(IPEPS_EINVAL, "null tensor pointer %d", t); break; }
-    st = upload_one(h, ket, h->A[0][t], buf);
-    if (st == IPEPS_OK) st = upload_one(h, bra, h->Bt[0][t], buf);
+    st = upload_one(h, ket, h->A[0][t], buf, t);
+    if (st == IPEPS_OK) st = upload_one(h, bra, h->Bt[0][t], buf, t);
   }
   if (st == IPEPS_OK) st = reset_status(h);
   if (st == IPEPS_OK) st = build_layers(h);
@@ -1074,12 +1081,25 @@ extern "C" uint64_t ipeps_ctm_launch_count(ipeps_ctm h) {
   return h ? launch_counter() - h->launches_at_create : 0;
 }
 
-static ipeps_status upload_one(ipeps_ctm h, const void* src, cplx* dst, std::vector<double>& buf) {
+static ipeps_status upload_one(ipeps_ctm h, const void* src, cplx* dst, std::vector<double>& buf, int t) {
   const long long n = (long long)h->d * h->D2 * h->D2;
   const double* sp = (const double*)src;
-  if (h->dtype == IPEPS_REAL64) {  // host-side promotion of real inputs
-    buf.resize(2 * n);
-    for (long long i = 0; i < n; ++i) { buf[2 * i] = sp[i]; buf[2 * i + 1] = 0.0; }
+  const int* L = h->leg[t];
+  const bool trivial = L[0] < h->D || L[1] < h->D || L[2] < h->D || L[3] < h->D;
+  if (h->dtype == IPEPS_REAL64 || trivial) {
+    // host-side promotion of real inputs; legs of size 1 embedded at index 0 of a D leg
+    buf.assign(2 * n, 0.0);
+    const int cw = h->dtype == IPEPS_REAL64 ? 1 : 2;  // doubles per input element
+    long long i = 0;
+    for (int p = 0; p < h->d; ++p)
+      for (int u = 0; u < L[0]; ++u)
+        for (int l = 0; l < L[1]; ++l)
+          for (int dd = 0; dd < L[2]; ++dd)
+            for (int r = 0; r < L[3]; ++r, ++i) {
+              const long long o = (((long long)p * h->D + u) * h->D + l) * h->D2 + (long long)dd * h->D + r;
+              buf[2 * o] = sp[cw * i];
+              buf[2 * o + 1] = cw == 2 ? sp[cw * i + 1] : 0.0;
+            }
     sp = buf.data();
   }
   CK(cudaMemcpyAsync(dst, sp, n * sizeof(cplx), cudaMemcpyHostToDevice, h->stream));
@@ -1098,8 +1118,8 @@ extern "C" ipeps_status ipeps_ctm_set_tensors(ipeps_ctm h, const void* const* te
   std::vector<double> buf;
   for (int t = 0; t < h->ntens; ++t) {
     if (!tensors[t] || (h->mixed && !tensors_bra[t])) return fail(IPEPS_EINVAL, "null tensor %d", t);
-    CKS(upload_one(h, tensors[t], h->A[0][t], buf));
-    CKS(upload_one(h, h->mixed ? tensors_bra[t] : tensors[t], h->Bt[0][t], buf));
+    CKS(upload_one(h, tensors[t], h->A[0][t], buf, t));
+    CKS(upload_one(h, h->mixed ? tensors_bra[t] : tensors[t], h->Bt[0][t], buf, t));
   }
   CKS(build_layers(h));
   CK(cudaStreamSynchronize(h->stream));
@@ -1793,11 +1813,36 @@ extern "C" ipeps_status ipeps_rdm(ipeps_ctm h, double* rho_h, double* rho_v) {
   return check_status(h);
 }
 
-static ipeps_status upload_bonds(ipeps_ctm h, const double J[3]) {
-  CM Hr(64), Hv(64);
-  ruby_bonds(J, &Hr, &Hv);
+// Star lattice (App. B) with Heisenberg couplings, one reading of its block
+// structure (the figure is not in the text): the three spins of a triangle
+// block site link to the left (spin 1), right (spin 2) and vertical (spin 3)
+// neighbours of the brick wall, A sites (x + y even) downwards, B sites
+// upwards, so the vertical bond with B on top is the trivial (D = 1) edge.
+// h_t = J_t (s1.s2 + s1.s3 + s2.s3) inside each triangle (half on each
+// horizontal bond), J_e s.s on the links between triangles; s = Pauli matrices.
+static CM dot_pair(int a, int b) {  // s_a (left/upper site) . s_b (right/lower site)
+  CM m(64);
+  for (char al : {'x', 'y', 'z'}) axpy(m, 1.0, kron(spin_op(al, a), spin_op(al, b)));
+  return m;
+}
+static void star_bonds(const double J[2], CM* Hh, CM* Hv) {
+  CM I8(8);
+  for (int i = 0; i < 8; ++i) I8.re[i * 8 + i] = 1.0;
+  CM ht(8);
+  const int pairs[3][2] = {{1, 2}, {1, 3}, {2, 3}};
+  for (const auto& pr : pairs)
+    for (char al : {'x', 'y', 'z'}) axpy(ht, J[0], matmul(spin_op(al, pr[0]), spin_op(al, pr[1])));
+  *Hh = CM(64);
+  axpy(*Hh, 0.5, kron(ht, I8));
+  axpy(*Hh, 0.5, kron(I8, ht));
+  axpy(*Hh, J[1], dot_pair(2, 1));
+  *Hv = CM(64);
+  axpy(*Hv, J[1], dot_pair(3, 3));
+}
+
+// bond operators H_r, H_l, H_u, H_d (64 x 64 complex, NULL = 0) to the device
+static ipeps_status upload_ops(ipeps_ctm h, const CM* const mats[4]) {
   std::vector<double> buf(2 * 64 * 64);
-  const CM* mats[4] = {&Hr, nullptr, &Hv, &Hv};  // H_r, H_l (= 0), H_u, H_d
   for (int m = 0; m < 4; ++m) {
     for (int i = 0; i < 64 * 64; ++i) {
       buf[2 * i] = mats[m] ? mats[m]->re[i] : 0.0;
@@ -1809,13 +1854,10 @@ static ipeps_status upload_bonds(ipeps_ctm h, const double J[3]) {
   return IPEPS_OK;
 }
 
-extern "C" ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e) {
-  if (!h || !J || !e) return fail(IPEPS_EINVAL, "null argument");
-  if (h->d != 8 || h->Lx != 2 || h->Ly != 2)
-    return fail(IPEPS_EINVAL, "the ruby energy needs a 2x2 cell of d = 8 block sites");
-  NvtxRange range("energy");
-  CKS(reset_status(h));
-  CKS(upload_bonds(h, J));
+// energy per spin = (1/12) sum over the cell's 8 bonds of Re tr(rho_b H_b), with
+// the operators of upload_ops: H_r / H_l for horizontal bonds with the A / B
+// site on the left, H_u / H_d for vertical bonds with A / B on top
+static ipeps_status energy_of_ops(ipeps_ctm h, double* e) {
   cplx *rh, *rv;
   CKS(rdm_buffers(h, &rh, &rv));
   const long long n2 = 64LL * 64 * 4;
@@ -1835,6 +1877,32 @@ extern "C" ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e) 
   CK(cudaMemcpyAsync(e, h->dacc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return check_status(h);
+}
+
+extern "C" ipeps_status ipeps_energy(ipeps_ctm h, const double J[3], double* e) {
+  if (!h || !J || !e) return fail(IPEPS_EINVAL, "null argument");
+  if (h->d != 8 || h->Lx != 2 || h->Ly != 2)
+    return fail(IPEPS_EINVAL, "the ruby energy needs a 2x2 cell of d = 8 block sites");
+  NvtxRange range("energy");
+  CKS(reset_status(h));
+  CM Hr(64), Hv(64);
+  ruby_bonds(J, &Hr, &Hv);
+  const CM* mats[4] = {&Hr, nullptr, &Hv, &Hv};  // H_r, H_l (= 0), H_u, H_d
+  CKS(upload_ops(h, mats));
+  return energy_of_ops(h, e);
+}
+
+extern "C" ipeps_status ipeps_energy_star(ipeps_ctm h, const double J[2], double* e) {
+  if (!h || !J || !e) return fail(IPEPS_EINVAL, "null argument");
+  if (h->d != 8 || h->Lx != 2 || h->Ly != 2)
+    return fail(IPEPS_EINVAL, "the star-lattice energy needs a 2x2 cell of d = 8 block sites");
+  NvtxRange range("energy star");
+  CKS(reset_status(h));
+  CM Hh(64), Hv(64);
+  star_bonds(J, &Hh, &Hv);
+  const CM* mats[4] = {&Hh, &Hh, &Hv, nullptr};  // H_r, H_l, H_u, H_d (the trivial edge)
+  CKS(upload_ops(h, mats));
+  return energy_of_ops(h, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -2174,6 +2242,11 @@ static ipeps_status half_ring_layout(ipeps_ctm h, int role, int xc, int y0, int 
 // contraction arithmetic, then one permutation into sigma.  Uses the handle's
 // scratch from its current top: t first, then the half rings and the
 // product's own work.  sigma must not overlap t.
+// complex elements of scratch the ring product's packed tensor-core operands
+// take, per n chi^2 (A: n x 2 chi^2 reals, B: 2n x 2 chi^2 reals, 2-byte parts:
+// two parts for BF16x3, three for BF16x6, one 4-byte part for TF32), with margin
+static double ring_pack_factor(ipeps_ctm h) { return h->opt.prec == IPEPS_PREC_BF16X6 ? 2.4 : 1.6; }
+
 static ipeps_status ring_sigma_dense(ipeps_ctm h, int role, int xc, int Nv, cplx* sigma) {
   const int c = h->chi, D = h->D;
   const int h1 = Nv / 2, h2 = Nv - h1;
@@ -2219,7 +2292,7 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
   // half rings: the last step's product output (chi^2 K^2) plus small
   // intermediates; ring product: its packed tensor-core operands (~1.5 n chi^2)
   const long long ring_work = std::max(c2 * std::max(K1 * K1, K2 * K2) * 5 / 4,
-                                       (long long)(1.6 * (double)n * (double)c2)) + (1LL << 24);
+                                       (long long)(ring_pack_factor(h) * (double)n * (double)c2)) + (1LL << 24);
   const long long ring_phase = n2 + c2 * (K1 * K1 + K2 * K2) + ring_work;
   const long long krylov_phase = 2 * n2 + lanczos_work_elems(n, max_iter) + 1024;
   const long long region_elems = std::max(ring_phase, krylov_phase);
@@ -2304,7 +2377,7 @@ extern "C" ipeps_status ipeps_boundary_renyi2(ipeps_ctm h, int x, int Nv, double
   for (int i = 0; i < Nv / 2; ++i) K1 *= h->D;
   for (int i = 0; i < Nv - Nv / 2; ++i) K2 *= h->D;
   const long long ring_work = std::max(c2 * std::max(K1 * K1, K2 * K2) * 5 / 4,
-                                       (long long)(1.6 * (double)n * (double)c2)) + (1LL << 24);
+                                       (long long)(ring_pack_factor(h) * (double)n * (double)c2)) + (1LL << 24);
   const long long ring_phase = n2 + c2 * (K1 * K1 + K2 * K2) + ring_work;
   // product phase: sigma_R, M and the product's packed operands (BF16x6: 2.25 n^2)
   const long long product_phase = 2 * n2 + (h->opt.prec == IPEPS_PREC_FP64 ? n2 : (9 * n2) / 4) + (1LL << 24);

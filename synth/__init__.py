@@ -178,3 +178,21 @@ def fidelity_line(seed: int = 0, n: int = 5, D: int = 2, d: int = 8, eps: float 
             ts.append(A)
         out.append(ts)
     return out
+
+
+def star_tensors(seed: int = 0, D: int = 2, d: int = 8, eps: float = 0.1):
+    """Block tensors of a star-lattice state on the 2x2 cell (App. B): the
+    all-up product state plus eps times complex normal noise, on the three
+    real legs of each triangle block site; the fourth leg is the trivial
+    (dimension 1) edge of the brick wall: u for A sites (pattern ids 0 and 3,
+    x + y even), d for B sites (ids 1 and 2).  Tensor t draws from stream
+    seed*16 + t.  Shapes (d, 1, D, D, D) for A, (d, D, D, 1, D) for B."""
+    out = []
+    for t in range(4):
+        shape = (d, 1, D, D, D) if t in (0, 3) else (d, D, D, 1, D)
+        size = int(np.prod(shape))
+        g = normal(seed * 16 + t, 2 * size)
+        A = eps * ((g[:size] + 1j * g[size:]) * np.sqrt(0.5)).reshape(shape)
+        A[0, 0, 0, 0, 0] += 1.0
+        out.append(A)
+    return out

@@ -24,9 +24,6 @@ beside this script, named for its workload:
     one sweep and the converged state (1e-10), with the number of sweeps
     taken.
 
-``product_noise_D5_chi100_cut5``
-    The same at cutoff 1e-5: one sweep and converged.
-
 ``product_noise_D5_chi100_rsvd_sweep1``
     One sweep of the D = 5, chi = 100 recipe with the randomized range finder
     (k = chi + 16, q = 2, test matrix from seed 7), for the record of how far
@@ -152,7 +149,6 @@ RECORDS = {
     "product_noise_D4_chi64_converged": d4_chi64,
     "product_noise_D5_chi100_cut8": lambda p: d5_chi100(p, 1e-8, converge=False),
     "product_noise_D5_chi100_cut6": lambda p: d5_chi100(p, 1e-6),
-    "product_noise_D5_chi100_cut5": lambda p: d5_chi100(p, 1e-5),
     "product_noise_D5_chi100_rsvd_sweep1": d5_rsvd_sweep1,
 }
 

@@ -74,11 +74,16 @@ def _good(lib):
     return cell, opt, ptrs
 
 
+_BAD_LEGS = (ctypes.c_int * 16)(*([4] * 7 + [2] + [4] * 8))  # leg 7 (tensor 1, r) neither 1 nor D
+
+
 def _set(obj, field, value):
     if field == "pattern":
         obj.pattern[2] = value
     elif field == "tensors":
         obj.tensors = None
+    elif field == "leg_dims":
+        obj.leg_dims = ctypes.cast(_BAD_LEGS, ctypes.POINTER(ctypes.c_int))
     else:
         setattr(obj, field, value)
 
@@ -90,6 +95,7 @@ _RULES = [
     ("cell", "pattern", 4, b"pattern"), ("cell", "pattern", -1, b"pattern"),
     ("cell", "d", 0, b"d in"), ("cell", "d", 65, b"d in"), ("cell", "D", 13, b"D in"),
     ("cell", "dtype", 9, b"dtype"), ("cell", "tensors", None, b"null tensors"),
+    ("cell", "leg_dims", None, b"leg_dims[7] = 2"),
     ("opt", "chi", 15, b"chi"), ("opt", "chi", 1025, b"chi > 1024"),
     ("opt", "rsvd_oversample", -1, b"rsvd"), ("opt", "rsvd_power", -1, b"rsvd"),
     ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 4, b"prec"),

@@ -876,3 +876,78 @@ def test_boundary_renyi2_equals_the_spectrum_purity():
     pst = O.sweep(O.make_state(ts, [[0, 1], [2, 3]], 1, 1), O.CTMOptions(chi=1, proj="svd"))
     S2, p = O.boundary_renyi2(pst, 0, 2)
     assert abs(S2) < 1e-14 and abs(p - 1) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# App. B: star lattice on the same block-site engine
+# ---------------------------------------------------------------------------
+def _star_link_energy(phis, Jt, Je):
+    """Energy per spin of a product of block-site states phi (8-vectors at
+    pattern [[0, 1], [2, 3]]) from an explicit list of the star lattice's
+    links in the cell: the three triangle edges of every site, the two
+    horizontal links per row (left site's spin 2 to right site's spin 1) and
+    the vertical links below the A sites (spin 3 to spin 3)."""
+    o = O.pauli_block_ops()
+
+    def ev(phi, op):
+        return np.vdot(phi, op @ phi).real / np.vdot(phi, phi).real
+
+    def spin(phi, k):
+        return np.array([ev(phi, o[f"{al}{k}"]) for al in "xyz"])
+
+    pat = [[0, 1], [2, 3]]
+    e = 0.0
+    for y in range(2):
+        for x in range(2):
+            p = phis[pat[y][x]]
+            e += Jt * sum(ev(p, sum(o[f"{al}{a}"] @ o[f"{al}{b}"] for al in "xyz"))
+                          for a, b in ((1, 2), (1, 3), (2, 3)))
+            right = phis[pat[y][(x + 1) % 2]]
+            e += Je * spin(p, 2) @ spin(right, 1)
+            if (x + y) % 2 == 0:  # A site: its link goes down
+                below = phis[pat[(y + 1) % 2][x]]
+                e += Je * spin(p, 3) @ spin(below, 3)
+    return e / 12.0
+
+
+def test_star_hamiltonian_terms():
+    H = O.star_bond_hamiltonians((0.7, 0.4))
+    for k in ("H_r", "H_l", "H_u"):
+        assert np.allclose(H[k], H[k].conj().T)
+    assert not np.any(H["H_d"])  # the trivial edge carries no term
+
+
+def test_star_product_states_closed_forms():
+    """D = 1 products: the CTM energy equals the link-list energy; the all-up
+    state gives J_t + J_e/2 per spin; a triangle in its total-spin-1/2 ground
+    space with J_e = 0 gives -J_t (sum_{i<j} s_i.s_j = 2 S(S+1) - 9/2 = -3 per
+    triangle)."""
+    rng = np.random.default_rng(17)
+    Jt, Je = 0.8, 0.35
+    phis = [rng.standard_normal(8) + 1j * rng.standard_normal(8) for _ in range(4)]
+    ts = [p.reshape(8, 1, 1, 1, 1) for p in phis]
+    pat = [[0, 1], [2, 3]]
+    st = O.sweep(O.make_state(ts, pat, 1, 1), O.CTMOptions(chi=1, proj="svd"))
+    e = O.energy_per_spin(O.bond_rdms(st, ts, pat), (Jt, Je), 2, 2, model="star")
+    assert abs(e - _star_link_energy(phis, Jt, Je)) < 1e-13
+    up = np.zeros(8)
+    up[0] = 1.0
+    st = O.sweep(O.make_state([up.reshape(8, 1, 1, 1, 1)] * 4, pat, 1, 1), O.CTMOptions(chi=1, proj="svd"))
+    e_up = O.energy_per_spin(O.bond_rdms(st, [up.reshape(8, 1, 1, 1, 1)] * 4, pat), (Jt, Je), 2, 2, model="star")
+    assert abs(e_up - (Jt + Je / 2)) < 1e-14
+    h = O.star_bond_hamiltonians((1.0, 0.0))["h_site"]
+    w, V = np.linalg.eigh(h)
+    assert abs(w[0] + 3.0) < 1e-12 and np.sum(np.abs(w + 3.0) < 1e-9) == 4  # S = 1/2 twice
+    gs = [V[:, 0].reshape(8, 1, 1, 1, 1)] * 4
+    st = O.sweep(O.make_state(gs, pat, 1, 1), O.CTMOptions(chi=1, proj="svd"))
+    e_gs = O.energy_per_spin(O.bond_rdms(st, gs, pat), (Jt, 0.0), 2, 2, model="star")
+    assert abs(e_gs + Jt) < 1e-13
+
+
+def test_star_tensors_trivial_legs():
+    """synth.star_tensors: the empty edge of each block site has dimension 1
+    (u for A sites, d for B sites), the product-state entry sits at index 0."""
+    ts = synth.star_tensors(seed=2, D=3)
+    assert [t.shape for t in ts] == [(8, 1, 3, 3, 3), (8, 3, 3, 1, 3), (8, 3, 3, 1, 3), (8, 1, 3, 3, 3)]
+    for t in ts:
+        assert abs(t[0, 0, 0, 0, 0] - 1.0) < 0.5
