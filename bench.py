@@ -398,9 +398,10 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-# DRAM bytes per launch of the dominant class from one ncu capture (profiles/),
-# keyed by (precision, bound); absent until captured for the current kernel
-TRAFFIC = {}
+# DRAM bytes per launch of the dominant class from one ncu capture (the mean of
+# the wide-product launches of profiles/bf16x6_path_D5_chi100_launches.md),
+# keyed by (precision, bound); absent where no capture of the current kernel exists
+TRAFFIC = {("bf16x6", "tensor"): 96.8e6}
 
 
 def flops_per_move(D, chi, q=2, over=16):
@@ -516,7 +517,8 @@ def run_scan(args, rank, world, local_rank):
         rep = members[0]
         times, es = {}, {}
         for prec in (args.prec, "fp64"):
-            g = CTM(rep["tensors"], rep["pattern"], chi, prec=prec, stream=stream.cuda_stream)
+            # the same truncation cutoff on both sides (the precision form's)
+            g = CTM(rep["tensors"], rep["pattern"], chi, prec=prec, cutoff=1e-6, stream=stream.cuda_stream)
             torch.cuda.synchronize()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(stream)
