@@ -265,6 +265,23 @@ ipeps_status ipeps_fidelity(ipeps_ctm h12, ipeps_ctm h11, ipeps_ctm h22, double*
 ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
                                 double* S_vn);
 
+/* Boundary spectrum beyond the ring approximation (Sec. IV: sigma_L and
+ * sigma_R are the dominant left and right eigenvectors of the cylinder's
+ * column transfer matrix; the rings of T approximate them).  Starting from
+ * the rings of ipeps_boundary_rho, power iteration with the exact transfer
+ * matrix of one cell period (sigma_R <- E_{x+1} .. E_{x+Lx} sigma_R, sigma_L
+ * <- sigma_L E_{x-Lx+1} .. E_x; E_c the column of double-layer tensors of
+ * cell column c, periodic over Nv rows), each iterate normalised and its
+ * phase aligned with the previous one, until both rings change by less than
+ * tol (Frobenius) or after iters iterations; then the spectrum and entropy as
+ * ipeps_boundary_rho.  *iters_used and *change report the iteration (either
+ * may be NULL); eig_out holds D^Nv doubles (caller-owned, may be NULL).
+ * Allocates about 9 D^(2 Nv) + 5 D^(2 Nv + 4) complex numbers for its
+ * duration.  Errors: EINVAL (Nv not a multiple of Ly, iters < 0, D^Nv > 4096,
+ * D^(2 Nv + 4) > 2^28), ENOMEM, ECUDA, ENUMERIC, ETIMEOUT (Jacobi budget). */
+ipeps_status ipeps_boundary_rho_refined(ipeps_ctm h, int x, int Nv, int iters, double tol, double* eig_out,
+                                        int* n_out, double* S_vn, int* iters_used, double* change);
+
 /* Second Renyi entropy of the boundary density operator (Sec. IV): with
  * sigma_L, sigma_R the rings of ipeps_boundary_rho (phase-fixed, Hermitised)
  * and M = sigma_L^T sigma_R formed densely (D^Nv x D^Nv, one GEMM in the

@@ -30,6 +30,9 @@ __all__ = [
     "boundary_spectrum",
     "spectrum_of_rings",
     "boundary_renyi2",
+    "column_transfer_apply",
+    "refined_rings",
+    "refined_boundary_spectrum",
     "boundary_spectrum_topk",
     "fixed_rings",
     "entropy",
@@ -417,6 +420,104 @@ def spectrum_of_rings(sL: np.ndarray, sR: np.ndarray) -> np.ndarray:
     H = W @ sR @ W
     lam = np.linalg.svd(H, compute_uv=False)
     return lam / lam.sum()
+
+
+_LETTERS = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+
+
+def column_transfer_apply(a_col, v: np.ndarray, side: str) -> np.ndarray:
+    """The cylinder's column transfer matrix (Sec. IV: sigma_L, sigma_R are its
+    dominant left and right eigenvectors) applied to a boundary vector.
+
+    a_col[i] is the double-layer tensor a[u, l, d, r] at row i of the column
+    (periodic vertically: the d leg of row Nv-1 meets the u leg of row 0); v
+    has one D^2 index per row.  side "R": (E v)(l_1..l_Nv) = sum over r, u of
+    prod_i a_i[u_i, l_i, u_{i+1}, r_i] v(r_1..r_Nv); side "L": the same sum
+    over l with v(l), leaving r.  Contracted row by row, the open up leg of
+    row 0 traced against the last row's down leg at the end
+    (``column_transfer_apply_dense`` writes the same sum as one einsum)."""
+    Nv = len(a_col)
+    D2 = a_col[0].shape[0]
+    w = v.reshape(D2, -1)
+    w = np.einsum("ulvr,rR->ulvR" if side == "R" else "ulvr,lR->urvR", a_col[0], w)
+    for i in range(1, Nv):
+        w = w.reshape(D2, D2 ** i, D2, D2, -1)
+        w = np.einsum("ALurR,ulvr->ALlvR" if side == "R" else "ALulR,ulvr->ALrvR", w, a_col[i])
+    w = w.reshape(D2, D2 ** Nv, D2)
+    return np.einsum("ALA->L", w).reshape([D2] * Nv)
+
+
+def column_transfer_apply_dense(a_col, v: np.ndarray, side: str) -> np.ndarray:
+    """``column_transfer_apply`` as a single einsum over the whole ring (for
+    small Nv: the check of the row-by-row order)."""
+    Nv = len(a_col)
+    L = _LETTERS
+    u, l, r = L[:Nv], L[Nv:2 * Nv], L[2 * Nv:3 * Nv]
+    ops = [f"{u[i]}{l[i]}{u[(i + 1) % Nv]}{r[i]}" for i in range(Nv)]
+    vin, vout = (r, l) if side == "R" else (l, r)
+    spec = ",".join(ops + [vin]) + "->" + vout
+    return np.einsum(spec, *a_col, v, optimize=True)
+
+
+def _ring_to_vector(S: np.ndarray, D: int, Nv: int) -> np.ndarray:
+    """Operator S[(k_1..k_Nv), (b_1..b_Nv)] as a vector over (k_i b_i) per row."""
+    t = S.reshape([D] * (2 * Nv))
+    perm = [q for i in range(Nv) for q in (i, Nv + i)]
+    return np.transpose(t, perm).reshape([D * D] * Nv)
+
+
+def _vector_to_ring(v: np.ndarray, D: int, Nv: int) -> np.ndarray:
+    t = v.reshape([D] * (2 * Nv))
+    perm = [2 * i for i in range(Nv)] + [2 * i + 1 for i in range(Nv)]
+    n = D ** Nv
+    return np.transpose(t, perm).reshape(n, n)
+
+
+def refined_rings(st: CTMState, x: int, Nv: int, iters: int, tol: float = 0.0):
+    """sigma_L and sigma_R of the cut between columns x and x+1 refined beyond
+    the ring approximation of Sec. IV: starting from the CTM rings (T4 at
+    column x+1, T2 at column x), power iteration with the exact column
+    transfer matrices of one cell period (sigma_R <- E_{x+1} ... E_{x+Lx}
+    sigma_R, sigma_L <- sigma_L E_{x-Lx+1} ... E_x), each iterate normalised
+    and its phase aligned with the previous one, until both change by less
+    than tol (Frobenius) or after iters iterations.  Returns (sigma_L,
+    sigma_R, iterations, last change) with the rings as D^Nv x D^Nv
+    operators."""
+    Lx, Ly, D = st.Lx, st.Ly, st.D
+    if Nv % Ly:
+        raise ValueError("Nv must be a multiple of the cell height")
+    col = {c: [st.a[i % Ly][c % Lx] for i in range(Nv)] for c in range(Lx)}
+    vs = {"L": _ring_to_vector(ring_sigma(st, "L", x, Nv), D, Nv),
+          "R": _ring_to_vector(ring_sigma(st, "R", x, Nv), D, Nv)}
+    for k in vs:
+        vs[k] = vs[k] / np.linalg.norm(vs[k])
+    it, change = 0, np.inf
+    while it < iters:
+        change = 0.0
+        for side in ("L", "R"):
+            v = vs[side]
+            cols = [(x + c) % Lx for c in range(Lx, 0, -1)] if side == "R" else \
+                   [(x - Lx + 1 + c) % Lx for c in range(Lx)]
+            for c in cols:
+                v = column_transfer_apply(col[c], v, side)
+            v = v / np.linalg.norm(v)
+            ov = np.vdot(vs[side], v)
+            v = v * (np.conj(ov) / abs(ov))
+            change = max(change, float(np.linalg.norm(v - vs[side])))
+            vs[side] = v
+        it += 1
+        if change < tol:
+            break
+    return _vector_to_ring(vs["L"], D, Nv), _vector_to_ring(vs["R"], D, Nv), it, change
+
+
+def refined_boundary_spectrum(st: CTMState, x: int, Nv: int, iters: int, tol: float = 0.0):
+    """The boundary spectrum (as ``boundary_spectrum``) of the refined rings,
+    and the iterations and last change of the refinement."""
+    sL, sR, it, change = refined_rings(st, x, Nv, iters, tol)
+    sL = sL * np.exp(-1j * np.angle(np.trace(sL)))
+    sR = sR * np.exp(-1j * np.angle(np.trace(sR)))
+    return spectrum_of_rings(0.5 * (sL + sL.conj().T), 0.5 * (sR + sR.conj().T)), it, change
 
 
 def boundary_renyi2(st: CTMState, x: int, Nv: int):

@@ -26,7 +26,7 @@ EXPORTS = [
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
     "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile", "ipeps_ctm_env_set",
     "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info", "ipeps_rdm_site", "ipeps_batch_fidelity",
-    "ipeps_boundary_renyi2", "ipeps_energy_star",
+    "ipeps_boundary_renyi2", "ipeps_energy_star", "ipeps_boundary_rho_refined",
 ]
 
 
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_batch_create.argtypes = [I, C.POINTER(Cell), C.POINTER(Options), I, C.POINTER(P)]
     lib.ipeps_batch_move.argtypes = [P, I, I]
     lib.ipeps_batch_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+    lib.ipeps_boundary_rho_refined.argtypes = [P, I, I, I, D, C.POINTER(D), C.POINTER(I), C.POINTER(D),
+                                               C.POINTER(I), C.POINTER(D)]
     lib.ipeps_energy_star.argtypes = [P, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_boundary_renyi2.argtypes = [P, I, I, C.POINTER(D), C.POINTER(D)]
     lib.ipeps_batch_fidelity.argtypes = [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(D),
@@ -350,6 +352,16 @@ class CTM:
         nout, S = C.c_int(), C.c_double()
         _check(self.lib.ipeps_boundary_rho(self.h, x, Nv, _dptr(eig), C.byref(nout), C.byref(S)))
         return eig[: nout.value], S.value
+
+    def boundary_rho_refined(self, x, Nv, iters=200, tol=1e-12):
+        """Boundary spectrum of the rings refined by the exact column transfer
+        matrix; returns (lam, S, iterations, last change)."""
+        n = self.D ** Nv
+        eig = np.zeros(n)
+        nout, S, it, ch = C.c_int(), C.c_double(), C.c_int(), C.c_double()
+        _check(self.lib.ipeps_boundary_rho_refined(self.h, x, Nv, iters, tol, _dptr(eig), C.byref(nout),
+                                                   C.byref(S), C.byref(it), C.byref(ch)))
+        return eig[: nout.value], S.value, it.value, ch.value
 
     def boundary_renyi2(self, x, Nv):
         """Second Renyi entropy of the boundary operator from traces; returns (S2, purity)."""

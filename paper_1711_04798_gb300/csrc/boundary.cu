@@ -153,9 +153,72 @@ __global__ void purity_finish_kernel(const double* __restrict__ partial, int nb,
   out[3] = b;
 }
 
+// ring operator S[(k_1..k_Nv), (b_1..b_Nv)] <-> vector v[(k_1 b_1) .. (k_Nv b_Nv)]
+// (base-D digits; to_vector selects the direction)
+__global__ void interleave_kernel(const cplx* __restrict__ in, cplx* __restrict__ out, int D, int Nv,
+                                  long long total, int to_vector) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    // e indexes the vector form: digits (k_1 b_1 ... k_Nv b_Nv), most significant first
+    long long rest = e, K = 0, B = 0, pw = 1;
+    for (int i = Nv - 1; i >= 0; --i) {
+      const long long b = rest % D;
+      rest /= D;
+      const long long k = rest % D;
+      rest /= D;
+      K += k * pw;
+      B += b * pw;
+      pw *= D;
+    }
+    const long long o = K * pw + B;  // pw = D^Nv: the operator's row length
+    if (to_vector)
+      out[e] = in[o];
+    else
+      out[o] = in[e];
+  }
+}
+
+// out = sum |a - b|^2 (fixed-order block partials, then one block)
+__global__ void diff_norm2_kernel(const cplx* __restrict__ a, const cplx* __restrict__ b, long long n,
+                                  double* __restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double dr = a[e].x - b[e].x, di = a[e].y - b[e].y;
+    s += dr * dr + di * di;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += partial[i];
+    *out = s;
+  }
+}
+
 }  // namespace
 
 namespace bnd {
+void launch_interleave(cudaStream_t s, const cplx* in, cplx* out, int D, int Nv, bool to_vector) {
+  long long total = 1;
+  for (int i = 0; i < 2 * Nv; ++i) total *= D;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  interleave_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, D, Nv, total, to_vector ? 1 : 0);
+}
+// *out = sum |a - b|^2; work >= 513 doubles
+void launch_diff_norm2(cudaStream_t s, const cplx* a, const cplx* b, long long n, double* work, double* out) {
+  diff_norm2_kernel<<<512, 256, 0, s>>>(a, b, n, work);
+  sum_partials_kernel<<<1, 32, 0, s>>>(work, 512, out);
+}
 // out[0..3] = tr M and tr M^2 (re, im) of the dense n x n M; work >= 2 + 2 * 1216 doubles
 void launch_purity(cudaStream_t s, const cplx* M, int n, double* work, double* out) {
   const int nb = 1216;  // 152 SMs x 8

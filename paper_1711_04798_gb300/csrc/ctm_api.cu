@@ -2125,30 +2125,13 @@ void launch_spectrum_finish(cudaStream_t s, const double* sigma, int n, double* 
 void launch_scale_cols(cudaStream_t s, cplx* G, int n, const double* sigma);
 }  // namespace bnd
 
-extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
-                                           double* S_vn) {
-  if (!h) return fail(IPEPS_EINVAL, "null handle");
-  if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
-  long long n = 1;
-  for (int i = 0; i < Nv; ++i) n *= h->D;
-  if (n > 4096) return fail(IPEPS_EINVAL, "D^Nv = %lld > 4096", n);
-  NvtxRange range("boundary rho");
-  CKS(reset_status(h));
-  const int nn = (int)n;
-  const long long mark = h->scratch_top;
-  cplx* sL = scratch_alloc(h, n * n);
-  cplx* sR = scratch_alloc(h, n * n);
-  cplx* G = scratch_alloc(h, n * n);
-  cplx* Hm = scratch_alloc(h, n * n);
-  cplx* Vt = scratch_alloc(h, n * n);
-  if (!sL || !sR || !G || !Hm || !Vt) return fail(IPEPS_ENOMEM, "scratch exhausted (boundary rho)");
-  const long long inner = h->scratch_top;
-  const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
-  CKS(ring_sigma(h, 3, xl, Nv, sL));
-  h->scratch_top = inner;
-  CKS(ring_sigma(h, 1, xr, Nv, sR));
-  h->scratch_top = inner;
-  // phase-fix by the trace, Hermitise; sL is replaced by sigma_L^T
+// Dense boundary spectrum of the rings sL, sR (n x n operators, overwritten):
+// phase-fix by the trace and Hermitise (sL replaced by sigma_L^T), the
+// |sigma_L^T|^(1/2) factor from a Jacobi SVD, the similar operator and its
+// singular values, normalised, with their entropy.  G, Hm, Vt: n^2 work each.
+static ipeps_status spectrum_of_rings_dev(ipeps_ctm h, cplx* sL, cplx* sR, int nn, cplx* G, cplx* Hm, cplx* Vt,
+                                          double* eig_out, double* S_vn) {
+  const long long n = nn;
   bnd::launch_phase_herm(h->stream, sL, nn, true, h->dwork);
   bnd::launch_phase_herm(h->stream, sR, nn, false, h->dwork);
   count_launch(2);
@@ -2178,9 +2161,189 @@ extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* e
   double S = 0;
   CK(cudaMemcpyAsync(&S, h->dacc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (S_vn) *S_vn = S;
+  return IPEPS_OK;
+}
+
+extern "C" ipeps_status ipeps_boundary_rho(ipeps_ctm h, int x, int Nv, double* eig_out, int* n_out,
+                                           double* S_vn) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
+  long long n = 1;
+  for (int i = 0; i < Nv; ++i) n *= h->D;
+  if (n > 4096) return fail(IPEPS_EINVAL, "D^Nv = %lld > 4096", n);
+  NvtxRange range("boundary rho");
+  CKS(reset_status(h));
+  const int nn = (int)n;
+  const long long mark = h->scratch_top;
+  cplx* sL = scratch_alloc(h, n * n);
+  cplx* sR = scratch_alloc(h, n * n);
+  cplx* G = scratch_alloc(h, n * n);
+  cplx* Hm = scratch_alloc(h, n * n);
+  cplx* Vt = scratch_alloc(h, n * n);
+  if (!sL || !sR || !G || !Hm || !Vt) return fail(IPEPS_ENOMEM, "scratch exhausted (boundary rho)");
+  const long long inner = h->scratch_top;
+  const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
+  CKS(ring_sigma(h, 3, xl, Nv, sL));
+  h->scratch_top = inner;
+  CKS(ring_sigma(h, 1, xr, Nv, sR));
+  h->scratch_top = inner;
+  CKS(spectrum_of_rings_dev(h, sL, sR, nn, G, Hm, Vt, eig_out, S_vn));
   h->scratch_top = mark;
   if (n_out) *n_out = nn;
-  if (S_vn) *S_vn = S;
+  return check_status(h);
+}
+
+namespace bnd {
+void launch_interleave(cudaStream_t s, const cplx* in, cplx* out, int D, int Nv, bool to_vector);
+void launch_diff_norm2(cudaStream_t s, const cplx* a, const cplx* b, long long n, double* work, double* out);
+}  // namespace bnd
+
+// One column of the cylinder's transfer matrix (rows 0..Nv-1 of column col,
+// periodic vertically) applied to a boundary vector v (one D^2 index per row):
+// right = true: out(l) = sum_{r,u} prod_i a_i[u_i, l_i, u_{i+1}, r_i] v(r);
+// right = false: the same with the roles of l and r exchanged (v from the left).
+// Rows are absorbed one at a time; the open u leg of row 0 (A) is traced with
+// the last row's d leg at the end.  w0, w1: D^(2 Nv + 4) complex each.
+static ipeps_status column_apply(ipeps_ctm h, int col, int Nv, const cplx* v, cplx* out, bool right, cplx* w0,
+                                 cplx* w1, const cplx* ident) {
+  const int D2 = h->D2;
+  long long Rn = 1;
+  for (int i = 0; i < Nv - 1; ++i) Rn *= D2;
+  cplx* wa = w0;
+  cplx* wb = w1;
+  CKS(contract(h, right ? "ulvr,rR->ulvR" : "ulvr,lR->urvR", tv(site_a(h, 0, col, 0), {D2, D2, D2, D2}), false,
+               tv((cplx*)v, {D2, (int)Rn}), false, tv(wa, {D2, D2, D2, (int)Rn})));
+  long long Ld = D2;
+  for (int i = 1; i < Nv; ++i) {
+    Rn /= D2;
+    CKS(contract(h, right ? "ALurR,ulvr->ALlvR" : "ALulR,ulvr->ALrvR",
+                 tv(wa, {D2, (int)Ld, D2, D2, (int)Rn}), false, tv(site_a(h, 0, col, i), {D2, D2, D2, D2}), false,
+                 tv(wb, {D2, (int)Ld, D2, D2, (int)Rn})));
+    Ld *= D2;
+    std::swap(wa, wb);
+  }
+  CKS(contract(h, "ALB,AB->L", tv(wa, {D2, (int)Ld, D2}), false, tv((cplx*)ident, {D2, D2}), false,
+               tv(out, {(int)Ld})));
+  return IPEPS_OK;
+}
+
+// Sec. IV beyond the ring approximation: sigma_L, sigma_R refined by power
+// iteration with the exact column transfer matrices of one cell period,
+// starting from the CTM rings; then the dense boundary spectrum.
+extern "C" ipeps_status ipeps_boundary_rho_refined(ipeps_ctm h, int x, int Nv, int iters, double tol,
+                                                   double* eig_out, int* n_out, double* S_vn, int* iters_used,
+                                                   double* change) {
+  if (!h) return fail(IPEPS_EINVAL, "null handle");
+  if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
+  if (iters < 0) return fail(IPEPS_EINVAL, "iters must be >= 0");
+  long long n = 1;
+  for (int i = 0; i < Nv; ++i) n *= h->D;
+  if (n > 4096) return fail(IPEPS_EINVAL, "D^Nv = %lld > 4096", n);
+  const long long n2 = n * n, big = n2 * h->D2 * h->D2;
+  if (big > (1LL << 28)) return fail(IPEPS_EINVAL, "D^(2 Nv + 4) = %lld above 2^28", big);
+  NvtxRange range("boundary rho refined");
+  CKS(reset_status(h));
+  // region: vectors vL, vR, res, tmp (n^2 each), identity, w0, w1 (big each),
+  // spectrum work (5 n^2), contraction scratch (the rest)
+  const long long D4 = (long long)h->D2 * h->D2;
+  const long long id_elems = (D4 + 15) & ~15LL;
+  const long long fixed = 4 * n2 + id_elems + 2 * big + 5 * n2;
+  const long long region_elems = fixed + 3 * big + 4 * (long long)h->chi * h->chi * (n + 64) + (1LL << 22);
+  cplx* mem = nullptr;
+  cudaError_t e = dev_alloc((void**)&mem, (size_t)region_elems * sizeof(cplx));
+  if (e != cudaSuccess)
+    return fail(IPEPS_ENOMEM, "boundary rho refined: cudaMalloc of %.1f GB failed: %s",
+                (double)region_elems * 16e-9, cudaGetErrorString(e));
+  cplx* vec[2] = {mem, mem + n2};  // [0] = sigma_L, [1] = sigma_R
+  cplx* res = mem + 2 * n2;
+  cplx* tmp = mem + 3 * n2;
+  cplx* ident = mem + 4 * n2;
+  cplx* w0 = ident + id_elems;
+  cplx* w1 = w0 + big;
+  cplx* sL = w1 + big;
+  cplx* sR = sL + n2;
+  cplx* G = sR + n2;
+  cplx* Hm = G + n2;
+  cplx* Vt = Hm + n2;
+  cplx* save_scratch = h->scratch;
+  const long long save_elems = h->scratch_elems, save_top = h->scratch_top;
+  h->scratch = mem + fixed;
+  h->scratch_elems = region_elems - fixed;
+  h->scratch_top = 0;
+  auto body = [&]() -> ipeps_status {
+    std::vector<double> id(2 * D4, 0.0);
+    for (int i = 0; i < h->D2; ++i) id[2 * (i * h->D2 + i)] = 1.0;
+    CK(cudaMemcpyAsync(ident, id.data(), id.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const int xl = ((x + 1) % h->Lx + h->Lx) % h->Lx, xr = ((x % h->Lx) + h->Lx) % h->Lx;
+    CKS(ring_sigma(h, 3, xl, Nv, sL));
+    h->scratch_top = 0;
+    CKS(ring_sigma(h, 1, xr, Nv, sR));
+    h->scratch_top = 0;
+    bnd::launch_interleave(h->stream, sL, vec[0], h->D, Nv, true);
+    bnd::launch_interleave(h->stream, sR, vec[1], h->D, Nv, true);
+    count_launch(2);
+    CK(cudaGetLastError());
+    for (int q = 0; q < 2; ++q) CK(normalize(h->stream, vec[q], n2, h->dwork, h->st));
+    double2* partial = (double2*)(h->dwork + 2048);  // 512 double2 after the norm work
+    double2* ovd = (double2*)(h->dwork + 3072);
+    double* d2 = h->dwork + 3080;
+    int it = 0;
+    double ch = INFINITY;
+    while (it < iters) {
+      ch = 0.0;
+      for (int q = 0; q < 2; ++q) {
+        const bool right = q == 1;
+        // one cell period: sigma_R <- E_{x+1} .. E_{x+Lx} sigma_R; sigma_L <- sigma_L E_{x-Lx+1} .. E_x
+        const cplx* in = vec[q];
+        cplx* bufs[2] = {res, tmp};
+        int nb = 0;
+        for (int c = 0; c < h->Lx; ++c) {
+          const int col = right ? ((x + h->Lx - c) % h->Lx + h->Lx) % h->Lx : ((x - h->Lx + 1 + c) % h->Lx + h->Lx) % h->Lx;
+          cplx* out = bufs[nb];
+          CKS(column_apply(h, col, Nv, in, out, right, w0, w1, ident));
+          h->scratch_top = 0;
+          in = out;
+          nb ^= 1;
+        }
+        cplx* nv = (cplx*)in;
+        CK(normalize(h->stream, nv, n2, h->dwork, h->st));
+        CK(zdotc_dev(h->stream, vec[q], nv, n2, partial, ovd));
+        double2 ov;
+        CK(cudaMemcpyAsync(&ov, ovd, sizeof ov, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const double m = hypot(ov.x, ov.y);
+        if (!(m > 0)) return fail(IPEPS_ENUMERIC, "boundary rho refined: orthogonal iterates");
+        const int dims1[1] = {(int)n2}, perm1[1] = {0};
+        CK(permute(h->stream, nv, nv, 1, dims1, perm1, false, make_double2(ov.x / m, -ov.y / m)));
+        bnd::launch_diff_norm2(h->stream, nv, vec[q], n2, h->dwork, d2);
+        count_launch(2);
+        double dd = 0.0;
+        CK(cudaMemcpyAsync(&dd, d2, sizeof dd, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(vec[q], nv, n2 * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        ch = std::max(ch, sqrt(dd));
+      }
+      ++it;
+      if (ch < tol) break;
+    }
+    bnd::launch_interleave(h->stream, vec[0], sL, h->D, Nv, false);
+    bnd::launch_interleave(h->stream, vec[1], sR, h->D, Nv, false);
+    count_launch(2);
+    CK(cudaGetLastError());
+    CKS(spectrum_of_rings_dev(h, sL, sR, (int)n, G, Hm, Vt, eig_out, S_vn));
+    if (iters_used) *iters_used = it;
+    if (change) *change = ch;
+    return IPEPS_OK;
+  };
+  const ipeps_status st = body();
+  h->scratch = save_scratch;
+  h->scratch_elems = save_elems;
+  h->scratch_top = save_top;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(mem);
+  CKS(st);
+  if (n_out) *n_out = (int)n;
   return check_status(h);
 }
 
