@@ -280,7 +280,7 @@ def kernel_classes(g, prec, ms_step, steps, peaks, peak_src, zpk):
     classes.append({"kernel": "Jacobi SVD kernels (FP64, projector cores and orthonormalisation)", "bound": "alu",
                     "ms": rd[1]["ms"], "work": None, "launches": rd[1]["launches"], "peak": None, "unit": None,
                     "peak_source": "latency-bound FP64 rotations; mean sweeps per call "
-                                   f"{rd[1]['flops']:.2f}"})
+                                   f"{rd[1]['flops']:.2f}", "mean_sweeps_per_call": rd[1]["flops"]})
     for c in classes:
         c["achieved"] = c["work"] / (c["ms"] * 1e-3) if c["ms"] and c["work"] else None
         c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
@@ -367,8 +367,9 @@ def run_ours(args, rank, world, local_rank):
             "dominant_by": "CUDA-event time per kernel class in a profiled pass of the same steps "
                            f"({ms_prof:.1f} ms per step with per-launch events, vs {ms_max / args.steps:.1f} ms "
                            "as CUDA graphs)",
-            "by_class": [{k: c.get(k) for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
-                                                "share_of_step", "launches", "ms_per_launch")} for c in classes]}
+            "by_class": [{k: c[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "share_of_step",
+                                            "launches", "ms_per_launch", "mean_sweeps_per_call") if k in c}
+                         for c in classes]}
     fp64_cmp = None
     if args.prec != "fp64" and not args.no_fp64_check:
         fp64_cmp = fp64_comparison(args, w, J, stream, torch, value)

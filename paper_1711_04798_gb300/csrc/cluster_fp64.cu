@@ -21,10 +21,6 @@ constexpr int JC_THREADS = 256;         // Jacobi: 8 warps per CTA, two per row 
 constexpr int CL_SMEM = 200 * 1024;     // dynamic shared memory bound per CTA
 int g_csize = 0;                        // CTAs per cluster (16 if schedulable, else 8)
 
-__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -64,11 +60,11 @@ __device__ __forceinline__ void pair_of(int r, int p, int np, int rounds, int* i
 }
 
 // One-sided Jacobi on the n rows of G (length m): rows and, with Vt, the rows
-// of the accumulated rotation (length n, from the identity) in the cluster's
-// shared memory.
+// of the accumulated rotation (length n, from the identity, or from Vt itself
+// with warm) in the cluster's shared memory.
 __global__ void __launch_bounds__(JC_THREADS)
     jacobi_cluster_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt, int max_sweeps,
-                          double tol, double4_16a* __restrict__ log, int* sweeps_used, DevStatus* st) {
+                          double tol, double4_16a* __restrict__ log, int* sweeps_used, DevStatus* st, int warm) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = JC_THREADS / 32;
@@ -89,7 +85,8 @@ __global__ void __launch_bounds__(JC_THREADS)
       f += x.x * x.x + x.y * x.y;
     }
     if (Vt)
-      for (int t = threadIdx.x; t < n; t += JC_THREADS) vl[(long long)l * n + t] = make_double2(t == i ? 1.0 : 0.0, 0.0);
+      for (int t = threadIdx.x; t < n; t += JC_THREADS)
+        vl[(long long)l * n + t] = warm ? Vt[(long long)i * n + t] : make_double2(t == i ? 1.0 : 0.0, 0.0);
   }
   f = warp_sum(f);
   __shared__ double s_w[JC_THREADS / 32];
@@ -171,19 +168,12 @@ __global__ void __launch_bounds__(JC_THREADS)
           c = __shfl_sync(0xffffffffu, c, 0);
           sn = __shfl_sync(0xffffffffu, sn, 0);
           const cplx ph = make_double2(__shfl_sync(0xffffffffu, phr, 0), __shfl_sync(0xffffffffu, phi, 0));
-          for (int q = lane + 32 * half; q < m; q += 64) {
-            const cplx x = gi[q], y = cmul(gj[q], ph);
-            gi[q] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
-            gj[q] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
-          }
+          const cplx sq = make_double2(sn * ph.x, sn * ph.y), sp = make_double2(sn * ph.x, -sn * ph.y);
+          for (int q = lane + 32 * half; q < m; q += 64) jac_rotate(gi[q], gj[q], c, sq, sp);
           if (Vt) {
             cplx* vi = vrow(i);
             cplx* vj = vrow(j);
-            for (int q = lane + 32 * half; q < n; q += 64) {
-              const cplx x = vi[q], y = cmul(vj[q], ph);
-              vi[q] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
-              vj[q] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
-            }
+            for (int q = lane + 32 * half; q < n; q += 64) jac_rotate(vi[q], vj[q], c, sq, sp);
           }
         }
       }
@@ -225,15 +215,17 @@ __global__ void __launch_bounds__(JC_THREADS)
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-// Vt (n x n) = the logged rotations applied to the identity, one CTA per
-// column q (columns are independent): thread p applies pair p of every round,
-// rounds in order, the column held in shared memory.  Rotation c = 2 marks a
-// pair that was not rotated.
+// Vt (n x n) = the logged rotations applied to the identity (warm: to Vt as
+// it is, in place), one CTA per column q (columns are independent: a CTA
+// reads and writes its own column only): thread p applies pair p of every
+// round, rounds in order, the column held in shared memory.  Rotation c = 2
+// marks a pair that was not rotated.
 __global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4_16a* __restrict__ log,
-                                     const int* __restrict__ sweeps_used) {
+                                     const int* __restrict__ sweeps_used, int warm) {
   extern __shared__ cplx col[];
   const int q = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = make_double2(i == q ? 1.0 : 0.0, 0.0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    col[i] = warm ? Vt[(long long)i * n + q] : make_double2(i == q ? 1.0 : 0.0, 0.0);
   __syncthreads();
   const int sweeps = *sweeps_used;
   const int np = (n + 1) & ~1;
@@ -247,9 +239,7 @@ __global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4
           int i, j;
           pair_of(r, p, np, rounds, &i, &j);
           const double c = rec.x, s = rec.y;
-          const cplx x = col[i], y = cmul(col[j], make_double2(rec.z, rec.w));
-          col[i] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-          col[j] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+          jac_rotate(col[i], col[j], c, make_double2(s * rec.z, s * rec.w), make_double2(s * rec.z, -s * rec.w));
         }
       }
       __syncthreads();
@@ -394,7 +384,7 @@ long long jacobi_log_elems(int n, int max_sweeps) {
 }
 
 cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
-                           DevStatus* st, cplx* rotlog, int* sweeps_used) {
+                           DevStatus* st, cplx* rotlog, int* sweeps_used, bool warm_v) {
   cudaError_t e;
   if ((e = cluster_init()) != cudaSuccess) return e;
   const bool replay = Vt && rotlog && sweeps_used && n <= 2048;
@@ -404,13 +394,15 @@ cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg,
   const long long R = (n + g_csize - 1) / g_csize;
   const size_t smem = (size_t)(R * ((long long)m + (Vin ? n : 0)) * sizeof(cplx));
   double tol = (double)m * 2.220446049250313e-16;
-  void* args[] = {&G, &n, &m, &ldg, &Vin, &max_sweeps, &tol, &logp, &su, &st};
+  int warm = warm_v && Vin ? 1 : 0;
+  void* args[] = {&G, &n, &m, &ldg, &Vin, &max_sweeps, &tol, &logp, &su, &st, &warm};
   e = launch_cluster((const void*)jacobi_cluster_kernel, args, smem, s, JC_THREADS);
   count_launch();
   if (e != cudaSuccess || !replay) return e;
   const int npairs = ((n + 1) & ~1) / 2;
   const int threads = (npairs + 31) / 32 * 32;
-  jacobi_replay_kernel<<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4_16a*)rotlog, sweeps_used);
+  jacobi_replay_kernel<<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4_16a*)rotlog, sweeps_used,
+                                                            warm_v ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }

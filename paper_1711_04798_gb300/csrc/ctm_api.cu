@@ -126,6 +126,10 @@ struct ipeps_ctm_s {
   cplx* Ptil[2];      // chi x K
   cplx* Vt;           // k x k
   cplx* Gsel;         // chi x k
+  // precision forms: per cut (frame, position), the right singular vectors of
+  // the core found at the previous visit (k x k, rows = columns of V), the
+  // start of the next Jacobi SVD of that cut
+  cplx* Vwarm[4][4];
   cplx* Hbond[4];     // 64x64 ruby bond operators: H_r, H_l, H_u, H_d
   double* sigma;
   double* s_sel;
@@ -339,6 +343,8 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   add(std::max(k, 4096), 4);
   add(4, 4);
   add(4096, 8);
+  if (prec != IPEPS_PREC_FP64)
+    for (int i = 0; i < 4 * Lx * Ly; ++i) add((long long)k * k, 16);
   s.total = tot + 4096;
   return s;
 }
@@ -819,6 +825,10 @@ static ipeps_status build_layers(ipeps_ctm h) {
 }
 
 static ipeps_status trace_init_env(ipeps_ctm h) {
+  // a fresh environment starts every cut's Jacobi SVD from the identity again
+  for (int f = 0; f < 4; ++f)
+    for (int i = 0; i < 4; ++i)
+      if (h->Vwarm[f][i]) CK(set_identity(h->stream, h->Vwarm[f][i], h->k));
   // role -> neighbouring site offset (frame 0)
   static const int off[8][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}, {0, -1}, {1, 0}, {0, 1}, {-1, 0}};
   for (int y = 0; y < h->Ly; ++y)
@@ -980,6 +990,11 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   need(h->alt.perm = carve<int>(h, std::max(h->k, 4096)));
   need(h->alt.counters = carve<int>(h, 4));
   need(h->alt.dwork = carve<double>(h, 4096));
+  for (int f = 0; f < 4; ++f)
+    for (int i = 0; i < 4; ++i)
+      h->Vwarm[f][i] = (o->prec != IPEPS_PREC_FP64 && i < h->Lx * h->Ly) ? carve<cplx>(h, (size_t)h->k * h->k) : nullptr;
+  for (int f = 0; f < 4 && o->prec != IPEPS_PREC_FP64; ++f)
+    for (int i = 0; i < h->Lx * h->Ly; ++i) need(h->Vwarm[f][i]);
   if (!ok) {
     if (h->own_mem) cudaFree(h->base);
     delete h;
@@ -1316,8 +1331,17 @@ static ipeps_status orth_chol(ipeps_ctm h, cplx* Y, cplx* tmp, bool twice) {
 // Precision form SVD of W (K x k, stored as the k rows Wt): W = Q R by
 // CholeskyQR2 (R = R2 R1, backward stable), one-sided Jacobi on the columns of
 // the k x k R (R V = U_R S), then out rows = (W v_i)^T = s_i u_i^T, sigma = s,
-// h->Vt rows = columns of V.
-static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
+// Vt rows = columns of V.
+//
+// Vt holds on entry the V this cut's SVD found at its previous visit (the
+// identity at the first): the Jacobi starts from R V_prev and accumulates its
+// rotations onto V_prev.  Between CTM iterations R changes little, so the
+// rotated core is already nearly column-orthogonal and the sweeps converge
+// quadratically from there; the SVD found is the same (the Jacobi stops on
+// the same orthogonality test whatever its start).  The unitarity of the
+// accumulated V degrades like sqrt(rotations) x 1e-16, ~1e-13 after thousands
+// of visits, far below the 1e-6 truncation of the precision forms.
+static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out, cplx* Vt) {
   const int k = h->k, K = h->K;
   const long long mark = h->scratch_top;
   cplx* R1 = scratch_alloc(h, (long long)k * k);
@@ -1328,18 +1352,20 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out) {
   CKS(cholqr_pass(h, out, nullptr, R2, 1e-14, false));  // only R2 is needed
   // Rt = (R2 R1)^T: rows of Rt are the columns of R
   CK(proj_zgemm(h, 8.0 * k * (k + 1.0) * (k + 2.0) / 6.0, k, k, k, R1, k, OP_T, R2, k, OP_T, Rt, k, ZG_A_LOWER));
+  // R1 = V_prev^T Rt: rows are the columns of R V_prev
+  CK(proj_zgemm(h, 8.0 * k * (double)k * k, k, k, k, Vt, k, OP_N, Rt, k, OP_N, R1, k, 0));
   {
     cudaEvent_t a = nullptr;
     prof_begin(h, &a);
     const long long nlog = jacobi_log_elems(k, h->opt.jacobi_max_sweeps);
     cplx* rotlog = scratch_alloc(h, nlog);
     if (!rotlog) return fail(IPEPS_ENOMEM, "scratch exhausted (rotation log)");
-    CK(jacobi_rows(h->stream, Rt, k, k, k, h->Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork,
-                   h->counters, h->st, rotlog, nlog, h->opt.wait_cycles));
+    CK(jacobi_rows(h->stream, R1, k, k, k, Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork, h->counters,
+                   h->st, rotlog, nlog, h->opt.wait_cycles, true));
     prof_end(h, a, 0.0, 1);
   }
   // out = V^T Wt  (rows (W v_i)^T)
-  CK(proj_zgemm(h, 8.0 * k * (double)K * k, k, K, k, h->Vt, k, OP_N, Wt, K, OP_N, out, K, 0));
+  CK(proj_zgemm(h, 8.0 * k * (double)K * k, k, K, k, Vt, k, OP_N, Wt, K, OP_N, out, K, 0));
   CK(row_norms(h->stream, out, k, K, K, h->sigma));
   h->scratch_top = mark;
   return IPEPS_OK;
@@ -1368,6 +1394,7 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   // W = X^H Q (K x k) stored as Wt; its SVD W = U_w S V_w^H gives X ~ (Q V_w) S U_w^H
   CKS(apply_XHT(h, Qt, Zt, k));
   cplx* Wrot;  // rows sigma_i u_i^T
+  cplx* Vt = h->Vt;  // rows = columns of V
   if (fp64) {
     cudaEvent_t a = nullptr;
     prof_begin(h, &a);
@@ -1376,7 +1403,10 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
     prof_end(h, a, 0.0, 1);
     Wrot = Zt;
   } else {
-    CKS(svd_rows_chol(h, Zt, h->thin[2]));
+    int lx, ly;
+    frame_dims(h, f, &lx, &ly);
+    Vt = h->Vwarm[f][y * lx + x];
+    CKS(svd_rows_chol(h, Zt, h->thin[2], Vt));
     Wrot = h->thin[2];
   }
   cplx* Vt_chi = (Wrot == Zt) ? h->thin[2] : Zt;
@@ -1386,7 +1416,7 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   // V_chi^T rows = selected columns of U_w (normalised rows of Wrot)
   CK(gather_rows(h->stream, Wrot, K, Vt_chi, K, h->perm, h->sigma, chi, K, true));
   // U_chi^T = (V_w[:, sel])^T Q^T
-  CK(gather_rows(h->stream, h->Vt, k, h->Gsel, k, h->perm, h->sigma, chi, k, false));
+  CK(gather_rows(h->stream, Vt, k, h->Gsel, k, h->perm, h->sigma, chi, k, false));
   CKS(gemm_dispatch(h, chi, K, k, h->Gsel, k, OP_N, Qt, K, OP_N, Ut_chi, K, ONE));
   // P^T = S^-1/2 V^T Q3 Q4^T ;  Ptil = S^-1/2 U^H Q2^T Q1^T
   if (!fp64) {
@@ -1560,15 +1590,19 @@ extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
     h->own_tuner = true;
   }
   drop_graphs(h);  // captured with the previous tile choices
-  // snapshot of the environment, restored after the tuning sweep
+  // snapshot of the environment and of the cuts' Jacobi starts, restored
+  // after the tuning sweep (later results do not depend on the tuning)
   const int ncell = h->Lx * h->Ly;
   const size_t cb = (size_t)h->chi * h->chi * sizeof(cplx), tb = (size_t)h->chi * h->D2 * h->chi * sizeof(cplx);
+  const size_t vb = (size_t)h->k * h->k * sizeof(cplx), env_bytes = 4 * ncell * (cb + tb);
   char* snap = nullptr;
-  CK(dev_alloc((void**)&snap, 4 * ncell * (cb + tb)));
+  CK(dev_alloc((void**)&snap, env_bytes + 4 * ncell * vb));
   for (int j = 0; j < 4; ++j)
     for (int i = 0; i < ncell; ++i) {
       CK(cudaMemcpyAsync(snap + (j * ncell + i) * (cb + tb), h->C[j][i], cb, cudaMemcpyDeviceToDevice, h->stream));
       CK(cudaMemcpyAsync(snap + (j * ncell + i) * (cb + tb) + cb, h->T[j][i], tb, cudaMemcpyDeviceToDevice,
+                         h->stream));
+      CK(cudaMemcpyAsync(snap + env_bytes + (j * ncell + i) * vb, h->Vwarm[j][i], vb, cudaMemcpyDeviceToDevice,
                          h->stream));
     }
   tc_tuner_set_measuring(h->tuner, true);
@@ -1582,6 +1616,8 @@ extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
     for (int i = 0; i < ncell; ++i) {
       cudaMemcpyAsync(h->C[j][i], snap + (j * ncell + i) * (cb + tb), cb, cudaMemcpyDeviceToDevice, h->stream);
       cudaMemcpyAsync(h->T[j][i], snap + (j * ncell + i) * (cb + tb) + cb, tb, cudaMemcpyDeviceToDevice, h->stream);
+      cudaMemcpyAsync(h->Vwarm[j][i], snap + env_bytes + (j * ncell + i) * vb, vb, cudaMemcpyDeviceToDevice,
+                      h->stream);
     }
   cudaError_t e = cudaStreamSynchronize(h->stream);
   cudaFree(snap);

@@ -39,6 +39,18 @@ __device__ __forceinline__ double f2d_bits(float f) {
 __device__ __forceinline__ double neg_bits(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
 }
+
+// One complex Jacobi rotation of a row pair (a, b) (Hestenes; Demmel and
+// Veselic 1992), with phi the phase of the inner product a^H b:
+//   a' = c a - s e^{-i phi} b,   b' = s e^{i phi} a + c b
+// (sq = s e^{-i phi}, sp = s e^{i phi}).  This form tends to the identity as
+// s -> 0, so rows keep their phases through small rotations and a start that
+// already diagonalises is left in place (a warm start stays a warm start).
+__device__ __forceinline__ void jac_rotate(cplx& a, cplx& b, double c, cplx sq, cplx sp) {
+  const cplx x = a, y = b;
+  a = make_double2(c * x.x - (sq.x * y.x - sq.y * y.y), c * x.y - (sq.x * y.y + sq.y * y.x));
+  b = make_double2(c * y.x + (sp.x * x.x - sp.y * x.y), c * y.y + (sp.x * x.y + sp.y * x.x));
+}
 #endif
 
 // ---------------------------------------------------------------------------
@@ -107,10 +119,14 @@ cudaError_t set_zero(cudaStream_t s, cplx* x, long long n);
 // wait_cycles: limit of each grid-barrier wait of the small-row kernel (<= 0:
 // about 2 s of clock); a wait that runs out is counted in st->barrier_timeouts
 // and its CTA stops.
+// warm_v: Vt holds a unitary n x n start V0^T on entry (the rotations are
+// accumulated onto it, Vt = J^T V0^T) instead of starting from the identity.
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
                         DevStatus* st, cplx* rotlog = nullptr, long long rotlog_elems = 0,
-                        long long wait_cycles = 0);
+                        long long wait_cycles = 0, bool warm_v = false);
+// V (n x n) = identity
+cudaError_t set_identity(cudaStream_t s, cplx* V, int n);
 // rows of G scaled to unit norm where sigma > tol*max(sigma), zero otherwise
 cudaError_t orth_rows_finish(cudaStream_t s, cplx* G, int n, int m, long long ldg,
                              const double* sigma, double tol);
@@ -173,9 +189,10 @@ cudaError_t fp64_cluster_init();
 bool jacobi_cluster_fits(int n, int m, bool vt_in_smem);
 // With rotlog (jacobi_log_elems(n, max_sweeps) complex slots) and sweeps_used
 // (one int), Vt is not held in the cluster: the rotations are logged and
-// replayed onto the identity by one CTA per column afterwards.
+// replayed onto the identity (onto Vt itself with warm_v) by one CTA per
+// column afterwards.
 cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
-                           DevStatus* st, cplx* rotlog, int* sweeps_used);
+                           DevStatus* st, cplx* rotlog, int* sweeps_used, bool warm_v = false);
 long long jacobi_log_elems(int n, int max_sweeps);
 bool chol_cluster_fits(int n);
 cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol);

@@ -244,19 +244,12 @@ __global__ void __launch_bounds__(JAC_THREADS)
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
           const cplx ph = make_double2(v[2] / g, -v[3] / g);  // exp(-i phi)
-          for (int q = threadIdx.x; q < m; q += blockDim.x) {
-            const cplx x = gi[q], y = cmul(gj[q], ph);
-            gi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-            gj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-          }
+          const cplx sq = make_double2(s * ph.x, s * ph.y), sp = make_double2(s * ph.x, -s * ph.y);
+          for (int q = threadIdx.x; q < m; q += blockDim.x) jac_rotate(gi[q], gj[q], c, sq, sp);
           if (Vt) {
             cplx* vi = Vt + (long long)i * n;
             cplx* vj = Vt + (long long)j * n;
-            for (int q = threadIdx.x; q < n; q += blockDim.x) {
-              const cplx x = vi[q], y = cmul(vj[q], ph);
-              vi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-              vj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-            }
+            for (int q = threadIdx.x; q < n; q += blockDim.x) jac_rotate(vi[q], vj[q], c, sq, sp);
           }
           if (threadIdx.x == 0) atomicAdd(&counters[sweep & 1], 1);
         }
@@ -377,20 +370,13 @@ __global__ void __launch_bounds__(32)
           const double zeta = (be - al) / (2.0 * g);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          const cplx ph = make_double2(gr / g, -gim / g);
-          for (int q = lane; q < m; q += 32) {
-            const cplx x = gi[q], y = cmul(gj[q], ph);
-            gi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-            gj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-          }
+          const cplx ph = make_double2(gr / g, -gim / g);  // exp(-i phi)
+          const cplx sq = make_double2(s * ph.x, s * ph.y), sp = make_double2(s * ph.x, -s * ph.y);
+          for (int q = lane; q < m; q += 32) jac_rotate(gi[q], gj[q], c, sq, sp);
           if (Vt) {
             cplx* vi = Vt + (long long)i * n;
             cplx* vj = Vt + (long long)j * n;
-            for (int q = lane; q < n; q += 32) {
-              const cplx x = vi[q], y = cmul(vj[q], ph);
-              vi[q] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-              vj[q] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-            }
+            for (int q = lane; q < n; q += 32) jac_rotate(vi[q], vj[q], c, sq, sp);
           }
           if (lane == 0) atomicAdd(&counters[sweep & 1], 1);
         }
@@ -620,7 +606,7 @@ cudaError_t kernels_init() {
 
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
-                        DevStatus* st, cplx* rotlog, long long rotlog_elems, long long wait_cycles) {
+                        DevStatus* st, cplx* rotlog, long long rotlog_elems, long long wait_cycles, bool warm_v) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
   if ((e = kernels_init()) != cudaSuccess) return e;
@@ -628,13 +614,13 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
   if (jacobi_cluster_fits(n, m, Vt != nullptr && !logged)) {
     // rows (and Vt unless logged) fit in one cluster's shared memory: no grid-wide barrier
     if ((e = jacobi_cluster(s, G, n, m, ldg, Vt, max_sweeps, st, logged ? rotlog : nullptr,
-                            logged ? counters : nullptr)) != cudaSuccess)
+                            logged ? counters : nullptr, warm_v)) != cudaSuccess)
       return e;
     row_norms_kernel<<<n < 1024 ? n : 1024, 256, 0, s>>>(G, n, m, ldg, sigma);
     count_launch();
     return cudaGetLastError();
   }
-  if (Vt) {
+  if (Vt && !warm_v) {
     init_identity_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(Vt, n);
     count_launch();
   }
@@ -669,6 +655,12 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
     if (e != cudaSuccess) return e;
   }
   row_norms_kernel<<<n < 1024 ? n : 1024, 256, 0, s>>>(G, n, m, ldg, sigma);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(cudaStream_t s, cplx* V, int n) {
+  init_identity_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(V, n);
   count_launch();
   return cudaGetLastError();
 }

@@ -34,18 +34,20 @@ constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2, PREC_BF16X6 = 3;
 
 
 
-// Tile configuration: 128 x BN output tile (BN = 128 or 256), 128-byte k-blocks,
-// as many pipeline stages as fit in ~192 KB of shared memory.  NOPS parts per
-// operand (1 TF32, 2 BF16 hi/lo, 3 BF16 hi/mid/lo); BF16x6 runs BN = 128 only
-// (two stages of three A and three B parts).
+// Tile configuration: 128 x BN output tile (BN = 128 or 256), k-blocks of 128
+// bytes (64 for BF16x6), as many pipeline stages as fit in ~192 KB of shared
+// memory.  NOPS parts per operand (1 TF32, 2 BF16 hi/lo, 3 BF16 hi/mid/lo);
+// BF16x6 runs BN = 128 only, with 64-byte k-blocks (64-byte swizzle) so that
+// four stages of three A and three B parts fit.
 template <int PREC, int BN_>
 struct Cfg {
   static constexpr int BN = BN_;
   static constexpr int ELEM = PREC == PREC_TF32 ? 4 : 2;
-  static constexpr int BK = 128 / ELEM;                 // elements per k-block (128 bytes)
+  static constexpr int KB_BYTES = PREC == PREC_BF16X6 ? 64 : 128;  // bytes of a k-block row
+  static constexpr int BK = KB_BYTES / ELEM;                        // elements per k-block
   static constexpr int NOPS = PREC == PREC_TF32 ? 1 : (PREC == PREC_BF16X3 ? 2 : 3);
-  static constexpr int A_BYTES = BM * 128;
-  static constexpr int B_BYTES = BN * 128;
+  static constexpr int A_BYTES = BM * KB_BYTES;
+  static constexpr int B_BYTES = BN * KB_BYTES;
   static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
   static_assert(PREC != PREC_BF16X6 || BN == 128, "BF16x6 tiles are 128 wide");
@@ -157,21 +159,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t b0 = base + K_::NOPS * K_::A_BYTES, b1 = b0 + K_::B_BYTES, b2 = b0 + 2 * K_::B_BYTES;
 #pragma unroll
       for (int j = 0; j < K_::KSTEPS; ++j) {
-        const uint32_t ko = j * 32;  // bytes of one MMA's K inside the 128-byte row
+        const uint32_t ko = j * 32;  // bytes of one MMA's K inside the k-block row
         const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
         if (K_::NOPS == 3) {
           // smallest parts first: p_i q_j with i + j = 2, then 1, then 0
-          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b2 + ko), acc);
-          umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b1 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc(a2 + ko), sdesc(b0 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b2 + ko), acc);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a2 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
         } else {
-          umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b0 + ko), acc);
+          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), acc);
           if (K_::NOPS == 2) {
-            umma<PREC, K_::IDESC>(tmem, sdesc(a0 + ko), sdesc(b1 + ko), 1u);
-            umma<PREC, K_::IDESC>(tmem, sdesc(a1 + ko), sdesc(b0 + ko), 1u);
+            umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
+            umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
           }
         }
       }
@@ -361,33 +363,19 @@ __global__ void pack_b_tr_kernel(const cplx* __restrict__ B, long long ldb, int 
     tile[i][threadIdx.x] = v;
   }
   __syncthreads();
+  // thread x writes the real pair of complex column k0 + x on each of the
+  // 64 real rows: a warp stores 128 contiguous bytes per part
+  const int k = k0 + threadIdx.x;
+  if (2 * k >= Krp) return;
   for (int r = threadIdx.y; r < 64; r += blockDim.y) {
     const int nr = 2 * n0 + r;
-    if (nr >= Nrp) continue;
-    const int nl = r >> 1, b = r & 1;
-    for (int c = threadIdx.x; c < 64; c += 32) {
-      const int kr = 2 * k0 + c;
-      if (kr >= Krp) continue;
-      const int kl = c >> 1, a = c & 1;
-      const cplx v = tile[kl][nl];
-      const double x = (a == b) ? v.x : (a == 0 ? v.y : neg_bits(v.y));
-      const long long e = (long long)nr * Krp + kr;
-      if (PREC == PREC_TF32) {
-        ((uint32_t*)o0)[e] = to_tf32(d2f_bits(x));
-      } else if (PREC == PREC_BF16X6) {
-        __nv_bfloat16 p0, p1, p2;
-        split3(d2f_rn_bits(x), p0, p1, p2);
-        ((__nv_bfloat16*)o0)[e] = p0;
-        ((__nv_bfloat16*)o1)[e] = p1;
-        ((__nv_bfloat16*)o2)[e] = p2;
-      } else {
-        const float xf = d2f_bits(x);
-        const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
-        ((__nv_bfloat16*)o0)[e] = hi;
-        ((__nv_bfloat16*)o1)[e] = lo;
-      }
-    }
+    if (nr >= Nrp) break;
+    const cplx v = tile[threadIdx.x][r >> 1];
+    const long long e = (long long)nr * Krp + 2 * (long long)k;
+    if (r & 1)
+      store_pair(PREC, e, v.y, v.x, o0, o1, o2);  // row 2n+1: (Im, Re)
+    else
+      store_pair(PREC, e, v.x, neg_bits(v.y), o0, o1, o2);  // row 2n: (Re, -Im)
   }
 }
 
@@ -423,6 +411,31 @@ __global__ void pack_a_view_kernel(TcView V, int M, int K, int Mp, int Krp, void
   }
 }
 
+// The same through 32 x 32 complex tiles in shared memory, for views whose
+// innermost row axis is the contiguous one (the plain kernel's warps would
+// read 32 elements a full row stride apart): reads run along m, writes along k.
+template <int PREC>
+__global__ void pack_a_view_tr_kernel(TcView V, int M, int K, int Mp, int Krp, void* __restrict__ o0,
+                                      void* __restrict__ o1, void* __restrict__ o2) {
+  __shared__ cplx tile[32][33];
+  const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i, m = m0 + threadIdx.x;
+    cplx v = make_double2(0.0, 0.0);
+    if (m < M && k < K) v = view_at(V, m, k);
+    tile[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (2 * k >= Krp) return;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int m = m0 + r;
+    if (m >= Mp) break;
+    const cplx v = tile[threadIdx.x][r];
+    store_pair(PREC, (long long)m * Krp + 2 * (long long)k, v.x, v.y, o0, o1, o2);
+  }
+}
+
 // Br^T[nr, kr] gathered through a view (rows n, columns k), padded to Nrp x Krp:
 // complex (n, k) gives rows 2n: (Re, -Im) and 2n+1: (Im, Re) at columns 2k, 2k+1
 template <int PREC>
@@ -453,14 +466,17 @@ cudaError_t get_encoder() {
 }
 
 // K-major [rows x kcols] operand, box of box_rows x (128 bytes)
-cudaError_t make_map(CUtensorMap* map, void* base, int prec, long long rows, long long kcols, int box_rows) {
+cudaError_t make_map(CUtensorMap* map, void* base, int prec, long long rows, long long kcols, int box_rows,
+                     int kb_bytes = 128) {
   const bool tf = prec == PREC_TF32;
+  const int esz = tf ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)kcols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)(kcols * (tf ? 4 : 2))};
-  const cuuint32_t box[2] = {(cuuint32_t)(tf ? 32 : 64), (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(kcols * esz)};
+  const cuuint32_t box[2] = {(cuuint32_t)(kb_bytes / esz), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        kb_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -493,7 +509,9 @@ cudaError_t pack_b_any(cudaStream_t s, const cplx* B, long long ldb, int opB, in
 
 template <int PREC>
 void padded(int N, int K, long long* Nrp, long long* Krp) {
-  constexpr int BK = Cfg<PREC, 128>::BK;
+  // BF16 operands (x3 and x6 alike) are padded to 64-element k-blocks, so that
+  // a corner packed once serves either mode's kernel
+  constexpr int BK = Cfg<PREC == PREC_BF16X6 ? PREC_BF16X3 : PREC, 128>::BK;
   *Krp = (2LL * K + BK - 1) / BK * BK;
   *Nrp = (2LL * N + NPAD - 1) / NPAD * NPAD;
 }
@@ -547,17 +565,18 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
   if ((e = ensure_attr<PREC, BN>()) != cudaSuccess) return e;
   if ((e = get_encoder()) != cudaSuccess) return e;
   CUtensorMap mA0, mA1, mA2, mB0, mB1, mB2;
-  if ((e = make_map(&mA0, o.a0, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
-  if ((e = make_map(&mB0, o.b0, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
+  constexpr int KB = K_::KB_BYTES;
+  if ((e = make_map(&mA0, o.a0, PREC, o.Mp, o.Krp, BM, KB)) != cudaSuccess) return e;
+  if ((e = make_map(&mB0, o.b0, PREC, o.Nrp, o.Krp, BN, KB)) != cudaSuccess) return e;
   mA1 = mA2 = mA0;
   mB1 = mB2 = mB0;
   if (K_::NOPS >= 2) {
-    if ((e = make_map(&mA1, o.a1, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
-    if ((e = make_map(&mB1, o.b1, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
+    if ((e = make_map(&mA1, o.a1, PREC, o.Mp, o.Krp, BM, KB)) != cudaSuccess) return e;
+    if ((e = make_map(&mB1, o.b1, PREC, o.Nrp, o.Krp, BN, KB)) != cudaSuccess) return e;
   }
   if (K_::NOPS == 3) {
-    if ((e = make_map(&mA2, o.a2, PREC, o.Mp, o.Krp, BM)) != cudaSuccess) return e;
-    if ((e = make_map(&mB2, o.b2, PREC, o.Nrp, o.Krp, BN)) != cudaSuccess) return e;
+    if ((e = make_map(&mA2, o.a2, PREC, o.Mp, o.Krp, BM, KB)) != cudaSuccess) return e;
+    if ((e = make_map(&mB2, o.b2, PREC, o.Nrp, o.Krp, BN, KB)) != cudaSuccess) return e;
   }
   S = eff_splits(o.kb_total, S);
   const int kps = (o.kb_total + S - 1) / S;
@@ -707,7 +726,11 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   }
   if (part_bytes(eff_splits(o.kb_total, choice.splits)) > part_room) return cudaErrorMemoryAllocation;
 
-  if (va && o.Mp * o.Krp < (1LL << 31))
+  if (va && o.Mp * o.Krp < (1LL << 31) && o.Mp / 32 <= 65535 && va->rstr[va->nr - 1] == 1 &&
+      va->cstr[va->nc - 1] != 1)
+    pack_a_view_tr_kernel<PREC><<<dim3((unsigned)((o.Krp / 2 + 31) / 32), (unsigned)(o.Mp / 32)), dim3(32, 8), 0,
+                                  s>>>(*va, M, K, (int)o.Mp, (int)o.Krp, o.a0, o.a1, o.a2);
+  else if (va && o.Mp * o.Krp < (1LL << 31))
     pack_a_view_kernel<PREC><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(*va, M, K, (int)o.Mp, (int)o.Krp, o.a0,
                                                                          o.a1, o.a2);
   else if (va)

@@ -58,6 +58,15 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// the same for rows of KB bytes (128: 128-byte swizzle; 64: 64-byte swizzle,
+// 8-row groups 512 B apart)
+template <int KB>
+__device__ __forceinline__ uint64_t sdesc_kb(uint32_t addr) {
+  static_assert(KB == 128 || KB == 64, "k-blocks of 64 or 128 bytes");
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * KB) >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)(KB == 128 ? 2 : 4) << 61);
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))

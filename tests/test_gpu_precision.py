@@ -24,7 +24,10 @@ CUT = 1e-6
 TARGET = {"E": 1e-6, "rho": 1e-6, "spec": 1e-5, "kappa": 1e-5, "fid": 1e-6, "lam": 1e-5}
 # measured levels of the modes that miss the targets (bounds at about 3x)
 MISS = {
-    "bf16x3": {"E": 5e-6, "rho": 3e-5, "spec": 3e-4, "kappa": 1e-4, "fid": 3e-6, "lam": 1e-4},
+    # BF16x3 fidelity: 2e-6 to 7e-6 across Jacobi rotation orders and phase
+    # conventions of the projector SVD (its 16-bit operands leave the
+    # truncated directions noisy at that level)
+    "bf16x3": {"E": 5e-6, "rho": 3e-5, "spec": 3e-4, "kappa": 1e-4, "fid": 1.5e-5, "lam": 1e-4},
     "tf32": {"E": 1.2e-4, "rho": 1.2e-3, "spec": 2e-2, "kappa": 1e-3, "fid": 1e-3, "lam": 1e-2},
 }
 
