@@ -431,11 +431,11 @@ ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA
 
 /* As ipeps_zgemm for the tensor-core precisions, with the tile choice fixed
  * instead of the default: output tiles of 128 x bn real columns (bn = 128 or
- * 256; BF16X6 tiles are 128 wide) and `splits` K splits (reduced to the
- * number of 128-byte k-blocks if larger).  For unit tests of every choice the
+ * 256) and `splits` K splits (reduced to the number of k-blocks, 128 bytes
+ * of K, 64 for BF16X6, if larger).  For unit tests of every choice the
  * batch autotuner can make (no paper counterpart).  Host buffers as
- * ipeps_zgemm.  Errors: EINVAL (prec FP64, bn not 128 or 256, bn 256 with
- * BF16X6, splits < 1, or as ipeps_zgemm), ECUDA, ETIMEOUT. */
+ * ipeps_zgemm.  Errors: EINVAL (prec FP64, bn not 128 or 256, splits < 1, or
+ * as ipeps_zgemm), ECUDA, ETIMEOUT. */
 ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K, const double* A, int opA,
                               const double* B, int opB, double* C);
 

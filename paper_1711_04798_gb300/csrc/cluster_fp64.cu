@@ -248,17 +248,25 @@ __global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4
 }
 
 // Right-looking Cholesky of the Hermitian n x n G (upper triangle used) with
-// dropped pivots (d <= tol * max diagonal: row of R zero): rows of the
-// working copy in the cluster's shared memory; at column j every CTA reads
-// row j from its owner and updates its own rows i > j.
+// dropped pivots (d <= tol * max diagonal: row of R zero), blocked by
+// CH_NB columns: rows of the working copy W live in the cluster's shared
+// memory (row i in CTA i mod csize).  For each block of rows j0 .. j0+nb-1
+// every CTA copies those rows from their owners, factors them into the rows
+// of R (the same arithmetic in every CTA, so the same values), and updates
+// its own rows below the block, W[i,l] -= conj(R[j,i]) R[j,l] for l >= i,
+// j in order: the operations and their order per element are those of the
+// column-by-column algorithm, with one cluster barrier per block instead of
+// one per column.
+constexpr int CH_NB = 8;
+
 __global__ void __launch_bounds__(CL_THREADS)
     chol_cluster_kernel(const cplx* __restrict__ G, cplx* __restrict__ Rout, int n, double tol) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
   const int R = (n + cs - 1) / cs;
-  extern __shared__ cplx sm[];  // [R x n] rows of the working copy W, then one row: R[j, :]
-  cplx* rj = sm + (long long)R * n;
-  __shared__ double s_max, s_rjj, s_inv;
+  extern __shared__ cplx sm[];  // [R x n] own rows of W, then [CH_NB x n] the block (rows of W, then of R)
+  cplx* pan = sm + (long long)R * n;
+  __shared__ double s_max, s_rjj[CH_NB], s_inv[CH_NB];
   for (int l = 0; l < R; ++l) {
     const int i = l * cs + rank;
     if (i >= n) break;
@@ -278,45 +286,76 @@ __global__ void __launch_bounds__(CL_THREADS)
   double dmax = 0.0;
   for (int r = 0; r < cs; ++r) dmax = fmax(dmax, *cl.map_shared_rank(&s_max, r));
   const double thr = tol * dmax;
-  for (int j = 0; j < n; ++j) {
-    const cplx* wj = cl.map_shared_rank(sm, j % cs) + (long long)(j / cs) * n;
-    // the pivot's root and reciprocal once per CTA (FP64 roots and divides
-    // are slow on this part), then row j of R once into local shared memory
-    if (threadIdx.x == 0) {
-      const double d = wj[j].x;
-      const bool keep = d > thr;
-      s_rjj = keep ? sqrt(d) : 0.0;
-      s_inv = keep ? 1.0 / s_rjj : 0.0;
+  for (int j0 = 0; j0 < n; j0 += CH_NB) {
+    const int nb = min(CH_NB, n - j0), w = n - j0;
+    // rows j0 .. j0+nb-1 of W (columns j0 .. n-1) from their owners
+    for (int e = threadIdx.x; e < nb * w; e += CL_THREADS) {
+      const int jj = e / w, l = j0 + e % w, j = j0 + jj;
+      pan[(long long)jj * n + l] = cl.map_shared_rank(sm, j % cs)[(long long)(j / cs) * n + l];
     }
     __syncthreads();
-    const double rjj = s_rjj, inv = s_inv;
-    const bool keep = rjj > 0.0;
-    for (int l = threadIdx.x; l < n; l += CL_THREADS) {
-      cplx v = make_double2(0.0, 0.0);
-      if (keep && l >= j) {
-        const cplx g = wj[l];
-        v = l == j ? make_double2(rjj, 0.0) : make_double2(g.x * inv, g.y * inv);
+    for (int jj = 0; jj < nb; ++jj) {
+      const int j = j0 + jj;
+      cplx* pj = pan + (long long)jj * n;
+      // the pivot's root and reciprocal once (FP64 roots and divides are slow
+      // on this part)
+      if (threadIdx.x == 0) {
+        const double d = pj[j].x;
+        const bool keep = d > thr;
+        s_rjj[jj] = keep ? sqrt(d) : 0.0;
+        s_inv[jj] = keep ? 1.0 / s_rjj[jj] : 0.0;
       }
-      rj[l] = v;
-      if (j % cs == rank) Rout[(long long)j * n + l] = v;  // zero row for a dropped direction
-    }
-    __syncthreads();
-    if (keep) {
-      // own rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i
-      for (int l0 = 0; l0 < R; ++l0) {
-        const int i = l0 * cs + rank;
-        if (i >= n) break;
-        if (i <= j) continue;
-        const cplx a = rj[i];
-        cplx* wi = sm + (long long)l0 * n;
-        for (int l = i + threadIdx.x; l < n; l += CL_THREADS) {
-          const cplx b = rj[l];
+      __syncthreads();
+      const double rjj = s_rjj[jj], inv = s_inv[jj];
+      const bool keep = rjj > 0.0;
+      // row j of R (zero left of the diagonal, and for a dropped direction)
+      for (int l = j0 + threadIdx.x; l < n; l += CL_THREADS) {
+        cplx v = make_double2(0.0, 0.0);
+        if (keep && l >= j) {
+          const cplx g = pj[l];
+          v = l == j ? make_double2(rjj, 0.0) : make_double2(g.x * inv, g.y * inv);
+        }
+        pj[l] = v;
+      }
+      __syncthreads();
+      if (keep) {
+        // the block's rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i
+        for (int e = threadIdx.x; e < (nb - 1 - jj) * w; e += CL_THREADS) {
+          const int i = j + 1 + e / w, l = j0 + e % w;
+          if (l < i) continue;
+          const cplx a = pj[i], b = pj[l];
+          cplx* wi = pan + (long long)(i - j0) * n;
           wi[l].x -= a.x * b.x + a.y * b.y;
           wi[l].y -= a.x * b.y - a.y * b.x;
         }
       }
+      __syncthreads();
     }
-    cl.sync();
+    // the owners store their rows of R
+    for (int jj = 0; jj < nb; ++jj) {
+      const int j = j0 + jj;
+      if (j % cs != rank) continue;
+      for (int l = threadIdx.x; l < n; l += CL_THREADS)
+        Rout[(long long)j * n + l] = l < j0 ? make_double2(0.0, 0.0) : pan[(long long)jj * n + l];
+    }
+    // own rows below the block
+    for (int l0 = 0; l0 < R; ++l0) {
+      const int i = l0 * cs + rank;
+      if (i >= n) break;
+      if (i < j0 + nb) continue;
+      cplx* wi = sm + (long long)l0 * n;
+      for (int l = i + threadIdx.x; l < n; l += CL_THREADS) {
+        cplx v = wi[l];
+        for (int jj = 0; jj < nb; ++jj) {
+          if (s_rjj[jj] == 0.0) continue;  // dropped direction: no update
+          const cplx a = pan[(long long)jj * n + i], b = pan[(long long)jj * n + l];
+          v.x -= a.x * b.x + a.y * b.y;
+          v.y -= a.x * b.y - a.y * b.x;
+        }
+        wi[l] = v;
+      }
+    }
+    cl.sync();  // the updated rows are read as the next block; no CTA leaves while another reads it
   }
 }
 
@@ -411,14 +450,14 @@ bool chol_cluster_fits(int n) {
   if (n < 32) return false;
   if (cluster_init() != cudaSuccess) return false;
   const long long R = (n + g_csize - 1) / g_csize;
-  return (R + 1) * n * (long long)sizeof(cplx) <= CL_SMEM;
+  return (R + CH_NB) * n * (long long)sizeof(cplx) <= CL_SMEM;
 }
 
 cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol) {
   cudaError_t e;
   if ((e = cluster_init()) != cudaSuccess) return e;
   const long long rows = (n + g_csize - 1) / g_csize;
-  const size_t smem = (size_t)((rows + 1) * n * sizeof(cplx));
+  const size_t smem = (size_t)((rows + CH_NB) * n * sizeof(cplx));
   void* args[] = {&G, &R, &n, &tol};
   e = launch_cluster((const void*)chol_cluster_kernel, args, smem, s);
   count_launch();

@@ -2679,7 +2679,7 @@ extern "C" ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, in
                                          const double* B, int opB, double* C) {
   if (prec != IPEPS_PREC_TF32 && prec != IPEPS_PREC_BF16X3 && prec != IPEPS_PREC_BF16X6)
     return fail(IPEPS_EINVAL, "tile choice needs TF32/BF16X3/BF16X6");
-  if ((bn != 128 && bn != 256) || splits < 1 || (prec == IPEPS_PREC_BF16X6 && bn != 128))
+  if ((bn != 128 && bn != 256) || splits < 1)
     return fail(IPEPS_EINVAL, "bad tile choice");
   const TcChoice c{bn, splits};
   return zgemm_host(prec, M, N, K, A, opA, B, opB, C, &c);

@@ -54,8 +54,9 @@ constexpr int OZ_STAGE = OZ_A_BYTES + OZ_DIGITS * OZ_B_BYTES;  // 44 KB
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_THREADS = 192;                       // producer, MMA issuer, 4 epilogue warps
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
-constexpr int OZ_TMEM_COLS = 256;                     // 7 groups x 32 columns, rounded up
-static_assert(OZ_GROUPS * OZ_BN <= OZ_TMEM_COLS, "the group accumulators fit the tensor-memory allocation");
+constexpr int OZ_ACC_COLS = 256;                      // one set of 7 groups x 32 columns, rounded up
+constexpr int OZ_TMEM_COLS = 2 * OZ_ACC_COLS;         // two sets: chunk c accumulates in set c % 2
+static_assert(OZ_GROUPS * OZ_BN <= OZ_ACC_COLS, "the group accumulators fit one accumulator set");
 static_assert(OZ_GROUPS == OZ_DIGITS, "weights 0..6 of the digit pairs s + t <= 6");
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
                               ((uint32_t)(OZ_BM >> 4) << 24);  // FP32 += BF16 x BF16, K-major, 128 x 32
@@ -127,83 +128,69 @@ __device__ __forceinline__ cplx oz_load(const cplx* X, long long ld, int op, int
   return v;
 }
 
-// e[r] = (largest biased exponent of row r of op(A), M x K complex) - 1022: the
-// power-of-two bound of that row of Ar; rows at or beyond M, and zero rows, 0.
-// One warp per row.
-__global__ void oz_exp_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp,
-                                int* __restrict__ ea) {
-  const int lane = threadIdx.x & 31;
-  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < Mp; r += gridDim.x * (blockDim.x >> 5)) {
-    int E = 0;
-    if (r < M)
-      for (int c = lane; c < K; c += 32) {
-        const cplx v = oz_load(A, lda, opA, r, c);
-        E = max(E, max(bexp(v.x), bexp(v.y)));
-      }
+// Both operands' exponents and digit planes in one launch.  Block b < Mp takes
+// row b of op(A) (M x K complex): e = (largest biased exponent of the row) -
+// 1022, the power-of-two bound of that row of Ar (0 for rows at or beyond M
+// and for zero rows), and digit plane s of Ar is [Mp x Krp] bf16 at
+// pa + s * Mp * Krp.  Block Mp + n takes column n of op(B) (K x N) the same
+// way: its bound goes to rows 2n and 2n+1 of Br^T, and complex (k, n) gives
+// row 2n (Re, -Im) and row 2n+1 (Im, Re) at columns 2k, 2k+1 of each plane of
+// Br^T [Nrp x Krp].  The block first reduces the row's largest exponent, then
+// writes its digits; the row is read twice, the second time from cache.
+constexpr int OZ_PREP_THREADS = 128;
+__global__ void __launch_bounds__(OZ_PREP_THREADS)
+    oz_prep_kernel(const cplx* __restrict__ A, long long lda, int opA, const cplx* __restrict__ B, long long ldb,
+                   int opB, int M, int N, int K, int Mp, int Nrp, int Krp, int* __restrict__ ea, int* __restrict__ eb,
+                   __nv_bfloat16* __restrict__ pa, __nv_bfloat16* __restrict__ pb) {
+  __shared__ int s_e[OZ_PREP_THREADS / 32];
+  const bool is_a = (int)blockIdx.x < Mp;
+  const int r = is_a ? (int)blockIdx.x : (int)blockIdx.x - Mp;  // row of op(A), or column of op(B)
+  const bool live = is_a ? r < M : r < N;
+  auto load = [&](int c) {
+    return is_a ? oz_load(A, lda, opA, r, c) : oz_load(B, ldb, opB, c, r);
+  };
+  int E = 0;
+  if (live)
+    for (int c = threadIdx.x; c < K; c += OZ_PREP_THREADS) {
+      const cplx v = load(c);
+      E = max(E, max(bexp(v.x), bexp(v.y)));
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-    if (lane == 0) ea[r] = E ? E - 1022 : 0;
-  }
-}
-
-// the same for the columns n of op(B) (K x N): rows 2n and 2n+1 of Br^T
-__global__ void oz_exp_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp,
-                                int* __restrict__ eb) {
-  const int lane = threadIdx.x & 31;
-  for (int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); n < Nrp / 2;
-       n += gridDim.x * (blockDim.x >> 5)) {
-    int E = 0;
-    if (n < N)
-      for (int k = lane; k < K; k += 32) {
-        const cplx v = oz_load(B, ldb, opB, k, n);
-        E = max(E, max(bexp(v.x), bexp(v.y)));
-      }
+  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = E;
+  __syncthreads();
+  E = s_e[0];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-    if (lane == 0) eb[2 * n] = eb[2 * n + 1] = E ? E - 1022 : 0;
+  for (int w = 1; w < OZ_PREP_THREADS / 32; ++w) E = max(E, s_e[w]);
+  const int e = E ? E - 1022 : 0;
+  if (threadIdx.x == 0) {
+    if (is_a)
+      ea[r] = e;
+    else
+      eb[2 * r] = eb[2 * r + 1] = e;
   }
-}
-
-// digit planes of Ar: plane s is [Mp x Krp] bf16 at planes + s * Mp * Krp;
-// one thread per complex element (its two reals stored as a pair)
-__global__ void oz_split_a_kernel(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int Krp,
-                                  const int* __restrict__ ea, __nv_bfloat16* __restrict__ planes) {
-  const long long kc = Krp / 2, total = (long long)Mp * kc, plane = (long long)Mp * Krp;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / kc), c = (int)(e - (long long)r * kc);
+  const long long kc = Krp / 2;
+  const long long plane = is_a ? (long long)Mp * Krp : (long long)Nrp * Krp;
+  for (int c = threadIdx.x; c < kc; c += OZ_PREP_THREADS) {
     cplx v = make_double2(0.0, 0.0);
-    if (r < M && c < K) v = oz_load(A, lda, opA, r, c);
+    if (live && c < K) v = load(c);
     int dr[OZ_DIGITS], di[OZ_DIGITS];
-    digits7(v.x, ea[r], dr);
-    digits7(v.y, ea[r], di);
-    __nv_bfloat162* out = (__nv_bfloat162*)(planes + (long long)r * Krp + 2LL * c);
+    digits7(v.x, e, dr);
+    digits7(v.y, e, di);
+    if (is_a) {
+      __nv_bfloat162* out = (__nv_bfloat162*)(pa + (long long)r * Krp + 2LL * c);
 #pragma unroll
-    for (int s = 0; s < OZ_DIGITS; ++s)
-      out[s * plane / 2] = __halves2bfloat162(__float2bfloat16_rn((float)dr[s]), __float2bfloat16_rn((float)di[s]));
-  }
-}
-
-// digit planes of Br^T [Nrp x Krp]: complex (k, n) of op(B) gives row 2n
-// (Re, -Im) and row 2n+1 (Im, Re) at columns 2k, 2k+1
-__global__ void oz_split_b_kernel(const cplx* __restrict__ B, long long ldb, int opB, int N, int K, int Nrp, int Krp,
-                                  const int* __restrict__ eb, __nv_bfloat16* __restrict__ planes) {
-  const long long kc = Krp / 2, total = (long long)(Nrp / 2) * kc, plane = (long long)Nrp * Krp;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(e / kc), k = (int)(e - (long long)n * kc);
-    cplx v = make_double2(0.0, 0.0);
-    if (n < N && k < K) v = oz_load(B, ldb, opB, k, n);
-    int dr[OZ_DIGITS], di[OZ_DIGITS];
-    digits7(v.x, eb[2 * n], dr);
-    digits7(v.y, eb[2 * n], di);
-    __nv_bfloat162* r0 = (__nv_bfloat162*)(planes + (long long)(2 * n) * Krp + 2LL * k);
-    __nv_bfloat162* r1 = (__nv_bfloat162*)(planes + (long long)(2 * n + 1) * Krp + 2LL * k);
+      for (int s = 0; s < OZ_DIGITS; ++s)
+        out[s * plane / 2] = __halves2bfloat162(__float2bfloat16_rn((float)dr[s]), __float2bfloat16_rn((float)di[s]));
+    } else {
+      __nv_bfloat162* r0 = (__nv_bfloat162*)(pb + (long long)(2 * r) * Krp + 2LL * c);
+      __nv_bfloat162* r1 = (__nv_bfloat162*)(pb + (long long)(2 * r + 1) * Krp + 2LL * c);
 #pragma unroll
-    for (int s = 0; s < OZ_DIGITS; ++s) {
-      const __nv_bfloat16 re = __float2bfloat16_rn((float)dr[s]), im = __float2bfloat16_rn((float)di[s]);
-      r0[s * plane / 2] = __halves2bfloat162(re, __float2bfloat16_rn((float)-di[s]));
-      r1[s * plane / 2] = __halves2bfloat162(im, re);
+      for (int s = 0; s < OZ_DIGITS; ++s) {
+        const __nv_bfloat16 re = __float2bfloat16_rn((float)dr[s]), im = __float2bfloat16_rn((float)di[s]);
+        r0[s * plane / 2] = __halves2bfloat162(re, __float2bfloat16_rn((float)-di[s]));
+        r1[s * plane / 2] = __halves2bfloat162(im, re);
+      }
     }
   }
 }
@@ -222,9 +209,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE);
   uint64_t* empty = full + OZ_STAGES;
-  uint64_t* acc_full = empty + OZ_STAGES;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* mma_done = acc_empty + 1;
+  uint64_t* acc_full = empty + OZ_STAGES;  // [2], per accumulator set
+  uint64_t* acc_empty = acc_full + 2;      // [2]
+  uint64_t* mma_done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tile = blockIdx.x, m_tile = blockIdx.y, split = blockIdx.z;
@@ -237,8 +224,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);  // one arrival per epilogue warp
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -274,13 +263,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int q = max(0, issued - OZ_STAGES); q < issued; ++q)
       if (!mbar_wait(&full[q % OZ_STAGES], (q / OZ_STAGES) & 1)) atomicAdd(timeouts, 1);
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: group g = s + t accumulates in tensor-memory columns 32 g ..
+    // MMA issuer: group g = s + t of chunk c accumulates in tensor-memory
+    // columns 256 (c % 2) + 32 g .., so that chunk c's products run while the
+    // epilogue drains chunk c - 1
     bool ok = true;
     for (int q = 0; q < nstage && ok; ++q) {
       const int slot = q % OZ_STAGES, round = q / OZ_STAGES;
       const int s = q % OZ_DIGITS, kbc = (q / OZ_DIGITS) % OZ_KB_PER_CHUNK, c = q / (OZ_DIGITS * OZ_KB_PER_CHUNK);
       const bool chunk_start = kbc == 0 && s == 0;
-      if (chunk_start && c > 0 && !mbar_wait(acc_empty, (c - 1) & 1)) {  // epilogue drained chunk c-1
+      // the set was drained: chunk c - 2 was that set's drain number c/2 - 1
+      if (chunk_start && c > 1 && !mbar_wait(&acc_empty[c & 1], ((c >> 1) - 1) & 1)) {
         atomicAdd(timeouts, 1);
         ok = false;
         break;
@@ -294,13 +286,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const uint32_t a = smem_u32(smem + slot * OZ_STAGE);
       for (int t = 0; t < OZ_DIGITS - s; ++t) {
         const uint32_t b = a + OZ_A_BYTES + t * OZ_B_BYTES;
-        const uint32_t d = tmem + (uint32_t)((s + t) * OZ_BN);
+        const uint32_t d = tmem + (uint32_t)((c & 1) * OZ_ACC_COLS + (s + t) * OZ_BN);
 #pragma unroll
         for (int ks = 0; ks < OZ_BK / 16; ++ks)
           umma_bf16(d, sdesc(a + ks * 32), sdesc(b + ks * 32), (chunk_start && ks == 0) ? 0u : 1u);
       }
       umma_commit(&empty[slot]);  // frees the slot when these MMAs are done
-      if (kbc == OZ_KB_PER_CHUNK - 1 && s == OZ_DIGITS - 1) umma_commit(acc_full);
+      if (kbc == OZ_KB_PER_CHUNK - 1 && s == OZ_DIGITS - 1) umma_commit(&acc_full[c & 1]);
     }
     // every MMA issued has completed before the accumulators are released
     umma_commit(mma_done);
@@ -319,32 +311,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
-      const bool ready = mbar_wait(acc_full, c & 1);
+      const bool ready = mbar_wait(&acc_full[c & 1], (c >> 1) & 1);
       if (!ready) {
         if (lane == 0) atomicAdd(timeouts, 1);
         ok = false;
         break;
       }
       fence_after();
+      const uint32_t tset = trow + (uint32_t)((c & 1) * OZ_ACC_COLS);
       float v[OZ_BN], t[OZ_BN];
       // groups 0..3: exact integers (below 2^24) into the 64-bit sum
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        tmem_ld32(trow + g * OZ_BN, v);
+        tmem_ld32(tset + g * OZ_BN, v);
 #pragma unroll
         for (int j = 0; j < OZ_BN; ++j) I[j] += (long long)__float2int_rn(v[j]) << (8 * (3 - g));
       }
       // groups 4..6 (weight 2^-32 and below relative to group 0): FP32
-      tmem_ld32(trow + 6 * OZ_BN, t);
-      tmem_ld32(trow + 5 * OZ_BN, v);
+      tmem_ld32(tset + 6 * OZ_BN, t);
+      tmem_ld32(tset + 5 * OZ_BN, v);
 #pragma unroll
       for (int j = 0; j < OZ_BN; ++j) t[j] = fmaf(t[j], 1.0f / 256.0f, v[j]);
-      tmem_ld32(trow + 4 * OZ_BN, v);
+      tmem_ld32(tset + 4 * OZ_BN, v);
 #pragma unroll
       for (int j = 0; j < OZ_BN; ++j) u[j] += fmaf(t[j], 1.0f / 256.0f, v[j]);
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[c & 1]);
     }
     if (ok) {
       const int col0 = n_tile * OZ_BN;
@@ -462,11 +455,9 @@ cudaError_t oz_zgemm(cudaStream_t s, int M, int N, int K, const cplx* A, long lo
   __nv_bfloat16* pb = (__nv_bfloat16*)(base + L.off_b);
   long long* pI = L.S > 1 ? (long long*)(base + L.off_pi) : nullptr;
   float* pU = L.S > 1 ? (float*)(base + L.off_pu) : nullptr;
-  oz_exp_a_kernel<<<oz_grid(32LL * L.Mp), 256, 0, s>>>(A, lda, opA, M, K, L.Mp, ea);
-  oz_exp_b_kernel<<<oz_grid(16LL * L.Nrp), 256, 0, s>>>(B, ldb, opB, N, K, L.Nrp, eb);
-  oz_split_a_kernel<<<oz_grid((long long)L.Mp * L.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, L.Mp, L.Krp, ea, pa);
-  oz_split_b_kernel<<<oz_grid((long long)L.Nrp * L.Krp / 4), 256, 0, s>>>(B, ldb, opB, N, K, L.Nrp, L.Krp, eb, pb);
-  count_launch(4);
+  oz_prep_kernel<<<(unsigned)(L.Mp + L.Nrp / 2), OZ_PREP_THREADS, 0, s>>>(A, lda, opA, B, ldb, opB, M, N, K, L.Mp,
+                                                                          L.Nrp, L.Krp, ea, eb, pa, pb);
+  count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if ((e = tc_encode_bf16_map(&mA, pa, (long long)OZ_DIGITS * L.Mp, L.Krp, OZ_BM)) != cudaSuccess) return e;

@@ -35,10 +35,10 @@ constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2, PREC_BF16X6 = 3;
 
 
 // Tile configuration: 128 x BN output tile (BN = 128 or 256), k-blocks of 128
-// bytes (64 for BF16x6), as many pipeline stages as fit in ~192 KB of shared
+// bytes (64 for BF16x6), as many pipeline stages as fit in ~220 KB of shared
 // memory.  NOPS parts per operand (1 TF32, 2 BF16 hi/lo, 3 BF16 hi/mid/lo);
-// BF16x6 runs BN = 128 only, with 64-byte k-blocks (64-byte swizzle) so that
-// four stages of three A and three B parts fit.
+// BF16x6 takes 64-byte k-blocks (64-byte swizzle) so that its three A and
+// three B parts fit four stages at BN = 128 and three at BN = 256.
 template <int PREC, int BN_>
 struct Cfg {
   static constexpr int BN = BN_;
@@ -49,8 +49,8 @@ struct Cfg {
   static constexpr int A_BYTES = BM * KB_BYTES;
   static constexpr int B_BYTES = BN * KB_BYTES;
   static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
-  static_assert(PREC != PREC_BF16X6 || BN == 128, "BF16x6 tiles are 128 wide");
+  static constexpr int STAGES = (220 * 1024) / STAGE_BYTES;
+  static_assert(STAGES >= 2, "at least two pipeline stages");
   static constexpr int UMMA_K = PREC == PREC_TF32 ? 8 : 16;  // K of one MMA
   static constexpr int KSTEPS = BK / UMMA_K;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
@@ -516,7 +516,7 @@ void padded(int N, int K, long long* Nrp, long long* Krp) {
   *Nrp = (2LL * N + NPAD - 1) / NPAD * NPAD;
 }
 
-// Default tile choice: 256-wide tiles (128 for BF16x6); a product with fewer
+// Default tile choice: 256-wide tiles; a product with fewer
 // output tiles than SMs splits K until about two waves of CTAs exist.
 TcChoice heuristic(long long Mp, long long Nrp, int kb_total, int bn = 256) {
   const long long tiles = (Mp / BM) * (Nrp / bn);
@@ -611,13 +611,9 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
 template <int PREC>
 cudaError_t launch_choice(cudaStream_t s, const Operands& o, TcChoice c, int M, int N, cplx alpha, cplx* C,
                           long long ldc, float* part, bool conj_out, int* timeouts, TcProbe* probe = nullptr) {
-  if constexpr (PREC == PREC_BF16X6) {
+  if (c.bn == 128)
     return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
-  } else {
-    if (c.bn == 128)
-      return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
-    return launch_main<PREC, 256>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
-  }
+  return launch_main<PREC, 256>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
 }
 
 }  // namespace
@@ -709,7 +705,7 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   o.b2 = (char*)o.b0 + 2 * bbytes;
   float* part = (float*)((char*)o.b0 + K_::NOPS * bbytes);
 
-  TcChoice choice = heuristic(o.Mp, o.Nrp, o.kb_total, PREC == PREC_BF16X6 ? 128 : 256);
+  TcChoice choice = heuristic(o.Mp, o.Nrp, o.kb_total);
   const TcTuner::Key key{PREC, M, N, K};
   bool tune_now = false;
   if (tuner) {
@@ -720,7 +716,7 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
       tune_now = tuner->measuring;
   }
   if (force) {
-    if (force->bn != 128 && (force->bn != 256 || PREC == PREC_BF16X6)) return cudaErrorInvalidValue;
+    if (force->bn != 128 && force->bn != 256) return cudaErrorInvalidValue;
     choice = TcChoice{force->bn, eff_splits(o.kb_total, force->splits)};
     tune_now = false;
   }
@@ -783,7 +779,6 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     static const int splits[7] = {1, 2, 4, 8, 12, 16, 32};
     for (int bn : bns)
       for (int S0 : splits) {
-        if (PREC == PREC_BF16X6 && bn != 128) continue;
         const int S = eff_splits(o.kb_total, S0);
         if (S != S0 && S0 != 1) continue;        // duplicate of a smaller split count
         if (S > 1 && o.kb_total / S < 2) continue;  // splits of a single k-block

@@ -190,7 +190,7 @@ def test_gemm_entry_points_reject_bad_shapes(lib):
     assert lib.ipeps_zgemm_tile(I(2), I(64), I(1), *args) == 1
     assert lib.ipeps_zgemm_tile(I(2), I(128), I(0), *args) == 1
     assert b"tile" in lib.ipeps_last_error()
-    assert lib.ipeps_zgemm_tile(I(3), I(256), I(1), *args) == 1  # BF16x6 tiles are 128 wide
+    assert lib.ipeps_zgemm_tile(I(3), I(192), I(1), *args) == 1
     assert b"tile" in lib.ipeps_last_error()
 
 
