@@ -248,15 +248,15 @@ __global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4
 }
 
 // Right-looking Cholesky of the Hermitian n x n G (upper triangle used) with
-// dropped pivots (d <= tol * max diagonal: row of R zero), blocked by
-// CH_NB columns: rows of the working copy W live in the cluster's shared
-// memory (row i in CTA i mod csize).  For each block of rows j0 .. j0+nb-1
-// every CTA copies those rows from their owners, factors them into the rows
-// of R (the same arithmetic in every CTA, so the same values), and updates
-// its own rows below the block, W[i,l] -= conj(R[j,i]) R[j,l] for l >= i,
-// j in order: the operations and their order per element are those of the
-// column-by-column algorithm, with one cluster barrier per block instead of
-// one per column.
+// dropped pivots (d <= tol * max diagonal: row of R zero), blocked by CH_NB
+// rows.  Rows of the working copy W live in the cluster's shared memory (row
+// i in CTA i mod csize).  For the block of rows j0 .. j0+nb-1 each CTA
+// factors the nb x nb diagonal block (every CTA the same arithmetic, so the
+// same pivots) and, for the columns l >= j0+nb it owns (l mod csize = rank),
+// the block's entries of R; after a cluster barrier every CTA gathers the
+// block's rows of R and updates its own rows below the block, W[i,l] -=
+// conj(R[j,i]) R[j,l] for l >= i, j in order.  The operations and their order
+// per element are those of the column-by-column algorithm.
 constexpr int CH_NB = 8;
 
 __global__ void __launch_bounds__(CL_THREADS)
@@ -286,11 +286,17 @@ __global__ void __launch_bounds__(CL_THREADS)
   double dmax = 0.0;
   for (int r = 0; r < cs; ++r) dmax = fmax(dmax, *cl.map_shared_rank(&s_max, r));
   const double thr = tol * dmax;
+  // columns of the block this CTA works on: the diagonal block (c < nb), then
+  // its own columns l >= j0 + nb (c >= nb: l = j0 + nb + (c - nb) * cs + off)
   for (int j0 = 0; j0 < n; j0 += CH_NB) {
-    const int nb = min(CH_NB, n - j0), w = n - j0;
-    // rows j0 .. j0+nb-1 of W (columns j0 .. n-1) from their owners
-    for (int e = threadIdx.x; e < nb * w; e += CL_THREADS) {
-      const int jj = e / w, l = j0 + e % w, j = j0 + jj;
+    const int nb = min(CH_NB, n - j0), jn = j0 + nb;
+    const int off = ((rank - jn) % cs + cs) % cs;  // first own column at or after jn is jn + off
+    const int nown = jn + off < n ? (n - 1 - (jn + off)) / cs + 1 : 0;
+    const int ncol = nb + nown;
+    auto col = [&](int c) { return c < nb ? j0 + c : jn + off + (c - nb) * cs; };
+    // the block's rows of W on those columns, from their owners
+    for (int e = threadIdx.x; e < nb * ncol; e += CL_THREADS) {
+      const int jj = e / ncol, l = col(e % ncol), j = j0 + jj;
       pan[(long long)jj * n + l] = cl.map_shared_rank(sm, j % cs)[(long long)(j / cs) * n + l];
     }
     __syncthreads();
@@ -308,8 +314,10 @@ __global__ void __launch_bounds__(CL_THREADS)
       __syncthreads();
       const double rjj = s_rjj[jj], inv = s_inv[jj];
       const bool keep = rjj > 0.0;
-      // row j of R (zero left of the diagonal, and for a dropped direction)
-      for (int l = j0 + threadIdx.x; l < n; l += CL_THREADS) {
+      // row j of R on the CTA's columns (zero left of the diagonal, and for a
+      // dropped direction)
+      for (int c = threadIdx.x; c < ncol; c += CL_THREADS) {
+        const int l = col(c);
         cplx v = make_double2(0.0, 0.0);
         if (keep && l >= j) {
           const cplx g = pj[l];
@@ -320,8 +328,8 @@ __global__ void __launch_bounds__(CL_THREADS)
       __syncthreads();
       if (keep) {
         // the block's rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i
-        for (int e = threadIdx.x; e < (nb - 1 - jj) * w; e += CL_THREADS) {
-          const int i = j + 1 + e / w, l = j0 + e % w;
+        for (int e = threadIdx.x; e < (nb - 1 - jj) * ncol; e += CL_THREADS) {
+          const int i = j + 1 + e / ncol, l = col(e % ncol);
           if (l < i) continue;
           const cplx a = pj[i], b = pj[l];
           cplx* wi = pan + (long long)(i - j0) * n;
@@ -331,6 +339,14 @@ __global__ void __launch_bounds__(CL_THREADS)
       }
       __syncthreads();
     }
+    cl.sync();  // every CTA's columns of the block's rows of R are final
+    // the other CTAs' columns of those rows
+    for (int e = threadIdx.x; e < nb * (n - jn); e += CL_THREADS) {
+      const int jj = e / (n - jn), l = jn + e % (n - jn);
+      const int o = l % cs;
+      if (o != rank) pan[(long long)jj * n + l] = cl.map_shared_rank(pan, o)[(long long)jj * n + l];
+    }
+    __syncthreads();
     // the owners store their rows of R
     for (int jj = 0; jj < nb; ++jj) {
       const int j = j0 + jj;
@@ -342,7 +358,7 @@ __global__ void __launch_bounds__(CL_THREADS)
     for (int l0 = 0; l0 < R; ++l0) {
       const int i = l0 * cs + rank;
       if (i >= n) break;
-      if (i < j0 + nb) continue;
+      if (i < jn) continue;
       cplx* wi = sm + (long long)l0 * n;
       for (int l = i + threadIdx.x; l < n; l += CL_THREADS) {
         cplx v = wi[l];
@@ -355,7 +371,7 @@ __global__ void __launch_bounds__(CL_THREADS)
         wi[l] = v;
       }
     }
-    cl.sync();  // the updated rows are read as the next block; no CTA leaves while another reads it
+    cl.sync();  // rows updated before they are read as the next block; gathers done before pan is rewritten
   }
 }
 

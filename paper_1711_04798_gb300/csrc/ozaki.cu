@@ -407,10 +407,18 @@ OzLayout oz_layout(int M, int N, int K) {
   L.Nrp = (2 * N + OZ_BN - 1) / OZ_BN * OZ_BN;
   L.Krp = (2 * K + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
   L.chunks = L.Krp / OZ_CHUNK;
+  // chunks per CTA: the fewest chunk-times over whole waves of CTAs (152 SMs,
+  // one CTA each), the fewer K splits on a tie
   const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Nrp / OZ_BN);
-  int S = (int)((2 * 152 + tiles - 1) / tiles);  // about two waves of CTAs
-  S = S < 1 ? 1 : (S > L.chunks ? L.chunks : S);
-  L.cps = (L.chunks + S - 1) / S;
+  long long best = -1;
+  for (int cps = 1; cps <= L.chunks; ++cps) {
+    const long long S = (L.chunks + cps - 1) / cps;
+    const long long cost = (tiles * S + 151) / 152 * cps;
+    if (best < 0 || cost <= best) {
+      best = cost;
+      L.cps = cps;
+    }
+  }
   L.S = (L.chunks + L.cps - 1) / L.cps;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   size_t o = 0;

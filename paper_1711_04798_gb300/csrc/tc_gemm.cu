@@ -516,13 +516,15 @@ void padded(int N, int K, long long* Nrp, long long* Krp) {
   *Nrp = (2LL * N + NPAD - 1) / NPAD * NPAD;
 }
 
-// Default tile choice: 256-wide tiles; a product with fewer
-// output tiles than SMs splits K until about two waves of CTAs exist.
+constexpr int NSM = 152;  // SMs of the part (one CTA of the main kernel per SM)
+
+// Default tile choice: 256-wide tiles; a product with fewer output tiles than
+// SMs splits K into at most two whole waves of CTAs.
 TcChoice heuristic(long long Mp, long long Nrp, int kb_total, int bn = 256) {
   const long long tiles = (Mp / BM) * (Nrp / bn);
   int S = 1;
-  if (tiles < 152) {
-    S = (int)((2 * 152 + tiles - 1) / tiles);
+  if (tiles < NSM) {
+    S = (int)((2 * NSM) / tiles);
     if (S > kb_total / 2) S = kb_total / 2;
     if (S < 1) S = 1;
   }
@@ -776,8 +778,14 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     ent.us = ent.heuristic_us;
     ent.candidates = 1;
     static const int bns[2] = {128, 256};
-    static const int splits[7] = {1, 2, 4, 8, 12, 16, 32};
-    for (int bn : bns)
+    for (int bn : bns) {
+      // powers of two, and the counts that fill one to four whole waves
+      const long long tiles = (o.Mp / BM) * (o.Nrp / bn);
+      std::vector<int> splits = {1, 2, 4, 8, 16, 32};
+      for (int w = 1; w <= 4; ++w) {
+        const int S = (int)((long long)w * NSM / tiles);
+        if (S > 1 && std::find(splits.begin(), splits.end(), S) == splits.end()) splits.push_back(S);
+      }
       for (int S0 : splits) {
         const int S = eff_splits(o.kb_total, S0);
         if (S != S0 && S0 != 1) continue;        // duplicate of a smaller split count
@@ -793,6 +801,7 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
           ent.choice = c;
         }
       }
+    }
     tuner->table[key] = ent;
     tuner->order.push_back(key);
     choice = ent.choice;
