@@ -29,7 +29,8 @@
 
 namespace {
 
-constexpr int BM = 128, NPAD = 256, NTHREADS = 128;  // N of every packed B operand padded to NPAD
+constexpr int BM = 128, NPAD = 256;  // N of every packed B operand padded to NPAD
+constexpr int NTHREADS = 192;        // main kernel: producer warp, MMA warp, four epilogue warps
 constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2, PREC_BF16X6 = 3;
 
 
@@ -77,37 +78,51 @@ __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uin
   }
 }
 
+// Persistent main kernel: CTA b takes the output tiles t = b, b + grid, ...
+// (t = n_tile + n_tiles * (m_tile + m_tiles * split)).  Warp 0 streams the
+// k-blocks of its tiles through the shared-memory stages (TMA), warp 1 issues
+// the MMAs of tile i into accumulator set i % 2 (tensor-memory columns
+// BN (i % 2) ..), warps 2..5 drain set i % 2 to global memory while the MMAs
+// of tile i + 1 run in the other set.
 template <int PREC, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
                    const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
-                   int kb_total, int kb_per_split, int M, int Nr, cplx alpha, cplx* __restrict__ C,
-                   long long ldc, float* __restrict__ partial, int Nrp, long long pstride, int conj_out,
-                   int unit_alpha, int* __restrict__ timeouts) {
+                   int kb_total, int kb_per_split, int n_tiles, int m_tiles, int tiles, int M, int Nr, cplx alpha,
+                   cplx* __restrict__ C, long long ldc, float* __restrict__ partial, int Nrp, long long pstride,
+                   int conj_out, int unit_alpha, int* __restrict__ timeouts) {
   using K_ = Cfg<PREC, BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + K_::STAGES * K_::STAGE_BYTES);
   uint64_t* empty = full + K_::STAGES;
-  uint64_t* accb = empty + K_::STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(accb + 1);
+  uint64_t* acc_full = empty + K_::STAGES;  // [2], per accumulator set
+  uint64_t* acc_empty = acc_full + 2;      // [2]
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y, split = blockIdx.z;
-  const int kb0 = split * kb_per_split;
-  const int nkb = min(kb_total, kb0 + kb_per_split) - kb0;  // >= 1 by construction
+  auto kblocks = [&](int t, int* kb0) {
+    const int split = t / (n_tiles * m_tiles);
+    *kb0 = split * kb_per_split;
+    return min(kb_total, *kb0 + kb_per_split) - *kb0;  // >= 1 by construction
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < K_::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -117,115 +132,150 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // producer: one k-block per stage
-    int issued = 0;
-    for (int i = 0; i < nkb; ++i) {
-      const int s = i % K_::STAGES, r = i / K_::STAGES;
-      if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
-        atomicAdd(timeouts, 1);
-        break;
+    // producer: one k-block per stage, the stages cycling across tiles
+    int q = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      int kb0;
+      const int nkb = kblocks(t, &kb0);
+      const int n_tile = t % n_tiles, m_tile = (t / n_tiles) % m_tiles;
+      for (int i = 0; i < nkb; ++i, ++q) {
+        const int s = q % K_::STAGES, r = q / K_::STAGES;
+        if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
+          atomicAdd(timeouts, 1);
+          ok = false;
+          break;
+        }
+        unsigned char* st = smem + s * K_::STAGE_BYTES;
+        mbar_expect_tx(&full[s], K_::STAGE_BYTES);
+        const int kx = (kb0 + i) * K_::BK;
+        unsigned char* sb = st + K_::NOPS * K_::A_BYTES;
+        tma_load_2d(st, &mA0, &full[s], kx, m_tile * BM);
+        tma_load_2d(sb, &mB0, &full[s], kx, n_tile * BN);
+        if (K_::NOPS >= 2) {
+          tma_load_2d(st + K_::A_BYTES, &mA1, &full[s], kx, m_tile * BM);
+          tma_load_2d(sb + K_::B_BYTES, &mB1, &full[s], kx, n_tile * BN);
+        }
+        if (K_::NOPS == 3) {
+          tma_load_2d(st + 2 * K_::A_BYTES, &mA2, &full[s], kx, m_tile * BM);
+          tma_load_2d(sb + 2 * K_::B_BYTES, &mB2, &full[s], kx, n_tile * BN);
+        }
       }
-      unsigned char* st = smem + s * K_::STAGE_BYTES;
-      mbar_expect_tx(&full[s], K_::STAGE_BYTES);
-      const int kx = (kb0 + i) * K_::BK;
-      unsigned char* sb = st + K_::NOPS * K_::A_BYTES;
-      tma_load_2d(st, &mA0, &full[s], kx, m_tile * BM);
-      tma_load_2d(sb, &mB0, &full[s], kx, n_tile * BN);
-      if (K_::NOPS >= 2) {
-        tma_load_2d(st + K_::A_BYTES, &mA1, &full[s], kx, m_tile * BM);
-        tma_load_2d(sb + K_::B_BYTES, &mB1, &full[s], kx, n_tile * BN);
-      }
-      if (K_::NOPS == 3) {
-        tma_load_2d(st + 2 * K_::A_BYTES, &mA2, &full[s], kx, m_tile * BM);
-        tma_load_2d(sb + 2 * K_::B_BYTES, &mB2, &full[s], kx, n_tile * BN);
-      }
-      issued = i + 1;
     }
     // the last loads of every stage have landed before the CTA can leave
     // (they are what an MMA issuer that gave up may not have waited for)
-    for (int i = max(0, issued - K_::STAGES); i < issued; ++i)
-      if (!mbar_wait(&full[i % K_::STAGES], (i / K_::STAGES) & 1)) atomicAdd(timeouts, 1);
+    for (int j = max(0, q - K_::STAGES); j < q; ++j)
+      if (!mbar_wait(&full[j % K_::STAGES], (j / K_::STAGES) & 1)) atomicAdd(timeouts, 1);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    for (int i = 0; i < nkb; ++i) {
-      const int s = i % K_::STAGES, r = i / K_::STAGES;
-      if (!mbar_wait(&full[s], r & 1)) {
+    int q = 0, it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+      int kb0;
+      const int nkb = kblocks(t, &kb0);
+      const int b = it & 1;
+      // the set was drained: tile it - 2 was that set's drain number it/2 - 1
+      if (it >= 2 && !mbar_wait(&acc_empty[b], ((it >> 1) - 1) & 1)) {
         atomicAdd(timeouts, 1);
+        ok = false;
         break;
       }
       fence_after();
-      const uint32_t base = smem_u32(smem + s * K_::STAGE_BYTES);
-      const uint32_t a0 = base, a1 = base + K_::A_BYTES, a2 = base + 2 * K_::A_BYTES;
-      const uint32_t b0 = base + K_::NOPS * K_::A_BYTES, b1 = b0 + K_::B_BYTES, b2 = b0 + 2 * K_::B_BYTES;
+      const uint32_t d = tmem + (uint32_t)(b * BN);
+      for (int i = 0; i < nkb; ++i, ++q) {
+        const int s = q % K_::STAGES, r = q / K_::STAGES;
+        if (!mbar_wait(&full[s], r & 1)) {
+          atomicAdd(timeouts, 1);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t base = smem_u32(smem + s * K_::STAGE_BYTES);
+        const uint32_t a0 = base, a1 = base + K_::A_BYTES, a2 = base + 2 * K_::A_BYTES;
+        const uint32_t b0 = base + K_::NOPS * K_::A_BYTES, b1 = b0 + K_::B_BYTES, b2 = b0 + 2 * K_::B_BYTES;
 #pragma unroll
-      for (int j = 0; j < K_::KSTEPS; ++j) {
-        const uint32_t ko = j * 32;  // bytes of one MMA's K inside the k-block row
-        const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
-        if (K_::NOPS == 3) {
-          // smallest parts first: p_i q_j with i + j = 2, then 1, then 0
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b2 + ko), acc);
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a2 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
-        } else {
-          umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), acc);
-          if (K_::NOPS == 2) {
-            umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
-            umma<PREC, K_::IDESC>(tmem, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+        for (int j = 0; j < K_::KSTEPS; ++j) {
+          const uint32_t ko = j * 32;  // bytes of one MMA's K inside the k-block row
+          const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
+          if (K_::NOPS == 3) {
+            // smallest parts first: p_i q_j with i + j = 2, then 1, then 0
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b2 + ko), acc);
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a2 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+          } else {
+            umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), acc);
+            if (K_::NOPS == 2) {
+              umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a0 + ko), sdesc_kb<K_::KB_BYTES>(b1 + ko), 1u);
+              umma<PREC, K_::IDESC>(d, sdesc_kb<K_::KB_BYTES>(a1 + ko), sdesc_kb<K_::KB_BYTES>(b0 + ko), 1u);
+            }
           }
         }
+        umma_commit(&empty[s]);  // frees the stage when these MMAs are done
       }
-      umma_commit(&empty[s]);  // frees the stage when these MMAs are done
+      if (ok) umma_commit(&acc_full[b]);
     }
-    umma_commit(accb);
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
-  const bool ready = mbar_wait(accb, 0);
-  if (!ready && lane == 0) atomicAdd(timeouts, 1);
-  __syncwarp();
-  fence_after();
-  if (ready) {
-    const int row = m_tile * BM + warp * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(trow + c0, v);
-      const int col = n_tile * BN + c0;  // real column
-      if (partial) {
-        float4* dst = (float4*)(partial + split * pstride + (long long)row * Nrp + col);
+    // every MMA issued has completed before the accumulators are released
+    umma_commit(mma_done);
+    if (!mbar_wait(mma_done, 0)) atomicAdd(timeouts, 1);
+  } else if (warp >= 2) {
+    // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. (the rows of its quarter)
+    const int quad = warp & 3;
+    int it = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+      const int split = t / (n_tiles * m_tiles);
+      const int n_tile = t % n_tiles, m_tile = (t / n_tiles) % m_tiles;
+      const int b = it & 1;
+      // every lane saw the set complete, or the warp stops (a wait that ran out)
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (it >> 1) & 1));
+      if (!ready) {
+        if (lane == 0) atomicAdd(timeouts, 1);
+        break;
+      }
+      fence_after();
+      const int row = m_tile * BM + quad * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+        const int col = n_tile * BN + c0;  // real column
+        if (partial) {
+          float4* dst = (float4*)(partial + split * pstride + (long long)row * Nrp + col);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      } else if (row < M) {
-        if (unit_alpha) {
-          // alpha = 1: exact FP32 -> FP64 widening on the integer pipe
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else if (row < M) {
+          if (unit_alpha) {
+            // alpha = 1: exact FP32 -> FP64 widening on the integer pipe
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            if (col + 2 * t < Nr) {
-              const double re = f2d_bits(v[2 * t]), im = f2d_bits(v[2 * t + 1]);
-              C[(long long)row * ldc + (col >> 1) + t] = make_double2(re, conj_out ? neg_bits(im) : im);
+            for (int u = 0; u < 8; ++u) {
+              if (col + 2 * u < Nr) {
+                const double re = f2d_bits(v[2 * u]), im = f2d_bits(v[2 * u + 1]);
+                C[(long long)row * ldc + (col >> 1) + u] = make_double2(re, conj_out ? neg_bits(im) : im);
+              }
             }
-          }
-        } else {
+          } else {
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            if (col + 2 * t < Nr) {
-              const double re = v[2 * t], im = v[2 * t + 1];
-              const double orr = alpha.x * re - alpha.y * im, oi = alpha.x * im + alpha.y * re;
-              C[(long long)row * ldc + (col >> 1) + t] = make_double2(orr, conj_out ? -oi : oi);
+            for (int u = 0; u < 8; ++u) {
+              if (col + 2 * u < Nr) {
+                const double re = v[2 * u], im = v[2 * u + 1];
+                const double orr = alpha.x * re - alpha.y * im, oi = alpha.x * im + alpha.y * re;
+                C[(long long)row * ldc + (col >> 1) + u] = make_double2(orr, conj_out ? -oi : oi);
+              }
             }
           }
         }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
   }
   fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
   }
 }
 
@@ -582,7 +632,16 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
   }
   S = eff_splits(o.kb_total, S);
   const int kps = (o.kb_total + S - 1) / S;
-  dim3 grid((unsigned)(o.Nrp / BN), (unsigned)(o.Mp / BM), (unsigned)S);
+  const int n_tiles = (int)(o.Nrp / BN), m_tiles = (int)(o.Mp / BM);
+  const long long tiles = (long long)n_tiles * m_tiles * S;
+  if (tiles >= (1LL << 31)) return cudaErrorInvalidValue;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  const unsigned grid = (unsigned)std::min<long long>(tiles, nsm);
   const int unit = alpha.x == 1.0 && alpha.y == 0.0;
   if (probe) {
     probe->Mp = o.Mp;
@@ -594,9 +653,10 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
     probe->elem_bytes = K_::ELEM;
     if ((e = cudaEventRecord(probe->ev[0], s)) != cudaSuccess) return e;
   }
-  tc_gemm_kernel<PREC, BN><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mA2, mB0, mB1, mB2, o.kb_total, kps, M, 2 * N, alpha,
-                                                             C, ldc, S > 1 ? part : nullptr, (int)o.Nrp,
-                                                             o.Mp * o.Nrp, conj_out ? 1 : 0, unit, timeouts);
+  tc_gemm_kernel<PREC, BN><<<grid, NTHREADS, K_::SMEM, s>>>(mA0, mA1, mA2, mB0, mB1, mB2, o.kb_total, kps, n_tiles,
+                                                             m_tiles, (int)tiles, M, 2 * N, alpha, C, ldc,
+                                                             S > 1 ? part : nullptr, (int)o.Nrp, o.Mp * o.Nrp,
+                                                             conj_out ? 1 : 0, unit, timeouts);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (probe && (e = cudaEventRecord(probe->ev[1], s)) != cudaSuccess) return e;
