@@ -59,10 +59,79 @@ __device__ __forceinline__ void pair_of(int r, int p, int np, int rounds, int* i
   *j = b;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value is an unevaluated sum hi + lo of two FP32
+// numbers, about 48 significand bits; Dekker 1971, Knuth's TwoSum): the
+// precision form's Jacobi runs its dot products and row rotations on the
+// FP32 pipe, which this part executes at 64 times its FP64 rate.  The
+// intrinsics below are never contracted into fused multiply-adds, which the
+// error-free transformations rely on.
+// ---------------------------------------------------------------------------
+struct df2 {
+  float h, l;
+};
+
+__device__ __forceinline__ df2 df_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ double df_val(df2 a) { return (double)a.h + (double)a.l; }
+
+// s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+}
+
+// acc += a b: the leading product exactly (its rounding error by an FMA), the
+// cross terms and the tails in FP32, the leading sum's rounding error carried
+// into acc.l
+__device__ __forceinline__ void acc_mul(df2& acc, df2 a, df2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  float s, t;
+  two_sum(acc.h, p, s, t);
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ df2 df_norm(df2 a) {
+  df2 r;
+  two_sum(a.h, a.l, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ df2 df_negate(df2 a) { return {-a.h, -a.l}; }
+
+// a complex element of a row: (Re hi, Re lo, Im hi, Im lo)
+__device__ __forceinline__ float4 df_elem(cplx x) {
+  const df2 r = df_of(x.x), i = df_of(x.y);
+  return make_float4(r.h, r.l, i.h, i.l);
+}
+
+__device__ __forceinline__ df2 warp_sum_df(df2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, v.h, o), ol = __shfl_xor_sync(0xffffffffu, v.l, o);
+    float s, t;
+    two_sum(v.h, oh, s, t);
+    v.h = s;
+    v.l = __fadd_rn(v.l, __fadd_rn(ol, t));
+  }
+  return df_norm(v);
+}
+
 // One-sided Jacobi on the n rows of G (length m): rows and, with Vt, the rows
 // of the accumulated rotation (length n, from the identity, or from Vt itself
-// with warm) in the cluster's shared memory.
-__global__ void __launch_bounds__(JC_THREADS)
+// with warm) in the cluster's shared memory.  DF: the rows are held, dotted
+// and rotated in double-float arithmetic (the rotation angles stay FP64;
+// only with a rotation log, Vt being rebuilt from it in FP64).
+template <bool DF>
+__global__ void __launch_bounds__(JC_THREADS, 1)
     jacobi_cluster_kernel(cplx* __restrict__ G, int n, int m, long long ldg, cplx* __restrict__ Vt, int max_sweeps,
                           double tol, double4_16a* __restrict__ log, int* sweeps_used, DevStatus* st, int warm) {
   cg::cluster_group cl = cg::this_cluster();
@@ -81,7 +150,10 @@ __global__ void __launch_bounds__(JC_THREADS)
     if (i >= n) break;
     for (int t = threadIdx.x; t < m; t += JC_THREADS) {
       const cplx x = G[(long long)i * ldg + t];
-      gl[(long long)l * m + t] = x;
+      if constexpr (DF)
+        ((float4*)gl)[(long long)l * m + t] = df_elem(x);
+      else
+        gl[(long long)l * m + t] = x;
       f += x.x * x.x + x.y * x.y;
     }
     if (Vt)
@@ -121,7 +193,33 @@ __global__ void __launch_bounds__(JC_THREADS)
         const bool active = p < npairs && j < n;
         cplx* gi = active ? grow(i) : nullptr;
         cplx* gj = active ? grow(j) : nullptr;
-        if (active) {
+        if (active && DF) {
+          df2 al = {0.f, 0.f}, be = {0.f, 0.f}, gr = {0.f, 0.f}, gim = {0.f, 0.f};
+          const float4* fi = (const float4*)gi;
+          const float4* fj = (const float4*)gj;
+          for (int t = lane + 32 * half; t < m; t += 64) {
+            const float4 x4 = fi[t], y4 = fj[t];
+            const df2 xr = {x4.x, x4.y}, xi = {x4.z, x4.w}, yr = {y4.x, y4.y}, yi = {y4.z, y4.w};
+            acc_mul(al, xr, xr);
+            acc_mul(al, xi, xi);
+            acc_mul(be, yr, yr);
+            acc_mul(be, yi, yi);
+            acc_mul(gr, xr, yr);
+            acc_mul(gr, xi, yi);
+            acc_mul(gim, xr, yi);
+            acc_mul(gim, df_negate(xi), yr);
+          }
+          al = warp_sum_df(al);
+          be = warp_sum_df(be);
+          gr = warp_sum_df(gr);
+          gim = warp_sum_df(gim);
+          if (lane == 0) {
+            s_part[slot][half][0] = df_val(al);
+            s_part[slot][half][1] = df_val(be);
+            s_part[slot][half][2] = df_val(gr);
+            s_part[slot][half][3] = df_val(gim);
+          }
+        } else if (active) {
           double al = 0.0, be = 0.0, gr = 0.0, gim = 0.0;
           for (int t = lane + 32 * half; t < m; t += 64) {
             const cplx x = gi[t], y = gj[t];
@@ -169,7 +267,37 @@ __global__ void __launch_bounds__(JC_THREADS)
           sn = __shfl_sync(0xffffffffu, sn, 0);
           const cplx ph = make_double2(__shfl_sync(0xffffffffu, phr, 0), __shfl_sync(0xffffffffu, phi, 0));
           const cplx sq = make_double2(sn * ph.x, sn * ph.y), sp = make_double2(sn * ph.x, -sn * ph.y);
-          for (int q = lane + 32 * half; q < m; q += 64) jac_rotate(gi[q], gj[q], c, sq, sp);
+          if constexpr (DF) {
+            // a' = c a - sq b, b' = c b + sp a (the form of jac_rotate)
+            const df2 cd = df_of(c), qr = df_of(sq.x), qi = df_of(sq.y), pr = df_of(sp.x), pi = df_of(sp.y);
+            float4* fi = (float4*)gi;
+            float4* fj = (float4*)gj;
+            for (int q = lane + 32 * half; q < m; q += 64) {
+              const float4 x4 = fi[q], y4 = fj[q];
+              const df2 xr = {x4.x, x4.y}, xi = {x4.z, x4.w}, yr = {y4.x, y4.y}, yi = {y4.z, y4.w};
+              df2 ar = {0.f, 0.f}, ai = {0.f, 0.f}, br = {0.f, 0.f}, bi = {0.f, 0.f};
+              acc_mul(ar, cd, xr);
+              acc_mul(ar, df_negate(qr), yr);
+              acc_mul(ar, qi, yi);
+              acc_mul(ai, cd, xi);
+              acc_mul(ai, df_negate(qr), yi);
+              acc_mul(ai, df_negate(qi), yr);
+              acc_mul(br, cd, yr);
+              acc_mul(br, pr, xr);
+              acc_mul(br, df_negate(pi), xi);
+              acc_mul(bi, cd, yi);
+              acc_mul(bi, pr, xi);
+              acc_mul(bi, pi, xr);
+              ar = df_norm(ar);
+              ai = df_norm(ai);
+              br = df_norm(br);
+              bi = df_norm(bi);
+              fi[q] = make_float4(ar.h, ar.l, ai.h, ai.l);
+              fj[q] = make_float4(br.h, br.l, bi.h, bi.l);
+            }
+          } else {
+            for (int q = lane + 32 * half; q < m; q += 64) jac_rotate(gi[q], gj[q], c, sq, sp);
+          }
           if (Vt) {
             cplx* vi = vrow(i);
             cplx* vj = vrow(j);
@@ -202,7 +330,14 @@ __global__ void __launch_bounds__(JC_THREADS)
   for (int l = 0; l < R; ++l) {
     const int i = l * cs + rank;
     if (i >= n) break;
-    for (int t = threadIdx.x; t < m; t += JC_THREADS) G[(long long)i * ldg + t] = gl[(long long)l * m + t];
+    for (int t = threadIdx.x; t < m; t += JC_THREADS) {
+      if constexpr (DF) {
+        const float4 x4 = ((const float4*)gl)[(long long)l * m + t];
+        G[(long long)i * ldg + t] = make_double2(df_val({x4.x, x4.y}), df_val({x4.z, x4.w}));
+      } else {
+        G[(long long)i * ldg + t] = gl[(long long)l * m + t];
+      }
+    }
     if (Vt)
       for (int t = threadIdx.x; t < n; t += JC_THREADS) Vt[(long long)i * n + t] = vl[(long long)l * n + t];
   }
@@ -380,7 +515,8 @@ __global__ void __launch_bounds__(CL_THREADS)
 static cudaError_t cluster_init() {
   if (g_csize) return cudaSuccess;
   cudaError_t e;
-  const void* fns[2] = {(const void*)jacobi_cluster_kernel, (const void*)chol_cluster_kernel};
+  const void* fns[3] = {(const void*)jacobi_cluster_kernel<false>, (const void*)jacobi_cluster_kernel<true>,
+                        (const void*)chol_cluster_kernel};
   for (const void* f : fns) {
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, CL_SMEM)) != cudaSuccess) return e;
@@ -399,7 +535,7 @@ static cudaError_t cluster_init() {
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)jacobi_cluster_kernel, &cfg) == cudaSuccess &&
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)jacobi_cluster_kernel<false>, &cfg) == cudaSuccess &&
       nclusters >= 1)
     csize = 16;
   cudaGetLastError();  // a refused query leaves no error behind
@@ -439,7 +575,7 @@ long long jacobi_log_elems(int n, int max_sweeps) {
 }
 
 cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
-                           DevStatus* st, cplx* rotlog, int* sweeps_used, bool warm_v) {
+                           DevStatus* st, cplx* rotlog, int* sweeps_used, bool warm_v, bool dfloat) {
   cudaError_t e;
   if ((e = cluster_init()) != cudaSuccess) return e;
   const bool replay = Vt && rotlog && sweeps_used && n <= 2048;
@@ -448,10 +584,15 @@ cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg,
   int* su = replay ? sweeps_used : nullptr;
   const long long R = (n + g_csize - 1) / g_csize;
   const size_t smem = (size_t)(R * ((long long)m + (Vin ? n : 0)) * sizeof(cplx));
-  double tol = (double)m * 2.220446049250313e-16;
+  // double-float rows only where Vt is rebuilt from the log in FP64; their
+  // dot products resolve orthogonality to about m 2^-48, so pairs are left
+  // alone below m 2^-44 (FP64: m eps)
+  const bool df = dfloat && replay;
+  double tol = df ? (double)m * 0x1p-44 : (double)m * 2.220446049250313e-16;
   int warm = warm_v && Vin ? 1 : 0;
   void* args[] = {&G, &n, &m, &ldg, &Vin, &max_sweeps, &tol, &logp, &su, &st, &warm};
-  e = launch_cluster((const void*)jacobi_cluster_kernel, args, smem, s, JC_THREADS);
+  e = launch_cluster(df ? (const void*)jacobi_cluster_kernel<true> : (const void*)jacobi_cluster_kernel<false>, args,
+                     smem, s, JC_THREADS);
   count_launch();
   if (e != cudaSuccess || !replay) return e;
   const int npairs = ((n + 1) & ~1) / 2;

@@ -1361,7 +1361,7 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out, cplx* 
     cplx* rotlog = scratch_alloc(h, nlog);
     if (!rotlog) return fail(IPEPS_ENOMEM, "scratch exhausted (rotation log)");
     CK(jacobi_rows(h->stream, R1, k, k, k, Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork, h->counters,
-                   h->st, rotlog, nlog, h->opt.wait_cycles, true));
+                   h->st, rotlog, nlog, h->opt.wait_cycles, true, true));
     prof_end(h, a, 0.0, 1);
   }
   // out = V^T Wt  (rows (W v_i)^T)
@@ -1813,6 +1813,39 @@ extern "C" ipeps_status ipeps_rdm_site(ipeps_ctm h, double* rho_s) {
 // all bond RDMs into device buffers rh, rv ([Ly][Lx][d^2][d^2] each)
 static ipeps_status all_rdms(ipeps_ctm h, cplx* rh, cplx* rv) {
   const long long n2 = (long long)h->d * h->d * h->d * h->d;
+  // both kinds of bond: horizontal bonds on the handle's stream, vertical ones
+  // on the second lane, each lane with half of the scratch arena, when half
+  // holds one bond's intermediates (the halves' six-leg tensors, the
+  // contraction temporaries and the packed tensor-core operands)
+  const long long c = h->chi, D = h->D, d = h->d;
+  const long long big = c * c * D * D * D * D * d;
+  const long long need = c * c * D * D * D * D + 4 * big + 2 * c * c * D * D * d * d + c * c * D * D + (1LL << 22);
+  const long long full = h->scratch_elems, half = (full / 2) & ~1023LL;
+  if (rh && rv && h->has_alt && !h->no_alt && h->opt.prec != IPEPS_PREC_FP64 && half >= need) {
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->alt.stream, h->ev_fork, 0));
+    h->scratch_elems = half;
+    h->alt.scratch = h->scratch + half;
+    h->alt.scratch_elems = full - half;
+    h->alt.scratch_top = 0;
+    ipeps_status s0 = IPEPS_OK, s1 = IPEPS_OK;
+    for (int y = 0; y < h->Ly && s0 == IPEPS_OK; ++y)
+      for (int x = 0; x < h->Lx && s0 == IPEPS_OK; ++x)
+        s0 = rdm_horizontal(h, 0, x, y, rh + (long long)(y * h->Lx + x) * n2);
+    if (s0 == IPEPS_OK) {
+      swap_lane(h);
+      for (int y = 0; y < h->Ly && s1 == IPEPS_OK; ++y)
+        for (int x = 0; x < h->Lx && s1 == IPEPS_OK; ++x)
+          s1 = rdm_horizontal(h, 1, y, -x, rv + (long long)(y * h->Lx + x) * n2);  // (x,y)-(x,y+1) in frame 1
+      swap_lane(h);
+    }
+    h->scratch_elems = full;
+    CK(cudaEventRecord(h->ev_join, h->alt.stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    CKS(s0);
+    CKS(s1);
+    return IPEPS_OK;
+  }
   for (int y = 0; y < h->Ly; ++y)
     for (int x = 0; x < h->Lx; ++x) {
       const long long o = (long long)(y * h->Lx + x) * n2;

@@ -121,10 +121,13 @@ cudaError_t set_zero(cudaStream_t s, cplx* x, long long n);
 // and its CTA stops.
 // warm_v: Vt holds a unitary n x n start V0^T on entry (the rotations are
 // accumulated onto it, Vt = J^T V0^T) instead of starting from the identity.
+// dfloat: where the cluster path rebuilds Vt from the rotation log, hold,
+// dot and rotate the rows in double-float arithmetic (about 48 bits; the
+// rotations themselves and Vt stay FP64), for the precision form.
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
                         DevStatus* st, cplx* rotlog = nullptr, long long rotlog_elems = 0,
-                        long long wait_cycles = 0, bool warm_v = false);
+                        long long wait_cycles = 0, bool warm_v = false, bool dfloat = false);
 // V (n x n) = identity
 cudaError_t set_identity(cudaStream_t s, cplx* V, int n);
 // rows of G scaled to unit norm where sigma > tol*max(sigma), zero otherwise
@@ -192,7 +195,8 @@ bool jacobi_cluster_fits(int n, int m, bool vt_in_smem);
 // replayed onto the identity (onto Vt itself with warm_v) by one CTA per
 // column afterwards.
 cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt, int max_sweeps,
-                           DevStatus* st, cplx* rotlog, int* sweeps_used, bool warm_v = false);
+                           DevStatus* st, cplx* rotlog, int* sweeps_used, bool warm_v = false,
+                           bool dfloat = false);
 long long jacobi_log_elems(int n, int max_sweeps);
 bool chol_cluster_fits(int n);
 cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol);

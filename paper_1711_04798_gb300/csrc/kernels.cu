@@ -606,7 +606,8 @@ cudaError_t kernels_init() {
 
 cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cplx* Vt,
                         double* sigma, int max_sweeps, double* work, int* counters,
-                        DevStatus* st, cplx* rotlog, long long rotlog_elems, long long wait_cycles, bool warm_v) {
+                        DevStatus* st, cplx* rotlog, long long rotlog_elems, long long wait_cycles, bool warm_v,
+                        bool dfloat) {
   if (n <= 0) return cudaSuccess;
   cudaError_t e;
   if ((e = kernels_init()) != cudaSuccess) return e;
@@ -614,7 +615,7 @@ cudaError_t jacobi_rows(cudaStream_t s, cplx* G, int n, int m, long long ldg, cp
   if (jacobi_cluster_fits(n, m, Vt != nullptr && !logged)) {
     // rows (and Vt unless logged) fit in one cluster's shared memory: no grid-wide barrier
     if ((e = jacobi_cluster(s, G, n, m, ldg, Vt, max_sweeps, st, logged ? rotlog : nullptr,
-                            logged ? counters : nullptr, warm_v)) != cudaSuccess)
+                            logged ? counters : nullptr, warm_v, dfloat)) != cudaSuccess)
       return e;
     row_norms_kernel<<<n < 1024 ? n : 1024, 256, 0, s>>>(G, n, m, ldg, sigma);
     count_launch();
