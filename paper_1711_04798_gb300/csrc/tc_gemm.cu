@@ -311,6 +311,39 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ P, int S, long lo
   }
 }
 
+// The same with a warp per output for many splits: lane l sums splits
+// l, l + 32, ... in order, then the lanes' sums meet in a fixed butterfly.
+__global__ void splitk_reduce_warp_kernel(const float* __restrict__ P, int S, long long pstride, int Nrp, int M,
+                                          int N, cplx alpha, cplx* __restrict__ C, long long ldc, int conj_out,
+                                          int unit_alpha) {
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)M * N;
+  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < total;
+       e += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int m = (int)(e / N), n = (int)(e % N);
+    float re = 0.0f, im = 0.0f;
+    for (int z = lane; z < S; z += 32) {
+      const float2 p = *(const float2*)(P + z * pstride + (long long)m * Nrp + 2 * n);
+      re += p.x;
+      im += p.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane != 0) continue;
+    if (unit_alpha) {
+      const double dr = f2d_bits(re), di = f2d_bits(im);
+      C[(long long)m * ldc + n] = make_double2(dr, conj_out ? neg_bits(di) : di);
+    } else {
+      const double r = re, i = im;
+      const double oi = alpha.x * i + alpha.y * r;
+      C[(long long)m * ldc + n] = make_double2(alpha.x * r - alpha.y * i, conj_out ? -oi : oi);
+    }
+  }
+}
+
 __device__ __forceinline__ cplx load_op(const cplx* X, long long ld, int op, int r, int c) {
   // element (r, c) of the operand in its GEMM role (A: (m,k); B: (k,n))
   cplx v = (op & OP_T) ? X[(long long)c * ld + r] : X[(long long)r * ld + c];
@@ -440,40 +473,33 @@ __device__ __forceinline__ long long view_off(unsigned idx, int n, const int* di
   return off;
 }
 
-__device__ __forceinline__ cplx view_at(const TcView& V, int r, int c) {
-  cplx v = V.p[view_off((unsigned)r, V.nr, V.rdim, V.rstr) + view_off((unsigned)c, V.nc, V.cdim, V.cstr)];
-  if (V.conj) v.y = neg_bits(v.y);
-  return v;
-}
 
 // Ar[m, kr] gathered through a view (rows m, columns k): a fused
-// permute-and-pack of the A operand, padded to Mp x Krp; one thread per
-// complex element (its two reals written as a pair)
+// permute-and-pack of the A operand, padded to Mp x Krp, by 32 x 32 complex
+// tiles.  The view offsets of the tile's 32 rows and 32 columns are computed
+// once per tile (the divisions of the index arithmetic would otherwise bound
+// the kernel); reads run along whichever of m or k is contiguous in the
+// source (row_contig: m), writes along k.
 template <int PREC>
-__global__ void pack_a_view_kernel(TcView V, int M, int K, int Mp, int Krp, void* __restrict__ o0,
-                                   void* __restrict__ o1, void* __restrict__ o2) {
-  const unsigned kc = (unsigned)(Krp >> 1), total = (unsigned)Mp * kc;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const unsigned m = e / kc, k = e - m * kc;
-    cplx v = make_double2(0.0, 0.0);
-    if ((int)m < M && (int)k < K) v = view_at(V, (int)m, (int)k);
-    store_pair(PREC, (long long)m * Krp + 2 * k, v.x, v.y, o0, o1, o2);
-  }
-}
-
-// The same through 32 x 32 complex tiles in shared memory, for views whose
-// innermost row axis is the contiguous one (the plain kernel's warps would
-// read 32 elements a full row stride apart): reads run along m, writes along k.
-template <int PREC>
-__global__ void pack_a_view_tr_kernel(TcView V, int M, int K, int Mp, int Krp, void* __restrict__ o0,
-                                      void* __restrict__ o1, void* __restrict__ o2) {
+__global__ void pack_a_tiled_kernel(TcView V, int M, int K, int Mp, int Krp, int row_contig, void* __restrict__ o0,
+                                    void* __restrict__ o1, void* __restrict__ o2) {
   __shared__ cplx tile[32][33];
+  __shared__ long long roff[32], coff[32];
   const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  if (threadIdx.y == 0) {
+    const int m = m0 + threadIdx.x, k = k0 + threadIdx.x;
+    roff[threadIdx.x] = m < M ? view_off((unsigned)m, V.nr, V.rdim, V.rstr) : -1;
+    coff[threadIdx.x] = k < K ? view_off((unsigned)k, V.nc, V.cdim, V.cstr) : -1;
+  }
+  __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int k = k0 + i, m = m0 + threadIdx.x;
+    const int mi = row_contig ? (int)threadIdx.x : i, ki = row_contig ? i : (int)threadIdx.x;
     cplx v = make_double2(0.0, 0.0);
-    if (m < M && k < K) v = view_at(V, m, k);
-    tile[i][threadIdx.x] = v;
+    if (roff[mi] >= 0 && coff[ki] >= 0) {
+      v = V.p[roff[mi] + coff[ki]];
+      if (V.conj) v.y = neg_bits(v.y);
+    }
+    tile[ki][mi] = v;
   }
   __syncthreads();
   const int k = k0 + threadIdx.x;
@@ -486,19 +512,42 @@ __global__ void pack_a_view_tr_kernel(TcView V, int M, int K, int Mp, int Krp, v
   }
 }
 
-// Br^T[nr, kr] gathered through a view (rows n, columns k), padded to Nrp x Krp:
-// complex (n, k) gives rows 2n: (Re, -Im) and 2n+1: (Im, Re) at columns 2k, 2k+1
+// Br^T[nr, kr] gathered through a view (rows n, columns k), padded to Nrp x Krp,
+// by 32 x 32 complex tiles as pack_a_tiled_kernel: complex (n, k) gives rows
+// 2n: (Re, -Im) and 2n+1: (Im, Re) at columns 2k, 2k+1
 template <int PREC>
-__global__ void pack_b_view_kernel(TcView V, int N, int K, int Nrp, int Krp, void* __restrict__ o0,
-                                   void* __restrict__ o1, void* __restrict__ o2) {
-  const unsigned kc = (unsigned)(Krp >> 1), total = (unsigned)(Nrp >> 1) * kc;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const unsigned n = e / kc, k = e - n * kc;
+__global__ void pack_b_tiled_kernel(TcView V, int N, int K, int Nrp, int Krp, int row_contig, void* __restrict__ o0,
+                                    void* __restrict__ o1, void* __restrict__ o2) {
+  __shared__ cplx tile[32][33];
+  __shared__ long long roff[32], coff[32];
+  const int k0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+  if (threadIdx.y == 0) {
+    const int n = n0 + threadIdx.x, k = k0 + threadIdx.x;
+    roff[threadIdx.x] = n < N ? view_off((unsigned)n, V.nr, V.rdim, V.rstr) : -1;
+    coff[threadIdx.x] = k < K ? view_off((unsigned)k, V.nc, V.cdim, V.cstr) : -1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int ni = row_contig ? (int)threadIdx.x : i, ki = row_contig ? i : (int)threadIdx.x;
     cplx v = make_double2(0.0, 0.0);
-    if ((int)n < N && (int)k < K) v = view_at(V, (int)n, (int)k);
-    const long long r0 = (long long)(2 * n) * Krp + 2 * k;
-    store_pair(PREC, r0, v.x, neg_bits(v.y), o0, o1, o2);
-    store_pair(PREC, r0 + Krp, v.y, v.x, o0, o1, o2);
+    if (roff[ni] >= 0 && coff[ki] >= 0) {
+      v = V.p[roff[ni] + coff[ki]];
+      if (V.conj) v.y = neg_bits(v.y);
+    }
+    tile[ki][ni] = v;
+  }
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (2 * k >= Krp) return;
+  for (int r = threadIdx.y; r < 64; r += blockDim.y) {
+    const int nr = 2 * n0 + r;
+    if (nr >= Nrp) break;
+    const cplx v = tile[threadIdx.x][r >> 1];
+    const long long e = (long long)nr * Krp + 2 * (long long)k;
+    if (r & 1)
+      store_pair(PREC, e, v.y, v.x, o0, o1, o2);  // row 2n+1: (Im, Re)
+    else
+      store_pair(PREC, e, v.x, neg_bits(v.y), o0, o1, o2);  // row 2n: (Re, -Im)
   }
 }
 
@@ -661,8 +710,12 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (probe && (e = cudaEventRecord(probe->ev[1], s)) != cudaSuccess) return e;
   if (S > 1) {
-    splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, o.Mp * o.Nrp, (int)o.Nrp, M, N, alpha,
-                                                                    C, ldc, conj_out ? 1 : 0, unit);
+    if (S >= 64)
+      splitk_reduce_warp_kernel<<<grid_for(32LL * M * N), 256, 0, s>>>(part, S, o.Mp * o.Nrp, (int)o.Nrp, M, N, alpha,
+                                                                      C, ldc, conj_out ? 1 : 0, unit);
+    else
+      splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, s>>>(part, S, o.Mp * o.Nrp, (int)o.Nrp, M, N,
+                                                                      alpha, C, ldc, conj_out ? 1 : 0, unit);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -784,21 +837,29 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
   }
   if (part_bytes(eff_splits(o.kb_total, choice.splits)) > part_room) return cudaErrorMemoryAllocation;
 
-  if (va && o.Mp * o.Krp < (1LL << 31) && o.Mp / 32 <= 65535 && va->rstr[va->nr - 1] == 1 &&
-      va->cstr[va->nc - 1] != 1)
-    pack_a_view_tr_kernel<PREC><<<dim3((unsigned)((o.Krp / 2 + 31) / 32), (unsigned)(o.Mp / 32)), dim3(32, 8), 0,
-                                  s>>>(*va, M, K, (int)o.Mp, (int)o.Krp, o.a0, o.a1, o.a2);
-  else if (va && o.Mp * o.Krp < (1LL << 31))
-    pack_a_view_kernel<PREC><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(*va, M, K, (int)o.Mp, (int)o.Krp, o.a0,
-                                                                         o.a1, o.a2);
-  else if (va)
+  // the A operand: a view, or a plain operand as a view (rows m, columns k of op(A))
+  TcView pa;
+  if (!va) {
+    const bool t = (opA & OP_T) != 0;
+    pa.p = A;
+    pa.conj = (opA & OP_CONJ) ? 1 : 0;
+    pa.nr = pa.nc = 1;
+    pa.rdim[0] = M;
+    pa.cdim[0] = K;
+    pa.rstr[0] = t ? 1 : lda;
+    pa.cstr[0] = t ? lda : 1;
+  }
+  const TcView& av = va ? *va : pa;
+  if (o.Mp / 32 <= 65535 && o.Mp * o.Krp < (1LL << 40)) {
+    const int row_contig = av.rstr[av.nr - 1] == 1 && av.cstr[av.nc - 1] != 1;
+    pack_a_tiled_kernel<PREC><<<dim3((unsigned)((o.Krp / 2 + 31) / 32), (unsigned)(o.Mp / 32)), dim3(32, 8), 0, s>>>(
+        av, M, K, (int)o.Mp, (int)o.Krp, row_contig, o.a0, o.a1, o.a2);
+  } else if (va) {
     return cudaErrorNotSupported;
-  else if (o.Mp * o.Krp < (1LL << 31))
-    pack_a_kernel<PREC, unsigned><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp, (int)o.Krp,
-                                                                         o.a0, o.a1, o.a2);
-  else
+  } else {
     pack_a_kernel<PREC, unsigned long long><<<grid_for(o.Mp * o.Krp / 2), 256, 0, s>>>(A, lda, opA, M, K, (int)o.Mp,
                                                                                    (int)o.Krp, o.a0, o.a1, o.a2);
+  }
   count_launch();
   cudaError_t e;
   if (pre) {
@@ -807,9 +868,10 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     o.b1 = pre->b1;
     o.b2 = pre->b2;
   } else if (vb) {
-    if (o.Nrp * o.Krp >= (1LL << 31)) return cudaErrorNotSupported;
-    pack_b_view_kernel<PREC><<<grid_for(o.Nrp * o.Krp / 4), 256, 0, s>>>(*vb, N, K, (int)o.Nrp, (int)o.Krp, o.b0,
-                                                                          o.b1, o.b2);
+    if (o.Nrp / 64 > 65535) return cudaErrorNotSupported;
+    const int row_contig = vb->rstr[vb->nr - 1] == 1 && vb->cstr[vb->nc - 1] != 1;
+    pack_b_tiled_kernel<PREC><<<dim3((unsigned)((o.Krp / 2 + 31) / 32), (unsigned)(o.Nrp / 64)), dim3(32, 8), 0, s>>>(
+        *vb, N, K, (int)o.Nrp, (int)o.Krp, row_contig, o.b0, o.b1, o.b2);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else if ((e = pack_b_any<PREC>(s, B, ldb, opB, N, K, o.Nrp, o.Krp, o.b0, o.b1, o.b2)) != cudaSuccess) {
