@@ -176,12 +176,13 @@ ipeps_status ipeps_ctm_reset_env(ipeps_ctm h);
 ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count);
 
 /* Implementation support (no paper counterpart).
- * Autotune the tensor-core products of this handle: one sweep is run with
- * every product shape timed under each candidate tile choice (128 x 128 or
- * 128 x 256 output tiles, K splits) and the fastest recorded; later moves use
- * the recorded choices (results change only by rounding).  The environment is
- * restored afterwards (a temporary device copy of it is allocated for the
- * call).  No-op for IPEPS_PREC_FP64.  ipeps_ctm_tuning_size: number of
+ * Autotune the tensor-core products of this handle: one sweep and one bond
+ * readout (the two-site RDMs) are run with every product shape timed under
+ * each candidate tile choice (128 x 128 or 128 x 256 output tiles, K splits)
+ * and the fastest recorded; later moves and readouts use the recorded choices
+ * (results change only by rounding).  The environment and the cuts' Jacobi
+ * starts are restored afterwards (a temporary device copy of them is
+ * allocated for the call).  No-op for IPEPS_PREC_FP64.  ipeps_ctm_tuning_size: number of
  * product shapes tuned.  Errors: ECUDA, ENOMEM-class CUDA failures, and any
  * status of the tuning sweep. */
 ipeps_status ipeps_ctm_autotune(ipeps_ctm h);
@@ -431,7 +432,8 @@ ipeps_status ipeps_zgemm(int prec, int M, int N, int K, const double* A, int opA
 
 /* As ipeps_zgemm for the tensor-core precisions, with the tile choice fixed
  * instead of the default: output tiles of 128 x bn real columns (bn = 128 or
- * 256) and `splits` K splits (reduced to the number of k-blocks, 128 bytes
+ * 256; 256 applies where 2N padded to 128 is a multiple of 256, else 128
+ * is used) and `splits` K splits (reduced to the number of k-blocks, 128 bytes
  * of K, 64 for BF16X6, if larger).  For unit tests of every choice the
  * batch autotuner can make (no paper counterpart).  Host buffers as
  * ipeps_zgemm.  Errors: EINVAL (prec FP64, bn not 128 or 256, splits < 1, or

@@ -1579,6 +1579,9 @@ extern "C" ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count) {
   return check_status(h);
 }
 
+static ipeps_status all_rdms(ipeps_ctm h, cplx* rh, cplx* rv);
+static ipeps_status rdm_buffers(ipeps_ctm h, cplx** rh, cplx** rv);
+
 extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
   if (h->opt.prec == IPEPS_PREC_FP64) return IPEPS_OK;  // no tensor-core products to tune
@@ -1609,6 +1612,16 @@ extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
   h->no_alt = true;  // cuts in sequence: timings unperturbed by the other lane
   ipeps_status st = reset_status(h);
   if (st == IPEPS_OK) st = ctm_enqueue_move(h, IPEPS_SWEEP);
+  if (st == IPEPS_OK) {
+    // the bond readout's products too (the environment is left as it is)
+    cplx *rh, *rv;
+    st = rdm_buffers(h, &rh, &rv);
+    const long long n2 = (long long)h->d * h->d * h->d * h->d * h->Lx * h->Ly;
+    const long long save = h->scratch_elems;
+    h->scratch_elems -= 2 * n2;
+    if (st == IPEPS_OK) st = all_rdms(h, rh, rv);
+    h->scratch_elems = save;
+  }
   if (st == IPEPS_OK) st = check_status(h);
   h->no_alt = false;
   tc_tuner_set_measuring(h->tuner, false);

@@ -29,7 +29,9 @@
 
 namespace {
 
-constexpr int BM = 128, NPAD = 256;  // N of every packed B operand padded to NPAD
+// N of every packed B operand padded to NPAD; 256-wide tiles only where the
+// padded N is a multiple of 256
+constexpr int BM = 128, NPAD = 128;
 constexpr int NTHREADS = 192;        // main kernel: producer warp, MMA warp, four epilogue warps
 constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2, PREC_BF16X6 = 3;
 
@@ -619,7 +621,8 @@ constexpr int NSM = 152;  // SMs of the part (one CTA of the main kernel per SM)
 
 // Default tile choice: 256-wide tiles; a product with fewer output tiles than
 // SMs splits K into at most two whole waves of CTAs.
-TcChoice heuristic(long long Mp, long long Nrp, int kb_total, int bn = 256) {
+TcChoice heuristic(long long Mp, long long Nrp, int kb_total) {
+  const int bn = Nrp % 256 == 0 ? 256 : 128;
   const long long tiles = (Mp / BM) * (Nrp / bn);
   int S = 1;
   if (tiles < NSM) {
@@ -726,7 +729,7 @@ cudaError_t launch_main(cudaStream_t s, const Operands& o, int S, int M, int N, 
 template <int PREC>
 cudaError_t launch_choice(cudaStream_t s, const Operands& o, TcChoice c, int M, int N, cplx alpha, cplx* C,
                           long long ldc, float* part, bool conj_out, int* timeouts, TcProbe* probe = nullptr) {
-  if (c.bn == 128)
+  if (c.bn == 128 || o.Nrp % 256 != 0)
     return launch_main<PREC, 128>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
   return launch_main<PREC, 256>(s, o, c.splits, M, N, alpha, C, ldc, part, conj_out, timeouts, probe);
 }
@@ -901,6 +904,7 @@ cudaError_t run(cudaStream_t s, int M, int N, int K, cplx alpha, const cplx* A, 
     ent.candidates = 1;
     static const int bns[2] = {128, 256};
     for (int bn : bns) {
+      if (o.Nrp % bn != 0) continue;
       // powers of two, and the counts that fill one to four whole waves
       const long long tiles = (o.Mp / BM) * (o.Nrp / bn);
       std::vector<int> splits = {1, 2, 4, 8, 16, 32};
