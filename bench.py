@@ -399,10 +399,11 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-# DRAM bytes per launch of the dominant class from one ncu capture (the mean of
-# the wide-product launches of profiles/bf16x6_path_D5_chi100_launches.md),
-# keyed by (precision, bound); absent where no capture of the current kernel exists
-TRAFFIC = {("bf16x6", "tensor"): 96.8e6}
+# DRAM bytes per launch of the dominant class from one ncu capture of the
+# current kernel (the mean of the wide-product launches in the profile summary
+# of the default workload), keyed by (precision, bound); absent where no
+# capture of the current kernel exists
+TRAFFIC = {("bf16x6", "tensor"): 93.6e6}
 
 
 def flops_per_move(D, chi, q=2, over=16):

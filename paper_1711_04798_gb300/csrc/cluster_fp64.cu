@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
   __shared__ double s_fro;
   __shared__ int s_rot, s_big;
   __shared__ double s_part[JC_THREADS / 64][2][4];  // [pair slot][half][al, be, Re g, Im g]
+  __shared__ double s_rp[JC_THREADS / 64][4];       // [pair slot][c, s, Re ph, Im ph]
+  __shared__ int s_rr[JC_THREADS / 64];             // [pair slot] rotated
   cplx* gl = sm;
   cplx* vl = sm + (long long)R * m;
   double f = 0.0;
@@ -232,40 +234,58 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
           if ((lane & 7) == 0) s_part[slot][half][lane >> 3] = tot;
         }
         __syncthreads();
-        double c = 1.0, sn = 0.0, phr = 1.0, phi = 0.0;
-        int rot = 0;
-        if (active && lane == 0) {
+        // the pair's rotation, by one thread of the pair (a lone FP64
+        // instruction occupies the sub-partition's FP64 unit as long as a
+        // full warp's).  c = 1/sqrt(1 + t^2) and the phase g/|g| in FP64, so
+        // that c^2 + s^2 = 1 and |ph| = 1 to FP64 rounding; the tangent t in
+        // FP32 for double-float rows (their angles only steer a convergence
+        // judged at 48 bits), in FP64 otherwise (an FP32 tangent raised the
+        // FP64 path's corner-spectrum noise from 2e-11 to 1e-10)
+        if (active && half == 0 && lane == 0) {
+          double c = 1.0, sn = 0.0, phr = 1.0, phi = 0.0;
+          int rot = 0;
           const double al = s_part[slot][0][0] + s_part[slot][1][0], be = s_part[slot][0][1] + s_part[slot][1][1];
           const double gr = s_part[slot][0][2] + s_part[slot][1][2], gim = s_part[slot][0][3] + s_part[slot][1][3];
           const double g2 = gr * gr + gim * gim;
           if (al > negligible && be > negligible && g2 > tol * tol * al * be) {
             const double ig = rsqrt(g2);
             const double zeta = 0.5 * (be - al) * ig;
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = rsqrt(1.0 + t * t);
+            double t;
+            if (!DF) {
+              t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            } else if (fabs(zeta) < 1e15) {
+              const float zf = (float)zeta;
+              t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f))));
+            } else {
+              t = 0.5 / zeta;  // t -> 1/(2 zeta)
+            }
+            c = rsqrt(fma(t, t, 1.0));
             sn = c * t;
             phr = gr * ig;
             phi = -gim * ig;
             rot = 1;
-            if (half == 0) {
-              atomicAdd(&s_rot, 1);
-              // a rotation with off-orthogonality or angle above 1e-8 keeps
-              // the sweep from being the last one
-              if (g2 > 1e-16 * al * be || fabs(sn) > 1e-8) s_big = 1;
-            }
+            atomicAdd(&s_rot, 1);
+            // a rotation with off-orthogonality or angle above 1e-8 keeps
+            // the sweep from being the last one
+            if (g2 > 1e-16 * al * be || fabs(sn) > 1e-8) s_big = 1;
           }
-          if (log && half == 0)
+          s_rp[slot][0] = c;
+          s_rp[slot][1] = sn;
+          s_rp[slot][2] = phr;
+          s_rp[slot][3] = phi;
+          s_rr[slot] = rot;
+          if (log)
             log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4_16a(c, sn, phr, phi)
                                                                    : make_double4_16a(2.0, 0.0, 0.0, 0.0);
-        } else if (!active && lane == 0 && half == 0 && log && p < npairs) {
-          log[((long long)sweep * rounds + r) * npairs + p] = make_double4_16a(2.0, 0.0, 0.0, 0.0);
+        } else if (!active && lane == 0 && half == 0) {
+          s_rr[slot] = 0;
+          if (log && p < npairs)
+            log[((long long)sweep * rounds + r) * npairs + p] = make_double4_16a(2.0, 0.0, 0.0, 0.0);
         }
-        __syncthreads();  // partial sums read before the next pair overwrites them
-        rot = __shfl_sync(0xffffffffu, rot, 0);
-        if (rot) {
-          c = __shfl_sync(0xffffffffu, c, 0);
-          sn = __shfl_sync(0xffffffffu, sn, 0);
-          const cplx ph = make_double2(__shfl_sync(0xffffffffu, phr, 0), __shfl_sync(0xffffffffu, phi, 0));
+        __syncthreads();  // the rotation is published; partial sums read before the next pair overwrites them
+        if (s_rr[slot]) {
+          const double c = s_rp[slot][0], sn = s_rp[slot][1];
+          const cplx ph = make_double2(s_rp[slot][2], s_rp[slot][3]);
           const cplx sq = make_double2(sn * ph.x, sn * ph.y), sp = make_double2(sn * ph.x, -sn * ph.y);
           if constexpr (DF) {
             // a' = c a - sq b, b' = c b + sp a (the form of jac_rotate)
@@ -354,32 +374,77 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
 // it is, in place), one CTA per column q (columns are independent: a CTA
 // reads and writes its own column only): thread p applies pair p of every
 // round, rounds in order, the column held in shared memory.  Rotation c = 2
-// marks a pair that was not rotated.
+// marks a pair that was not rotated.  DF (the precision form): the column in
+// double-float arithmetic on the FP32 pipe; the unitarity of V then holds to
+// about 2^-48 per rotation instead of 2^-53, some 1e-12 after thousands of
+// visits of a cut, far below the precision form's 1e-6 truncation.
+template <bool DF>
 __global__ void jacobi_replay_kernel(cplx* __restrict__ Vt, int n, const double4_16a* __restrict__ log,
                                      const int* __restrict__ sweeps_used, int warm) {
-  extern __shared__ cplx col[];
+  extern __shared__ cplx col[];  // DF: (Re hi, Re lo, Im hi, Im lo) per element, the same 16 bytes
+  float4* colf = (float4*)col;
   const int q = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    col[i] = warm ? Vt[(long long)i * n + q] : make_double2(i == q ? 1.0 : 0.0, 0.0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const cplx v = warm ? Vt[(long long)i * n + q] : make_double2(i == q ? 1.0 : 0.0, 0.0);
+    if constexpr (DF)
+      colf[i] = df_elem(v);
+    else
+      col[i] = v;
+  }
   __syncthreads();
   const int sweeps = *sweeps_used;
   const int np = (n + 1) & ~1;
   const int rounds = np - 1, npairs = np / 2;
-  for (int sw = 0; sw < sweeps; ++sw)
-    for (int r = 0; r < rounds; ++r) {
-      const int p = threadIdx.x;
-      if (p < npairs) {
-        const double4_16a rec = log[((long long)sw * rounds + r) * npairs + p];
-        if (rec.x < 1.5) {
-          int i, j;
-          pair_of(r, p, np, rounds, &i, &j);
-          const double c = rec.x, s = rec.y;
-          jac_rotate(col[i], col[j], c, make_double2(s * rec.z, s * rec.w), make_double2(s * rec.z, -s * rec.w));
-        }
+  const int p = threadIdx.x;
+  const long long steps = (long long)sweeps * rounds;
+  // the next round's record is loaded while this round's rotation runs
+  double4_16a next = make_double4_16a(2.0, 0.0, 0.0, 0.0);
+  if (p < npairs && steps > 0) next = log[p];
+  for (long long st = 0; st < steps; ++st) {
+    const int r = (int)(st % rounds);
+    const double4_16a rec = next;
+    if (p < npairs && st + 1 < steps) next = log[(st + 1) * npairs + p];
+    if (p < npairs && rec.x < 1.5) {
+      int i, j;
+      pair_of(r, p, np, rounds, &i, &j);
+      const double c = rec.x, s = rec.y;
+      if constexpr (DF) {
+        const df2 cd = df_of(c), qr = df_of(s * rec.z), qi = df_of(s * rec.w), pr = qr, pi = df_negate(qi);
+        const float4 x4 = colf[i], y4 = colf[j];
+        const df2 xr = {x4.x, x4.y}, xi = {x4.z, x4.w}, yr = {y4.x, y4.y}, yi = {y4.z, y4.w};
+        df2 ar = {0.f, 0.f}, ai = {0.f, 0.f}, br = {0.f, 0.f}, bi = {0.f, 0.f};
+        acc_mul(ar, cd, xr);
+        acc_mul(ar, df_negate(qr), yr);
+        acc_mul(ar, qi, yi);
+        acc_mul(ai, cd, xi);
+        acc_mul(ai, df_negate(qr), yi);
+        acc_mul(ai, df_negate(qi), yr);
+        acc_mul(br, cd, yr);
+        acc_mul(br, pr, xr);
+        acc_mul(br, df_negate(pi), xi);
+        acc_mul(bi, cd, yi);
+        acc_mul(bi, pr, xi);
+        acc_mul(bi, pi, xr);
+        ar = df_norm(ar);
+        ai = df_norm(ai);
+        br = df_norm(br);
+        bi = df_norm(bi);
+        colf[i] = make_float4(ar.h, ar.l, ai.h, ai.l);
+        colf[j] = make_float4(br.h, br.l, bi.h, bi.l);
+      } else {
+        jac_rotate(col[i], col[j], c, make_double2(s * rec.z, s * rec.w), make_double2(s * rec.z, -s * rec.w));
       }
-      __syncthreads();
     }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) Vt[(long long)i * n + q] = col[i];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if constexpr (DF) {
+      const float4 x4 = colf[i];
+      Vt[(long long)i * n + q] = make_double2(df_val({x4.x, x4.y}), df_val({x4.z, x4.w}));
+    } else {
+      Vt[(long long)i * n + q] = col[i];
+    }
+  }
 }
 
 // Right-looking Cholesky of the Hermitian n x n G (upper triangle used) with
@@ -438,13 +503,14 @@ __global__ void __launch_bounds__(CL_THREADS)
     for (int jj = 0; jj < nb; ++jj) {
       const int j = j0 + jj;
       cplx* pj = pan + (long long)jj * n;
-      // the pivot's root and reciprocal once (FP64 roots and divides are slow
-      // on this part)
+      // the pivot's reciprocal root once, r = d / sqrt(d) from it (FP64
+      // roots and divides are slow on this part, a lone thread's the more)
       if (threadIdx.x == 0) {
         const double d = pj[j].x;
         const bool keep = d > thr;
-        s_rjj[jj] = keep ? sqrt(d) : 0.0;
-        s_inv[jj] = keep ? 1.0 / s_rjj[jj] : 0.0;
+        const double inv = keep ? rsqrt(d) : 0.0;
+        s_inv[jj] = inv;
+        s_rjj[jj] = keep ? d * inv : 0.0;
       }
       __syncthreads();
       const double rjj = s_rjj[jj], inv = s_inv[jj];
@@ -597,8 +663,12 @@ cudaError_t jacobi_cluster(cudaStream_t s, cplx* G, int n, int m, long long ldg,
   if (e != cudaSuccess || !replay) return e;
   const int npairs = ((n + 1) & ~1) / 2;
   const int threads = (npairs + 31) / 32 * 32;
-  jacobi_replay_kernel<<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4_16a*)rotlog, sweeps_used,
-                                                            warm_v ? 1 : 0);
+  if (df)
+    jacobi_replay_kernel<true><<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4_16a*)rotlog, sweeps_used,
+                                                                  warm_v ? 1 : 0);
+  else
+    jacobi_replay_kernel<false><<<n, threads, n * sizeof(cplx), s>>>(Vt, n, (const double4_16a*)rotlog, sweeps_used,
+                                                                   warm_v ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }

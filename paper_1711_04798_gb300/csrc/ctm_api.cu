@@ -1339,8 +1339,9 @@ static ipeps_status orth_chol(ipeps_ctm h, cplx* Y, cplx* tmp, bool twice) {
 // rotated core is already nearly column-orthogonal and the sweeps converge
 // quadratically from there; the SVD found is the same (the Jacobi stops on
 // the same orthogonality test whatever its start).  The unitarity of the
-// accumulated V degrades like sqrt(rotations) x 1e-16, ~1e-13 after thousands
-// of visits, far below the 1e-6 truncation of the precision forms.
+// accumulated V degrades like sqrt(rotations) x 2^-48 (the rotations are
+// replayed in double-float arithmetic), ~1e-12 after thousands of visits, far
+// below the 1e-6 truncation of the precision forms.
 static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out, cplx* Vt) {
   const int k = h->k, K = h->K;
   const long long mark = h->scratch_top;
