@@ -163,6 +163,30 @@ def oracle_move_seconds(D, chi, n_moves=1):
     return (time.perf_counter() - t0) / n_moves
 
 
+def oracle_column_seconds_one_thread(D, chi):
+    """The oracle on one host thread (BLAS thread pools pinned to one in a
+    fresh interpreter): one column of a left move of the same workload (its
+    two cuts' corners and projectors and their absorption), half a move."""
+    code = (
+        "import sys, time\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import bench, oracle as O, synth\n"
+        f"D, chi = {int(D)}, {int(chi)}\n"
+        "w = bench.workload(D, chi, 0)\n"
+        "st = O.make_state(w['tensors'], w['pattern'], D, chi)\n"
+        "K, k = chi * D * D, chi + 16\n"
+        "opt = O.CTMOptions(chi=chi, proj='rsvd', omega=synth.omega(7, K, k))\n"
+        "t0 = time.perf_counter()\n"
+        "O.left_move(st, opt, columns=[0])\n"
+        "print(time.perf_counter() - t0)\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-400:])
+    return float(out.stdout.strip().splitlines()[-1])
+
+
 # ---------------------------------------------------------------------------
 # multi-rank bookkeeping (replicas: one independent instance per rank, no
 # collective on the data path; only the timing is reduced)
@@ -378,6 +402,10 @@ def run_ours(args, rank, world, local_rank):
         secs = oracle_move_seconds(args.D, args.chi)
         cpu = {"value": 1.0 / secs, "unit": "moves/s", "cores": host_cores(), "kind": "oracle",
                "sample": "one left move of the same workload (numpy/LAPACK FP64, all host cores)"}
+        col = oracle_column_seconds_one_thread(args.D, args.chi)
+        cpu["one_thread"] = {"value": 1.0 / (2.0 * col), "unit": "moves/s", "cores": 1,
+                             "sample": "one column of a left move (half a move) on one thread, "
+                                       "BLAS thread pools pinned to one"}
     line = {
         "metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
