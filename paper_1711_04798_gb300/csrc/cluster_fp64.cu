@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
   __shared__ int s_rot, s_big;
   __shared__ double s_part[JC_THREADS / 64][2][4];  // [pair slot][half][al, be, Re g, Im g]
   __shared__ double s_rp[JC_THREADS / 64][4];       // [pair slot][c, s, Re ph, Im ph]
+  __shared__ float s_rf[JC_THREADS / 64][6];        // DF: c, Re sq, Im sq as double-float pairs
   __shared__ int s_rr[JC_THREADS / 64];             // [pair slot] rotated
   cplx* gl = sm;
   cplx* vl = sm + (long long)R * m;
@@ -274,6 +275,16 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
           s_rp[slot][2] = phr;
           s_rp[slot][3] = phi;
           s_rr[slot] = rot;
+          if (DF) {
+            // the rotation's double-float factors once here, not in every thread
+            const df2 cd = df_of(c), qr = df_of(sn * phr), qi = df_of(sn * phi);
+            s_rf[slot][0] = cd.h;
+            s_rf[slot][1] = cd.l;
+            s_rf[slot][2] = qr.h;
+            s_rf[slot][3] = qr.l;
+            s_rf[slot][4] = qi.h;
+            s_rf[slot][5] = qi.l;
+          }
           if (log)
             log[((long long)sweep * rounds + r) * npairs + p] = rot ? make_double4_16a(c, sn, phr, phi)
                                                                    : make_double4_16a(2.0, 0.0, 0.0, 0.0);
@@ -284,12 +295,10 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         }
         __syncthreads();  // the rotation is published; partial sums read before the next pair overwrites them
         if (s_rr[slot]) {
-          const double c = s_rp[slot][0], sn = s_rp[slot][1];
-          const cplx ph = make_double2(s_rp[slot][2], s_rp[slot][3]);
-          const cplx sq = make_double2(sn * ph.x, sn * ph.y), sp = make_double2(sn * ph.x, -sn * ph.y);
           if constexpr (DF) {
-            // a' = c a - sq b, b' = c b + sp a (the form of jac_rotate)
-            const df2 cd = df_of(c), qr = df_of(sq.x), qi = df_of(sq.y), pr = df_of(sp.x), pi = df_of(sp.y);
+            // a' = c a - sq b, b' = c b + sp a (the form of jac_rotate), sp = conj(sq)
+            const df2 cd = {s_rf[slot][0], s_rf[slot][1]}, qr = {s_rf[slot][2], s_rf[slot][3]},
+                      qi = {s_rf[slot][4], s_rf[slot][5]}, pr = qr, pi = df_negate(qi);
             float4* fi = (float4*)gi;
             float4* fj = (float4*)gj;
             for (int q = lane + 32 * half; q < m; q += 64) {
@@ -316,12 +325,15 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
               fj[q] = make_float4(br.h, br.l, bi.h, bi.l);
             }
           } else {
+            const double c = s_rp[slot][0], sn = s_rp[slot][1];
+            const cplx ph = make_double2(s_rp[slot][2], s_rp[slot][3]);
+            const cplx sq = make_double2(sn * ph.x, sn * ph.y), sp = make_double2(sn * ph.x, -sn * ph.y);
             for (int q = lane + 32 * half; q < m; q += 64) jac_rotate(gi[q], gj[q], c, sq, sp);
-          }
-          if (Vt) {
-            cplx* vi = vrow(i);
-            cplx* vj = vrow(j);
-            for (int q = lane + 32 * half; q < n; q += 64) jac_rotate(vi[q], vj[q], c, sq, sp);
+            if (Vt) {
+              cplx* vi = vrow(i);
+              cplx* vj = vrow(j);
+              for (int q = lane + 32 * half; q < n; q += 64) jac_rotate(vi[q], vj[q], c, sq, sp);
+            }
           }
         }
       }
@@ -464,8 +476,9 @@ __global__ void __launch_bounds__(CL_THREADS)
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
   const int R = (n + cs - 1) / cs;
-  extern __shared__ cplx sm[];  // [R x n] own rows of W, then [CH_NB x n] the block (rows of W, then of R)
+  extern __shared__ cplx sm[];  // [R x n] own rows of W, then [CH_NB x n] the block's rows of W, then of R
   cplx* pan = sm + (long long)R * n;
+  cplx* rpan = pan + (long long)CH_NB * n;
   __shared__ double s_max, s_rjj[CH_NB], s_inv[CH_NB];
   for (int l = 0; l < R; ++l) {
     const int i = l * cs + rank;
@@ -515,8 +528,10 @@ __global__ void __launch_bounds__(CL_THREADS)
       __syncthreads();
       const double rjj = s_rjj[jj], inv = s_inv[jj];
       const bool keep = rjj > 0.0;
-      // row j of R on the CTA's columns (zero left of the diagonal, and for a
-      // dropped direction)
+      // row j of R on the CTA's columns into its own buffer (zero left of the
+      // diagonal, and for a dropped direction), and in the same phase the
+      // block's rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i, with
+      // R[j,.] = W[j,.] / r formed from row j of W, which this phase only reads
       for (int c = threadIdx.x; c < ncol; c += CL_THREADS) {
         const int l = col(c);
         cplx v = make_double2(0.0, 0.0);
@@ -524,15 +539,13 @@ __global__ void __launch_bounds__(CL_THREADS)
           const cplx g = pj[l];
           v = l == j ? make_double2(rjj, 0.0) : make_double2(g.x * inv, g.y * inv);
         }
-        pj[l] = v;
+        rpan[(long long)jj * n + l] = v;
       }
-      __syncthreads();
       if (keep) {
-        // the block's rows i > j: W[i,l] -= conj(R[j,i]) R[j,l] for l >= i
         for (int e = threadIdx.x; e < (nb - 1 - jj) * ncol; e += CL_THREADS) {
           const int i = j + 1 + e / ncol, l = col(e % ncol);
           if (l < i) continue;
-          const cplx a = pj[i], b = pj[l];
+          const cplx a = make_double2(pj[i].x * inv, pj[i].y * inv), b = make_double2(pj[l].x * inv, pj[l].y * inv);
           cplx* wi = pan + (long long)(i - j0) * n;
           wi[l].x -= a.x * b.x + a.y * b.y;
           wi[l].y -= a.x * b.y - a.y * b.x;
@@ -545,7 +558,7 @@ __global__ void __launch_bounds__(CL_THREADS)
     for (int e = threadIdx.x; e < nb * (n - jn); e += CL_THREADS) {
       const int jj = e / (n - jn), l = jn + e % (n - jn);
       const int o = l % cs;
-      if (o != rank) pan[(long long)jj * n + l] = cl.map_shared_rank(pan, o)[(long long)jj * n + l];
+      if (o != rank) rpan[(long long)jj * n + l] = cl.map_shared_rank(rpan, o)[(long long)jj * n + l];
     }
     __syncthreads();
     // the owners store their rows of R
@@ -553,7 +566,7 @@ __global__ void __launch_bounds__(CL_THREADS)
       const int j = j0 + jj;
       if (j % cs != rank) continue;
       for (int l = threadIdx.x; l < n; l += CL_THREADS)
-        Rout[(long long)j * n + l] = l < j0 ? make_double2(0.0, 0.0) : pan[(long long)jj * n + l];
+        Rout[(long long)j * n + l] = l < j0 ? make_double2(0.0, 0.0) : rpan[(long long)jj * n + l];
     }
     // own rows below the block
     for (int l0 = 0; l0 < R; ++l0) {
@@ -565,14 +578,14 @@ __global__ void __launch_bounds__(CL_THREADS)
         cplx v = wi[l];
         for (int jj = 0; jj < nb; ++jj) {
           if (s_rjj[jj] == 0.0) continue;  // dropped direction: no update
-          const cplx a = pan[(long long)jj * n + i], b = pan[(long long)jj * n + l];
+          const cplx a = rpan[(long long)jj * n + i], b = rpan[(long long)jj * n + l];
           v.x -= a.x * b.x + a.y * b.y;
           v.y -= a.x * b.y - a.y * b.x;
         }
         wi[l] = v;
       }
     }
-    cl.sync();  // rows updated before they are read as the next block; gathers done before pan is rewritten
+    cl.sync();  // rows updated before they are read as the next block; gathers done before rpan is rewritten
   }
 }
 
@@ -677,14 +690,14 @@ bool chol_cluster_fits(int n) {
   if (n < 32) return false;
   if (cluster_init() != cudaSuccess) return false;
   const long long R = (n + g_csize - 1) / g_csize;
-  return (R + CH_NB) * n * (long long)sizeof(cplx) <= CL_SMEM;
+  return (R + 2 * CH_NB) * n * (long long)sizeof(cplx) <= CL_SMEM;
 }
 
 cudaError_t chol_cluster(cudaStream_t s, const cplx* G, cplx* R, int n, double tol) {
   cudaError_t e;
   if ((e = cluster_init()) != cudaSuccess) return e;
   const long long rows = (n + g_csize - 1) / g_csize;
-  const size_t smem = (size_t)((rows + CH_NB) * n * sizeof(cplx));
+  const size_t smem = (size_t)((rows + 2 * CH_NB) * n * sizeof(cplx));
   void* args[] = {&G, &R, &n, &tol};
   e = launch_cluster((const void*)chol_cluster_kernel, args, smem, s);
   count_launch();
