@@ -116,6 +116,12 @@ typedef struct {
                                        Jacobi), in SM clock cycles; after it the
                                        wait gives up and the call reports
                                        ETIMEOUT.  <= 0: 4e9 (about 2 s)        */
+  int corners;                      /* projector of a cut (Sec. II.C): 4 (or 0)
+                                       the ring of the four enlarged corners of
+                                       the plaquette, X = (Q1 Q2)^T (Q4 Q3^T); 2
+                                       the two corners on the cut's side,
+                                       X = Q1^T Q4 (about a third of the work);
+                                       else EINVAL                             */
 } ipeps_options;
 
 /* Fill *opt (caller-owned) with the defaults: prec FP64, oversample 16,

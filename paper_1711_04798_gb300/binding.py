@@ -42,7 +42,7 @@ class Options(C.Structure):
                 ("rsvd_power", C.c_int), ("svd_cutoff", C.c_double), ("orth_tol", C.c_double),
                 ("omega_seed", C.c_uint64), ("jacobi_max_sweeps", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("wait_cycles", C.c_longlong)]
+                ("wait_cycles", C.c_longlong), ("corners", C.c_int)]
 
 
 class CTMError(RuntimeError):
@@ -179,7 +179,7 @@ def _make_cell(tensors, pattern, bra=None):
 
 
 def _make_options(lib, chi, prec="fp64", oversample=16, power=2, cutoff=0.0, orth_tol=1e-14,
-                  omega_seed=7, jacobi_max_sweeps=40, stream=None, workspace=None, wait_cycles=0):
+                  omega_seed=7, jacobi_max_sweeps=40, stream=None, workspace=None, wait_cycles=0, corners=4):
     opt = Options()
     lib.ipeps_default_options(C.byref(opt))
     opt.chi = chi
@@ -189,6 +189,7 @@ def _make_options(lib, chi, prec="fp64", oversample=16, power=2, cutoff=0.0, ort
     opt.omega_seed = omega_seed
     opt.jacobi_max_sweeps = jacobi_max_sweeps
     opt.wait_cycles = wait_cycles
+    opt.corners = corners
     opt.stream = stream
     if workspace is not None:
         opt.workspace = C.c_void_p(workspace[0])
@@ -206,7 +207,7 @@ class CTM:
 
     def __init__(self, tensors, pattern, chi, prec="fp64", bra=None, oversample=16, power=2,
                  cutoff=0.0, orth_tol=1e-14, omega_seed=7, jacobi_max_sweeps=40, stream=None,
-                 workspace=None, wait_cycles=0):
+                 workspace=None, wait_cycles=0, corners=4):
         lib = load_library()
         self.lib = lib
         self._borrowed = False
@@ -214,7 +215,7 @@ class CTM:
         self._keep, self._keep_bra, self._ptrs, self._bptrs, self._dtype, self._legs = keep
         self._set_meta(tensors, pattern, chi)
         opt = _make_options(lib, chi, prec, oversample, power, cutoff, orth_tol, omega_seed,
-                            jacobi_max_sweeps, stream, workspace, wait_cycles)
+                            jacobi_max_sweeps, stream, workspace, wait_cycles, corners)
         self._cell, self._opt = cell, opt
         h = C.c_void_p()
         _check(lib.ipeps_ctm_create(C.byref(cell), C.byref(opt), C.byref(h)))

@@ -776,6 +776,7 @@ extern "C" void ipeps_default_options(ipeps_options* o) {
   o->orth_tol = 1e-14;
   o->omega_seed = 7;
   o->jacobi_max_sweeps = 40;
+  o->corners = 4;
 }
 
 static ipeps_status validate(const ipeps_cell* c, const ipeps_options* o) {
@@ -797,6 +798,7 @@ static ipeps_status validate(const ipeps_cell* c, const ipeps_options* o) {
   if (o->chi + o->rsvd_oversample > 1024) return fail(IPEPS_EINVAL, "chi + oversample > 1024");
   if (o->prec < IPEPS_PREC_FP64 || o->prec > IPEPS_PREC_BF16X6) return fail(IPEPS_EINVAL, "bad prec");
   if (o->jacobi_max_sweeps < 1) return fail(IPEPS_EINVAL, "jacobi_max_sweeps >= 1");
+  if (o->corners != 0 && o->corners != 2 && o->corners != 4) return fail(IPEPS_EINVAL, "corners must be 2 or 4");
   return IPEPS_OK;
 }
 
@@ -1154,6 +1156,9 @@ extern "C" ipeps_status ipeps_ctm_reset_env(ipeps_ctm h) {
 // Enlarged corners of the plaquette with upper-left site (x,y) in frame f:
 //   Q1[(d_T4,d_a),(r_T1,r_a)]  Q2[(l_T1,l_a),(d_T2,d_a)]
 //   Q3[(u_T2,u_a),(l_T3,l_a)]  Q4[(u_T4,u_a),(r_T3,r_a)]
+// the two-corner projector (ipeps_options.corners = 2): X = Q1^T Q4
+static bool two_corners(ipeps_ctm h) { return h->opt.corners == 2; }
+
 static ipeps_status enlarged_corners(ipeps_ctm h, int f, int x, int y) {
   const int c = h->chi, D2 = h->D2;
   const long long entry = h->scratch_top;
@@ -1169,6 +1174,7 @@ static ipeps_status enlarged_corners(ipeps_ctm h, int f, int x, int y) {
   CKS(contract(h, "decr,ceDR->dDrR", tv(w2, {c, D2, D2, c}), false,
                tv(site_a(h, f, x, y), {D2, D2, D2, D2}), false, tv(h->Q[0], {c, D2, c, D2})));
   h->scratch_top = mark;
+  if (two_corners(h)) goto lower_left;  // Q2 and Q3 are not part of the two-corner ring
   // Q2 = ((T1 C2) T2) a
   CKS(contract(h, "Ltg,gh->Lth", tv(envT(h, f, 0, x + 1, y), {c, D2, c}), false,
                tv(envC(h, f, 1, x + 1, y), {c, c}), false, tv(w1, {c, D2, c})));
@@ -1185,6 +1191,7 @@ static ipeps_status enlarged_corners(ipeps_ctm h, int f, int x, int y) {
   CKS(contract(h, "UmtL,uKtm->UuLK", tv(w2, {c, D2, D2, c}), false,
                tv(site_a(h, f, x + 1, y + 1), {D2, D2, D2, D2}), false, tv(h->Q[2], {c, D2, c, D2})));
   h->scratch_top = mark;
+lower_left:
   // Q4 = ((C4 T4) T3) a
   CKS(contract(h, "gh,hmU->gmU", tv(envC(h, f, 3, x, y + 1), {c, c}), false,
                tv(envT(h, f, 3, x, y + 1), {c, D2, c}), false, tv(w1, {c, D2, c})));
@@ -1220,17 +1227,30 @@ static ipeps_status thin_mul_packed(ipeps_ctm h, const cplx* in, int opin, cplx*
 }
 
 static ipeps_status pack_corners(ipeps_ctm h) {
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 4; ++q) {
+    if (two_corners(h) && (q == 1 || q == 2)) continue;
     for (int v = 0; v < 2; ++v)
       CK(tc_pack_b(h->stream, (int)h->opt.prec, h->Q[q], h->K, v ? OP_T : OP_N, h->K, h->K, h->Qpmem[q][v],
                    &h->Qp[q][v]));
+  }
   return IPEPS_OK;
 }
 
 static bool packed_path(ipeps_ctm h) { return h->opt.prec != IPEPS_PREC_FP64; }
 
 // Yt = In * Q3 * Q4^T * Q1 * Q2      (the transpose of X * In^T)
+// two corners: Yt = In * Q4^T * Q1
 static ipeps_status apply_XT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
+  if (two_corners(h)) {
+    if (packed_path(h)) {
+      CKS(thin_mul_packed(h, in, OP_N, h->thin[2], 3, 1, rows, false));
+      CKS(thin_mul_packed(h, h->thin[2], OP_N, out, 0, 0, rows, false));
+    } else {
+      CKS(thin_mul(h, in, OP_N, h->thin[2], h->Q[3], OP_T, rows));
+      CKS(thin_mul(h, h->thin[2], OP_N, out, h->Q[0], OP_N, rows));
+    }
+    return IPEPS_OK;
+  }
   if (packed_path(h)) {
     CKS(thin_mul_packed(h, in, OP_N, h->thin[2], 2, 0, rows, false));
     CKS(thin_mul_packed(h, h->thin[2], OP_N, h->thin[3], 3, 1, rows, false));
@@ -1246,7 +1266,18 @@ static ipeps_status apply_XT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
 }
 // Zt = In * Q2^H * Q1^H * conj(Q4) * Q3^H   (the transpose of X^H * In^T)
 //    = conj( conj(In) * Q2^T * Q1^T * Q4 * Q3^T )
+// two corners: Zt = In * Q1^H * conj(Q4) = conj( conj(In) * Q1^T * Q4 )
 static ipeps_status apply_XHT(ipeps_ctm h, const cplx* in, cplx* out, int rows) {
+  if (two_corners(h)) {
+    if (packed_path(h)) {
+      CKS(thin_mul_packed(h, in, OP_C, h->thin[2], 0, 1, rows, false));
+      CKS(thin_mul_packed(h, h->thin[2], OP_N, out, 3, 0, rows, true));
+    } else {
+      CKS(thin_mul(h, in, OP_N, h->thin[2], h->Q[0], OP_H, rows));
+      CKS(thin_mul(h, h->thin[2], OP_N, out, h->Q[3], OP_C, rows));
+    }
+    return IPEPS_OK;
+  }
   if (packed_path(h)) {
     CKS(thin_mul_packed(h, in, OP_C, h->thin[2], 1, 1, rows, false));
     CKS(thin_mul_packed(h, h->thin[2], OP_N, h->thin[3], 0, 1, rows, false));
@@ -1420,7 +1451,13 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   CK(gather_rows(h->stream, Vt, k, h->Gsel, k, h->perm, h->sigma, chi, k, false));
   CKS(gemm_dispatch(h, chi, K, k, h->Gsel, k, OP_N, Qt, K, OP_N, Ut_chi, K, ONE));
   // P^T = S^-1/2 V^T Q3 Q4^T ;  Ptil = S^-1/2 U^H Q2^T Q1^T
-  if (!fp64) {
+  // (two corners: P^T = S^-1/2 V^T Q4^T ;  Ptil = S^-1/2 U^H Q1^T)
+  if (two_corners(h)) {
+    if (!fp64)
+      CKS(thin_mul_packed(h, Vt_chi, OP_N, PT, 3, 1, chi, false));
+    else
+      CKS(thin_mul(h, Vt_chi, OP_N, PT, h->Q[3], OP_T, chi));
+  } else if (!fp64) {
     CKS(thin_mul_packed(h, Vt_chi, OP_N, tmp, 2, 0, chi, false));
     CKS(thin_mul_packed(h, tmp, OP_N, PT, 3, 1, chi, false));
   } else {
@@ -1428,7 +1465,12 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
     CKS(thin_mul(h, tmp, OP_N, PT, h->Q[3], OP_T, chi));
   }
   CK(scale_rows_isqrt(h->stream, PT, chi, K, K, h->s_sel));
-  if (!fp64) {
+  if (two_corners(h)) {
+    if (!fp64)
+      CKS(thin_mul_packed(h, Ut_chi, OP_C, Ptil, 0, 1, chi, false));
+    else
+      CKS(thin_mul(h, Ut_chi, OP_C, Ptil, h->Q[0], OP_T, chi));
+  } else if (!fp64) {
     CKS(thin_mul_packed(h, Ut_chi, OP_C, tmp, 1, 1, chi, false));
     CKS(thin_mul_packed(h, tmp, OP_N, Ptil, 0, 1, chi, false));
   } else {

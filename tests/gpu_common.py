@@ -25,7 +25,7 @@ def oracle_options(chi, D, proj="svd", **kw):
     K, k = chi * D * D, chi + o["oversample"]
     omega = synth.omega(o["omega_seed"], K, k) if proj == "rsvd" else None
     return O.CTMOptions(chi=chi, proj=proj, oversample=o["oversample"], power=o["power"],
-                        cutoff=o["cutoff"], orth_tol=o["orth_tol"], omega=omega)
+                        cutoff=o["cutoff"], orth_tol=o["orth_tol"], omega=omega, corners=o.get("corners", 4))
 
 
 def gpu_ctm(tensors, pattern, chi, **kw):

@@ -100,6 +100,7 @@ _RULES = [
     ("opt", "rsvd_oversample", -1, b"rsvd"), ("opt", "rsvd_power", -1, b"rsvd"),
     ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 4, b"prec"),
     ("opt", "prec", -1, b"prec"), ("opt", "jacobi_max_sweeps", 0, b"jacobi"),
+    ("opt", "corners", 3, b"corners"), ("opt", "corners", -4, b"corners"),
 ]
 
 

@@ -78,3 +78,28 @@ def test_full_size_range_finder_gap_from_stored_records():
         gap_s = spectra_err(b["spectra_sweep1"], a["spectra_sweep1"])
     print(f"D5 chi100 one sweep: rsvd vs svd  dE/E {gap_e:.1e}  rdm {gap_r:.1e}  spectra {gap_s:.1e}")
     assert gap_e < GAP and gap_r < GAP and gap_s < GAP
+
+
+@pytest.mark.parametrize("D,chi,seed,sweeps,spec_gap", [(2, 16, 0, 6, GAP), (3, 18, 2, 3, 1e-7)])
+def test_two_corner_route_gap(D, chi, seed, sweeps, spec_gap):
+    """The two-corner projector (X = Q1^T Q4, the option of the GPU parity
+    test of that route): energies and RDMs of the range finder stay within
+    1e-10 of the exact SVD; its corner spectra do at D = 2, chi = 16 but not
+    at D = 3, chi = 18, where the two-corner ring's singular values decay more
+    slowly and the range finder (k = chi + 16, q = 2) sits 4e-8 away."""
+    w = synth.workload("product_noise", seed=seed, D=D, chi=chi)
+    res = {}
+    for proj in ("svd", "rsvd"):
+        st = O.make_state(w["tensors"], w["pattern"], D, chi)
+        opt = oracle_options(chi, D, proj=proj, corners=2)
+        for _ in range(sweeps):
+            st = O.sweep(st, opt)
+        assert not opt.ties
+        rd = O.bond_rdms(st, w["tensors"], w["pattern"])
+        res[proj] = (O.energy_per_spin(rd, w["J"], 2, 2), rd, O.corner_spectra(st))
+    (ea, ra, sa), (eb, rb, sb) = res["svd"], res["rsvd"]
+    gap_e = abs(ea - eb) / abs(ea)
+    gap_r = max(rel_err(rb[k], ra[k]) for k in ("h", "v"))
+    gap_s = spectra_err(sb, sa)
+    print(f"two corners D{D} chi{chi}: rsvd vs svd  dE/E {gap_e:.1e}  rdm {gap_r:.1e}  spectra {gap_s:.1e}")
+    assert gap_e < GAP and gap_r < GAP and gap_s < spec_gap
