@@ -347,6 +347,22 @@ def run_ours(args, rank, world, local_rank):
     ms_max = max_over_ranks(ms, dist)
     value = job_value(args.steps * MOVES_PER_STEP, world, ms_max * 1e-3)
 
+    # the step's parts in a separate pass of the same handle (CUDA events on
+    # the stream): the sweep of four moves and the bond readout with the energy
+    def part_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    breakdown = {"sweep_ms": part_ms(lambda: g.sweep(1)), "readout_ms": part_ms(lambda: g.energy(J)),
+                 "rebuild_ms": part_ms(g.rebuild)}
+    breakdown["sweep_moves_per_s"] = MOVES_PER_STEP / (breakdown["sweep_ms"] * 1e-3)
+
     # end to end through the public API: host tensors in, energy out, every step
     host_tensors = w["tensors"]
     h2d = sum(a.nbytes for a in host_tensors)
@@ -418,6 +434,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "cpu_baseline": cpu, "fp64_comparison": fp64_cmp,
         "e2e": {"value": e2e_value, "unit": "moves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
         "gpu_launches": launches, "host_graph_launches_per_step": MOVES_PER_STEP // 4,
+        "step_breakdown": breakdown,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
