@@ -65,9 +65,15 @@ typedef enum {
   IPEPS_PREC_FP64 = 0,   /* complex FP64 on the CUDA cores                    */
   IPEPS_PREC_TF32 = 1,   /* tcgen05 TF32 tensor cores, FP32 accumulate        */
   IPEPS_PREC_BF16X3 = 2, /* tcgen05 split-BF16 (hi*hi + hi*lo + lo*hi), FP32  */
-  IPEPS_PREC_BF16X6 = 3  /* tcgen05 split-BF16 in three parts p0+p1+p2 (24    *
+  IPEPS_PREC_BF16X6 = 3, /* tcgen05 split-BF16 in three parts p0+p1+p2 (24   *
                           * significand bits), the six products p_i q_j with  *
                           * i + j <= 2, FP32 accumulate: FP32-class products  */
+  IPEPS_PREC_FP64TC = 4  /* FP64-accurate products on tcgen05: each operand  *
+                          * row split exactly into seven base-256 digit       *
+                          * planes (BF16), the 28 plane pairs of weight <= 6  *
+                          * summed exactly, one rounding to FP64 (after       *
+                          * Ozaki, Ogita, Oishi and Rump 2012); every other   *
+                          * step exactly as IPEPS_PREC_FP64                   */
 } ipeps_prec;
 
 typedef enum {
@@ -103,8 +109,8 @@ typedef struct {
   int rsvd_oversample;              /* projector range finder width k = chi + p    */
   int rsvd_power;                   /* subspace iterations q                       */
   double svd_cutoff;                /* keep singular values > cutoff * largest;
-                                       <= 0: 1e-8 (FP64), 1e-6 (BF16X3, BF16X6),
-                                       1e-5 (TF32) */
+                                       <= 0: 1e-8 (FP64, FP64TC), 1e-6 (BF16X3,
+                                       BF16X6), 1e-5 (TF32)                    */
   double orth_tol;                  /* range-finder basis: drop s < tol * largest  */
   uint64_t omega_seed;              /* SplitMix64 stream of the test matrix        */
   int jacobi_max_sweeps;            /* iteration budget of every Jacobi SVD        */
@@ -424,10 +430,9 @@ void ipeps_ctm_destroy(ipeps_ctm h);
  * (row-major; op 0 = N, 1 = T, 2 = conj, 3 = conj-transpose, so that opA(A)
  * is M x K and A is stored M x K for op 0/2 and K x M for op 1/3).  prec as
  * ipeps_prec: FP64 CUDA-core kernel or the tcgen05 TF32 / split-BF16x3 /
- * split-BF16x6 kernel, or 4: the FP64-accurate tensor-core product of the
- * precision form's projector step (exact base-256 digit splitting of both
- * operands, digit-plane products summed exactly; the one rounding to FP64 is
- * the last)
+ * split-BF16x6 kernel, or IPEPS_PREC_FP64TC: the FP64-accurate tensor-core
+ * product (exact base-256 digit splitting of both operands, digit-plane
+ * products summed exactly; the one rounding to FP64 is the last)
  * (with its operand packing and split-K reduction).  Allocates and frees its
  * own device buffers; synchronises the device.  A, B, C are caller-owned host
  * arrays.  Errors: EINVAL (M, N or K <= 0, NULL pointer, prec or op out of

@@ -10,7 +10,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libipeps_ctm.so")
 
-PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3}
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 2, "bf16x6": 3, "fp64tc": 4}
 DIRS = {"L": 0, "U": 1, "R": 2, "D": 3, "sweep": 4}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT",
           6: "ENUMERIC", 7: "EUNSUPPORTED", 8: "EIO"}

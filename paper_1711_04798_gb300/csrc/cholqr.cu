@@ -98,7 +98,30 @@ __global__ void tri_inv_kernel(const cplx* __restrict__ R, cplx* __restrict__ Ri
   }
 }
 
+// G += coef * tr(G) I (one CTA): the shift of shifted CholeskyQR (Fukaya,
+// Kannan, Nakatsukasa, Yamamoto and Yanagisawa 2020), with the trace of the
+// Gram (the squared Frobenius norm of Y) bounding the squared 2-norm.
+__global__ void __launch_bounds__(256) gram_shift_kernel(cplx* __restrict__ G, int n, double coef) {
+  __shared__ double s_part[8];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += G[(long long)i * n + i].x;
+  t = warp_sum_d(t);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = t;
+  __syncthreads();
+  double tr = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) tr += s_part[w];
+  const double shift = coef * tr;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) G[(long long)i * n + i].x += shift;
+}
+
 }  // namespace
+
+cudaError_t gram_shift(cudaStream_t s, cplx* G, int n, double coef) {
+  gram_shift_kernel<<<1, 256, 0, s>>>(G, n, coef);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n, double tol) {
   cudaError_t e;

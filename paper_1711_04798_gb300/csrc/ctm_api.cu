@@ -283,6 +283,13 @@ static cplx* scratch_alloc(ipeps_ctm h, long long n) {
   return p;
 }
 
+// the precision forms whose contraction products run on the BF16/TF32 tensor
+// cores (FP32 accumulation); IPEPS_PREC_FP64TC runs every other step as the
+// FP64 path does and only its products on the tensor cores, FP64-accurate
+static bool tc_form(int prec) {
+  return prec == IPEPS_PREC_TF32 || prec == IPEPS_PREC_BF16X3 || prec == IPEPS_PREC_BF16X6;
+}
+
 // sizes of everything a handle carves from its memory
 struct Sizes {
   long long tens, a, C, T, Q, thin, proj, scratch;
@@ -305,7 +312,10 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   const long long rdm = 6 * (long long)chi * chi * D2 * D2 * d + 3 * (long long)chi * chi * D2 * d * d;
   s.scratch = std::max(6 * s.Q, rdm) + (1 << 16);
   // packed tensor-core operands (padded to 128 x 256 tiles) and split-K partials
-  if (prec != IPEPS_PREC_FP64) s.scratch = s.scratch * (prec == IPEPS_PREC_BF16X6 ? 2 : 3) / 2 + (1 << 22);
+  if (tc_form(prec)) s.scratch = s.scratch * (prec == IPEPS_PREC_BF16X6 ? 2 : 3) / 2 + (1 << 22);
+  // digit planes of the FP64-accurate products: 28 B per complex element of
+  // the A side, 56 B of the B side, and the exact split partials
+  if (prec == IPEPS_PREC_FP64TC) s.scratch = s.scratch * 3 + (1 << 22);
   size_t tot = 0;
   auto add = [&](long long n, size_t el) { tot += align_up((size_t)n * el); };
   for (int i = 0; i < 2 * 4 * ntens; ++i) add(s.tens, 16);
@@ -314,7 +324,7 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   for (int i = 0; i < 4; ++i) add(s.C, 16);
   for (int i = 0; i < 2; ++i) add(s.T, 16);
   for (int i = 0; i < 4; ++i) add(s.Q, 16);
-  if (prec != IPEPS_PREC_FP64)
+  if (tc_form(prec))
     for (int i = 0; i < 8; ++i) tot += align_up(tc_packed_bytes(prec, (int)K, (int)K));
   add(s.thin, 16);
   for (int i = 0; i < 4; ++i) add(s.thin, 16);
@@ -333,7 +343,7 @@ static Sizes plan_sizes(int Lx, int Ly, int d, int D, int chi, int k, int ntens,
   add(s.scratch, 16);
   // second projector lane (the other cut of a column runs concurrently)
   for (int i = 0; i < 4; ++i) add(s.Q, 16);
-  if (prec != IPEPS_PREC_FP64)
+  if (tc_form(prec))
     for (int i = 0; i < 8; ++i) tot += align_up(tc_packed_bytes(prec, (int)K, (int)K));
   for (int i = 0; i < 4; ++i) add(s.thin, 16);
   add((long long)k * k, 16);
@@ -420,8 +430,16 @@ static ipeps_status gemm_dispatch(ipeps_ctm h, int M, int N, int K, const cplx* 
 static ipeps_status gemm_dispatch_raw(ipeps_ctm h, int M, int N, int K, const cplx* A, long long lda,
                                       int opA, const cplx* B, long long ldb, int opB, cplx* C,
                                       long long ldc, cplx alpha) {
+  // FP64-accurate tensor-core products (unit alpha, the digit planes within
+  // the scratch left); smaller products and the rest on the FP64 CUDA cores
+  if (h->opt.prec == IPEPS_PREC_FP64TC && M >= 64 && N >= 32 && K >= 16 && alpha.x == 1.0 && alpha.y == 0.0 &&
+      oz_work_bytes(M, N, K) <= (size_t)(h->scratch_elems - h->scratch_top) * sizeof(cplx)) {
+    CK(oz_zgemm(h->stream, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, h->scratch + h->scratch_top,
+                (size_t)(h->scratch_elems - h->scratch_top) * sizeof(cplx), &h->st->tc_timeouts));
+    return IPEPS_OK;
+  }
   // small products (a few tiles of zero padding would dominate) stay FP64
-  if (h->opt.prec != IPEPS_PREC_FP64 && M >= 64 && N >= 32 && K >= 16) {
+  if (tc_form(h->opt.prec) && M >= 64 && N >= 32 && K >= 16) {
     TcProbe pr;
     TcProbe* p = tc_probe_begin(h, &pr);
     cudaError_t e = tc_zgemm(h->stream, (int)h->opt.prec, M, N, K, alpha, A, lda, opA, B, ldb,
@@ -531,7 +549,7 @@ static ipeps_status contract(ipeps_ctm h, const char* spec, TV A, bool conjA, TV
   // Tensor-core products: an operand that is not already in GEMM form is
   // gathered by the operand packing through a view (fused permute-and-pack)
   // instead of being permuted into a copy first.
-  const bool tc = h->opt.prec != IPEPS_PREC_FP64 &&
+  const bool tc = tc_form(h->opt.prec) &&
                   ((direct && swap) ? (N >= 64 && M >= 32 && Kd >= 16) : (M >= 64 && N >= 32 && Kd >= 16)) &&
                   (2 * std::max(M, N) + 512) * (2 * Kd + 128) < (1LL << 31);  // gathers index in 32 bits
   // arrange one operand as [free..., k...] (op N) or [k..., free...] (op T)
@@ -796,7 +814,7 @@ static ipeps_status validate(const ipeps_cell* c, const ipeps_options* o) {
   if (o->chi > 1024) return fail(IPEPS_EINVAL, "chi > 1024");
   if (o->rsvd_oversample < 0 || o->rsvd_power < 0) return fail(IPEPS_EINVAL, "bad rsvd options");
   if (o->chi + o->rsvd_oversample > 1024) return fail(IPEPS_EINVAL, "chi + oversample > 1024");
-  if (o->prec < IPEPS_PREC_FP64 || o->prec > IPEPS_PREC_BF16X6) return fail(IPEPS_EINVAL, "bad prec");
+  if (o->prec < IPEPS_PREC_FP64 || o->prec > IPEPS_PREC_FP64TC) return fail(IPEPS_EINVAL, "bad prec");
   if (o->jacobi_max_sweeps < 1) return fail(IPEPS_EINVAL, "jacobi_max_sweeps >= 1");
   if (o->corners != 0 && o->corners != 2 && o->corners != 4) return fail(IPEPS_EINVAL, "corners must be 2 or 4");
   return IPEPS_OK;
@@ -917,7 +935,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   h->dtype = c->dtype;
   h->opt = *o;
   if (!(h->opt.svd_cutoff > 0.0))  // automatic: above the noise floor of the contraction arithmetic
-    h->opt.svd_cutoff = o->prec == IPEPS_PREC_FP64 ? 1e-8 : (o->prec == IPEPS_PREC_TF32 ? 1e-5 : 1e-6);
+    h->opt.svd_cutoff = !tc_form(o->prec) ? 1e-8 : (o->prec == IPEPS_PREC_TF32 ? 1e-5 : 1e-6);
   h->stream = (cudaStream_t)o->stream;
   Sizes sz = plan_sizes(h->Lx, h->Ly, h->d, h->D, h->chi, h->k, h->ntens, o->prec);
   if (o->workspace) {
@@ -957,7 +975,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
     need(h->spareT[i] = carve<cplx>(h, sz.T));
   }
   for (int i = 0; i < 4; ++i) need(h->Q[i] = carve<cplx>(h, sz.Q));
-  if (o->prec != IPEPS_PREC_FP64)
+  if (tc_form(o->prec))
     for (int i = 0; i < 4; ++i)
       for (int v = 0; v < 2; ++v) need(h->Qpmem[i][v] = carve<char>(h, tc_packed_bytes(o->prec, h->K, h->K)));
   need(h->omt = carve<cplx>(h, sz.thin));
@@ -981,7 +999,7 @@ extern "C" ipeps_status ipeps_ctm_create(const ipeps_cell* c, const ipeps_option
   h->scratch_elems = sz.scratch;
   h->scratch_top = 0;
   for (int i = 0; i < 4; ++i) need(h->alt.Q[i] = carve<cplx>(h, sz.Q));
-  if (o->prec != IPEPS_PREC_FP64)
+  if (tc_form(o->prec))
     for (int i = 0; i < 4; ++i)
       for (int v = 0; v < 2; ++v) need(h->alt.Qpmem[i][v] = carve<char>(h, tc_packed_bytes(o->prec, h->K, h->K)));
   for (int i = 0; i < 4; ++i) need(h->alt.thin[i] = carve<cplx>(h, sz.thin));
@@ -1236,7 +1254,7 @@ static ipeps_status pack_corners(ipeps_ctm h) {
   return IPEPS_OK;
 }
 
-static bool packed_path(ipeps_ctm h) { return h->opt.prec != IPEPS_PREC_FP64; }
+static bool packed_path(ipeps_ctm h) { return tc_form(h->opt.prec); }
 
 // Yt = In * Q3 * Q4^T * Q1 * Q2      (the transpose of X * In^T)
 // two corners: Yt = In * Q4^T * Q1
@@ -1324,7 +1342,7 @@ static cudaError_t proj_zgemm(ipeps_ctm h, double flops, int M, int N, int K, co
 // R^{-T} in (rows orthonormal on the kept directions, zero elsewhere).  R is
 // left in Rout (k x k) when given.
 static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Rout, double tol,
-                                bool apply = true) {
+                                bool apply = true, bool shifted = false) {
   const int k = h->k, K = h->K;
   const long long mark = h->scratch_top;
   cplx* G = scratch_alloc(h, (long long)k * k);
@@ -1334,6 +1352,8 @@ static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Ro
   if (!G || !W || !R || !Ri) return fail(IPEPS_ENOMEM, "scratch exhausted (cholqr)");
   // Hermitian Gram: the Cholesky reads its upper triangle only
   CK(proj_zgemm(h, 8.0 * K * (0.5 * k * (k + 1)), k, k, K, in, K, OP_C, in, K, OP_T, G, k, ZG_UPPER_TILES));
+  // shifted CholeskyQR: s = 11 (m n + n (n + 1)) u ||Y||^2 with u = 2^-53
+  if (shifted) CK(gram_shift(h->stream, G, k, 11.0 * ((double)K * k + (double)k * (k + 1)) * 0x1p-53));
   CK(chol_drop(h->stream, G, W, R, k, tol));
   if (apply) {
     CK(tri_inv(h->stream, R, Ri, k));
@@ -1347,6 +1367,21 @@ static ipeps_status cholqr_pass(ipeps_ctm h, const cplx* in, cplx* out, cplx* Ro
 // Precision form orthonormalisation: CholeskyQR2 (directions below ~1e-7 of
 // the largest singular value dropped in the first pass).
 static ipeps_status orth_chol(ipeps_ctm h, cplx* Y, cplx* tmp, bool twice) {
+  if (h->opt.prec == IPEPS_PREC_FP64TC) {
+    // FP64-accurate form: no direction of the basis is dropped for being
+    // small.  Shifted CholeskyQR (the shift keeps the Cholesky defined at any
+    // condition number; the result spans the same space with condition below
+    // about 1e5) and then one CholeskyQR pass (intermediate bases of the
+    // subspace iteration) or two (the final basis: shifted CholeskyQR3), whose
+    // pivots are dropped only where the shifted pass left rounding noise.
+    CKS(cholqr_pass(h, Y, tmp, nullptr, 0.0, true, true));
+    CKS(cholqr_pass(h, tmp, Y, nullptr, 1e-14));
+    if (twice) {
+      CKS(cholqr_pass(h, Y, tmp, nullptr, 1e-14));
+      CK(cudaMemcpyAsync(Y, tmp, (size_t)h->k * h->K * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return IPEPS_OK;
+  }
   if (!twice) {
     // intermediate bases of the subspace iteration only need to stay well
     // conditioned: one pass (orthogonality ~ eps cond^2 below the dropped 1e-7)
@@ -1380,10 +1415,27 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out, cplx* 
   cplx* R2 = scratch_alloc(h, (long long)k * k);
   cplx* Rt = scratch_alloc(h, (long long)k * k);
   if (!R1 || !R2 || !Rt) return fail(IPEPS_ENOMEM, "scratch exhausted (svd chol)");
-  CKS(cholqr_pass(h, Wt, out, R1, 1e-14));
-  CKS(cholqr_pass(h, out, nullptr, R2, 1e-14, false));  // only R2 is needed
-  // Rt = (R2 R1)^T: rows of Rt are the columns of R
-  CK(proj_zgemm(h, 8.0 * k * (k + 1.0) * (k + 2.0) / 6.0, k, k, k, R1, k, OP_T, R2, k, OP_T, Rt, k, ZG_A_LOWER));
+  const bool fp64tc = h->opt.prec == IPEPS_PREC_FP64TC;
+  cplx* Q3 = nullptr;
+  if (fp64tc) {
+    // shifted CholeskyQR3: W = Q3 R3 R2 R1 (no direction dropped for being small)
+    cplx* R3 = scratch_alloc(h, (long long)k * k);
+    cplx* Q2 = scratch_alloc(h, (long long)k * K);
+    cplx* R21 = scratch_alloc(h, (long long)k * k);
+    Q3 = scratch_alloc(h, (long long)k * K);
+    if (!R3 || !Q2 || !R21 || !Q3) return fail(IPEPS_ENOMEM, "scratch exhausted (svd chol)");
+    CKS(cholqr_pass(h, Wt, out, R1, 0.0, true, true));
+    CKS(cholqr_pass(h, out, Q2, R2, 1e-14));
+    CKS(cholqr_pass(h, Q2, Q3, R3, 1e-14));
+    // Rt = (R3 R2 R1)^T = (R2 R1)^T R3^T
+    CK(proj_zgemm(h, 8.0 * k * (k + 1.0) * (k + 2.0) / 6.0, k, k, k, R1, k, OP_T, R2, k, OP_T, R21, k, ZG_A_LOWER));
+    CK(proj_zgemm(h, 8.0 * k * (k + 1.0) * (k + 2.0) / 6.0, k, k, k, R21, k, OP_N, R3, k, OP_T, Rt, k, ZG_A_LOWER));
+  } else {
+    CKS(cholqr_pass(h, Wt, out, R1, 1e-14));
+    CKS(cholqr_pass(h, out, nullptr, R2, 1e-14, false));  // only R2 is needed
+    // Rt = (R2 R1)^T: rows of Rt are the columns of R
+    CK(proj_zgemm(h, 8.0 * k * (k + 1.0) * (k + 2.0) / 6.0, k, k, k, R1, k, OP_T, R2, k, OP_T, Rt, k, ZG_A_LOWER));
+  }
   // R1 = V_prev^T Rt: rows are the columns of R V_prev
   CK(proj_zgemm(h, 8.0 * k * (double)k * k, k, k, k, Vt, k, OP_N, Rt, k, OP_N, R1, k, 0));
   {
@@ -1393,11 +1445,19 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out, cplx* 
     cplx* rotlog = scratch_alloc(h, nlog);
     if (!rotlog) return fail(IPEPS_ENOMEM, "scratch exhausted (rotation log)");
     CK(jacobi_rows(h->stream, R1, k, k, k, Vt, h->sigma, h->opt.jacobi_max_sweeps, h->dwork, h->counters,
-                   h->st, rotlog, nlog, h->opt.wait_cycles, true, true));
+                   h->st, rotlog, nlog, h->opt.wait_cycles, true, !fp64tc));
     prof_end(h, a, 0.0, 1);
   }
-  // out = V^T Wt  (rows (W v_i)^T)
-  CK(proj_zgemm(h, 8.0 * k * (double)K * k, k, K, k, Vt, k, OP_N, Wt, K, OP_N, out, K, 0));
+  if (fp64tc) {
+    // out = R1 Q3^T: rows (Q3 R v_i)^T = s_i (Q3 u_R,i)^T.  The left singular
+    // vectors of W as the orthonormal basis Q3 times those of the core, rather
+    // than W v_i / s_i, whose division by a small s_i magnifies the rounding
+    // of W v_i (FP64-level agreement with the exact SVD needs the former).
+    CK(proj_zgemm(h, 8.0 * k * (double)K * k, k, K, k, R1, k, OP_N, Q3, K, OP_N, out, K, 0));
+  } else {
+    // out = V^T Wt  (rows (W v_i)^T)
+    CK(proj_zgemm(h, 8.0 * k * (double)K * k, k, K, k, Vt, k, OP_N, Wt, K, OP_N, out, K, 0));
+  }
   CK(row_norms(h->stream, out, k, K, K, h->sigma));
   h->scratch_top = mark;
   return IPEPS_OK;
@@ -1407,8 +1467,10 @@ static ipeps_status svd_rows_chol(ipeps_ctm h, const cplx* Wt, cplx* out, cplx* 
 static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx* Ptil) {
   CKS(enlarged_corners(h, f, x, y));
   const int k = h->k, K = h->K, chi = h->chi;
+  // the FP64 path orthonormalises by Jacobi; the other forms by CholeskyQR on
+  // FP64-accurate Grams (FP64TC: its products unpacked, on the digit planes)
   const bool fp64 = h->opt.prec == IPEPS_PREC_FP64;
-  if (!fp64) CKS(pack_corners(h));
+  if (packed_path(h)) CKS(pack_corners(h));
   cplx* Qt = h->thin[0];
   cplx* Zt = h->thin[1];
   auto orth_any = [&](cplx* Y, bool last) -> ipeps_status {
@@ -1453,11 +1515,11 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   // P^T = S^-1/2 V^T Q3 Q4^T ;  Ptil = S^-1/2 U^H Q2^T Q1^T
   // (two corners: P^T = S^-1/2 V^T Q4^T ;  Ptil = S^-1/2 U^H Q1^T)
   if (two_corners(h)) {
-    if (!fp64)
+    if (packed_path(h))
       CKS(thin_mul_packed(h, Vt_chi, OP_N, PT, 3, 1, chi, false));
     else
       CKS(thin_mul(h, Vt_chi, OP_N, PT, h->Q[3], OP_T, chi));
-  } else if (!fp64) {
+  } else if (packed_path(h)) {
     CKS(thin_mul_packed(h, Vt_chi, OP_N, tmp, 2, 0, chi, false));
     CKS(thin_mul_packed(h, tmp, OP_N, PT, 3, 1, chi, false));
   } else {
@@ -1466,11 +1528,11 @@ static ipeps_status projectors(ipeps_ctm h, int f, int x, int y, cplx* PT, cplx*
   }
   CK(scale_rows_isqrt(h->stream, PT, chi, K, K, h->s_sel));
   if (two_corners(h)) {
-    if (!fp64)
+    if (packed_path(h))
       CKS(thin_mul_packed(h, Ut_chi, OP_C, Ptil, 0, 1, chi, false));
     else
       CKS(thin_mul(h, Ut_chi, OP_C, Ptil, h->Q[0], OP_T, chi));
-  } else if (!fp64) {
+  } else if (packed_path(h)) {
     CKS(thin_mul_packed(h, Ut_chi, OP_C, tmp, 1, 1, chi, false));
     CKS(thin_mul_packed(h, tmp, OP_N, Ptil, 0, 1, chi, false));
   } else {
@@ -1627,7 +1689,7 @@ static ipeps_status rdm_buffers(ipeps_ctm h, cplx** rh, cplx** rv);
 
 extern "C" ipeps_status ipeps_ctm_autotune(ipeps_ctm h) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
-  if (h->opt.prec == IPEPS_PREC_FP64) return IPEPS_OK;  // no tensor-core products to tune
+  if (!tc_form(h->opt.prec)) return IPEPS_OK;  // no tiled tensor-core products to tune
   CK(kernels_init());
   CK(tc_init());
   if (!h->tuner) {
@@ -1877,7 +1939,7 @@ static ipeps_status all_rdms(ipeps_ctm h, cplx* rh, cplx* rv) {
   const long long big = c * c * D * D * D * D * d;
   const long long need = c * c * D * D * D * D + 4 * big + 2 * c * c * D * D * d * d + c * c * D * D + (1LL << 22);
   const long long full = h->scratch_elems, half = (full / 2) & ~1023LL;
-  if (rh && rv && h->has_alt && !h->no_alt && h->opt.prec != IPEPS_PREC_FP64 && half >= need) {
+  if (rh && rv && h->has_alt && !h->no_alt && tc_form(h->opt.prec) && half >= need) {
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(h->alt.stream, h->ev_fork, 0));
     h->scratch_elems = half;
@@ -2620,7 +2682,7 @@ extern "C" ipeps_status ipeps_boundary_rho_topk(ipeps_ctm h, int x, int Nv, int 
     prof_begin(h, &pl);
     if (e == cudaSuccess)
       e = lanczos_leading(h->stream, sL, sR, n, k, max_iter, tol, h->opt.omega_seed ^ 0x5bd1e995ULL, work,
-                          work_elems, h->s_sel, h->opt.prec != IPEPS_PREC_FP64, &res);
+                          work_elems, h->s_sel, tc_form(h->opt.prec), &res);
     prof_end(h, pl, (double)res.iters, 4);
     double2* partial = (double2*)work;
     double2* trd = partial + 512;
@@ -2652,7 +2714,7 @@ void launch_purity(cudaStream_t s, const cplx* M, int n, double* work, double* o
 extern "C" ipeps_status ipeps_boundary_renyi2(ipeps_ctm h, int x, int Nv, double* S2, double* purity) {
   if (!h) return fail(IPEPS_EINVAL, "null handle");
   if (Nv < 2 || Nv % h->Ly) return fail(IPEPS_EINVAL, "Nv must be a multiple of Ly and >= 2");
-  const long long n_max = h->opt.prec == IPEPS_PREC_FP64 ? 4096 : 200000;
+  const long long n_max = !tc_form(h->opt.prec) ? 4096 : 200000;
   long long n = 1;
   for (int i = 0; i < Nv; ++i) {
     n *= h->D;
@@ -2668,7 +2730,7 @@ extern "C" ipeps_status ipeps_boundary_renyi2(ipeps_ctm h, int x, int Nv, double
                                        (long long)(ring_pack_factor(h) * (double)n * (double)c2)) + (1LL << 24);
   const long long ring_phase = n2 + c2 * (K1 * K1 + K2 * K2) + ring_work;
   // product phase: sigma_R, M and the product's packed operands (BF16x6: 2.25 n^2)
-  const long long product_phase = 2 * n2 + (h->opt.prec == IPEPS_PREC_FP64 ? n2 : (9 * n2) / 4) + (1LL << 24);
+  const long long product_phase = 2 * n2 + (!tc_form(h->opt.prec) ? n2 : (9 * n2) / 4) + (1LL << 24);
   const long long region_elems = std::max(ring_phase, product_phase);
   cplx* mem = nullptr;
   cudaError_t e = dev_alloc((void**)&mem, (size_t)(n2 + region_elems) * sizeof(cplx));
@@ -2754,7 +2816,7 @@ void ctm_geometry(ipeps_ctm h, int g[10]) {
 // stand-alone complex GEMM (building block, host buffers) for unit tests
 // ---------------------------------------------------------------------------
 // prec code of ipeps_zgemm for the FP64-accurate tensor-core GEMM (ozaki.cu)
-constexpr int ZGEMM_FP64_TC = 4;
+constexpr int ZGEMM_FP64_TC = IPEPS_PREC_FP64TC;
 
 static ipeps_status zgemm_host(int prec, int M, int N, int K, const double* A, int opA, const double* B, int opB,
                                double* C, const TcChoice* force);

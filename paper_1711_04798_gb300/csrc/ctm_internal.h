@@ -155,6 +155,9 @@ cudaError_t trace_normalize(cudaStream_t s, cplx* rho, int n, double* work);
 cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n, double tol);
 // inverse of upper-triangular R on its kept block (zero where R[i,i] == 0)
 cudaError_t tri_inv(cudaStream_t s, const cplx* R, cplx* Rinv, int n);
+// G += coef * tr(G) * I for the Hermitian n x n Gram G (device): the diagonal
+// shift of shifted CholeskyQR
+cudaError_t gram_shift(cudaStream_t s, cplx* G, int n, double coef);
 
 // ---------------------------------------------------------------------------
 // Krylov readout of the boundary density operator (lanczos.cu)

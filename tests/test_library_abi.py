@@ -98,7 +98,7 @@ _RULES = [
     ("cell", "leg_dims", None, b"leg_dims[7] = 2"),
     ("opt", "chi", 15, b"chi"), ("opt", "chi", 1025, b"chi > 1024"),
     ("opt", "rsvd_oversample", -1, b"rsvd"), ("opt", "rsvd_power", -1, b"rsvd"),
-    ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 4, b"prec"),
+    ("opt", "rsvd_oversample", 1000, b"oversample"), ("opt", "prec", 5, b"prec"),
     ("opt", "prec", -1, b"prec"), ("opt", "jacobi_max_sweeps", 0, b"jacobi"),
     ("opt", "corners", 3, b"corners"), ("opt", "corners", -4, b"corners"),
 ]
