@@ -512,11 +512,7 @@ def fp64_comparison(args, w, J, stream, torch, value):
 
     # polish: FP64-accurate tensor-core sweeps from the precision form's environment
     gp = CTM(w["tensors"], w["pattern"], args.chi, prec="fp64tc", cutoff=cut, stream=stream.cuda_stream)
-    Ly, Lx = len(w["pattern"]), len(w["pattern"][0])
-    for role in range(8):
-        for y in range(Ly):
-            for x in range(Lx):
-                gp.set_env(role, x, y, gm.env(role, x, y))
+    gp.copy_env_from(gm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     n2, delta2, ok2 = gp.converge(1e-10, 30)

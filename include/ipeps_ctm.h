@@ -353,6 +353,15 @@ ipeps_status ipeps_ctm_env_get(ipeps_ctm h, int role, int x, int y, double* host
  * pointer, role outside 0..7, position outside the cell), ECUDA. */
 ipeps_status ipeps_ctm_env_set(ipeps_ctm h, int role, int x, int y, const double* host_in);
 
+/* Copy the whole environment (every C and T of the cell, Sec. II.C) of src
+ * into dst on the device, e.g. from a precision-form handle into an
+ * IPEPS_PREC_FP64TC or IPEPS_PREC_FP64 one to finish a convergence in FP64
+ * arithmetic.  The handles must have the same Lx, Ly, D and chi (their site
+ * tensors and options may differ).  Asynchronous: queued on dst's stream after
+ * the work queued on src's, and src's stream waits for the copy.  No paper
+ * counterpart.  Errors: EINVAL (NULL handle, different cell geometry), ECUDA. */
+ipeps_status ipeps_ctm_env_copy(ipeps_ctm dst, ipeps_ctm src);
+
 /* Checkpoint and resume of the environment (the CTM state that moves
  * update; the site tensors and options are the caller's and are not stored).
  * No paper counterpart: persistence of the state of Sec. II.C.

@@ -26,7 +26,7 @@ EXPORTS = [
     "ipeps_batch_sync", "ipeps_batch_destroy", "ipeps_batch_stream", "ipeps_boundary_rho_topk",
     "ipeps_ctm_autotune", "ipeps_ctm_tuning_size", "ipeps_zgemm_tile", "ipeps_ctm_env_set",
     "ipeps_ctm_save", "ipeps_ctm_load", "ipeps_env_file_info", "ipeps_rdm_site", "ipeps_batch_fidelity",
-    "ipeps_boundary_renyi2", "ipeps_energy_star", "ipeps_boundary_rho_refined",
+    "ipeps_boundary_renyi2", "ipeps_energy_star", "ipeps_boundary_rho_refined", "ipeps_ctm_env_copy",
 ]
 
 
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
     lib.ipeps_boundary_rho.argtypes = [P, I, I, C.POINTER(D), C.POINTER(I), C.POINTER(D)]
     lib.ipeps_ctm_env_get.argtypes = [P, I, I, I, C.POINTER(D)]
     lib.ipeps_ctm_env_set.argtypes = [P, I, I, I, C.POINTER(D)]
+    lib.ipeps_ctm_env_copy.argtypes = [P, P]
     lib.ipeps_ctm_save.argtypes = [P, C.c_char_p]
     lib.ipeps_ctm_load.argtypes = [P, C.c_char_p]
     lib.ipeps_env_file_info.argtypes = [C.c_char_p, C.POINTER(I)]
@@ -393,6 +394,10 @@ class CTM:
         if buf.size != n:
             raise ValueError(f"role {role} needs {n} complex elements, got {buf.size}")
         _check(self.lib.ipeps_ctm_env_set(self.h, role, x, y, _dptr(buf.view(np.float64))))
+
+    def copy_env_from(self, other: "CTM"):
+        """Take other's whole environment (same cell, D and chi), on the device."""
+        _check(self.lib.ipeps_ctm_env_copy(self.h, other.h))
 
     def save(self, path):
         """Write the environment to a checkpoint file."""

@@ -2806,6 +2806,33 @@ extern "C" ipeps_status ipeps_ctm_env_set(ipeps_ctm h, int role, int x, int y, c
   return IPEPS_OK;
 }
 
+extern "C" ipeps_status ipeps_ctm_env_copy(ipeps_ctm dst, ipeps_ctm src) {
+  if (!dst || !src) return fail(IPEPS_EINVAL, "null handle");
+  if (dst == src) return IPEPS_OK;
+  if (dst->Lx != src->Lx || dst->Ly != src->Ly || dst->D != src->D || dst->chi != src->chi)
+    return fail(IPEPS_EINVAL, "env copy: the handles differ in Lx, Ly, D or chi");
+  // the copies run on dst's stream after everything queued on src's
+  cudaEvent_t ev = nullptr, done = nullptr;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, src->stream));
+  CK(cudaStreamWaitEvent(dst->stream, ev, 0));
+  const long long nc = (long long)dst->chi * dst->chi, nt = (long long)dst->chi * dst->D2 * dst->chi;
+  for (int role = 0; role < 4; ++role)
+    for (int i = 0; i < dst->Lx * dst->Ly; ++i) {
+      CK(cudaMemcpyAsync(dst->C[role][i], src->C[role][i], nc * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                         dst->stream));
+      CK(cudaMemcpyAsync(dst->T[role][i], src->T[role][i], nt * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                         dst->stream));
+    }
+  // src may be used (or destroyed) once its copies are done
+  CK(cudaEventRecord(done, dst->stream));
+  CK(cudaStreamWaitEvent(src->stream, done, 0));
+  cudaEventDestroy(ev);  // released by the runtime once complete
+  cudaEventDestroy(done);
+  return IPEPS_OK;
+}
+
 // geometry for the checkpoint module: Lx, Ly, d, D, chi, n_tensors, pattern[4]
 void ctm_geometry(ipeps_ctm h, int g[10]) {
   g[0] = h->Lx; g[1] = h->Ly; g[2] = h->d; g[3] = h->D; g[4] = h->chi; g[5] = h->ntens;

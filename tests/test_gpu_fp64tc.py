@@ -115,3 +115,32 @@ def test_boundary_spectrum(Nv):
     assert np.max(np.abs(lam - lam_ref)) < TOL
     assert abs(S - O.entropy(lam_ref)) < TOL
     g.close()
+
+
+def test_precision_form_polished_to_the_oracle_fixed_point():
+    """A BF16x6 convergence (its spectra settle at a floor set by FP32
+    accumulation) continued by FP64-accurate sweeps from its environment
+    (ipeps_ctm_env_copy, device to device): converged to 1e-10, the result is
+    the FP64 oracle's converged one at the same cutoff (1e-6), 1e-10."""
+    w, chi, cut = synth.workload("product_noise", seed=2, D=3, chi=18), 18, 1e-6
+    gm = gpu_ctm(w["tensors"], w["pattern"], chi, prec="bf16x6", cutoff=cut)
+    n1, d1, _ = gm.converge(1e-8, 30)
+    gp = gpu_ctm(w["tensors"], w["pattern"], chi, prec="fp64tc", cutoff=cut)
+    gp.copy_env_from(gm)
+    assert np.max(np.abs(gp.env(4, 1, 0) - gm.env(4, 1, 0))) == 0.0
+    n2, d2, ok = gp.converge(1e-10, 40)
+    st = O.make_state(w["tensors"], w["pattern"], w["D"], chi)
+    st, n_ref, d_ref = O.ctm_converge(st, oracle_options(chi, w["D"], cutoff=cut), 1e-10, 100)
+    rd = O.bond_rdms(st, w["tensors"], w["pattern"])
+    e_ref = O.energy_per_spin(rd, w["J"], 2, 2)
+    e = gp.energy(w["J"])
+    r = gp.rdms()
+    s_err = spectra_err(gp.spectra(), O.corner_spectra(st))
+    print(f"bf16x6 {n1} sweeps (delta {d1:.1e}), then fp64tc {n2} sweeps (delta {d2:.1e}); oracle {n_ref}: "
+          f"|dE|/|E| {abs(e - e_ref) / abs(e_ref):.1e}, spectra {s_err:.1e}")
+    assert ok
+    assert abs(e - e_ref) < TOL * abs(e_ref)
+    assert rel_err(r["h"], rd["h"]) < TOL and rel_err(r["v"], rd["v"]) < TOL
+    assert s_err < TOL
+    gm.close()
+    gp.close()

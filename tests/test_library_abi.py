@@ -253,6 +253,7 @@ def test_checkpoint_header_and_checksum_verified_without_gpu(lib, tmp_path):
 def test_checkpoint_calls_reject_null_handles(lib, tmp_path):
     buf = (ctypes.c_double * 8)()
     assert lib.ipeps_ctm_env_set(None, 0, 0, 0, buf) == 1
+    assert lib.ipeps_ctm_env_copy(None, None) == 1
     assert lib.ipeps_ctm_save(None, str(tmp_path / "x").encode()) == 1
     assert lib.ipeps_ctm_load(None, str(tmp_path / "x").encode()) == 1
     assert lib.ipeps_env_file_info(None, (ctypes.c_int * 11)()) == 1
