@@ -69,6 +69,32 @@ __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// The same MMA with the A operand kept in the tensor core's collector buffer
+// across consecutive MMAs that share it: FILL reads A from shared memory and
+// keeps it, USE takes the kept A, LAST takes it and releases the buffer.
+enum { COLL_FILL = 1, COLL_USE = 2, COLL_LAST = 3 };
+template <int COLL>
+__device__ __forceinline__ void umma_bf16_coll(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+  if constexpr (COLL == COLL_FILL)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+        : "memory");
+  else if constexpr (COLL == COLL_USE)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(
@@ -281,12 +307,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       fence_after();
       const uint32_t a = smem_u32(smem + slot * OZ_STAGE);
-      for (int t = 0; t < OZ_DIGITS - s; ++t) {
-        const uint32_t b = a + OZ_A_BYTES + t * OZ_B_BYTES;
-        const uint32_t d = tmem + (uint32_t)((c & 1) * OZ_ACC_COLS + (s + t) * OZ_BN);
+      // per k-step, A plane s meets the B planes t = 0 .. 6 - s in turn (group
+      // s + t each): A is read from shared memory once per k-step and kept in
+      // the collector buffer for the other B planes
+      const int nt = OZ_DIGITS - s;
+      const uint32_t d0 = tmem + (uint32_t)((c & 1) * OZ_ACC_COLS + s * OZ_BN);
 #pragma unroll
-        for (int ks = 0; ks < OZ_BK / 16; ++ks)
-          umma_bf16(d, sdesc(a + ks * 32), sdesc(b + ks * 32), (chunk_start && ks == 0) ? 0u : 1u);
+      for (int ks = 0; ks < OZ_BK / 16; ++ks) {
+        const uint64_t ad = sdesc(a + ks * 32);
+        const uint32_t acc = (chunk_start && ks == 0) ? 0u : 1u;
+        const uint32_t b0 = a + OZ_A_BYTES + ks * 32;
+        if (nt == 1) {
+          umma_bf16(d0, ad, sdesc(b0), acc);
+          continue;
+        }
+        umma_bf16_coll<COLL_FILL>(d0, ad, sdesc(b0), acc);
+        for (int t = 1; t < nt - 1; ++t)
+          umma_bf16_coll<COLL_USE>(d0 + t * OZ_BN, ad, sdesc(b0 + t * OZ_B_BYTES), acc);
+        umma_bf16_coll<COLL_LAST>(d0 + (nt - 1) * OZ_BN, ad, sdesc(b0 + (nt - 1) * OZ_B_BYTES), acc);
       }
       umma_commit(&empty[slot]);  // frees the slot when these MMAs are done
       if (kbc == OZ_KB_PER_CHUNK - 1 && s == OZ_DIGITS - 1) umma_commit(&acc_full[c & 1]);
@@ -405,12 +443,16 @@ OzLayout oz_layout(int M, int N, int K) {
   L.Krp = (2 * K + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
   L.chunks = L.Krp / OZ_CHUNK;
   // chunks per CTA: the fewest chunk-times over whole waves of CTAs (152 SMs,
-  // one CTA each), the fewer K splits on a tie
+  // one CTA each), counting a CTA's start (barriers, tensor memory, the
+  // pipeline's fill) as one chunk-time and, for K splits, the exact partials'
+  // round trip through memory (24 bytes per output element and split, about
+  // 16 MB per chunk-time); the fewer K splits on a tie
   const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Nrp / OZ_BN);
-  long long best = -1;
+  double best = -1.0;
   for (int cps = 1; cps <= L.chunks; ++cps) {
     const long long S = (L.chunks + cps - 1) / cps;
-    const long long cost = (tiles * S + 151) / 152 * cps;
+    const double partials = S > 1 ? 24.0 * (double)S * L.Mp * L.Nrp / 16.0e6 : 0.0;
+    const double cost = (double)((tiles * S + 151) / 152) * (cps + 1) + partials;
     if (best < 0 || cost <= best) {
       best = cost;
       L.cps = cps;
