@@ -111,3 +111,18 @@ def test_fp64_tensor_core_product_matches_the_fp64_kernel(shape, ops):
     e_fp64 = np.max(np.abs(C4 - C0) / scale)
     print(f"shape {shape} ops {ops}: digit-split vs numpy {e_ref:.2e}, vs FP64 kernel {e_fp64:.2e}")
     assert e_ref < 1e-15 and e_fp64 < 1e-15
+
+
+def test_fp64_tensor_core_wide_product():
+    """The shape of the enlarged corner's dominant product at D = 5, chi = 100
+    (chi^2 x D^4 x D^4 = 10^4 x 625 x 625): whole waves of 128 x 32 tiles
+    without K splits, against numpy on every element, 1e-15 of the scale."""
+    M, N, K = 10000, 625, 625
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))
+    C4 = _zgemm(4, A, 0, B, 0, M, N, K)
+    scale = np.abs(A) @ np.abs(B)
+    e_ref = np.max(np.abs(C4 - A @ B) / scale)
+    print(f"wide digit-split product vs numpy {e_ref:.2e}")
+    assert e_ref < 1e-15
