@@ -298,9 +298,13 @@ def kernel_classes(g, prec, ms_step, steps, peaks, peak_src, zpk):
         classes.append({"kernel": "splitk_reduce_kernel (FP32 partial sums)", "bound": "hbm", "ms": rd[8]["ms"],
                         "work": rd[8]["flops"] / 1e9, "launches": rd[8]["launches"], "peak": hbm, "unit": "GB/s",
                         "peak_source": f"HBM copy ({peak_src})"})
-        classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM): CholeskyQR Grams/applies of the projectors",
-                        "bound": "alu", "ms": rd[2]["ms"], "work": rd[2]["flops"] / 1e12,
-                        "launches": rd[2]["launches"], "peak": zpk, "unit": "TFLOP/s", "peak_source": zsrc})
+        classes.append({"kernel": "oz_gemm_kernel with its digit preparation and exact reduction (FP64-accurate "
+                                  "digit-split products on tcgen05): CholeskyQR Grams/applies and core products "
+                                  "of the projectors",
+                        "bound": "latency", "ms": rd[2]["ms"], "work": rd[2]["flops"] / 1e12,
+                        "launches": rd[2]["launches"], "peak": zpk, "unit": "TFLOP/s",
+                        "peak_source": zsrc + "; the FP64-pipe rate these products replace (frac > 1: faster than "
+                                              "that pipe can run them); algorithmic FP64 flops"})
     classes.append({"kernel": "Jacobi SVD kernels (FP64, projector cores and orthonormalisation)", "bound": "alu",
                     "ms": rd[1]["ms"], "work": None, "launches": rd[1]["launches"], "peak": None, "unit": None,
                     "peak_source": "latency-bound FP64 rotations; mean sweeps per call "
