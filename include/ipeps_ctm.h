@@ -476,8 +476,8 @@ ipeps_status ipeps_zgemm_tile(int prec, int bn, int splits, int M, int N, int K,
  * the library (every GPU that loads the library holds it until exit), so
  * chi is limited to 1..256; larger chi returns EINVAL.  Every call looks up
  * that array's device address with the caller's device current; the first
- * call on a device also loads the library's device code there, so make the
- * first call before any stream capture.  All calls share the array: two
+ * call on a device also loads the library's device code there.  All calls
+ * share the array: two
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and give wrong results.  Errors: EINVAL (null pointer, chi out of range),
  * ECUDA, ETIMEOUT (Jacobi sweep budget), with ipeps_last_error(). */
