@@ -44,28 +44,43 @@ namespace {
 
 constexpr int OZ_DIGITS = 7;                          // base-256 digits per element
 constexpr int OZ_GROUPS = 7;                          // weights g = s + t = 0..6
-constexpr int OZ_BM = 128, OZ_BN = 32;                // output tile (rows, real columns)
+constexpr int OZ_BM = 128;                            // output tile rows
 constexpr int OZ_BK = 64;                             // bf16 elements per k-block (128 bytes)
 constexpr int OZ_CHUNK = 128;                         // reals of K per exact FP32 chunk
 constexpr int OZ_KB_PER_CHUNK = OZ_CHUNK / OZ_BK;     // 2
 constexpr int OZ_A_BYTES = OZ_BM * 128;               // one A plane k-block: 16 KB
-constexpr int OZ_B_BYTES = OZ_BN * 128;               // one B plane k-block: 4 KB
-constexpr int OZ_STAGE = OZ_A_BYTES + OZ_DIGITS * OZ_B_BYTES;  // 44 KB
-constexpr int OZ_STAGES = 4;
-constexpr int OZ_THREADS = 192;                       // producer, MMA issuer, 4 epilogue warps
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
-constexpr int OZ_ACC_COLS = 256;                      // one set of 7 groups x 32 columns, rounded up
-constexpr int OZ_TMEM_COLS = 2 * OZ_ACC_COLS;         // two sets: chunk c accumulates in set c % 2
-static_assert(OZ_GROUPS * OZ_BN <= OZ_ACC_COLS, "the group accumulators fit one accumulator set");
+constexpr int OZ_TMEM_COLS = 512;
 static_assert(OZ_GROUPS == OZ_DIGITS, "weights 0..6 of the digit pairs s + t <= 6");
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(OZ_BM >> 4) << 24);  // FP32 += BF16 x BF16, K-major, 128 x 32
 
-__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+// Output tiles of 128 x BN real columns.  BN = 32: two sets of the seven group
+// accumulators (224 of 256 columns each), so that a chunk's products run
+// while the epilogue drains the previous chunk; four 44 KB stages; four
+// epilogue warps.  BN = 64: one set (448 columns), the products of a chunk
+// wait for the previous chunk's drain, but each MMA does twice the work (the
+// narrow MMAs' issue bounds the 32-wide tile); three 72 KB stages; eight
+// epilogue warps (two per lane quarter, 32 columns each).
+template <int BN>
+struct OzTile {
+  static constexpr int B_BYTES = BN * 128;                       // one B plane k-block
+  static constexpr int STAGE = OZ_A_BYTES + OZ_DIGITS * B_BYTES;  // 44 KB / 72 KB
+  static constexpr int STAGES = BN == 32 ? 4 : 3;
+  static constexpr int SETS = BN == 32 ? 2 : 1;
+  static constexpr int ACC_COLS = BN == 32 ? 256 : 512;          // columns per accumulator set
+  static constexpr int EPI_WARPS = BN / 8;
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;            // producer, MMA issuer, epilogue
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(OZ_BM >> 4) << 24);  // FP32 += BF16 x BF16, K-major
+  static_assert(OZ_GROUPS * BN <= ACC_COLS && SETS * ACC_COLS <= OZ_TMEM_COLS, "accumulators fit");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
 }
 
@@ -74,42 +89,27 @@ __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b
 // keeps it, USE takes the kept A, LAST takes it and releases the buffer.
 enum { COLL_FILL = 1, COLL_USE = 2, COLL_LAST = 3 };
 template <int COLL>
-__device__ __forceinline__ void umma_bf16_coll(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void umma_bf16_coll(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accum) {
   if constexpr (COLL == COLL_FILL)
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
   else if constexpr (COLL == COLL_USE)
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
   else
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accum)
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
 }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 
 // 2^k for k in the normal range, built from its bit pattern
 __device__ __forceinline__ double pow2(int k) {
@@ -223,11 +223,14 @@ __device__ __forceinline__ double oz_value(long long I, float u, int ea, int eb)
   return ((double)I + (double)u * (1.0 / 256.0)) * pow2(ea + eb - 38);
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+template <int BN>
+__global__ void __launch_bounds__(OzTile<BN>::THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int Mp, int Nrp,
                    int chunks_total, int chunks_per_split, int M, int N, const int* __restrict__ ea,
                    const int* __restrict__ eb, cplx* __restrict__ C, long long ldc, long long* __restrict__ pI,
                    float* __restrict__ pU, int* __restrict__ timeouts) {
+  using T = OzTile<BN>;
+  constexpr int OZ_STAGES = T::STAGES, OZ_STAGE = T::STAGE, OZ_B_BYTES = T::B_BYTES, SETS = T::SETS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE);
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], T::EPI_WARPS);  // one arrival per epilogue warp
     }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_expect_tx(&full[slot], OZ_A_BYTES + (OZ_DIGITS - s) * OZ_B_BYTES);
       tma_load_2d(st, &mA, &full[slot], kb * OZ_BK, s * Mp + m_tile * OZ_BM);
       for (int t = 0; t < OZ_DIGITS - s; ++t)
-        tma_load_2d(st + OZ_A_BYTES + t * OZ_B_BYTES, &mB, &full[slot], kb * OZ_BK, t * Nrp + n_tile * OZ_BN);
+        tma_load_2d(st + OZ_A_BYTES + t * OZ_B_BYTES, &mB, &full[slot], kb * OZ_BK, t * Nrp + n_tile * BN);
       issued = q + 1;
     }
     // the last loads of every slot have landed before the CTA can leave
@@ -287,15 +290,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (!mbar_wait(&full[q % OZ_STAGES], (q / OZ_STAGES) & 1)) atomicAdd(timeouts, 1);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: group g = s + t of chunk c accumulates in tensor-memory
-    // columns 256 (c % 2) + 32 g .., so that chunk c's products run while the
-    // epilogue drains chunk c - 1
+    // columns ACC_COLS (c % SETS) + BN g .. (with two sets chunk c's products
+    // run while the epilogue drains chunk c - 1)
     bool ok = true;
     for (int q = 0; q < nstage && ok; ++q) {
       const int slot = q % OZ_STAGES, round = q / OZ_STAGES;
       const int s = q % OZ_DIGITS, kbc = (q / OZ_DIGITS) % OZ_KB_PER_CHUNK, c = q / (OZ_DIGITS * OZ_KB_PER_CHUNK);
       const bool chunk_start = kbc == 0 && s == 0;
-      // the set was drained: chunk c - 2 was that set's drain number c/2 - 1
-      if (chunk_start && c > 1 && !mbar_wait(&acc_empty[c & 1], ((c >> 1) - 1) & 1)) {
+      // the set was drained: chunk c - SETS was that set's drain number c/SETS - 1
+      if (chunk_start && c >= SETS && !mbar_wait(&acc_empty[c % SETS], ((c / SETS) - 1) & 1)) {
         atomicAdd(timeouts, 1);
         ok = false;
         break;
@@ -311,83 +314,90 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       // s + t each): A is read from shared memory once per k-step and kept in
       // the collector buffer for the other B planes
       const int nt = OZ_DIGITS - s;
-      const uint32_t d0 = tmem + (uint32_t)((c & 1) * OZ_ACC_COLS + s * OZ_BN);
+      const uint32_t d0 = tmem + (uint32_t)((c % SETS) * T::ACC_COLS + s * BN);
 #pragma unroll
       for (int ks = 0; ks < OZ_BK / 16; ++ks) {
         const uint64_t ad = sdesc(a + ks * 32);
         const uint32_t acc = (chunk_start && ks == 0) ? 0u : 1u;
         const uint32_t b0 = a + OZ_A_BYTES + ks * 32;
         if (nt == 1) {
-          umma_bf16(d0, ad, sdesc(b0), acc);
+          umma_bf16(d0, ad, sdesc(b0), T::IDESC, acc);
           continue;
         }
-        umma_bf16_coll<COLL_FILL>(d0, ad, sdesc(b0), acc);
+        umma_bf16_coll<COLL_FILL>(d0, ad, sdesc(b0), T::IDESC, acc);
         for (int t = 1; t < nt - 1; ++t)
-          umma_bf16_coll<COLL_USE>(d0 + t * OZ_BN, ad, sdesc(b0 + t * OZ_B_BYTES), acc);
-        umma_bf16_coll<COLL_LAST>(d0 + (nt - 1) * OZ_BN, ad, sdesc(b0 + (nt - 1) * OZ_B_BYTES), acc);
+          umma_bf16_coll<COLL_USE>(d0 + t * BN, ad, sdesc(b0 + t * OZ_B_BYTES), T::IDESC, acc);
+        umma_bf16_coll<COLL_LAST>(d0 + (nt - 1) * BN, ad, sdesc(b0 + (nt - 1) * OZ_B_BYTES), T::IDESC, acc);
       }
       umma_commit(&empty[slot]);  // frees the slot when these MMAs are done
-      if (kbc == OZ_KB_PER_CHUNK - 1 && s == OZ_DIGITS - 1) umma_commit(&acc_full[c & 1]);
+      if (kbc == OZ_KB_PER_CHUNK - 1 && s == OZ_DIGITS - 1) umma_commit(&acc_full[c % SETS]);
     }
     // every MMA issued has completed before the accumulators are released
     umma_commit(mma_done);
     if (!mbar_wait(mma_done, 0)) atomicAdd(timeouts, 1);
   } else if (warp >= 2) {
-    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (the rows of its quarter)
-    const int q4 = warp & 3;
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (the rows of its
+    // quarter), columns 32 h .. 32 h + 31 of each group (h = 0, and 1 for the
+    // second four epilogue warps of BN = 64)
+    constexpr int EC = 32;  // columns per epilogue thread
+    const int q4 = warp & 3, h = (warp - 2) >> 2;
     const int row = m_tile * OZ_BM + 32 * q4 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
-    long long I[OZ_BN];
-    float u[OZ_BN];
+    const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(EC * h);
+    long long I[EC];
+    float u[EC];
 #pragma unroll
-    for (int j = 0; j < OZ_BN; ++j) {
+    for (int j = 0; j < EC; ++j) {
       I[j] = 0;
       u[j] = 0.0f;
     }
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
-      const bool ready = mbar_wait(&acc_full[c & 1], (c >> 1) & 1);
+      const bool ready = mbar_wait(&acc_full[c % SETS], (c / SETS) & 1);
       if (!ready) {
         if (lane == 0) atomicAdd(timeouts, 1);
         ok = false;
         break;
       }
       fence_after();
-      const uint32_t tset = trow + (uint32_t)((c & 1) * OZ_ACC_COLS);
-      float v[OZ_BN], t[OZ_BN];
-      // groups 0..3: exact integers (below 2^24) into the 64-bit sum
+      const uint32_t tset = trow + (uint32_t)((c % SETS) * T::ACC_COLS);
+      // two halves of 16 columns (fewer live registers beside the running sums)
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        tmem_ld32(tset + g * OZ_BN, v);
+      for (int hf = 0; hf < 2; ++hf) {
+        float v[16], t[16];
+        // groups 0..3: exact integers (below 2^24) into the 64-bit sum
 #pragma unroll
-        for (int j = 0; j < OZ_BN; ++j) I[j] += (long long)__float2int_rn(v[j]) << (8 * (3 - g));
+        for (int g = 0; g < 4; ++g) {
+          tmem_ld16(tset + g * BN + 16 * hf, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) I[16 * hf + j] += (long long)__float2int_rn(v[j]) << (8 * (3 - g));
+        }
+        // groups 4..6 (weight 2^-32 and below relative to group 0): FP32
+        tmem_ld16(tset + 6 * BN + 16 * hf, t);
+        tmem_ld16(tset + 5 * BN + 16 * hf, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) t[j] = fmaf(t[j], 1.0f / 256.0f, v[j]);
+        tmem_ld16(tset + 4 * BN + 16 * hf, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) u[16 * hf + j] += fmaf(t[j], 1.0f / 256.0f, v[j]);
       }
-      // groups 4..6 (weight 2^-32 and below relative to group 0): FP32
-      tmem_ld32(tset + 6 * OZ_BN, t);
-      tmem_ld32(tset + 5 * OZ_BN, v);
-#pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) t[j] = fmaf(t[j], 1.0f / 256.0f, v[j]);
-      tmem_ld32(tset + 4 * OZ_BN, v);
-#pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) u[j] += fmaf(t[j], 1.0f / 256.0f, v[j]);
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[c & 1]);
+      if (lane == 0) mbar_arrive(&acc_empty[c % SETS]);
     }
     if (ok) {
-      const int col0 = n_tile * OZ_BN;
+      const int col0 = n_tile * BN + EC * h;
       if (pI) {
         // exact partial sums of this K range
         const long long base = ((long long)split * Mp + row) * Nrp + col0;
 #pragma unroll
-        for (int j = 0; j < OZ_BN; ++j) {
+        for (int j = 0; j < EC; ++j) {
           pI[base + j] = I[j];
           pU[base + j] = u[j];
         }
       } else if (row < M) {
         const int er = ea[row];
 #pragma unroll
-        for (int j = 0; j < OZ_BN; j += 2) {
+        for (int j = 0; j < EC; j += 2) {
           const int n = (col0 + j) >> 1;
           if (n < N)
             C[(long long)row * ldc + n] = make_double2(oz_value(I[j], u[j], er, eb[col0 + j]),
@@ -432,14 +442,16 @@ unsigned oz_grid(long long n) {
 }
 
 struct OzLayout {
-  int Mp, Nrp, Krp, chunks, S, cps;
+  int Mp, Nrp, Krp, chunks, S, cps, bn;
   size_t off_ea, off_eb, off_a, off_b, off_pi, off_pu, total;
 };
 
 OzLayout oz_layout(int M, int N, int K) {
   OzLayout L;
   L.Mp = (M + OZ_BM - 1) / OZ_BM * OZ_BM;
-  L.Nrp = (2 * N + OZ_BN - 1) / OZ_BN * OZ_BN;
+  // 64-wide tiles where they still fill a wave of CTAs, else 32-wide
+  L.bn = (long long)(L.Mp / OZ_BM) * ((2 * N + 63) / 64) >= 152 ? 64 : 32;
+  L.Nrp = (2 * N + L.bn - 1) / L.bn * L.bn;
   L.Krp = (2 * K + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
   L.chunks = L.Krp / OZ_CHUNK;
   // chunks per CTA: the fewest chunk-times over whole waves of CTAs (152 SMs,
@@ -447,7 +459,7 @@ OzLayout oz_layout(int M, int N, int K) {
   // pipeline's fill) as one chunk-time and, for K splits, the exact partials'
   // round trip through memory (24 bytes per output element and split, about
   // 16 MB per chunk-time); the fewer K splits on a tie
-  const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Nrp / OZ_BN);
+  const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Nrp / L.bn);
   double best = -1.0;
   for (int cps = 1; cps <= L.chunks; ++cps) {
     const long long S = (L.chunks + cps - 1) / cps;
@@ -490,8 +502,11 @@ cudaError_t oz_zgemm(cudaStream_t s, int M, int N, int K, const cplx* A, long lo
   static bool attr = false;
   cudaError_t e;
   if (!attr) {
-    if ((e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(oz_gemm_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  OzTile<32>::SMEM)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(oz_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  OzTile<64>::SMEM)) != cudaSuccess)
       return e;
     attr = true;
   }
@@ -508,10 +523,14 @@ cudaError_t oz_zgemm(cudaStream_t s, int M, int N, int K, const cplx* A, long lo
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if ((e = tc_encode_bf16_map(&mA, pa, (long long)OZ_DIGITS * L.Mp, L.Krp, OZ_BM)) != cudaSuccess) return e;
-  if ((e = tc_encode_bf16_map(&mB, pb, (long long)OZ_DIGITS * L.Nrp, L.Krp, OZ_BN)) != cudaSuccess) return e;
-  dim3 grid((unsigned)(L.Nrp / OZ_BN), (unsigned)(L.Mp / OZ_BM), (unsigned)L.S);
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, L.Mp, L.Nrp, L.chunks, L.cps, M, N, ea, eb, C, ldc, pI, pU,
-                                                   timeouts);
+  if ((e = tc_encode_bf16_map(&mB, pb, (long long)OZ_DIGITS * L.Nrp, L.Krp, L.bn)) != cudaSuccess) return e;
+  dim3 grid((unsigned)(L.Nrp / L.bn), (unsigned)(L.Mp / OZ_BM), (unsigned)L.S);
+  if (L.bn == 64)
+    oz_gemm_kernel<64><<<grid, OzTile<64>::THREADS, OzTile<64>::SMEM, s>>>(mA, mB, L.Mp, L.Nrp, L.chunks, L.cps, M,
+                                                                          N, ea, eb, C, ldc, pI, pU, timeouts);
+  else
+    oz_gemm_kernel<32><<<grid, OzTile<32>::THREADS, OzTile<32>::SMEM, s>>>(mA, mB, L.Mp, L.Nrp, L.chunks, L.cps, M,
+                                                                          N, ea, eb, C, ldc, pI, pU, timeouts);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (L.S > 1) {
