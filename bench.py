@@ -32,7 +32,7 @@ def parse():
     p.add_argument("--steps", type=int, default=4)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--prec", default="bf16x6", choices=["fp64", "tf32", "bf16x3", "bf16x6"])
+    p.add_argument("--prec", default="bf16x6", choices=["fp64", "tf32", "bf16x3", "bf16x6", "fp64tc"])
     p.add_argument("--no-fp64-check", action="store_true",
                    help="skip the FP64 comparison run (moves/s and |dE| of the plain FP64 GPU path)")
     p.add_argument("--D", type=int, default=5)
@@ -252,8 +252,8 @@ def run_reference(args, rank, world):
 
 
 GOLDEN = os.path.join(ROOT, "tests", "golden")
-PASSES = {"fp64": 1, "tf32": 1, "bf16x3": 3, "bf16x6": 6}  # tensor-core products per complex product
-DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}
+PASSES = {"fp64": 1, "tf32": 1, "bf16x3": 3, "bf16x6": 6, "fp64tc": 28}  # tensor-core products per product
+DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16x3": "bf16x3", "bf16x6": "bf16x6", "fp64tc": "f64"}
 
 
 def stored_oracle(D, chi, seed, cutoff):
@@ -280,6 +280,15 @@ def kernel_classes(g, prec, ms_step, steps, peaks, peak_src, zpk):
         classes.append({"kernel": "zgemm_kernel (complex FP64 GEMM, CUDA cores): contractions", "bound": "alu",
                         "ms": c0["ms"], "work": c0["flops"] / 1e12, "launches": c0["launches"], "peak": zpk,
                         "unit": "TFLOP/s", "peak_source": zsrc})
+    elif prec == "fp64tc":
+        c0 = g.profile_read(0)
+        classes.append({"kernel": "oz_gemm_kernel with its digit preparation and exact reduction (FP64-accurate "
+                                  "digit-split products on tcgen05): contractions, range finder, readouts",
+                        "bound": "tensor", "ms": c0["ms"], "work": c0["flops"] * PASSES[prec] / 1e12,
+                        "launches": c0["launches"], "peak": bf16, "unit": "TFLOP/s",
+                        "peak_source": f"bf16 dense sustained ({peak_src}); executed flops = 8MNK algorithmic x 28 "
+                                       "digit-plane products (tile padding not counted)",
+                        "fp64_equivalent_tflops": c0["flops"] / (c0["ms"] * 1e-3) / 1e12 if c0["ms"] else None})
     else:
         npass = PASSES[prec]
         # a contraction takes the peak of its own dtype: BF16 dense (measured); TF32 at half of it
@@ -298,6 +307,7 @@ def kernel_classes(g, prec, ms_step, steps, peaks, peak_src, zpk):
         classes.append({"kernel": "splitk_reduce_kernel (FP32 partial sums)", "bound": "hbm", "ms": rd[8]["ms"],
                         "work": rd[8]["flops"] / 1e9, "launches": rd[8]["launches"], "peak": hbm, "unit": "GB/s",
                         "peak_source": f"HBM copy ({peak_src})"})
+    if prec != "fp64":
         classes.append({"kernel": "oz_gemm_kernel with its digit preparation and exact reduction (FP64-accurate "
                                   "digit-split products on tcgen05): CholeskyQR Grams/applies and core products "
                                   "of the projectors",

@@ -449,25 +449,30 @@ struct OzLayout {
 OzLayout oz_layout(int M, int N, int K) {
   OzLayout L;
   L.Mp = (M + OZ_BM - 1) / OZ_BM * OZ_BM;
-  // 64-wide tiles where they still fill a wave of CTAs, else 32-wide
-  L.bn = (long long)(L.Mp / OZ_BM) * ((2 * N + 63) / 64) >= 152 ? 64 : 32;
-  L.Nrp = (2 * N + L.bn - 1) / L.bn * L.bn;
   L.Krp = (2 * K + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
   L.chunks = L.Krp / OZ_CHUNK;
-  // chunks per CTA: the fewest chunk-times over whole waves of CTAs (152 SMs,
-  // one CTA each), counting a CTA's start (barriers, tensor memory, the
-  // pipeline's fill) as one chunk-time and, for K splits, the exact partials'
-  // round trip through memory (24 bytes per output element and split, about
-  // 16 MB per chunk-time); the fewer K splits on a tie
-  const long long tiles = (long long)(L.Mp / OZ_BM) * (L.Nrp / L.bn);
+  // tile width and chunks per CTA: the fewest chunk-times over whole waves of
+  // CTAs (152 SMs, one CTA each), counting a CTA's start (barriers, tensor
+  // memory, the pipeline's fill) as one chunk-time and, for K splits, the
+  // exact partials' round trip through memory (24 bytes per output element
+  // and split, about 16 MB per chunk-time).  A chunk of a 64-wide tile takes
+  // about the time of a 32-wide one (measured: its MMAs do twice the work at
+  // the same issue rate, its drain is not overlapped).  Ties: the wider tile,
+  // the fewer K splits.
   double best = -1.0;
-  for (int cps = 1; cps <= L.chunks; ++cps) {
-    const long long S = (L.chunks + cps - 1) / cps;
-    const double partials = S > 1 ? 24.0 * (double)S * L.Mp * L.Nrp / 16.0e6 : 0.0;
-    const double cost = (double)((tiles * S + 151) / 152) * (cps + 1) + partials;
-    if (best < 0 || cost <= best) {
-      best = cost;
-      L.cps = cps;
+  for (int bn = 64; bn >= 32; bn -= 32) {
+    const int Nrp = (2 * N + bn - 1) / bn * bn;
+    const long long tiles = (long long)(L.Mp / OZ_BM) * (Nrp / bn);
+    for (int cps = L.chunks; cps >= 1; --cps) {
+      const long long S = (L.chunks + cps - 1) / cps;
+      const double partials = S > 1 ? 24.0 * (double)S * L.Mp * Nrp / 16.0e6 : 0.0;
+      const double cost = (double)((tiles * S + 151) / 152) * (cps + 1) + partials;
+      if (best < 0 || cost < best) {
+        best = cost;
+        L.bn = bn;
+        L.Nrp = Nrp;
+        L.cps = cps;
+      }
     }
   }
   L.S = (L.chunks + L.cps - 1) / L.cps;
