@@ -422,7 +422,8 @@ def run_ours(args, rank, world, local_rank):
                            f"({ms_prof:.1f} ms per step with per-launch events, vs {ms_max / args.steps:.1f} ms "
                            "as CUDA graphs)",
             "by_class": [{k: c[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "share_of_step",
-                                            "launches", "ms_per_launch", "mean_sweeps_per_call") if k in c}
+                                            "launches", "ms_per_launch", "mean_sweeps_per_call", "fp64_equivalent_tflops",
+                                            "algorithmic_tflops") if k in c}
                          for c in classes]}
     fp64_cmp = None
     if args.prec != "fp64" and not args.no_fp64_check:

@@ -67,35 +67,45 @@ __global__ void __launch_bounds__(1024) chol_drop_kernel(const cplx* __restrict_
 
 // Rinv = inverse of the upper-triangular R on its kept block (zero rows and
 // columns where R[i,i] == 0).  One warp per column c: back substitution
-// R x = e_c, x_i for i = c .. 0.
+// R x = e_c, x_i for i = c .. 0, with x held in the warp's slice of shared
+// memory (each step reads the entries the previous steps wrote) and written
+// to Rinv at the end.
+constexpr int TRI_WARPS = 4;
 __global__ void tri_inv_kernel(const cplx* __restrict__ R, cplx* __restrict__ Rinv, int n) {
-  const int warps = blockDim.x >> 5;
-  const int c = blockIdx.x * warps + (threadIdx.x >> 5);
+  extern __shared__ cplx xs_all[];  // [TRI_WARPS][n] solution columns, then [n] reciprocal diagonal
+  double* rinv = (double*)(xs_all + (long long)TRI_WARPS * n);
+  const int w = threadIdx.x >> 5;
+  const int c = blockIdx.x * TRI_WARPS + w;
   const int lane = threadIdx.x & 31;
-  if (c >= n) return;
-  for (int i = lane; i < n; i += 32) Rinv[(long long)i * n + c] = make_double2(0.0, 0.0);
-  __syncwarp();
-  if (R[(long long)c * n + c].x == 0.0) return;
-  for (int i = c; i >= 0; --i) {
-    const double rii = R[(long long)i * n + i].x;
-    double sr = 0.0, si = 0.0;
-    for (int j = i + 1 + lane; j <= c; j += 32) {
-      const cplx a = R[(long long)i * n + j], x = Rinv[(long long)j * n + c];
-      sr += a.x * x.x - a.y * x.y;
-      si += a.x * x.y + a.y * x.x;
-    }
-    sr = warp_sum_d(sr);
-    si = warp_sum_d(si);
-    if (lane == 0) {
-      cplx v = make_double2(0.0, 0.0);
-      if (rii != 0.0) {
-        const double br = (i == c ? 1.0 : 0.0) - sr, bi = -si;
-        v = make_double2(br / rii, bi / rii);
-      }
-      Rinv[(long long)i * n + c] = v;
-    }
-    __syncwarp();
+  // the diagonal's reciprocals once per block, off the substitution's serial chain
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = R[(long long)i * n + i].x;
+    rinv[i] = d != 0.0 ? 1.0 / d : 0.0;
   }
+  __syncthreads();
+  if (c >= n) return;
+  cplx* xs = xs_all + (long long)w * n;
+  for (int i = lane; i < n; i += 32) xs[i] = make_double2(0.0, 0.0);
+  __syncwarp();
+  if (R[(long long)c * n + c].x != 0.0) {
+    for (int i = c; i >= 0; --i) {
+      const cplx* Ri = R + (long long)i * n;
+      double sr = 0.0, si = 0.0;
+      for (int j = i + 1 + lane; j <= c; j += 32) {
+        const cplx a = Ri[j], x = xs[j];
+        sr += a.x * x.x - a.y * x.y;
+        si += a.x * x.y + a.y * x.x;
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if (lane == 0) {
+        const double ri = rinv[i];  // 0 for a dropped direction
+        xs[i] = make_double2(((i == c ? 1.0 : 0.0) - sr) * ri, -si * ri);
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < n; i += 32) Rinv[(long long)i * n + c] = xs[i];
 }
 
 // G += coef * tr(G) I (one CTA): the shift of shifted CholeskyQR (Fukaya,
@@ -133,8 +143,15 @@ cudaError_t chol_drop(cudaStream_t s, const cplx* G, cplx* work, cplx* R, int n,
 }
 
 cudaError_t tri_inv(cudaStream_t s, const cplx* R, cplx* Rinv, int n) {
-  const int warps = 4;
-  tri_inv_kernel<<<(n + warps - 1) / warps, warps * 32, 0, s>>>(R, Rinv, n);
+  const size_t smem = (size_t)TRI_WARPS * n * sizeof(cplx) + (size_t)n * sizeof(double);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;  // n above about 3000
+  static size_t attr = 48 * 1024;
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = 200 * 1024;
+  }
+  tri_inv_kernel<<<(n + TRI_WARPS - 1) / TRI_WARPS, TRI_WARPS * 32, smem, s>>>(R, Rinv, n);
   count_launch();
   return cudaGetLastError();
 }
