@@ -72,8 +72,10 @@ typedef enum {
                           * row split exactly into seven base-256 digit       *
                           * planes (BF16), the 28 plane pairs of weight <= 6  *
                           * summed exactly, one rounding to FP64 (after       *
-                          * Ozaki, Ogita, Oishi and Rump 2012); every other   *
-                          * step exactly as IPEPS_PREC_FP64                   */
+                          * Ozaki, Ogita, Oishi and Rump 2012); the range     *
+                          * finder's bases by shifted CholeskyQR3 (Fukaya et  *
+                          * al. 2020) instead of Jacobi, cutoff and results   *
+                          * as IPEPS_PREC_FP64 (to rounding)                  */
 } ipeps_prec;
 
 typedef enum {
@@ -194,7 +196,8 @@ ipeps_status ipeps_ctm_move(ipeps_ctm h, int dir, int count);
  * and the fastest recorded; later moves and readouts use the recorded choices
  * (results change only by rounding).  The environment and the cuts' Jacobi
  * starts are restored afterwards (a temporary device copy of them is
- * allocated for the call).  No-op for IPEPS_PREC_FP64.  ipeps_ctm_tuning_size: number of
+ * allocated for the call).  No-op for IPEPS_PREC_FP64 and IPEPS_PREC_FP64TC (their
+ * digit-split products choose tiles by a cost model).  ipeps_ctm_tuning_size: number of
  * product shapes tuned.  Errors: ECUDA, ENOMEM-class CUDA failures, and any
  * status of the tuning sweep. */
 ipeps_status ipeps_ctm_autotune(ipeps_ctm h);
