@@ -59,8 +59,10 @@ typedef enum {
 
 typedef enum { IPEPS_REAL64 = 0, IPEPS_COMPLEX128 = 1 } ipeps_dtype;
 
-/* Arithmetic of the contraction GEMMs.  Projector orthonormalisation, the
- * Jacobi SVDs, normalisation and readouts are FP64 in every mode. */
+/* Arithmetic of the contraction GEMMs.  Projector orthonormalisation (its
+ * Grams FP64 or FP64-accurate on the tensor cores), normalisation and readouts
+ * are FP64 in every mode; the projector-core Jacobi SVD is FP64, in the
+ * TF32 / BF16 forms double-float (FP32 pairs, about 48 significand bits). */
 typedef enum {
   IPEPS_PREC_FP64 = 0,   /* complex FP64 on the CUDA cores                    */
   IPEPS_PREC_TF32 = 1,   /* tcgen05 TF32 tensor cores, FP32 accumulate        */
