@@ -2,7 +2,8 @@
 //
 // GB300 runs FP64 at a small fraction of its tensor-core rate, so the FP64
 // products of the projector step (CholeskyQR Grams and applies of k x K
-// matrices) are computed here by exact splitting into integer digit planes,
+// matrices), and in the FP64-accurate form every contraction product, are
+// computed here by exact splitting into integer digit planes,
 // after the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012),
 // arranged for BF16 tensor cores with FP32 accumulation:
 //
@@ -30,11 +31,12 @@
 // of the rows involved rather than to sum |a||b|: FP64-level for rows
 // without a wide spread of magnitudes, as the projector step's are.
 //
-// One CTA computes a 128 x 32 tile of Cr over a range of K chunks: warp 0
-// issues the TMA loads (per stage one A digit plane and the B planes it
-// pairs with), warp 1 the tcgen05.mma, warps 2..5 drain the seven group
-// accumulators after each chunk.  Ranges of K are split over the grid; the
-// exact partials (I, u) are summed by a second kernel.
+// One CTA computes a 128 x 32 or 128 x 64 tile of Cr over a range of K
+// chunks: warp 0 issues the TMA loads (per stage one A digit plane and the B
+// planes it pairs with), warp 1 the tcgen05.mma, the other warps (four or
+// eight) drain the seven group accumulators after each chunk.  Ranges of K
+// are split over the grid; the exact partials (I, u) are summed by a second
+// kernel.
 #include <cuda_bf16.h>
 
 #include "tc_gemm.h"
