@@ -144,3 +144,41 @@ def test_precision_form_polished_to_the_oracle_fixed_point():
     assert s_err < TOL
     gm.close()
     gp.close()
+
+
+def test_two_corner_route():
+    """The two-corner projectors (corners = 2, X = Q1^T Q4) in the FP64-accurate
+    form against the exact-SVD oracle of that route, FP64 tolerances."""
+    w = synth.workload("product_noise", seed=0, D=2, chi=16)
+    g = gpu_ctm(w["tensors"], w["pattern"], 16, prec="fp64tc", corners=2)
+    g.sweep(6)
+    st = _oracle(w, 16, 6, corners=2)
+    rd = O.bond_rdms(st, w["tensors"], w["pattern"])
+    e_ref = O.energy_per_spin(rd, w["J"], 2, 2)
+    e = g.energy(w["J"])
+    r = g.rdms()
+    s_err = spectra_err(g.spectra(), O.corner_spectra(st))
+    print(f"two corners: |dE|/|E| {abs(e - e_ref) / abs(e_ref):.1e}, spectra {s_err:.1e}")
+    assert abs(e - e_ref) < TOL * abs(e_ref)
+    assert rel_err(r["h"], rd["h"]) < TOL and rel_err(r["v"], rd["v"]) < TOL
+    assert s_err < TOL
+    g.close()
+
+
+def test_batch_of_uneven_instances():
+    """The batched scan (one graph launch per move over instances of uneven D
+    and chi) in the FP64-accurate form: every instance's energy and corner
+    spectra against its own oracle run, FP64 tolerances."""
+    from paper_1711_04798_gb300 import Batch
+    from gpu_common import DEFAULTS
+    insts = synth.scan(seed=5, n=4, Ds=(2, 3), chis=(9, 12, 16))
+    b = Batch(insts, tune=False, prec="fp64tc", **DEFAULTS)
+    b.sweep(1)
+    b.sweep(1)  # the second call replays the captured graph
+    e = b.energies([i["J"] for i in insts])
+    for i, inst in enumerate(insts):
+        st = _oracle(inst, inst["chi"], 2)
+        e_ref = O.energy_per_spin(O.bond_rdms(st, inst["tensors"], inst["pattern"]), inst["J"], 2, 2)
+        assert abs(e[i] - e_ref) < TOL * abs(e_ref), (i, e[i], e_ref)
+        assert spectra_err(b.instance(i).spectra(), O.corner_spectra(st)) < TOL, i
+    b.close()
