@@ -1,4 +1,5 @@
-"""Host logic of bench.py that needs no GPU: the clock/throttle summary the
+"""Host logic of bench.py that needs no GPU: the per-form kernel classes and
+roofline fractions, the clock/throttle summary the
 bench line carries (nvidia-smi CSV rows as the sampler receives them) and the
 roofline denominators' source."""
 import os
@@ -43,3 +44,40 @@ def test_peaks_come_from_the_measured_file_when_present():
     else:
         assert source == "fallback" and peaks["hbm_gbs"] == 6800.0
     assert peaks
+
+
+class _FakeProfile:
+    """Stands in for a handle's profile_read: kind -> (ms, launches, flops)."""
+
+    def __init__(self, table):
+        self.table = table
+
+    def profile_read(self, kind):
+        ms, n, fl = self.table.get(kind, (0.0, 0, 0.0))
+        return {"ms": ms, "launches": n, "flops": fl}
+
+
+def test_kernel_classes_of_each_precision_form():
+    """Class records and roofline fractions from profiled times: executed flops
+    credit 6 products for BF16x6 and 28 digit-plane products for the
+    FP64-accurate form, against the BF16 peak; the FP64 path against the FP64
+    GEMM rate."""
+    import bench
+    peaks = {"bf16_tflops_sustained": 1000.0, "hbm_gbs": 5000.0}
+    # BF16x6: 10 ms of wide products with 1e12 algorithmic flops -> 6e12 executed -> 600 TFLOP/s
+    g = _FakeProfile({5: (10.0, 4, 1e12), 7: (2.0, 8, 5e9), 8: (1.0, 8, 1e9), 2: (1.0, 10, 1e9), 1: (3.0, 2, 4.0)})
+    cl = bench.kernel_classes(g, "bf16x6", 20.0, 1, peaks, "test", 1.0)
+    wide = cl[0]
+    assert wide["bound"] == "tensor" and abs(wide["achieved"] - 600.0) < 1e-9 and abs(wide["frac"] - 0.6) < 1e-12
+    assert cl[1]["bound"] == "hbm" and abs(cl[1]["achieved"] - 2500.0) < 1e-9
+    assert any(c["bound"] == "latency" for c in cl) and cl[-1]["mean_sweeps_per_call"] == 4.0
+    # FP64-accurate: 100 ms of products with 1e12 algorithmic flops -> 28e12 executed -> 280 TFLOP/s
+    g = _FakeProfile({0: (100.0, 50, 1e12), 2: (5.0, 20, 1e9), 1: (4.0, 2, 7.0)})
+    cl = bench.kernel_classes(g, "fp64tc", 200.0, 1, peaks, "test", 1.0)
+    assert cl[0]["bound"] == "tensor" and abs(cl[0]["achieved"] - 280.0) < 1e-9
+    assert abs(cl[0]["fp64_equivalent_tflops"] - 10.0) < 1e-9 and abs(cl[0]["frac"] - 0.28) < 1e-12
+    # FP64: the CUDA-core GEMM class against the FP64 rate
+    g = _FakeProfile({0: (1000.0, 50, 1e12), 1: (4.0, 2, 7.0)})
+    cl = bench.kernel_classes(g, "fp64", 2000.0, 1, peaks, "test", 1.1)
+    assert cl[0]["bound"] == "alu" and abs(cl[0]["frac"] - 1.0 / 1.1) < 1e-12
+    assert not any(c["bound"] == "latency" for c in cl)
